@@ -1,0 +1,330 @@
+"""Benchmark: Voronoi cells/s on one (or N) GB300, FP32+FP64-recheck vs plain FP64.
+
+One step = one whole tessellation (grid sort, kNN, clipping with every
+re-queue pass, emit of neighbours + full geometry + volume + centroid) of the
+1,048,576-point half-uniform / half-clustered cloud, inputs resident in HBM.
+
+Prints ONE JSON line (rank 0). See the design doc for the roofline figures.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload mixed-1m|mixed-8m]
+  python bench.py --impl reference ...   # the FP64 CPU oracle as the reference arm
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Voronoi cells/sec at 1M & 8M pts, 1 GB300: FP32+FP64-recheck vs plain FP64"
+WORKLOADS = {
+    "mixed-1m": dict(n=1 << 20, seed=1, desc="1,048,576 float32 points in [0,1)^3: 524,288 uniform + 524,288 in "
+                     "1,000 isotropic Gaussian clumps (centres uniform, sigma log-uniform in [1e-3,1e-2], "
+                     "out-of-box draws resampled), seed 1; k0=16 with doubling to 256 then the exhaustive pass; "
+                     "outputs neighbours (CSR, original ids) + volume + centroid + full geometry"),
+    "mixed-8m": dict(n=1 << 23, seed=2, desc="8,388,608 float32 points, same recipe as mixed-1m, seed 2"),
+}
+# FP32 FMA peak from the unit counts and the maximum SM clock: 152 SMs x 128
+# FP32 lanes x 2 flops x 2.070 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def dist_setup(gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def dist_max(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def cpu_oracle_rate(pts: np.ndarray, sample_cells: int, seed: int = 12345) -> dict:
+    """Times the FP64 CPU oracle on a random sample of the workload's cells."""
+    import oracle
+
+    idx = np.sort(np.random.default_rng(seed).choice(len(pts), sample_cells, replace=False))
+    cores = oracle.default_threads()
+    oracle.tessellate(pts[:2000], k0=16)  # load the library, warm the allocator
+    t0 = time.perf_counter()
+    r = oracle.tessellate(pts, k0=16, cells=idx, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sample_cells / dt, "seconds": dt, "cores": cores, "flops_per_cell": float(oracle.clip_flops(r).mean()),
+            "sample": f"{sample_cells} random cells of the same {len(pts)}-point workload (kd-tree build included), "
+                      f"FP64 oracle, {cores} threads"}
+
+
+def run_reference(args, rank: int, world: int):
+    """The reference arm: the FP64 CPU oracle on bounded samples, rank 0 only."""
+    if rank != 0:
+        return
+    from paper_2412_04514_gb300 import workloads as W
+
+    wl = WORKLOADS[args.workload]
+    pts = W.mixed(wl["n"], wl["seed"])
+    per_step = args.ref_cells
+    for i in range(args.warmup):
+        cpu_oracle_rate(pts, min(2000, per_step), seed=100 + i)
+    times = []
+    cores = None
+    for i in range(args.steps):
+        r = cpu_oracle_rate(pts, per_step, seed=200 + i)
+        times.append(r["seconds"])
+        cores = r["cores"]
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "n_points": wl["n"], "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} random cells per step of the {wl['n']}-point workload"},
+        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank: int, world: int, local: int):
+    import torch
+
+    import paper_2412_04514_gb300 as vt
+    from paper_2412_04514_gb300 import workloads as W
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device (no CPU fallback)"
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    wl = WORKLOADS[args.workload]
+    n = wl["n"]
+    pts_np = W.mixed(n, wl["seed"] + 1000 * rank)
+    pts = torch.from_numpy(pts_np).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    emit = ("nbr", "vol", "cen", "geom")
+
+    def timed(params: vt.Params, steps: int, warmup: int, stage_times: bool):
+        ws = vt.Workspace(params, n, dev)
+        p = vt.Params(**{**params.__dict__, "stage_times": stage_times})
+        for _ in range(warmup):
+            vt.tessellate(pts, p, workspace=ws)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream(dev)
+        ms, stats = [], []
+        launches0 = vt.launch_count()
+        dist_barrier(world)
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            cells = vt.tessellate(pts, p, workspace=ws)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            stats.append(cells.stats)
+        torch.cuda.synchronize()
+        dist_barrier(world)
+        launches = vt.launch_count() - launches0
+        return ms, stats, launches, cells
+
+    # warm up both forms, then time: FP32+recheck (headline) and plain FP64
+    p32 = vt.Params(precision="fp32", emit=emit)
+    p64 = vt.Params(precision="fp64", emit=emit)
+    with Clocks(local) as clk:
+        ms32, st32, launches32, cells = timed(p32, args.steps, args.warmup, stage_times=True)
+    clocks = clk.summary()
+    ms64, st64, _, _ = timed(p64, max(1, args.steps_fp64), max(3, min(args.warmup, 3)), stage_times=True)
+
+    tot32 = dist_max(sum(ms32), world)
+    tot64 = dist_max(sum(ms64), world)
+    value = n * world * len(ms32) / (tot32 / 1e3)
+    value64 = n * world * len(ms64) / (tot64 / 1e3)
+
+    # end to end through the public API with host buffers
+    host = torch.from_numpy(pts_np).pin_memory()
+    e2e_ms = []
+    h2d = host.numel() * 4
+    d2h = 0
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = vt.tessellate_host(host, p32, device=dev)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        d2h = sum(getattr(out, f).numel() * getattr(out, f).element_size()
+                  for f in ("vol", "cen", "nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx_off",
+                            "face_vtx") if getattr(out, f) is not None)
+    e2e_tot = dist_max(sum(e2e_ms), world)
+    e2e_value = n * world * len(e2e_ms) / (e2e_tot / 1e3)
+
+    if rank != 0:
+        return
+
+    # roofline of the dominant stage (the clipper), from the live event times
+    stage = {k: statistics.mean(s[k] for s in st32) for k in ("ms_grid", "ms_knn", "ms_clip", "ms_emit")}
+    peaks = _peaks()
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(pts_np, args.cpu_cells)
+    flops_per_cell = cpu["flops_per_cell"] if cpu else args.flops_per_cell
+    clip_launches = statistics.mean(s["clip_launches"] for s in st32)
+    achieved = n * flops_per_cell / (stage["ms_clip"] / 1e3) / 1e12
+    roofline = {
+        "kernel": "k_clip<float,8,8,64> (all re-queue passes of one step)",
+        "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+        "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (unit counts and max SM clock)",
+        "units": f"{n} validated cells x {flops_per_cell:.0f} algorithmic FP32 flops/cell over {clip_launches:.1f} "
+                 f"clip launches",
+        "stage_ms": stage,
+        "hbm_peak_gbs": peaks.get("hbm_gbs"),
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": len(ms32),
+        "warmup": args.warmup, "ms_per_step": tot32 / len(ms32), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "n_points": n, "precision": "fp32+fp64-recheck",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world} (independent clouds)"},
+        "fp64_form": {"value": value64, "unit": "cells/s", "ms_per_step": tot64 / len(ms64), "steps": len(ms64),
+                      "stage_ms": {k: statistics.mean(s[k] for s in st64) for k in ("ms_grid", "ms_knn", "ms_clip",
+                                                                                    "ms_emit")},
+                      "fp32_speedup": value / value64},
+        "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": e2e_tot / len(e2e_ms)},
+        "roofline": roofline,
+        "cpu_baseline": None if cpu is None else {"value": cpu["value"], "unit": "cells/s", "cores": cpu["cores"],
+                                                  "kind": "oracle", "sample": cpu["sample"]},
+        "gpu_launches": int(launches32),
+        "clocks": clocks,
+        "passes": {"k_of_pass": st32[-1]["k_of_pass"], "cells_of_pass": st32[-1]["cells_of_pass"],
+                   "fp64_rechecks": st32[-1]["fp64_rechecks"], "precision_retries": st32[-1]["precision_retries"],
+                   "capacity_retries": st32[-1]["capacity_retries"], "unvalidated": st32[-1]["unvalidated"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps-fp64", type=int, default=3)
+    ap.add_argument("--workload", default="mixed-1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-cells", type=int, default=100_000)
+    ap.add_argument("--ref-cells", type=int, default=20_000)
+    ap.add_argument("--flops-per-cell", type=float, default=25134.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_setup(args.gpus)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_gpu(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,254 @@
+/*
+ * vt.h -- C ABI of the GB300 Voronoi tessellation library (libvt.so).
+ *
+ * The library computes 3D Voronoi cells one cell at a time, the method of the
+ * votess paper (Summary): the generators are sorted into a uniform grid, a
+ * k-nearest-neighbour search runs per generator, and each cell is obtained by
+ * clipping the bounding box with the perpendicular bisector planes of the
+ * generator and its neighbours, nearest first, until the "security radius"
+ * condition proves that no farther generator can cut it. Cells that fail the
+ * condition are re-run on the device with k doubled (where the paper falls
+ * back to the CPU); cells that still fail at k_max are finished by clipping
+ * with every generator that can still cut them (all generators within twice
+ * the cell's radius), also on the device.
+ *
+ * Conventions (every entry point):
+ *  - Every array argument is a DEVICE pointer unless its comment says host.
+ *    Buffers are owned by the caller; the library never allocates, frees or
+ *    keeps a pointer after a call returns.
+ *  - Scratch memory is a caller-allocated device workspace of at least
+ *    vt_workspace_size() bytes, passed as (ws, ws_bytes). Its contents need not
+ *    be initialised and are clobbered.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Stage calls (vt_grid_build, vt_knn, vt_clip_cells, vt_emit) only
+ *    enqueue work and return; vt_tessellate synchronises the stream once per
+ *    re-queue pass to read a 64-byte status block (documented below).
+ *  - Points are float32 (x, y, z) triples inside the half-open box
+ *    [box_lo, box_hi), pairwise distinct.
+ *  - Return value: vt_status. On failure vt_last_error() (per host thread)
+ *    describes the problem. A CUDA launch error is VT_ERR_CUDA.
+ *  - "sorted index" = position of a generator after the grid sort;
+ *    "original index" = its row in the caller's input.
+ */
+#ifndef VT_H
+#define VT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VT_API __attribute__((visibility("default")))
+#else
+#define VT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ */
+/* status, parameters, outputs                                         */
+/* ------------------------------------------------------------------ */
+
+typedef enum {
+    VT_OK = 0,
+    VT_ERR_INVALID_ARG = 1,      /* bad argument, or a point that is not finite or not inside the box */
+    VT_ERR_CUDA = 2,             /* a CUDA call failed (see vt_last_error) */
+    VT_ERR_CAPACITY = 3,         /* an output buffer is too small: vt_cells_out.needed_* hold the sizes */
+    VT_ERR_UNVALIDATED = 4,      /* some cells could not be validated (count in vt_stats.unvalidated) */
+    VT_ERR_DUPLICATE_POINTS = 5, /* two generators coincide (a neighbour at distance 0) */
+    VT_ERR_TIMEOUT = 6,          /* a bounded device wait gave up */
+    VT_ERR_WORKSPACE = 7         /* ws_bytes smaller than vt_workspace_size() */
+} vt_status;
+
+enum { VT_FP64 = 0, VT_FP32_RECHECK = 1 };          /* vt_params.precision */
+enum { VT_INDEX_ORIGINAL = 0, VT_INDEX_SORTED = 1 }; /* vt_params.index_space */
+
+/* vt_params.emit bitmask */
+enum {
+    VT_EMIT_NBR = 1,   /* neighbour CSR (nbr_off, nbr) */
+    VT_EMIT_VOL = 2,   /* cell volume */
+    VT_EMIT_CEN = 4,   /* cell centroid */
+    VT_EMIT_M2 = 8,    /* second moment: integral of |x - p_i|^2 over the cell */
+    VT_EMIT_GEOM = 16  /* vertices and faces (vtx_off/vtx, face_off/face_nbr/face_vtx_off/face_vtx) */
+};
+
+typedef struct vt_params {
+    int k0;                 /* initial k of the neighbour lists (default 16) */
+    int k_max;              /* largest k of the doubling passes, <= 256 (default 256) */
+    float grid_density;     /* target generators per grid cell rho; G = ceil(cbrt(n / rho)) (default 2) */
+    int grid_res;           /* G override per axis (0 = derive from grid_density) */
+    int threads_per_cell;   /* lanes cooperating on one cell: 8, 16 or 32 (0 = default 8) */
+    int precision;          /* VT_FP64 or VT_FP32_RECHECK */
+    int emit;               /* VT_EMIT_* bitmask */
+    int index_space;        /* VT_INDEX_ORIGINAL (default) or VT_INDEX_SORTED */
+    float box_lo[3];        /* domain box, non-periodic */
+    float box_hi[3];
+    int flags;              /* VT_FLAG_* bitmask (default 0) */
+} vt_params;
+
+/* vt_params.flags */
+enum {
+    VT_FLAG_STAGE_TIMES = 1 /* time every kernel group with CUDA events on the call's stream
+                               (vt_stats.ms_*); costs one event pair per launch group */
+};
+
+/* Fills *p with the defaults above, unit box, FP32_RECHECK, emit NBR|VOL|CEN. */
+VT_API void vt_params_default(vt_params* p);
+
+/* Outputs of a tessellation. Index space per vt_params.index_space: cell i is
+ * original generator i (ORIGINAL) or sorted generator i (SORTED), and
+ * neighbour / face ids use the same space. Any pointer whose VT_EMIT bit is
+ * off may be NULL. Variable-length arrays are CSR: cell i owns entries
+ * [off[i], off[i+1]). Every face list is counter-clockwise seen from outside
+ * the cell. Wall faces carry ids -1..-6 (x=lo, x=hi, y=lo, y=hi, z=lo, z=hi). */
+typedef struct vt_cells_out {
+    double* vol;            /* [n] */
+    double* cen;            /* [n*3] */
+    double* m2;             /* [n] */
+    int64_t* nbr_off;       /* [n+1] */
+    int32_t* nbr;           /* [nbr_cap] neighbour ids, ascending per cell */
+    int64_t nbr_cap;
+    int64_t* vtx_off;       /* [n+1] */
+    double* vtx;            /* [vtx_cap*3] vertex coordinates (global frame) */
+    int64_t vtx_cap;
+    int64_t* face_off;      /* [n+1] faces of cell i */
+    int32_t* face_nbr;      /* [face_cap] neighbour id or wall id of each face */
+    int64_t* face_vtx_off;  /* [face_cap+1] CSR over face_vtx, global */
+    int32_t* face_vtx;      /* [face_vtx_cap] vertex index within the cell's vertex list */
+    int64_t face_cap;
+    int64_t face_vtx_cap;
+    int32_t* perm;          /* [n] optional: sorted index -> original index */
+    /* filled by vt_tessellate / vt_emit (host memory, inside this struct) */
+    int64_t needed_nbr, needed_vtx, needed_face, needed_face_vtx;
+} vt_cells_out;
+
+#define VT_MAX_PASSES 16
+
+typedef struct vt_stats {
+    int passes;                          /* clip passes run (1 + doubling passes + exhaustive) */
+    int k_of_pass[VT_MAX_PASSES];        /* k of each pass (0 = exhaustive pass) */
+    int64_t cells_of_pass[VT_MAX_PASSES];/* cells entering each pass */
+    int64_t exhaustive_cells;            /* cells finished by the exhaustive pass */
+    int64_t capacity_retries;            /* cells re-run because a polyhedron outgrew its slots */
+    int64_t precision_retries;           /* FP32 cells re-run in FP64 after an inconsistency */
+    int64_t fp64_rechecks;               /* FP32 sign / radius tests re-decided in FP64 */
+    int64_t unvalidated;                 /* cells left without a validated cell */
+    int grid_res;                        /* G used */
+    int launches;                        /* kernels launched by the call */
+    int clip_launches;                   /* clipper launches among them */
+    int knn_launches;                    /* kNN launches among them */
+    double ms_grid, ms_knn, ms_clip, ms_emit; /* device time per stage (VT_FLAG_STAGE_TIMES), else 0 */
+} vt_stats;
+
+/* ------------------------------------------------------------------ */
+/* sizing                                                              */
+/* ------------------------------------------------------------------ */
+
+/* Grid resolution G per axis that vt_tessellate uses for n generators. */
+VT_API int vt_grid_resolution(const vt_params* p, int64_t n);
+
+/* Bytes of device workspace needed by vt_tessellate (and by any stage call
+ * with the same p and n). Writes *bytes; returns VT_ERR_INVALID_ARG for a bad
+ * p or n < 0. Host-only; no CUDA call. */
+VT_API int vt_workspace_size(const vt_params* p, int64_t n, size_t* bytes);
+
+/* ------------------------------------------------------------------ */
+/* stage 1: grid counting sort (paper, Summary)                        */
+/* ------------------------------------------------------------------ */
+
+/* Sorts the n points pts[n*3] into a G^3 uniform grid over the box.
+ * cell id = (ix*G + iy)*G + iz with ix = min(G-1, floor(fl(fl(x - lo) * s)))
+ * and s = float32(G) / (hi - lo) in float32 (every operation rounded
+ * separately). The sort is stable: generators in a grid cell keep input order.
+ * Outputs: sorted[n*4] = (x, y, z, original index as int32 bits), perm[n]
+ * (sorted index -> original index), cell_off[G^3+1] (first sorted index of
+ * each grid cell; cell_off[G^3] = n). Checks that every point is finite and
+ * inside the box; a violation sets a device flag that vt_tessellate reports
+ * as VT_ERR_INVALID_ARG (stage callers read it with vt_read_status). */
+VT_API int vt_grid_build(const float* pts, int64_t n, const vt_params* p, int G,
+                  float* sorted, int32_t* perm, int32_t* cell_off,
+                  void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* stage 2: k nearest neighbours (paper, Summary)                      */
+/* ------------------------------------------------------------------ */
+
+/* k nearest generators of each query (self excluded), nearest first, by a
+ * walk over Chebyshev shells of grid cells around the query's cell.
+ * queries[nq]: sorted indices to search for (NULL = all n, in order).
+ * nbr[nq*k]: sorted indices of the neighbours; d2[nq*k]: squared distances
+ * (double for VT_FP64, float for VT_FP32_RECHECK; may be NULL).
+ * Order: (d2, original index) ascending. VT_FP64 computes
+ * d2 = ((dx*dx + dy*dy) + dz*dz) in double with dx = double(x_j) - double(x_i)
+ * and no fused multiply-add, so lists are exact and reproducible;
+ * VT_FP32_RECHECK evaluates the same expression in float32.
+ * 1 <= k <= 256. If fewer than k other generators exist, the remaining
+ * slots get -1 and +inf. */
+VT_API int vt_knn(const float* sorted, const int32_t* cell_off, int G, int64_t n,
+           const int32_t* queries, int64_t nq, int k, const vt_params* p,
+           int32_t* nbr, void* d2, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* stage 3: per-cell bisector clipping (paper, Summary)                */
+/* ------------------------------------------------------------------ */
+
+/* Clips the box around each query generator by the bisectors of its k
+ * listed neighbours, nearest first, checking the security radius before each
+ * clip: the cell is final when 4 R^2 <= d2 of the next listed neighbour
+ * (R = largest vertex distance from the generator), or, after all k, when
+ * 4 R^2 <= d2 of the k-th; when the list holds every other generator the cell
+ * is final by construction. k = 0 selects the exhaustive mode (no list:
+ * every generator closer than 2R, found by a grid walk).
+ * Writes vol/cen/m2 of finished cells into `out` (at the cell's index in the
+ * chosen index space) and the cell's faces and vertices into the workspace
+ * for vt_emit. Cells that are not validated are appended to failed[] (sorted
+ * indices) and counted in *n_failed (a device int32 the caller zeroes).
+ * The workspace must be the one that vt_grid_build / vt_tessellate use. */
+VT_API int vt_clip_cells(const float* sorted, const int32_t* cell_off, int G, int64_t n,
+                  const int32_t* queries, int64_t nq, const int32_t* nbr, const void* d2, int k,
+                  const vt_params* p, vt_cells_out* out, int32_t* failed, int32_t* n_failed,
+                  void* ws, size_t ws_bytes, void* stream);
+
+/* Writes the variable-length outputs (neighbour CSR, geometry) of the last
+ * vt_tessellate call on this workspace into `out`. Blocking: reads the totals
+ * back to fill out->needed_*; returns VT_ERR_CAPACITY when a *_cap is too
+ * small (nothing written). */
+VT_API int vt_emit(int64_t n, const vt_params* p, vt_cells_out* out, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* whole path                                                          */
+/* ------------------------------------------------------------------ */
+
+/* Tessellates the n generators pts[n*3] (device) in the box of p: grid sort,
+ * kNN with k0, clipping, re-queue with k doubled up to k_max, exhaustive pass
+ * for what is left, then the requested outputs. Synchronises `stream` once
+ * per pass (a 64-byte device-to-host read of the failed count) and once at
+ * the end. Returns VT_ERR_CAPACITY (with out->needed_* set and vol/cen/m2
+ * written) when a variable-length buffer is too small: allocate and call
+ * vt_emit. stats may be NULL. n = 0 is valid (nothing to do); n = 1 gives
+ * the whole box. */
+VT_API int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cells_out* out,
+                  vt_stats* stats, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* diagnostics                                                         */
+/* ------------------------------------------------------------------ */
+
+/* Reads the device status flags of the workspace (blocking on `stream`):
+ * returns VT_OK, VT_ERR_INVALID_ARG (bad point) or VT_ERR_DUPLICATE_POINTS. */
+VT_API int vt_read_status(void* ws, size_t ws_bytes, void* stream);
+
+/* Message of the last failure on this host thread ("" if none). */
+VT_API const char* vt_last_error(void);
+
+/* Number of kernels this library has launched in this process. */
+VT_API int64_t vt_launch_count(void);
+
+/* Library version string. */
+VT_API const char* vt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VT_H */

@@ -33,7 +33,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libvto.so")
-_SOURCES = [os.path.join(_HERE, "vt_oracle.c"), os.path.join(_HERE, "vt_adjoint.c")]
+_SOURCES = [os.path.join(_HERE, "vt_oracle.c")]
 _lock = threading.Lock()
 _lib = None
 
@@ -87,6 +87,9 @@ class _Result(ctypes.Structure):
         ("face_vtx", ctypes.POINTER(ctypes.c_double)),
         ("n_faces", ctypes.c_int64),
         ("n_face_vtx", ctypes.c_int64),
+        ("work_sign", ctypes.POINTER(ctypes.c_int64)),
+        ("work_newv", ctypes.POINTER(ctypes.c_int64)),
+        ("work_nbrs", ctypes.POINTER(ctypes.c_int64)),
     ]
 
 
@@ -254,6 +257,9 @@ def tessellate(points, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), k0: int = 16, mod
             "face_cen": _arr(r.face_cen, 3 * nf, np.float64, (nf, 3)),
             "face_plane": _arr(r.face_plane, 4 * nf, np.float64, (nf, 4)),
             "face_size": _arr(r.face_size, nf, np.int32),
+            "work_sign": _arr(r.work_sign, nc, np.int64),
+            "work_newv": _arr(r.work_newv, nc, np.int64),
+            "work_nbrs": _arr(r.work_nbrs, nc, np.int64),
         }
         if geometry:
             out["face_vtx"] = _arr(r.face_vtx, 3 * r.n_face_vtx, np.float64, (r.n_face_vtx, 3))
@@ -262,6 +268,21 @@ def tessellate(points, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), k0: int = 16, mod
     if st != VTO_OK:
         raise OracleError(f"vto_tessellate failed with status {st}")
     return out
+
+
+# FP32 operations of one validated cell, an FMA counted as 2 (the clipper's
+# minimal work: no re-queue repeats): per bisector tested, the plane and the
+# security-radius test (12); per vertex-plane sign test, one 3-term dot product
+# minus the offset (6); per vertex created, a 3x3 solve by Cramer's rule plus
+# its squared radius (60); per final vertex, its three (vertex, face) moment
+# terms (3 x 60).
+FLOPS_PER_NBR, FLOPS_PER_SIGN, FLOPS_PER_NEWV, FLOPS_PER_FINAL_VERTEX = 12, 6, 60, 180
+
+
+def clip_flops(res: dict) -> np.ndarray:
+    """Algorithmic FP32 flops of each cell's validated clipping (see constants)."""
+    return (FLOPS_PER_NBR * res["work_nbrs"] + FLOPS_PER_SIGN * res["work_sign"]
+            + FLOPS_PER_NEWV * res["work_newv"] + FLOPS_PER_FINAL_VERTEX * res["nvert"].astype(np.int64))
 
 
 def neighbour_lists(res: dict) -> list[np.ndarray]:

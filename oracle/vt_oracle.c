@@ -287,6 +287,9 @@ typedef struct {
     vec3 tmp[MAXF * 2];
     kv* knn;             /* neighbour list buffer */
     int knn_cap;
+    int64_t work_sign;   /* vertex-plane sign tests of the validating run */
+    int64_t work_newv;   /* vertices created by cuts in the validating run */
+    int64_t work_nbrs;   /* bisector planes tested in the validating run */
 } scratch_t;
 
 /* orthonormal in-plane basis (u, w) with u x w = n/|n| */
@@ -374,6 +377,10 @@ static int add_unique(vec3* set, int m, vec3 p)
  * returns 0 if nothing is cut (Q untouched), 1 if clipped into Q, <0 on capacity error */
 static int clip(const poly_t* P, poly_t* Q, vec3 n, double b, int32_t tag, scratch_t* S)
 {
+    int fv = 0;
+    for (int f = 0; f < P->nf; ++f) fv += P->f[f].nv;
+    S->work_sign += fv / 3;  /* each vertex of a simple polyhedron lies on 3 faces */
+    S->work_nbrs += 1;
     int any_out = 0;
     for (int f = 0; f < P->nf && !any_out; ++f)
         for (int i = 0; i < P->f[f].nv; ++i)
@@ -399,7 +406,9 @@ static int clip(const poly_t* P, poly_t* Q, vec3 n, double b, int32_t tag, scrat
                 if (m >= MAXFV) return -1;
                 G->v[m++] = p;
                 if (ncap >= MAXF * 2) return -1;
+                int before = ncap;
                 ncap = add_unique(S->cap, ncap, p);
+                S->work_newv += ncap - before;
             }
         }
         /* drop repeated consecutive points (cyclic) */
@@ -540,6 +549,7 @@ static int one_cell(const float* pts, int64_t n, vec3 lo, vec3 hi, const vto_kdt
     *n_clips = 0;
 
     if (mode != VTO_MODE_SECURITY) {
+        S->work_sign = S->work_newv = S->work_nbrs = 0;
         poly_t *cur = &S->a, *nxt = &S->b;
         init_box(cur, llo, lhi, S);
         for (int64_t t = 0; t < n; ++t) {
@@ -569,6 +579,7 @@ static int one_cell(const float* pts, int64_t n, vec3 lo, vec3 hi, const vto_kdt
         init_box(cur, llo, lhi, S);
         int valid = 0;
         *n_clips = 0;
+        S->work_sign = S->work_newv = S->work_nbrs = 0;
         for (int a = 0; a < m; ++a) {
             if (S->knn[a].d2 == 0) return VTO_ERR_DUPLICATE;
             if (4.0 * max_r2(cur) <= S->knn[a].d2) { valid = 1; break; }
@@ -603,6 +614,7 @@ typedef struct {
     int32_t* nbr; int nnbr;
     cell_meas M;
     int k_used, n_clips;
+    int64_t work_sign, work_newv, work_nbrs;
 } cell_rec;
 
 static int cmp_i32(const void* a, const void* b)
@@ -636,6 +648,9 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
     R->euler = (int32_t*)calloc((size_t)nc + 1, sizeof(int32_t));
     R->nvert = (int32_t*)calloc((size_t)nc + 1, sizeof(int32_t));
     R->face_off = (int64_t*)calloc((size_t)nc + 1, sizeof(int64_t));
+    R->work_sign = (int64_t*)calloc((size_t)nc + 1, sizeof(int64_t));
+    R->work_newv = (int64_t*)calloc((size_t)nc + 1, sizeof(int64_t));
+    R->work_nbrs = (int64_t*)calloc((size_t)nc + 1, sizeof(int64_t));
     cell_rec* recs = (cell_rec*)calloc((size_t)nc + 1, sizeof(cell_rec));
     vto_kdtree* T = mode == VTO_MODE_SECURITY ? vto_kdtree_build(pts, n) : NULL;
     int status = VTO_OK;
@@ -656,6 +671,9 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
             if (i < 0 || i >= n) { rc->status = VTO_ERR_ARG; continue; }
             poly_t* P = NULL;
             rc->status = one_cell(pts, n, lo, hi, T, i, k0, mode, order, S, &P, &rc->k_used, &rc->n_clips);
+            rc->work_sign = S->work_sign;
+            rc->work_newv = S->work_newv;
+            rc->work_nbrs = S->work_nbrs;
             if (rc->status != VTO_OK) continue;
             vec3 p = v3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
             measure(P, p, &rc->M, farea, fcen, uniq, loop, lsize, used);
@@ -734,6 +752,9 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
         }
         R->k_used[c] = rc->k_used;
         R->n_clips[c] = rc->n_clips;
+        R->work_sign[c] = rc->work_sign;
+        R->work_newv[c] = rc->work_newv;
+        R->work_nbrs[c] = rc->work_nbrs;
         free(rc->tag); free(rc->area); free(rc->fcen); free(rc->fnrm); free(rc->fsize);
         free(rc->fvtx); free(rc->nbr);
     }
@@ -752,5 +773,6 @@ void vto_result_free(vto_result* R)
     free(R->k_used); free(R->n_clips); free(R->euler); free(R->nvert);
     free(R->face_off); free(R->face_tag); free(R->face_area); free(R->face_cen);
     free(R->face_plane); free(R->face_size); free(R->face_vtx);
+    free(R->work_sign); free(R->work_newv); free(R->work_nbrs);
     free(R);
 }

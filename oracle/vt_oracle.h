@@ -50,6 +50,9 @@ typedef struct {
     int32_t* face_size;     /* vertices per face */
     double* face_vtx;       /* [sum face_size * 3] CCW loops seen from outside (global); NULL unless geometry wanted */
     int64_t n_faces, n_face_vtx;
+    int64_t* work_sign;     /* [n_cells] vertex-plane sign tests of the validating run */
+    int64_t* work_newv;     /* [n_cells] vertices created by its cuts */
+    int64_t* work_nbrs;     /* [n_cells] bisector planes it tested */
 } vto_result;
 
 /* exact k nearest neighbours (self excluded) by (d2, index); missing slots get -1 / +inf */

@@ -1,0 +1,321 @@
+"""PyTorch binding of the Voronoi library: argument marshalling only.
+
+Every computation happens in libvt.so's CUDA kernels; these functions only
+allocate torch tensors (device memory), pass their pointers and the current
+CUDA stream through the C ABI of include/vt.h, and wrap the results.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _lib as L
+
+_EMIT_BITS = {"nbr": L.VT_EMIT_NBR, "vol": L.VT_EMIT_VOL, "cen": L.VT_EMIT_CEN, "m2": L.VT_EMIT_M2,
+              "geom": L.VT_EMIT_GEOM}
+_PREC = {"fp64": L.VT_FP64, "fp32": L.VT_FP32_RECHECK}
+
+
+@dataclass
+class Params:
+    """Run-time parameters (vt_params). ``precision`` is ``"fp32"`` (float32
+    clipping with FP64 rechecks) or ``"fp64"`` (plain FP64)."""
+
+    k0: int = 16
+    k_max: int = 256
+    grid_density: float = 2.0
+    grid_res: int = 0
+    threads_per_cell: int = 0
+    precision: str = "fp32"
+    emit: tuple = ("nbr", "vol", "cen")
+    index_space: str = "original"
+    box_lo: tuple = (0.0, 0.0, 0.0)
+    box_hi: tuple = (1.0, 1.0, 1.0)
+    stage_times: bool = False
+
+    def c(self) -> L.VtParams:
+        p = L.VtParams()
+        p.k0, p.k_max = self.k0, self.k_max
+        p.grid_density, p.grid_res = self.grid_density, self.grid_res
+        p.threads_per_cell = self.threads_per_cell
+        p.precision = _PREC[self.precision]
+        bits = 0
+        for e in self.emit:
+            bits |= _EMIT_BITS[e]
+        p.emit = bits
+        p.index_space = {"original": L.VT_INDEX_ORIGINAL, "sorted": L.VT_INDEX_SORTED}[self.index_space]
+        for a in range(3):
+            p.box_lo[a] = self.box_lo[a]
+            p.box_hi[a] = self.box_hi[a]
+        p.flags = L.VT_FLAG_STAGE_TIMES if self.stage_times else 0
+        return p
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device: torch.device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _check_points(points: torch.Tensor) -> torch.Tensor:
+    if points.dim() != 2 or points.shape[1] != 3:
+        raise ValueError("points must have shape (n, 3)")
+    if points.dtype != torch.float32:
+        raise ValueError("points must be float32")
+    if not points.is_cuda:
+        raise ValueError("points must be a CUDA tensor (use tessellate_host for host arrays)")
+    return points.contiguous()
+
+
+def workspace_size(params: Params, n: int) -> int:
+    lib = L.load()
+    b = ctypes.c_size_t()
+    L.check(lib.vt_workspace_size(ctypes.byref(params.c()), n, ctypes.byref(b)))
+    return b.value
+
+
+def grid_resolution(params: Params, n: int) -> int:
+    g = L.load().vt_grid_resolution(ctypes.byref(params.c()), n)
+    if g < 1:
+        raise ValueError("invalid parameters")
+    return g
+
+
+class Workspace:
+    """Device scratch memory for (params, n), reused across calls."""
+
+    def __init__(self, params: Params, n: int, device="cuda"):
+        self.nbytes = workspace_size(params, n)
+        self.buf = torch.empty(max(self.nbytes, 256), dtype=torch.uint8, device=device)
+
+    def fits(self, params: Params, n: int) -> bool:
+        return workspace_size(params, n) <= self.buf.numel()
+
+
+@dataclass
+class Cells:
+    vol: torch.Tensor | None = None
+    cen: torch.Tensor | None = None
+    m2: torch.Tensor | None = None
+    nbr_off: torch.Tensor | None = None
+    nbr: torch.Tensor | None = None
+    vtx_off: torch.Tensor | None = None
+    vtx: torch.Tensor | None = None
+    face_off: torch.Tensor | None = None
+    face_nbr: torch.Tensor | None = None
+    face_vtx_off: torch.Tensor | None = None
+    face_vtx: torch.Tensor | None = None
+    perm: torch.Tensor | None = None
+    stats: dict = field(default_factory=dict)
+
+
+def _out_struct(cells: Cells) -> L.VtCellsOut:
+    o = L.VtCellsOut()
+    for name in ("vol", "cen", "m2", "nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx_off",
+                 "face_vtx", "perm"):
+        t = getattr(cells, name)
+        setattr(o, name, None if t is None else t.data_ptr())
+    o.nbr_cap = 0 if cells.nbr is None else cells.nbr.numel()
+    o.vtx_cap = 0 if cells.vtx is None else cells.vtx.shape[0]
+    o.face_cap = 0 if cells.face_nbr is None else cells.face_nbr.numel()
+    o.face_vtx_cap = 0 if cells.face_vtx is None else cells.face_vtx.numel()
+    return o
+
+
+def _alloc(params: Params, n: int, dev, want_perm: bool, guess: dict | None = None) -> Cells:
+    e = set(params.emit)
+    g = guess or {}
+    c = Cells()
+    f64 = dict(dtype=torch.float64, device=dev)
+    i64 = dict(dtype=torch.int64, device=dev)
+    i32 = dict(dtype=torch.int32, device=dev)
+    if "vol" in e:
+        c.vol = torch.empty(n, **f64)
+    if "cen" in e:
+        c.cen = torch.empty((n, 3), **f64)
+    if "m2" in e:
+        c.m2 = torch.empty(n, **f64)
+    if "nbr" in e:
+        c.nbr_off = torch.empty(n + 1, **i64)
+        c.nbr = torch.empty(max(g.get("nbr", 20 * n + 64), 1), **i32)
+    if "geom" in e:
+        c.vtx_off = torch.empty(n + 1, **i64)
+        c.vtx = torch.empty((max(g.get("vtx", 34 * n + 64), 1), 3), **f64)
+        c.face_off = torch.empty(n + 1, **i64)
+        nf = max(g.get("face", 20 * n + 64), 1)
+        c.face_nbr = torch.empty(nf, **i32)
+        c.face_vtx_off = torch.empty(nf + 1, **i64)
+        c.face_vtx = torch.empty(max(g.get("face_vtx", 100 * n + 64), 1), **i32)
+    if want_perm:
+        c.perm = torch.empty(max(n, 1), **i32)
+    return c
+
+
+def _trim(c: Cells, o: L.VtCellsOut) -> None:
+    if c.nbr is not None:
+        c.nbr = c.nbr[: o.needed_nbr]
+    if c.vtx is not None:
+        c.vtx = c.vtx[: o.needed_vtx]
+        c.face_nbr = c.face_nbr[: o.needed_face]
+        c.face_vtx_off = c.face_vtx_off[: o.needed_face + 1]
+        c.face_vtx = c.face_vtx[: o.needed_face_vtx]
+
+
+def tessellate(points: torch.Tensor, params: Params | None = None, workspace: Workspace | None = None,
+               want_perm: bool = False, strict: bool = True) -> Cells:
+    """Voronoi cells of the generators ``points`` (float32 CUDA tensor (n, 3)).
+
+    Runs vt_tessellate on the current CUDA stream. Variable-length outputs are
+    sized from a first guess; if too small they are reallocated from the
+    library's exact counts and written by vt_emit. ``strict=False`` returns
+    the cells even when some could not be validated (status in
+    ``stats["status"]``).
+    """
+    params = params or Params()
+    pts = _check_points(points)
+    n = pts.shape[0]
+    dev = pts.device
+    lib = L.load()
+    ws = workspace if workspace is not None and workspace.fits(params, n) else Workspace(params, n, dev)
+    cells = _alloc(params, n, dev, want_perm)
+    o = _out_struct(cells)
+    st = L.VtStats()
+    pc = params.c()
+    s = _stream(dev)
+    code = lib.vt_tessellate(_ptr(pts), n, ctypes.byref(pc), ctypes.byref(o), ctypes.byref(st), _ptr(ws.buf),
+                             ws.buf.numel(), s)
+    if code == L.VT_ERR_CAPACITY and o.needed_nbr >= 0:
+        guess = {"nbr": o.needed_nbr, "vtx": o.needed_vtx, "face": o.needed_face, "face_vtx": o.needed_face_vtx}
+        fresh = _alloc(Params(**{**params.__dict__, "emit": tuple(x for x in params.emit if x in ("nbr", "geom"))}),
+                       n, dev, False, guess)
+        for name in ("nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx_off", "face_vtx"):
+            setattr(cells, name, getattr(fresh, name))
+        o = _out_struct(cells)
+        code = lib.vt_emit(n, ctypes.byref(pc), ctypes.byref(o), _ptr(ws.buf), ws.buf.numel(), s)
+    cells.stats = st.as_dict()
+    cells.stats["status"] = L.STATUS_NAMES.get(code, code)
+    if code not in (L.VT_OK, L.VT_ERR_UNVALIDATED) or (strict and code != L.VT_OK):
+        L.check(code)
+    _trim(cells, o)
+    return cells
+
+
+def tessellate_host(points, params: Params | None = None, device="cuda") -> Cells:
+    """End-to-end call on host arrays: copies the points to the device (from
+    pinned memory), tessellates, copies every output back to host memory."""
+    t = torch.as_tensor(points, dtype=torch.float32)
+    if not t.is_pinned():
+        t = t.pin_memory()
+    d = t.to(device, non_blocking=True)
+    cells = tessellate(d, params)
+    out = Cells(stats=cells.stats)
+    for name in ("vol", "cen", "m2", "nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx_off",
+                 "face_vtx", "perm"):
+        v = getattr(cells, name)
+        setattr(out, name, None if v is None else v.to("cpu"))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# stage calls (vt_grid_build, vt_knn, vt_clip_cells, vt_emit)
+# ---------------------------------------------------------------------------
+
+def grid_build(points: torch.Tensor, params: Params | None = None, workspace: Workspace | None = None):
+    """Stable grid counting sort. Returns (sorted float32[n,4], perm int32[n],
+    cell_off int32[G^3+1], G, workspace)."""
+    params = params or Params()
+    pts = _check_points(points)
+    n = pts.shape[0]
+    dev = pts.device
+    lib = L.load()
+    G = grid_resolution(params, n)
+    ws = workspace if workspace is not None and workspace.fits(params, n) else Workspace(params, n, dev)
+    sorted_ = torch.empty((max(n, 1), 4), dtype=torch.float32, device=dev)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    cell_off = torch.empty(G**3 + 1, dtype=torch.int32, device=dev)
+    L.check(lib.vt_grid_build(_ptr(pts), n, ctypes.byref(params.c()), G, _ptr(sorted_), _ptr(perm), _ptr(cell_off),
+                              _ptr(ws.buf), ws.buf.numel(), _stream(dev)))
+    L.check(lib.vt_read_status(_ptr(ws.buf), ws.buf.numel(), _stream(dev)))
+    return sorted_[:n], perm[:n], cell_off, G, ws
+
+
+def knn(sorted_: torch.Tensor, cell_off: torch.Tensor, G: int, k: int, params: Params | None = None,
+        queries: torch.Tensor | None = None, workspace: Workspace | None = None):
+    """k nearest neighbours (sorted indices, nearest first) and squared
+    distances (float64 for fp64, float32 for fp32)."""
+    params = params or Params()
+    n = sorted_.shape[0]
+    dev = sorted_.device
+    lib = L.load()
+    ws = workspace if workspace is not None and workspace.fits(params, n) else Workspace(params, n, dev)
+    nq = n if queries is None else queries.numel()
+    nbr = torch.empty((max(nq, 1), k), dtype=torch.int32, device=dev)
+    d2 = torch.empty((max(nq, 1), k), dtype=torch.float64 if params.precision == "fp64" else torch.float32, device=dev)
+    q = None if queries is None else queries.to(torch.int32).contiguous()
+    L.check(lib.vt_knn(_ptr(sorted_), _ptr(cell_off), G, n, _ptr(q), nq, k, ctypes.byref(params.c()), _ptr(nbr),
+                       _ptr(d2), _ptr(ws.buf), ws.buf.numel(), _stream(dev)))
+    return nbr[:nq], d2[:nq]
+
+
+def clip_cells(sorted_: torch.Tensor, cell_off: torch.Tensor, G: int, nbr: torch.Tensor | None,
+               d2: torch.Tensor | None, params: Params | None = None, queries: torch.Tensor | None = None,
+               workspace: Workspace | None = None):
+    """Clips the cells of ``queries`` (default all) with their lists (k =
+    nbr.shape[1]; nbr=None runs the exhaustive mode). Returns (Cells with
+    vol/cen/m2 written for validated cells, failed sorted indices, workspace)."""
+    params = params or Params()
+    n = sorted_.shape[0]
+    dev = sorted_.device
+    lib = L.load()
+    ws = workspace if workspace is not None and workspace.fits(params, n) else Workspace(params, n, dev)
+    nq = n if queries is None else queries.numel()
+    k = 0 if nbr is None else nbr.shape[1]
+    cells = Cells()
+    e = set(params.emit)
+    if "vol" in e:
+        cells.vol = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    if "cen" in e:
+        cells.cen = torch.full((n, 3), float("nan"), dtype=torch.float64, device=dev)
+    if "m2" in e:
+        cells.m2 = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    o = _out_struct(cells)
+    failed = torch.empty(max(nq, 1), dtype=torch.int32, device=dev)
+    n_failed = torch.zeros(1, dtype=torch.int32, device=dev)
+    q = None if queries is None else queries.to(torch.int32).contiguous()
+    L.check(lib.vt_clip_cells(_ptr(sorted_), _ptr(cell_off), G, n, _ptr(q), nq,
+                              None if nbr is None else _ptr(nbr.contiguous()),
+                              None if d2 is None else _ptr(d2.contiguous()), k, ctypes.byref(params.c()),
+                              ctypes.byref(o), _ptr(failed), _ptr(n_failed), _ptr(ws.buf), ws.buf.numel(),
+                              _stream(dev)))
+    nf = int(n_failed.item())
+    return cells, failed[:nf], ws
+
+
+def emit(n: int, params: Params, workspace: Workspace, guess: dict | None = None) -> Cells:
+    """Writes the neighbour CSR / geometry of the last clipping on
+    ``workspace`` (vt_emit)."""
+    lib = L.load()
+    dev = workspace.buf.device
+    p2 = Params(**{**params.__dict__, "emit": tuple(x for x in params.emit if x in ("nbr", "geom"))})
+    cells = _alloc(p2, n, dev, False, guess)
+    o = _out_struct(cells)
+    code = lib.vt_emit(n, ctypes.byref(params.c()), ctypes.byref(o), _ptr(workspace.buf), workspace.buf.numel(),
+                       _stream(dev))
+    if code == L.VT_ERR_CAPACITY:
+        return emit(n, params, workspace, {"nbr": o.needed_nbr, "vtx": o.needed_vtx, "face": o.needed_face,
+                                           "face_vtx": o.needed_face_vtx})
+    L.check(code)
+    _trim(cells, o)
+    return cells
+
+
+def launch_count() -> int:
+    return int(L.load().vt_launch_count())
+
+
+def version() -> str:
+    return L.load().vt_version().decode()

@@ -1,0 +1,13 @@
+// clip_f32.cu -- FP32 clipper instantiations (8, 16, 32 lanes per cell).
+#include "clip_impl.cuh"
+
+namespace vt {
+
+cudaError_t launch_clip_f32(const ClipArgs& a, int t, cudaStream_t s)
+{
+    if (t == 32) return launch_variant<float, 32, 2, 64, false>(a, s);
+    if (t == 16) return launch_variant<float, 16, 4, 64, false>(a, s);
+    return launch_variant<float, 8, 8, 64, false>(a, s);
+}
+
+}  // namespace vt

@@ -1,0 +1,20 @@
+// clip_robust.cu -- robust FP64 clipper (a warp per cell, 128 vertex slots,
+// 128 planes) for cells that outgrow the regular capacity or whose FP32
+// topology became inconsistent; plus the variant dispatch.
+#include "clip_impl.cuh"
+
+namespace vt {
+
+cudaError_t launch_clip_f32(const ClipArgs& a, int t, cudaStream_t s);
+cudaError_t launch_clip_f64(const ClipArgs& a, int t, cudaStream_t s);
+
+cudaError_t launch_clip(const ClipArgs& a, int variant, int threads_per_cell, cudaStream_t s)
+{
+    if (a.nq <= 0) return cudaSuccess;
+    const int t = threads_per_cell == 0 ? 8 : threads_per_cell;
+    if (variant == 2) return launch_variant<double, 32, 4, 128, true>(a, s);
+    if (variant == 0) return launch_clip_f32(a, t, s);
+    return launch_clip_f64(a, t, s);
+}
+
+}  // namespace vt

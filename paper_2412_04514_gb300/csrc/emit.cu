@@ -1,0 +1,113 @@
+// emit.cu -- variable-length outputs (votess paper, Features: the neighbours
+// of each cell as a jagged array; Summary: cell geometry).
+//
+// The clipper leaves one fixed-stride record per cell in the workspace. Emit
+// counts the entries of every record, turns the counts into CSR offsets with
+// grid-wide scans, then one warp per cell copies its record into the caller's
+// CSR arrays (neighbour ids, vertices, faces, face-vertex lists).
+#include "vt_internal.cuh"
+
+namespace vt {
+
+namespace {
+
+__global__ void k_emit_count(const uint8_t* __restrict__ rec, size_t stride, int64_t n, int geom,
+                             int32_t* __restrict__ cnt)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const RecHeader h = *reinterpret_cast<const RecHeader*>(rec + (size_t)i * stride);
+        cnt[i] = h.nnbr;
+        if (geom) {
+            cnt[n + i] = h.nvtx;
+            cnt[2 * n + i] = h.nface;
+            cnt[3 * n + i] = h.nfv;
+        }
+    }
+}
+
+__global__ void k_emit_totals(const int64_t* __restrict__ off, int64_t n, int geom, DevStatus* st)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        for (int a = 0; a < 4; ++a) st->totals[a] = (a == 0 || geom) ? off[a * (n + 1) + n] : 0;
+    }
+}
+
+__global__ void k_emit_write(const uint8_t* __restrict__ rec, size_t stride, int64_t n, int emit,
+                             const int64_t* __restrict__ off, vt_cells_out out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t* o_nbr = off;
+    const int64_t* o_vtx = off + (n + 1);
+    const int64_t* o_face = off + 2 * (n + 1);
+    const int64_t* o_fv = off + 3 * (n + 1);
+    for (int64_t i = wid; i < n; i += nw) {
+        const uint8_t* r = rec + (size_t)i * stride;
+        const RecHeader h = *reinterpret_cast<const RecHeader*>(r);
+        if (emit & VT_EMIT_NBR) {
+            const int64_t b = o_nbr[i];
+            const int32_t* src = reinterpret_cast<const int32_t*>(r + REC_NBR_OFF);
+            for (int t = lane; t < h.nnbr; t += 32) out.nbr[b + t] = src[t];
+            if (lane == 0) {
+                out.nbr_off[i] = b;
+                if (i == n - 1) out.nbr_off[n] = o_nbr[n];
+            }
+        }
+        if (emit & VT_EMIT_GEOM) {
+            const int64_t bv = o_vtx[i], bf = o_face[i], bfv = o_fv[i];
+            const double* v = reinterpret_cast<const double*>(r + REC_VTX_OFF);
+            for (int t = lane; t < 3 * h.nvtx; t += 32) out.vtx[3 * bv + t] = v[t];
+            const int32_t* fn = reinterpret_cast<const int32_t*>(r + REC_FNBR_OFF);
+            const uint8_t* fd = r + REC_FDEG_OFF;
+            const uint8_t* fv = r + REC_FVTX_OFF;
+            for (int t = lane; t < h.nface; t += 32) out.face_nbr[bf + t] = fn[t];
+            for (int t = lane; t < h.nfv; t += 32) out.face_vtx[bfv + t] = fv[t];
+            // per-face offsets: prefix of the degrees (faces per cell are few)
+            if (lane == 0) {
+                int64_t p = bfv;
+                for (int t = 0; t < h.nface; ++t) {
+                    out.face_vtx_off[bf + t] = p;
+                    p += fd[t];
+                }
+                out.vtx_off[i] = bv;
+                out.face_off[i] = bf;
+                if (i == n - 1) {
+                    out.vtx_off[n] = o_vtx[n];
+                    out.face_off[n] = o_face[n];
+                    out.face_vtx_off[o_face[n]] = o_fv[n];
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_emit_count(const EmitArgs& a, cudaStream_t s)
+{
+    const int geom = (a.emit & VT_EMIT_GEOM) ? 1 : 0;
+    if (a.n > 0) {
+        int64_t blocks = (a.n + 255) / 256;
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        k_emit_count<<<(unsigned)blocks, 256, 0, s>>>(a.rec, a.rec_stride, a.n, geom, a.cnt);
+        count_launch();
+    }
+    const int narr = geom ? 4 : 1;
+    for (int k = 0; k < narr; ++k) exclusive_scan_i32_to_i64(a.cnt + k * a.n, a.off64 + k * (a.n + 1), a.n, a.scan_tmp, s);
+    k_emit_totals<<<1, 32, 0, s>>>(a.off64, a.n, geom, a.st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit_write(const EmitArgs& a, const vt_cells_out& out, cudaStream_t s)
+{
+    if (a.n <= 0) return cudaSuccess;
+    int64_t blocks = (a.n + 7) / 8;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_emit_write<<<(unsigned)blocks, 256, 0, s>>>(a.rec, a.rec_stride, a.n, a.emit, a.off64, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace vt

@@ -1,0 +1,243 @@
+// knn.cu -- stage 2: k nearest neighbours per generator (votess paper,
+// Summary: a k-nearest-neighbour search over the grid-sorted points).
+//
+// One warp per query. The warp walks Chebyshev shells s = 0, 1, 2, ... of
+// grid cells around the query's cell. Cells (x, y, z..z') with consecutive z
+// are consecutive in the sorted array, so each (x, y) row of a shell is one
+// contiguous, coalesced float4 range; the 32 lanes take 32 candidates at a
+// time. The k best candidates so far live in a sorted list spread over the
+// warp's registers (entry e = r*32 + lane, KPL registers per lane); a
+// qualifying candidate is inserted with one ballot per register row and one
+// shuffle-shift. After each shell the walk stops once the list is full and the
+// k-th distance is no larger than the distance from the query to the outside
+// of the scanned block (minus a rounding margin), or the block covers the grid.
+#include <float.h>
+#include <limits.h>
+
+#include "vt_internal.cuh"
+
+namespace vt {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename Real>
+struct Dist;
+
+template <>
+struct Dist<double> {
+    // the exact key of the FP64 form: ((dx*dx + dy*dy) + dz*dz), no contraction
+    static __device__ __forceinline__ double d2(float4 a, float4 b)
+    {
+        double dx = __dsub_rn((double)b.x, (double)a.x);
+        double dy = __dsub_rn((double)b.y, (double)a.y);
+        double dz = __dsub_rn((double)b.z, (double)a.z);
+        return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    }
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+};
+
+template <>
+struct Dist<float> {
+    static __device__ __forceinline__ float d2(float4 a, float4 b)
+    {
+        float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+        return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    }
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+};
+
+template <typename Real>
+__device__ __forceinline__ bool key_less(Real da, int oa, Real db, int ob)
+{
+    return da < db || (da == db && oa < ob);
+}
+
+template <typename Real, int KPL>
+struct WarpList {
+    Real d[KPL];
+    int o[KPL];  // original index (tie-break key)
+    int j[KPL];  // sorted index (payload)
+
+    __device__ void init()
+    {
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) { d[r] = Dist<Real>::inf(); o[r] = INT_MAX; j[r] = -1; }
+    }
+
+    // inserts (cd, co, cj) if it ranks among the first k; warp-uniform call
+    __device__ void insert(Real cd, int co, int cj, int k, int lane)
+    {
+        int p = 0;
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) p += __popc(__ballot_sync(FULL, key_less(d[r], o[r], cd, co)));
+        if (p >= k) return;
+        Real nd[KPL];
+        int no[KPL], nj[KPL];
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+            Real ud = __shfl_up_sync(FULL, d[r], 1);
+            int uo = __shfl_up_sync(FULL, o[r], 1);
+            int uj = __shfl_up_sync(FULL, j[r], 1);
+            Real wd = ud;
+            int wo = uo, wj = uj;
+            if (r > 0) {
+                wd = __shfl_sync(FULL, d[r - 1], 31);
+                wo = __shfl_sync(FULL, o[r - 1], 31);
+                wj = __shfl_sync(FULL, j[r - 1], 31);
+            }
+            Real pd = lane == 0 ? wd : ud;
+            int po = lane == 0 ? wo : uo, pj = lane == 0 ? wj : uj;
+            int e = r * 32 + lane;
+            nd[r] = e > p ? pd : (e == p ? cd : d[r]);
+            no[r] = e > p ? po : (e == p ? co : o[r]);
+            nj[r] = e > p ? pj : (e == p ? cj : j[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) { d[r] = nd[r]; o[r] = no[r]; j[r] = nj[r]; }
+    }
+
+    // key of entry e (warp-uniform e)
+    __device__ void entry(int e, Real& kd, int& ko) const
+    {
+        Real dd = d[0];
+        int oo = o[0];
+#pragma unroll
+        for (int r = 1; r < KPL; ++r)
+            if (r == e / 32) { dd = d[r]; oo = o[r]; }
+        kd = __shfl_sync(FULL, dd, e % 32);
+        ko = __shfl_sync(FULL, oo, e % 32);
+    }
+};
+
+template <typename Real, int KPL>
+__global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, const int32_t* __restrict__ cell_off,
+                                             GridDesc g, const int32_t* __restrict__ queries, int64_t nq, int k,
+                                             int32_t* __restrict__ nbr, Real* __restrict__ d2out, DevStatus* st)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int G = g.G;
+    for (int64_t c = wid; c < nq; c += nw) {
+        const int q = queries ? queries[c] : (int)c;
+        const float4 pq = sorted[q];
+        const int ix = cell_coord(pq.x, g.lo[0], g.scale[0], G);
+        const int iy = cell_coord(pq.y, g.lo[1], g.scale[1], G);
+        const int iz = cell_coord(pq.z, g.lo[2], g.scale[2], G);
+        WarpList<Real, KPL> L;
+        L.init();
+        int count = 0;
+        Real kd = Dist<Real>::inf();
+        int ko = INT_MAX;
+        bool dup = false;
+
+        auto scan_range = [&](int a, int b) {
+            for (int base = a; base < b; base += 32) {
+                const int jj = base + lane;
+                bool valid = jj < b && jj != q;
+                Real cd = Dist<Real>::inf();
+                int co = INT_MAX;
+                if (valid) {
+                    float4 pc = sorted[jj];
+                    cd = Dist<Real>::d2(pq, pc);
+                    co = __float_as_int(pc.w);
+                    if (pc.x == pq.x && pc.y == pq.y && pc.z == pq.z) dup = true;
+                }
+                unsigned m = __ballot_sync(FULL, valid && (count < k || key_less(cd, co, kd, ko)));
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    Real bd = __shfl_sync(FULL, cd, src);
+                    int bo = __shfl_sync(FULL, co, src);
+                    int bj = __shfl_sync(FULL, jj, src);
+                    L.insert(bd, bo, bj, k, lane);
+                    if (count < k) ++count;
+                    if (count == k) L.entry(k - 1, kd, ko);
+                }
+            }
+        };
+
+        for (int s = 0;; ++s) {
+            for (int dx = -s; dx <= s; ++dx) {
+                const int x = ix + dx;
+                if (x < 0 || x >= G) continue;
+                for (int dy = -s; dy <= s; ++dy) {
+                    const int y = iy + dy;
+                    if (y < 0 || y >= G) continue;
+                    const bool full = dx == -s || dx == s || dy == -s || dy == s;
+                    if (full) {
+                        const int z0 = max(iz - s, 0), z1 = min(iz + s, G - 1);
+                        scan_range(cell_off[cell_id(x, y, z0, G)], cell_off[cell_id(x, y, z1, G) + 1]);
+                    } else {
+                        if (iz - s >= 0) {
+                            const int cc = cell_id(x, y, iz - s, G);
+                            scan_range(cell_off[cc], cell_off[cc + 1]);
+                        }
+                        if (iz + s < G) {
+                            const int cc = cell_id(x, y, iz + s, G);
+                            scan_range(cell_off[cc], cell_off[cc + 1]);
+                        }
+                    }
+                }
+            }
+            // stop rule
+            const bool covers = ix - s <= 0 && iy - s <= 0 && iz - s <= 0 && ix + s >= G - 1 && iy + s >= G - 1 &&
+                                iz + s >= G - 1;
+            if (covers) break;
+            if (count == k) {
+                const double qc[3] = {(double)pq.x, (double)pq.y, (double)pq.z};
+                const int ic[3] = {ix, iy, iz};
+                double gap = 1e300;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (ic[a] - s > 0) gap = fmin(gap, qc[a] - ((double)g.lo[a] + (ic[a] - s) * g.cw[a]) - g.margin);
+                    if (ic[a] + s + 1 < G)
+                        gap = fmin(gap, ((double)g.lo[a] + (ic[a] + s + 1) * g.cw[a]) - qc[a] - g.margin);
+                }
+                if (gap > 0 && (double)kd <= gap * gap * (1.0 - 1e-6)) break;
+            }
+        }
+        if (__any_sync(FULL, dup) && lane == 0) atomicExch((int*)&st->duplicate, 1);
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+            const int e = r * 32 + lane;
+            if (e < k) {
+                nbr[c * k + e] = L.j[r];
+                if (d2out) d2out[c * k + e] = L.d[r];
+            }
+        }
+    }
+}
+
+template <typename Real>
+cudaError_t launch_knn_t(const float4* sorted, const int32_t* cell_off, const GridDesc& g, const int32_t* queries,
+                         int64_t nq, int k, int32_t* nbr, Real* d2, DevStatus* st, cudaStream_t s)
+{
+    if (nq <= 0) return cudaSuccess;
+    int64_t blocks = (nq + 7) / 8;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    dim3 grid((unsigned)blocks), block(256);
+    if (k <= 32) k_knn<Real, 1><<<grid, block, 0, s>>>(sorted, cell_off, g, queries, nq, k, nbr, d2, st);
+    else if (k <= 64) k_knn<Real, 2><<<grid, block, 0, s>>>(sorted, cell_off, g, queries, nq, k, nbr, d2, st);
+    else if (k <= 128) k_knn<Real, 4><<<grid, block, 0, s>>>(sorted, cell_off, g, queries, nq, k, nbr, d2, st);
+    else k_knn<Real, 8><<<grid, block, 0, s>>>(sorted, cell_off, g, queries, nq, k, nbr, d2, st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_knn(const float4* sorted, const int32_t* cell_off, const GridDesc& g, int64_t n,
+                       const int32_t* queries, int64_t nq, int k, int precision, int32_t* nbr, void* d2,
+                       DevStatus* st, cudaStream_t s)
+{
+    (void)n;
+    if (k < 1 || k > 256) return cudaErrorInvalidValue;
+    if (precision == VT_FP64)
+        return launch_knn_t<double>(sorted, cell_off, g, queries, nq, k, nbr, (double*)d2, st, s);
+    return launch_knn_t<float>(sorted, cell_off, g, queries, nq, k, nbr, (float*)d2, st, s);
+}
+
+}  // namespace vt

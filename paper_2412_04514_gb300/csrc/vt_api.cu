@@ -1,0 +1,619 @@
+// vt_api.cu -- the C ABI (include/vt.h): argument checks, workspace layout
+// and the host-side orchestration of the pass loop. Every step of the
+// computation runs in the kernels of grid.cu, knn.cu, clip.cu, emit.cu and
+// scan.cu; the host only launches them and reads a status block once per
+// pass.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vt_internal.cuh"
+
+namespace vt {
+
+namespace {
+thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int check_params(const vt_params* p)
+{
+    if (!p) return fail(VT_ERR_INVALID_ARG, "params is NULL");
+    if (p->k0 < 1 || p->k0 > 256) return fail(VT_ERR_INVALID_ARG, "k0 must be in [1, 256], got %d", p->k0);
+    if (p->k_max < p->k0 || p->k_max > 256)
+        return fail(VT_ERR_INVALID_ARG, "k_max must be in [k0, 256], got %d", p->k_max);
+    if (p->grid_res < 0 || p->grid_res > 1024) return fail(VT_ERR_INVALID_ARG, "grid_res must be in [0, 1024]");
+    if (p->grid_res == 0 && !(p->grid_density > 0.0f))
+        return fail(VT_ERR_INVALID_ARG, "grid_density must be > 0 when grid_res is 0");
+    const int t = p->threads_per_cell;
+    if (!(t == 0 || t == 8 || t == 16 || t == 32))
+        return fail(VT_ERR_INVALID_ARG, "threads_per_cell must be 0, 8, 16 or 32, got %d", t);
+    if (p->precision != VT_FP64 && p->precision != VT_FP32_RECHECK)
+        return fail(VT_ERR_INVALID_ARG, "precision must be VT_FP64 or VT_FP32_RECHECK");
+    if (p->index_space != VT_INDEX_ORIGINAL && p->index_space != VT_INDEX_SORTED)
+        return fail(VT_ERR_INVALID_ARG, "index_space must be VT_INDEX_ORIGINAL or VT_INDEX_SORTED");
+    if (p->emit & ~(VT_EMIT_NBR | VT_EMIT_VOL | VT_EMIT_CEN | VT_EMIT_M2 | VT_EMIT_GEOM))
+        return fail(VT_ERR_INVALID_ARG, "unknown emit bits 0x%x", p->emit);
+    for (int a = 0; a < 3; ++a)
+        if (!(std::isfinite(p->box_lo[a]) && std::isfinite(p->box_hi[a]) && p->box_hi[a] > p->box_lo[a]))
+            return fail(VT_ERR_INVALID_ARG, "box must satisfy lo < hi (finite) on every axis");
+    return VT_OK;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(VT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
+
+static int grid_res_for(const vt_params* p, int64_t n)
+{
+    if (p->grid_res > 0) return p->grid_res;
+    if (n <= 0) return 1;
+    double g = std::ceil(std::cbrt((double)n / (double)p->grid_density) - 1e-9);
+    double cap = std::ceil(std::cbrt(8.0 * (double)n)) + 1.0;
+    if (g > cap) g = cap;
+    if (g > 1024) g = 1024;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+GridDesc make_grid(const vt_params* p, int G)
+{
+    GridDesc g;
+    g.G = G;
+    double ext_max = 0;
+    for (int a = 0; a < 3; ++a) {
+        g.lo[a] = p->box_lo[a];
+        g.hi[a] = p->box_hi[a];
+        const float ext = p->box_hi[a] - p->box_lo[a];
+        g.scale[a] = (float)G / ext;
+        g.cw[a] = ((double)p->box_hi[a] - (double)p->box_lo[a]) / (double)G;
+        ext_max = std::fmax(ext_max, (double)p->box_hi[a] - (double)p->box_lo[a]);
+    }
+    // cell assignment in float32 may differ from exact arithmetic by a few
+    // ulps of the scaled coordinate; the shell-walk stop rule stays clear of it
+    g.margin = 16.0 * ext_max * std::ldexp(1.0, -24);
+    return g;
+}
+
+Layout make_layout(const vt_params* p, int64_t n)
+{
+    Layout L{};
+    L.G = grid_res_for(p, n);
+    L.n = n;
+    L.g3 = (int64_t)L.G * L.G * L.G;
+    const int64_t nn = n > 0 ? n : 1;
+    int64_t cap = nn * (int64_t)p->k0;
+    if (cap < (int64_t)p->k_max * 64) cap = (int64_t)p->k_max * 64;
+    L.knn_cap = cap;
+    const bool recs = (p->emit & (VT_EMIT_NBR | VT_EMIT_GEOM)) != 0;
+    L.rec_stride = !recs ? 0 : ((p->emit & VT_EMIT_GEOM) ? REC_STRIDE_GEOM : REC_STRIDE_NBR);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    L.status = take(sizeof(DevStatus));
+    L.cid = take(sizeof(int32_t) * nn);
+    L.ticket = take(sizeof(int32_t) * nn);
+    L.counts = take(sizeof(int32_t) * (L.g3 + 1));
+    L.cell_off = take(sizeof(int32_t) * (L.g3 + 1));
+    L.big = take(sizeof(int32_t) * (L.g3 + 1));
+    size_t st1 = scan_tmp_bytes(L.g3), st2 = scan_tmp_bytes(nn);
+    L.scan_tmp = take(st1 > st2 ? st1 : st2);
+    L.sorted = take(sizeof(float4) * nn);
+    L.perm = take(sizeof(int32_t) * nn);
+    L.list_a = take(sizeof(int32_t) * nn * 6);  // six cell lists of n entries
+    L.knn_nbr = take(sizeof(int32_t) * L.knn_cap);
+    L.knn_d2 = take(sizeof(double) * L.knn_cap);
+    L.rec = take(L.rec_stride * (size_t)nn);
+    L.cnt = take(sizeof(int32_t) * 4 * nn);
+    L.off64 = take(sizeof(int64_t) * 4 * (nn + 1));
+    L.total = off;
+    return L;
+}
+
+}  // namespace vt
+
+using namespace vt;
+
+namespace vt_host {
+
+// CUDA-event timing of kernel groups on the call's stream (VT_FLAG_STAGE_TIMES)
+struct StageTimer {
+    enum { GRID = 0, KNN = 1, CLIP = 2, EMIT = 3 };
+    bool on = false;
+    cudaStream_t s = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
+    int open_stage = -1;
+    void begin(int stage)
+    {
+        if (!on) return;
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+        ev[stage].push_back({a, b});
+        open_stage = stage;
+    }
+    void end()
+    {
+        if (!on || open_stage < 0) return;
+        cudaEventRecord(ev[open_stage].back().second, s);
+        open_stage = -1;
+    }
+    // call after the stream is synchronised
+    double total(int stage)
+    {
+        double t = 0;
+        for (auto& e : ev[stage]) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) t += ms;
+        }
+        return t;
+    }
+    ~StageTimer()
+    {
+        for (auto& v : ev)
+            for (auto& e : v) {
+                cudaEventDestroy(e.first);
+                cudaEventDestroy(e.second);
+            }
+    }
+};
+
+struct Ctx {
+    Layout L;
+    uint8_t* base;
+    cudaStream_t s;
+    DevStatus* st;
+    GridDesc g;
+    StageTimer* timer = nullptr;
+    int* clip_launches = nullptr;
+    int* knn_launches = nullptr;
+    template <typename X>
+    X* at(size_t off) const { return reinterpret_cast<X*>(base + off); }
+};
+
+int make_ctx(const vt_params* p, int64_t n, void* ws, size_t ws_bytes, void* stream, Ctx& c)
+{
+    int e = check_params(p);
+    if (e) return e;
+    if (n < 0 || n > (int64_t)INT32_MAX / 2) return fail(VT_ERR_INVALID_ARG, "n out of range: %lld", (long long)n);
+    c.L = make_layout(p, n);
+    if (!ws) return fail(VT_ERR_WORKSPACE, "workspace is NULL");
+    if (ws_bytes < c.L.total)
+        return fail(VT_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu bytes needed", ws_bytes, c.L.total);
+    c.base = (uint8_t*)ws;
+    c.s = (cudaStream_t)stream;
+    c.st = c.at<DevStatus>(c.L.status);
+    c.g = make_grid(p, c.L.G);
+    return VT_OK;
+}
+
+int read_status(const Ctx& c, DevStatus& h)
+{
+    cudaError_t e = cudaMemcpyAsync(&h, c.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.s);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    return VT_OK;
+}
+
+int zero_counters(const Ctx& c)
+{
+    cudaError_t e = cudaMemsetAsync(&c.st->n_fail_next, 0, 2 * sizeof(int32_t), c.s);
+    return e == cudaSuccess ? VT_OK : cuda_fail(e, "counter reset");
+}
+
+__global__ void k_iota(int32_t* a, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (int32_t)i;
+}
+
+// one clip pass over `list` (m cells): kNN with k in chunks that fit the
+// list buffer, then the clipper; k == 0 runs the exhaustive clipper
+int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, int k, int variant, int knn_prec,
+              vt_cells_out* out, int32_t* fail_next, int32_t* fail_robust)
+{
+    const Layout& L = c.L;
+    ClipArgs a{};
+    a.sorted = c.at<float4>(L.sorted);
+    a.cell_off = c.at<int32_t>(L.cell_off);
+    a.g = c.g;
+    a.n = L.n;
+    a.k = k;
+    a.emit = p->emit;
+    a.index_space = p->index_space;
+    a.vol = (p->emit & VT_EMIT_VOL) ? out->vol : nullptr;
+    a.cen = (p->emit & VT_EMIT_CEN) ? out->cen : nullptr;
+    a.m2 = (p->emit & VT_EMIT_M2) ? out->m2 : nullptr;
+    a.rec = L.rec_stride ? c.at<uint8_t>(L.rec) : nullptr;
+    a.rec_stride = L.rec_stride;
+    a.fail_next = fail_next;
+    a.fail_robust = fail_robust;
+    a.ctr_next = &c.st->n_fail_next;
+    a.ctr_robust = &c.st->n_fail_robust;
+    a.st = c.st;
+    const int tpc = p->threads_per_cell;
+    StageTimer dummy;
+    StageTimer& T = c.timer ? *c.timer : dummy;
+    if (k == 0) {
+        a.queries = list;
+        a.nq = m;
+        T.begin(StageTimer::CLIP);
+        cudaError_t e = launch_clip(a, variant, tpc, c.s);
+        T.end();
+        if (c.clip_launches) ++*c.clip_launches;
+        return e == cudaSuccess ? VT_OK : cuda_fail(e, "clip launch");
+    }
+    const int64_t chunk = L.knn_cap / k;
+    for (int64_t o = 0; o < m; o += chunk) {
+        const int64_t cnt = (m - o) < chunk ? (m - o) : chunk;
+        const int32_t* q = list ? list + o : nullptr;
+        if (!list && o > 0) return fail(VT_ERR_INVALID_ARG, "internal: implicit list needs one chunk");
+        T.begin(StageTimer::KNN);
+        cudaError_t e = launch_knn(a.sorted, a.cell_off, c.g, L.n, q, cnt, k, knn_prec, c.at<int32_t>(L.knn_nbr),
+                                   c.at<void>(L.knn_d2), c.st, c.s);
+        T.end();
+        if (c.knn_launches) ++*c.knn_launches;
+        if (e != cudaSuccess) return cuda_fail(e, "knn launch");
+        a.queries = q;
+        a.nq = cnt;
+        a.nbr = c.at<int32_t>(L.knn_nbr);
+        a.d2 = c.at<void>(L.knn_d2);
+        T.begin(StageTimer::CLIP);
+        e = launch_clip(a, variant, tpc, c.s);
+        T.end();
+        if (c.clip_launches) ++*c.clip_launches;
+        if (e != cudaSuccess) return cuda_fail(e, "clip launch");
+    }
+    return VT_OK;
+}
+
+int status_errors(const DevStatus& h)
+{
+    if (h.bad_point)
+        return fail(VT_ERR_INVALID_ARG, "point %d is not finite or not inside [box_lo, box_hi)", h.bad_point - 1);
+    if (h.duplicate) return fail(VT_ERR_DUPLICATE_POINTS, "two generators coincide");
+    return VT_OK;
+}
+
+int emit_outputs(const Ctx& c, const vt_params* p, vt_cells_out* out)
+{
+    const Layout& L = c.L;
+    const int64_t n = L.n;
+    if (!(p->emit & (VT_EMIT_NBR | VT_EMIT_GEOM))) return VT_OK;
+    if (n == 0) {
+        int64_t z = 0;
+        if ((p->emit & VT_EMIT_NBR) && out->nbr_off)
+            cudaMemcpyAsync(out->nbr_off, &z, sizeof(z), cudaMemcpyHostToDevice, c.s);
+        if (p->emit & VT_EMIT_GEOM) {
+            if (out->vtx_off) cudaMemcpyAsync(out->vtx_off, &z, sizeof(z), cudaMemcpyHostToDevice, c.s);
+            if (out->face_off) cudaMemcpyAsync(out->face_off, &z, sizeof(z), cudaMemcpyHostToDevice, c.s);
+            if (out->face_vtx_off) cudaMemcpyAsync(out->face_vtx_off, &z, sizeof(z), cudaMemcpyHostToDevice, c.s);
+        }
+        cudaStreamSynchronize(c.s);
+        out->needed_nbr = out->needed_vtx = out->needed_face = out->needed_face_vtx = 0;
+        return VT_OK;
+    }
+    EmitArgs e{};
+    e.n = n;
+    e.emit = p->emit;
+    e.rec = c.at<uint8_t>(L.rec);
+    e.rec_stride = L.rec_stride;
+    e.cnt = c.at<int32_t>(L.cnt);
+    e.off64 = c.at<int64_t>(L.off64);
+    e.scan_tmp = c.at<void>(L.scan_tmp);
+    e.st = c.st;
+    StageTimer dummy;
+    StageTimer& T = c.timer ? *c.timer : dummy;
+    T.begin(StageTimer::EMIT);
+    cudaError_t ce = launch_emit_count(e, c.s);
+    T.end();
+    if (ce != cudaSuccess) return cuda_fail(ce, "emit count");
+    DevStatus h;
+    int r = read_status(c, h);
+    if (r) return r;
+    out->needed_nbr = h.totals[0];
+    out->needed_vtx = h.totals[1];
+    out->needed_face = h.totals[2];
+    out->needed_face_vtx = h.totals[3];
+    if (h.record_overflow) return fail(VT_ERR_CAPACITY, "%d cells exceed the per-cell record size", h.record_overflow);
+    if (p->emit & VT_EMIT_NBR) {
+        if (!out->nbr_off || (!out->nbr && h.totals[0] > 0))
+            return fail(VT_ERR_INVALID_ARG, "VT_EMIT_NBR needs nbr_off and nbr");
+        if (out->nbr_cap < h.totals[0])
+            return fail(VT_ERR_CAPACITY, "nbr_cap %lld < needed %lld", (long long)out->nbr_cap, (long long)h.totals[0]);
+    }
+    if (p->emit & VT_EMIT_GEOM) {
+        if (!out->vtx_off || !out->vtx || !out->face_off || !out->face_nbr || !out->face_vtx_off || !out->face_vtx)
+            return fail(VT_ERR_INVALID_ARG, "VT_EMIT_GEOM needs every geometry pointer");
+        if (out->vtx_cap < h.totals[1] || out->face_cap < h.totals[2] || out->face_vtx_cap < h.totals[3])
+            return fail(VT_ERR_CAPACITY, "geometry buffers too small (need vtx %lld, faces %lld, face_vtx %lld)",
+                        (long long)h.totals[1], (long long)h.totals[2], (long long)h.totals[3]);
+    }
+    T.begin(StageTimer::EMIT);
+    ce = launch_emit_write(e, *out, c.s);
+    T.end();
+    if (ce != cudaSuccess) return cuda_fail(ce, "emit write");
+    return VT_OK;
+}
+
+}  // namespace vt_host
+
+using namespace vt_host;
+
+extern "C" {
+
+void vt_params_default(vt_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->k0 = 16;
+    p->k_max = 256;
+    p->grid_density = 2.0f;
+    p->grid_res = 0;
+    p->threads_per_cell = 0;
+    p->precision = VT_FP32_RECHECK;
+    p->emit = VT_EMIT_NBR | VT_EMIT_VOL | VT_EMIT_CEN;
+    p->index_space = VT_INDEX_ORIGINAL;
+    for (int a = 0; a < 3; ++a) { p->box_lo[a] = 0.0f; p->box_hi[a] = 1.0f; }
+}
+
+int vt_grid_resolution(const vt_params* p, int64_t n)
+{
+    if (check_params(p)) return -1;
+    return grid_res_for(p, n);
+}
+
+int vt_workspace_size(const vt_params* p, int64_t n, size_t* bytes)
+{
+    int e = check_params(p);
+    if (e) return e;
+    if (n < 0 || !bytes) return fail(VT_ERR_INVALID_ARG, "n < 0 or bytes is NULL");
+    *bytes = make_layout(p, n).total;
+    return VT_OK;
+}
+
+int vt_grid_build(const float* pts, int64_t n, const vt_params* p, int G, float* sorted, int32_t* perm,
+                  int32_t* cell_off, void* ws, size_t ws_bytes, void* stream)
+{
+    Ctx c;
+    int e = make_ctx(p, n, ws, ws_bytes, stream, c);
+    if (e) return e;
+    if (G != c.L.G) return fail(VT_ERR_INVALID_ARG, "G = %d differs from vt_grid_resolution = %d", G, c.L.G);
+    if ((n > 0 && (!pts || !sorted || !perm)) || !cell_off) return fail(VT_ERR_INVALID_ARG, "NULL buffer");
+    cudaError_t ce = cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "status reset");
+    ce = launch_grid_build(pts, n, c.g, (float4*)sorted, perm, cell_off, c.at<int32_t>(c.L.cid),
+                           c.at<int32_t>(c.L.ticket), c.at<int32_t>(c.L.counts), c.at<int32_t>(c.L.big),
+                           c.at<void>(c.L.scan_tmp), c.st, c.s);
+    return ce == cudaSuccess ? VT_OK : cuda_fail(ce, "grid build");
+}
+
+int vt_knn(const float* sorted, const int32_t* cell_off, int G, int64_t n, const int32_t* queries, int64_t nq, int k,
+           const vt_params* p, int32_t* nbr, void* d2, void* ws, size_t ws_bytes, void* stream)
+{
+    Ctx c;
+    int e = make_ctx(p, n, ws, ws_bytes, stream, c);
+    if (e) return e;
+    if (G != c.L.G) return fail(VT_ERR_INVALID_ARG, "G = %d differs from vt_grid_resolution = %d", G, c.L.G);
+    if (k < 1 || k > 256) return fail(VT_ERR_INVALID_ARG, "k must be in [1, 256], got %d", k);
+    if (nq < 0 || (nq > 0 && (!sorted || !cell_off || !nbr))) return fail(VT_ERR_INVALID_ARG, "bad buffers");
+    if (!queries && nq > n) return fail(VT_ERR_INVALID_ARG, "nq > n without a query list");
+    cudaError_t ce = launch_knn((const float4*)sorted, cell_off, c.g, n, queries, nq, k, p->precision, nbr, d2, c.st, c.s);
+    return ce == cudaSuccess ? VT_OK : cuda_fail(ce, "knn");
+}
+
+int vt_clip_cells(const float* sorted, const int32_t* cell_off, int G, int64_t n, const int32_t* queries, int64_t nq,
+                  const int32_t* nbr, const void* d2, int k, const vt_params* p, vt_cells_out* out, int32_t* failed,
+                  int32_t* n_failed, void* ws, size_t ws_bytes, void* stream)
+{
+    Ctx c;
+    int e = make_ctx(p, n, ws, ws_bytes, stream, c);
+    if (e) return e;
+    if (G != c.L.G) return fail(VT_ERR_INVALID_ARG, "G = %d differs from vt_grid_resolution = %d", G, c.L.G);
+    if (k < 0 || k > 256) return fail(VT_ERR_INVALID_ARG, "k must be in [0, 256]");
+    if (!out || !failed || !n_failed || !sorted || !cell_off) return fail(VT_ERR_INVALID_ARG, "NULL buffer");
+    if (k > 0 && (!nbr || !d2)) return fail(VT_ERR_INVALID_ARG, "list mode needs nbr and d2");
+    if (!queries && nq > n) return fail(VT_ERR_INVALID_ARG, "nq > n without a query list");
+    ClipArgs a{};
+    a.sorted = (const float4*)sorted;
+    a.cell_off = cell_off;
+    a.g = c.g;
+    a.n = n;
+    a.queries = queries;
+    a.nq = nq;
+    a.nbr = nbr;
+    a.d2 = d2;
+    a.k = k;
+    a.emit = p->emit;
+    a.index_space = p->index_space;
+    a.vol = (p->emit & VT_EMIT_VOL) ? out->vol : nullptr;
+    a.cen = (p->emit & VT_EMIT_CEN) ? out->cen : nullptr;
+    a.m2 = (p->emit & VT_EMIT_M2) ? out->m2 : nullptr;
+    a.rec = c.L.rec_stride ? c.at<uint8_t>(c.L.rec) : nullptr;
+    a.rec_stride = c.L.rec_stride;
+    a.fail_next = failed;
+    a.fail_robust = failed;
+    a.ctr_next = n_failed;
+    a.ctr_robust = n_failed;
+    a.st = c.st;
+    cudaError_t ce = launch_clip(a, p->precision == VT_FP64 ? 1 : 0, p->threads_per_cell, c.s);
+    return ce == cudaSuccess ? VT_OK : cuda_fail(ce, "clip");
+}
+
+int vt_emit(int64_t n, const vt_params* p, vt_cells_out* out, void* ws, size_t ws_bytes, void* stream)
+{
+    Ctx c;
+    int e = make_ctx(p, n, ws, ws_bytes, stream, c);
+    if (e) return e;
+    if (!out) return fail(VT_ERR_INVALID_ARG, "out is NULL");
+    return emit_outputs(c, p, out);
+}
+
+int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cells_out* out, vt_stats* stats, void* ws,
+                  size_t ws_bytes, void* stream)
+{
+    Ctx c;
+    int e = make_ctx(p, n, ws, ws_bytes, stream, c);
+    if (e) return e;
+    if (!out) return fail(VT_ERR_INVALID_ARG, "out is NULL");
+    if (n > 0 && !pts) return fail(VT_ERR_INVALID_ARG, "pts is NULL");
+    if ((p->emit & VT_EMIT_VOL) && n > 0 && !out->vol) return fail(VT_ERR_INVALID_ARG, "VT_EMIT_VOL needs vol");
+    if ((p->emit & VT_EMIT_CEN) && n > 0 && !out->cen) return fail(VT_ERR_INVALID_ARG, "VT_EMIT_CEN needs cen");
+    if ((p->emit & VT_EMIT_M2) && n > 0 && !out->m2) return fail(VT_ERR_INVALID_ARG, "VT_EMIT_M2 needs m2");
+    const int64_t l0 = launches();
+    vt_stats S{};
+    S.grid_res = c.L.G;
+    const Layout& L = c.L;
+    StageTimer timer;
+    timer.on = (p->flags & VT_FLAG_STAGE_TIMES) != 0;
+    timer.s = c.s;
+    c.timer = &timer;
+    c.clip_launches = &S.clip_launches;
+    c.knn_launches = &S.knn_launches;
+    cudaError_t ce = cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "status reset");
+    if (n > 0) {
+        timer.begin(StageTimer::GRID);
+        ce = launch_grid_build(pts, n, c.g, c.at<float4>(L.sorted), c.at<int32_t>(L.perm), c.at<int32_t>(L.cell_off),
+                               c.at<int32_t>(L.cid), c.at<int32_t>(L.ticket), c.at<int32_t>(L.counts),
+                               c.at<int32_t>(L.big), c.at<void>(L.scan_tmp), c.st, c.s);
+        timer.end();
+        if (ce != cudaSuccess) return cuda_fail(ce, "grid build");
+        if (out->perm) {
+            ce = cudaMemcpyAsync(out->perm, c.at<int32_t>(L.perm), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c.s);
+            if (ce != cudaSuccess) return cuda_fail(ce, "perm copy");
+        }
+    }
+    // six lists of n cells: regular current/next, robust current/next, robust new, unvalidated
+    int32_t* lists = c.at<int32_t>(L.list_a);
+    int32_t* reg_cur = lists;
+    int32_t* reg_nxt = lists + n;
+    int32_t* rob_cur = lists + 2 * n;
+    int32_t* rob_nxt = lists + 3 * n;
+    int32_t* rob_new = lists + 4 * n;
+    int32_t* unval = lists + 5 * n;
+    const int variant_reg = p->precision == VT_FP64 ? 1 : 0;
+    int64_t m_reg = n, m_rob = 0, n_unval = 0;
+    bool implicit = true;  // the first pass runs over all cells without a list
+    int k = p->k0;
+    int r = VT_OK;
+    DevStatus h{};
+    while (m_reg + m_rob > 0) {
+        const bool exhaustive = k > p->k_max;
+        const int kk = exhaustive ? 0 : k;
+        if (S.passes < VT_MAX_PASSES) {
+            S.k_of_pass[S.passes] = kk;
+            S.cells_of_pass[S.passes] = m_reg + m_rob;
+        }
+        ++S.passes;
+        if (exhaustive) S.exhaustive_cells = m_reg + m_rob;
+        int64_t got_next = 0, got_rob = 0;
+        if (m_reg > 0) {
+            if ((r = zero_counters(c))) return r;
+            if (implicit && (int64_t)kk * m_reg > L.knn_cap) {
+                k_iota<<<(unsigned)((m_reg + 255) / 256 < 152 * 64 ? (m_reg + 255) / 256 : 152 * 64), 256, 0, c.s>>>(
+                    reg_cur, m_reg);
+                count_launch();
+                implicit = false;
+            }
+            r = clip_pass(c, p, implicit ? nullptr : reg_cur, m_reg, kk, variant_reg, p->precision, out, reg_nxt,
+                          rob_new);
+            if (r) return r;
+            if ((r = read_status(c, h))) return r;
+            if ((r = status_errors(h))) return r;
+            got_next = h.n_fail_next;
+            got_rob = h.n_fail_robust;
+        }
+        implicit = false;
+        if (got_rob > 0) {
+            ce = cudaMemcpyAsync(rob_cur + m_rob, rob_new, sizeof(int32_t) * got_rob, cudaMemcpyDeviceToDevice, c.s);
+            if (ce != cudaSuccess) return cuda_fail(ce, "list copy");
+            m_rob += got_rob;
+        }
+        int64_t rob_next = 0;
+        if (m_rob > 0) {
+            if ((r = zero_counters(c))) return r;
+            r = clip_pass(c, p, rob_cur, m_rob, kk, 2, VT_FP64, out, rob_nxt, unval + n_unval);
+            if (r) return r;
+            if ((r = read_status(c, h))) return r;
+            if ((r = status_errors(h))) return r;
+            rob_next = h.n_fail_next;
+            n_unval += h.n_fail_robust;
+        }
+        std::swap(reg_cur, reg_nxt);
+        std::swap(rob_cur, rob_nxt);
+        m_reg = got_next;
+        m_rob = rob_next;
+        if (exhaustive) {
+            n_unval += m_reg + m_rob;  // cannot happen: the exhaustive pass always concludes
+            break;
+        }
+        k *= 2;
+    }
+    S.unvalidated = n_unval;
+    r = emit_outputs(c, p, out);
+    if ((r = r ? r : read_status(c, h))) {
+        if (stats) *stats = S;
+        return r;
+    }
+    S.fp64_rechecks = (int64_t)h.fp64_rechecks;
+    S.capacity_retries = (int64_t)h.capacity_events;
+    S.precision_retries = (int64_t)h.precision_events;
+    S.launches = (int)(launches() - l0);
+    if (timer.on) {
+        S.ms_grid = timer.total(StageTimer::GRID);
+        S.ms_knn = timer.total(StageTimer::KNN);
+        S.ms_clip = timer.total(StageTimer::CLIP);
+        S.ms_emit = timer.total(StageTimer::EMIT);
+    }
+    if (stats) *stats = S;
+    if (n_unval > 0) return fail(VT_ERR_UNVALIDATED, "%lld cells could not be validated", (long long)n_unval);
+    return VT_OK;
+}
+
+int vt_read_status(void* ws, size_t ws_bytes, void* stream)
+{
+    if (!ws || ws_bytes < sizeof(DevStatus)) return fail(VT_ERR_WORKSPACE, "workspace too small");
+    Ctx c;
+    c.base = (uint8_t*)ws;
+    c.s = (cudaStream_t)stream;
+    c.st = (DevStatus*)ws;  // the status block is the first region of every layout
+    DevStatus h;
+    int r = read_status(c, h);
+    if (r) return r;
+    return status_errors(h);
+}
+
+const char* vt_last_error(void) { return g_err.c_str(); }
+
+int64_t vt_launch_count(void) { return launches(); }
+
+const char* vt_version(void) { return "vt 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// vt_internal.cuh -- shared declarations of the CUDA path (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vt.h"
+
+namespace vt {
+
+// ---------------------------------------------------------------------------
+// grid description (host-computed, passed by value to kernels)
+// ---------------------------------------------------------------------------
+struct GridDesc {
+    int G;            // cells per axis
+    float lo[3];      // box
+    float hi[3];
+    float scale[3];   // float32(G) / (hi - lo), rounded once on the host
+    double cw[3];     // cell width (hi - lo) / G in double (stop-rule geometry only)
+    double margin;    // safety margin of the shell-walk stop rule (coordinates)
+};
+
+GridDesc make_grid(const vt_params* p, int G);
+
+// grid cell of a point: every operation a separately rounded float32 op
+__device__ __forceinline__ int cell_coord(float x, float lo, float scale, int G)
+{
+    float t = __fmul_rn(__fsub_rn(x, lo), scale);
+    int c = (int)floorf(t);
+    c = c < 0 ? 0 : c;
+    return c > G - 1 ? G - 1 : c;
+}
+
+__device__ __forceinline__ int cell_id(int ix, int iy, int iz, int G) { return (ix * G + iy) * G + iz; }
+
+// ---------------------------------------------------------------------------
+// device status block at the start of every workspace
+// ---------------------------------------------------------------------------
+struct DevStatus {
+    int32_t bad_point;        // 1 + smallest offending input index, 0 if none
+    int32_t duplicate;        // nonzero once a neighbour at distance 0 was seen
+    int32_t n_fail_next;      // cells that need the next k (failed validation)
+    int32_t n_fail_robust;    // cells that need the robust variant (capacity / precision)
+    int32_t n_big_cells;      // grid cells too large for the per-thread fix-up sort
+    int32_t record_overflow;  // cells whose final polyhedron does not fit an output record
+    int32_t pad[2];
+    unsigned long long fp64_rechecks;
+    unsigned long long capacity_events;
+    unsigned long long precision_events;
+    long long totals[4];      // nbr, vtx, face, face_vtx totals written by the emit scan
+    long long pad2[5];
+};
+static_assert(sizeof(DevStatus) % 64 == 0, "status block must stay 64-byte sized");
+
+// ---------------------------------------------------------------------------
+// per-cell output record (fixed stride, in the workspace)
+// ---------------------------------------------------------------------------
+constexpr int REC_FACES = 64;      // faces of a final cell
+constexpr int REC_VERTS = 128;     // vertices of a final cell
+struct RecHeader {
+    int32_t nnbr;                  // neighbours kept (area > threshold)
+    int32_t nface;                 // faces written (geometry)
+    int32_t nvtx;                  // vertices written (geometry)
+    int32_t nfv;                   // face-vertex entries (geometry)
+};
+// layout: RecHeader | int32 nbr[REC_FACES] | (geometry:) int32 face_nbr[REC_FACES] |
+//         uint8 face_deg[REC_FACES] | uint8 face_vtx[3*REC_VERTS] | double vtx[REC_VERTS*3]
+constexpr size_t REC_NBR_OFF = sizeof(RecHeader);
+constexpr size_t REC_FNBR_OFF = REC_NBR_OFF + 4 * REC_FACES;
+constexpr size_t REC_FDEG_OFF = REC_FNBR_OFF + 4 * REC_FACES;
+constexpr size_t REC_FVTX_OFF = REC_FDEG_OFF + REC_FACES;
+constexpr size_t REC_VTX_OFF = (REC_FVTX_OFF + 3 * REC_VERTS + 15) / 16 * 16;
+constexpr size_t REC_STRIDE_NBR = REC_FNBR_OFF;                              // 272 B
+constexpr size_t REC_STRIDE_GEOM = REC_VTX_OFF + 8 * 3 * REC_VERTS;          // ~4 KB
+
+// fail reasons stored per cell
+enum : int8_t { CELL_DONE = 0, CELL_NEED_K = 1, CELL_NEED_ROBUST = 2, CELL_UNVALIDATED = 3 };
+
+// ---------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------
+struct Layout {
+    int G;
+    int64_t n, g3;
+    int64_t knn_cap;            // entries of the neighbour-list buffer
+    size_t rec_stride;
+    size_t status, cid, ticket, counts, cell_off, big, scan_tmp, sorted, perm;
+    size_t list_a, list_b, list_r, knn_nbr, knn_d2, rec, cnt, off64;
+    size_t total;
+};
+Layout make_layout(const vt_params* p, int64_t n);
+
+// ---------------------------------------------------------------------------
+// launch helpers shared by the translation units
+// ---------------------------------------------------------------------------
+void count_launch(int n = 1);
+int64_t launches();
+
+// exclusive scans (grid-wide, multi-kernel); tmp needs scan_tmp_bytes(n)
+size_t scan_tmp_bytes(int64_t n);
+void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, void* tmp, cudaStream_t s);
+void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s);
+
+// stage launchers (return cudaError_t of the launch)
+cudaError_t launch_grid_build(const float* pts, int64_t n, const GridDesc& g, float4* sorted, int32_t* perm,
+                              int32_t* cell_off, int32_t* cid, int32_t* ticket, int32_t* counts, int32_t* big,
+                              void* scan_tmp, DevStatus* st, cudaStream_t s);
+
+cudaError_t launch_knn(const float4* sorted, const int32_t* cell_off, const GridDesc& g, int64_t n,
+                       const int32_t* queries, int64_t nq, int k, int precision, int32_t* nbr, void* d2,
+                       DevStatus* st, cudaStream_t s);
+
+struct ClipArgs {
+    const float4* sorted;
+    const int32_t* cell_off;
+    GridDesc g;
+    int64_t n;
+    const int32_t* queries;   // sorted indices (NULL = 0..nq-1)
+    int64_t nq;
+    const int32_t* nbr;       // [nq*k] (k > 0)
+    const void* d2;           // [nq*k] float or double
+    int k;                    // 0 = exhaustive mode
+    int emit;
+    int index_space;
+    double* vol;
+    double* cen;
+    double* m2;
+    uint8_t* rec;             // records base (NULL = none)
+    size_t rec_stride;
+    int32_t* fail_next;       // appended: cells needing a larger k
+    int32_t* fail_robust;     // appended: cells needing the robust variant (or, from
+                              // the robust variant itself, cells left unvalidated)
+    int32_t* ctr_next;        // device counters of the two lists
+    int32_t* ctr_robust;
+    DevStatus* st;
+};
+// variant: 0 = FP32 regular, 1 = FP64 regular, 2 = FP64 robust (bigger capacity)
+cudaError_t launch_clip(const ClipArgs& a, int variant, int threads_per_cell, cudaStream_t s);
+
+struct EmitArgs {
+    int64_t n;
+    int emit;
+    const uint8_t* rec;
+    size_t rec_stride;
+    int32_t* cnt;             // [4*n] scratch counts
+    int64_t* off64;           // [4*(n+1)] scratch offsets
+    void* scan_tmp;
+    DevStatus* st;
+};
+cudaError_t launch_emit_count(const EmitArgs& a, cudaStream_t s);  // counts + scans + totals
+cudaError_t launch_emit_write(const EmitArgs& a, const vt_cells_out& out, cudaStream_t s);
+
+}  // namespace vt

@@ -1,0 +1,85 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/vt.h declares; host-only entry points behave (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2412_04514_gb300 import _lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "vt.h")).read()
+    return re.findall(r"VT_API\s+[\w\s\*]+?\b(vt_\w+)\s*\(", txt)
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for want in ("vt_grid_build", "vt_knn", "vt_clip_cells", "vt_tessellate"):
+        assert want in names
+    assert sorted(names) == sorted(L.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = L.load()
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_struct_sizes_match_the_header():
+    # vt_params: 8 ints/floats + 6 floats; vt_cells_out: pointers and int64s
+    assert ctypes.sizeof(L.VtParams) == 4 * 8 + 4 * 6 + 4
+    assert ctypes.sizeof(L.VtCellsOut) == 8 * 20
+
+
+def test_host_only_calls():
+    lib = L.load()
+    p = L.VtParams()
+    lib.vt_params_default(ctypes.byref(p))
+    assert (p.k0, p.k_max, p.precision) == (16, 256, L.VT_FP32_RECHECK)
+    assert lib.vt_grid_resolution(ctypes.byref(p), 1 << 20) == 81
+    assert lib.vt_grid_resolution(ctypes.byref(p), 1 << 23) == 162
+    b = ctypes.c_size_t()
+    assert lib.vt_workspace_size(ctypes.byref(p), 4096, ctypes.byref(b)) == L.VT_OK
+    assert b.value > 4096 * 16
+    assert lib.vt_version().decode().startswith("vt ")
+
+
+@pytest.mark.parametrize("field,value", [("k0", 0), ("k_max", 512), ("threads_per_cell", 12), ("precision", 7)])
+def test_bad_params_are_rejected_on_the_host(field, value):
+    lib = L.load()
+    p = L.VtParams()
+    lib.vt_params_default(ctypes.byref(p))
+    setattr(p, field, value)
+    b = ctypes.c_size_t()
+    assert lib.vt_workspace_size(ctypes.byref(p), 10, ctypes.byref(b)) == L.VT_ERR_INVALID_ARG
+    assert lib.vt_last_error().decode()
+
+
+def test_bad_box_and_small_workspace_are_rejected_before_any_cuda_call():
+    lib = L.load()
+    p = L.VtParams()
+    lib.vt_params_default(ctypes.byref(p))
+    p.box_hi[1] = p.box_lo[1]
+    b = ctypes.c_size_t()
+    assert lib.vt_workspace_size(ctypes.byref(p), 10, ctypes.byref(b)) == L.VT_ERR_INVALID_ARG
+    lib.vt_params_default(ctypes.byref(p))
+    o = L.VtCellsOut()
+    st = L.VtStats()
+    code = lib.vt_tessellate(None, 0, ctypes.byref(p), ctypes.byref(o), ctypes.byref(st), None, 0, None)
+    assert code == L.VT_ERR_WORKSPACE
+
+
+def test_grid_resolution_agrees_with_the_oracle_reading():
+    import oracle
+
+    lib = L.load()
+    p = L.VtParams()
+    lib.vt_params_default(ctypes.byref(p))
+    for n in (1, 2, 16, 4096, 1 << 20, 3_000_000):
+        for rho in (1.0, 2.0, 3.0):
+            p.grid_density = rho
+            assert lib.vt_grid_resolution(ctypes.byref(p), n) == oracle.grid_resolution(n, rho)
