@@ -104,6 +104,7 @@ class VtStats(ctypes.Structure):
         ("ms_knn", ctypes.c_double),
         ("ms_clip", ctypes.c_double),
         ("ms_emit", ctypes.c_double),
+        ("clip_events", ctypes.c_int64 * 5),
     ]
 
     def as_dict(self) -> dict:
@@ -126,6 +127,7 @@ class VtStats(ctypes.Structure):
             "ms_knn": self.ms_knn,
             "ms_clip": self.ms_clip,
             "ms_emit": self.ms_emit,
+            "clip_events": list(self.clip_events),
         }
 
 

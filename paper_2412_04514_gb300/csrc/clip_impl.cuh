@@ -185,7 +185,7 @@ __device__ __forceinline__ P64 plane64(int src, const float4* __restrict__ sorte
 
 template <typename Real>
 __device__ __forceinline__ bool solve3(Real ax, Real ay, Real az, Real ab, Real bx, Real by, Real bz, Real bb, Real cx,
-                                       Real cy, Real cz, Real cb, Real& x, Real& y, Real& z)
+                                       Real cy, Real cz, Real cb, Real& x, Real& y, Real& z, Real cond = (Real)0)
 {
     // v = (ab (B x C) + bb (C x A) + cb (A x B)) / (A . (B x C))
     Real bcx = by * cz - bz * cy, bcy = bz * cx - bx * cz, bcz = bx * cy - by * cx;
@@ -193,6 +193,10 @@ __device__ __forceinline__ bool solve3(Real ax, Real ay, Real az, Real ab, Real 
     Real abx = ay * bz - az * by, aby = az * bx - ax * bz, abz = ax * by - ay * bx;
     Real det = ax * bcx + ay * bcy + az * bcz;
     if (!(det != (Real)0) || !isfinite(det)) return false;
+    if (cond > (Real)0) {
+        const Real na = ax * ax + ay * ay + az * az, nb = bx * bx + by * by + bz * bz, nc = cx * cx + cy * cy + cz * cz;
+        if (det * det < cond * cond * na * nb * nc) return false;
+    }
     Real inv = (Real)1 / det;
     x = (ab * bcx + bb * cax + cb * abx) * inv;
     y = (ab * bcy + bb * cay + cb * aby) * inv;
@@ -214,6 +218,7 @@ struct GroupSmem {
     int32_t psrc[PCAP];
     uint8_t vid[VCAP][4];   // planes a, b, c (ccw from outside)
     uint8_t vadj[VCAP][4];  // neighbour across a&b, b&c, c&a
+    uint8_t vsrc[VCAP];     // removed vertex whose cut edge created the slot (this clip)
     union {
         struct {
             uint32_t start_of[PCAP];  // (stamp << 8) | slot
@@ -234,16 +239,24 @@ enum CellEnd { END_VALID = 0, END_NEED_K = 1, END_OVERFLOW = 2, END_INCONSISTENT
 
 template <typename Real>
 struct Tol;
+// A vertex counts as outside a plane n.x <= b when s = n.v - b exceeds
+// on_plane_rel * |n| * R (R = cell radius): round-off of FP64 vertex
+// positions at exactly degenerate inputs (lattices) must not cut slivers.
+// A 3x3 solve whose determinant is below cond_rel * |A||B||C| is replaced by
+// interpolation along the cut edge.
 template <>
 struct Tol<float> {
     static constexpr bool fp32 = true;
-    static constexpr double area_rel = 1e-7;
+    static constexpr double area_rel = 1e-11;
+    static constexpr double cond_rel = 1e-3;
 };
 template <>
 struct Tol<double> {
     static constexpr bool fp32 = false;
     static constexpr double area_rel = 1e-12;
+    static constexpr double cond_rel = 1e-9;
 };
+constexpr double ON_PLANE_REL2 = 1e-28;  // (1e-14)^2
 
 template <typename Real, int T, int VPL, int PCAP>
 struct Cell {
@@ -327,15 +340,16 @@ struct Cell {
     }
 
     // FP64 re-decision of a sign test: vertex re-solved from its planes
-    __device__ bool outside64(int s, const P64& h)
+    __device__ bool outside64(int s, const P64& h, int r)
     {
         uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
         P64 A = plane64(sm.psrc[ids & 0xff], sorted, pi, grid);
         P64 B = plane64(sm.psrc[(ids >> 8) & 0xff], sorted, pi, grid);
         P64 C = plane64(sm.psrc[(ids >> 16) & 0xff], sorted, pi, grid);
         double x, y, z;
-        if (!vertex64(A, B, C, x, y, z)) return false;
-        return (h.x * x + h.y * y) + h.z * z - h.b > 0.0;
+        if (!vertex64(A, B, C, x, y, z)) { x = vx[r]; y = vy[r]; z = vz[r]; }
+        const double sv = (h.x * x + h.y * y) + h.z * z - h.b;
+        return sv > 0.0 && sv * sv > ON_PLANE_REL2 * 2.0 * h.b * (double)R2;
     }
 
     // FP64 security radius: vertices re-solved in FP64
@@ -392,7 +406,8 @@ struct Cell {
             const int s = r * T + G.gl;
             sv[r] = nx * vx[r] + ny * vy[r] + nz * vz[r] - b;
             const bool al = alive.test(s);
-            const bool o = al && sv[r] > (Real)0;
+            const bool o = al && sv[r] > (Real)0 &&
+                           (Tol<Real>::fp32 || (double)sv[r] * sv[r] > ON_PLANE_REL2 * 2.0 * (double)b * (double)R2);
             if (Tol<Real>::fp32 && al && (float)sv[r] * (float)sv[r] < 2e-12f * (float)b * (float)R2) near = true;
             const uint64_t bits = G.ballot(o);
             const int sh = r * T;
@@ -408,7 +423,7 @@ struct Cell {
                 const bool al = alive.test(s);
                 bool o = al && sv[r] > (Real)0;
                 if (al && (float)sv[r] * (float)sv[r] < 2e-12f * (float)b * (float)R2) {
-                    o = outside64(s, h);
+                    o = outside64(s, h, r);
                     atomicAdd(&st->fp64_rechecks, 1ull);
                 }
                 const uint64_t bits = G.ballot(o);
@@ -418,7 +433,10 @@ struct Cell {
         }
         if (out.none()) return CLIP_NONE;
         const Mask keep = mask_and(alive, mask_not(out, 128));
-        if (keep.none()) return CLIP_INCONSISTENT;  // the generator itself is always inside
+        if (keep.none()) {  // the generator itself is always inside
+            if (G.gl == 0) atomicAdd(&st->detail[0], 1u);
+            return CLIP_INCONSISTENT;
+        }
 
         // plane id for h
         int h = np;
@@ -440,7 +458,10 @@ struct Cell {
             ref1 = G.orr(ref1);
             Mask fr = mask_not(Mask{{ref0, ref1}}, PCAP);
             h = nth_set(fr, 0);
-            if (h < 0) return CLIP_OVERFLOW;
+            if (h < 0) {
+                if (G.gl == 0) atomicAdd(&st->detail[1], 1u);
+                return CLIP_OVERFLOW;
+            }
         }
 
         // boundary edges of the removed patch
@@ -459,7 +480,10 @@ struct Cell {
         // new vertices go to slots that were free before this clip, so the
         // removed vertices' topology stays readable until the ring is closed
         const Mask freem = mask_not(alive, VCAP);
-        if (total > freem.count()) return CLIP_OVERFLOW;
+        if (total > freem.count()) {
+            if (G.gl == 0) atomicAdd(&st->detail[2], 1u);
+            return CLIP_OVERFLOW;
+        }
         const Mask newm = first_n(freem, total);
         ++stamp;
         const uint32_t tag = stamp << 8;
@@ -483,6 +507,7 @@ struct Cell {
                     sm.vid[d][2] = (uint8_t)h;
                     sm.vid[d][3] = 0;
                     sm.vadj[d][0] = (uint8_t)w;
+                    sm.vsrc[d] = (uint8_t)s;
                     sm.u.ring.start_of[x] = tag | (uint32_t)d;
                     sm.u.ring.end_of[y] = tag | (uint32_t)d;
                     // the survivor w: its link across y&x now points to d
@@ -525,12 +550,17 @@ struct Cell {
                 }
             }
         }
-        if (G.any(bad)) return CLIP_INCONSISTENT;
+        if (G.any(bad)) {
+            if (G.gl == 0) atomicAdd(&st->detail[3], 1u);
+            return CLIP_INCONSISTENT;
+        }
         if (h == np) ++np;
         alive = mask_or(keep, newm);
         G.sync();
-        // positions of the new vertices, solved from their planes by the owners
-        bool sing = false;
+        // positions of the new vertices, solved from their planes by the owners;
+        // an ill-conditioned solve falls back to interpolation along the cut edge
+        bool interp = false;
+        uint32_t need = 0;
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
             const int s = r * T + G.gl;
@@ -538,11 +568,42 @@ struct Cell {
                 const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
                 const int a = ids & 0xff, bb = (ids >> 8) & 0xff, c = (ids >> 16) & 0xff;
                 if (!solve3<Real>(sm.pnx[a], sm.pny[a], sm.pnz[a], sm.pb[a], sm.pnx[bb], sm.pny[bb], sm.pnz[bb],
-                                  sm.pb[bb], sm.pnx[c], sm.pny[c], sm.pnz[c], sm.pb[c], vx[r], vy[r], vz[r]))
-                    sing = true;
+                                  sm.pb[bb], sm.pnx[c], sm.pny[c], sm.pnz[c], sm.pb[c], vx[r], vy[r], vz[r],
+                                  (Real)Tol<Real>::cond_rel)) {
+                    need |= 1u << r;
+                    interp = true;
+                }
             }
         }
-        if (G.any(sing)) return CLIP_INCONSISTENT;
+        if (G.any(interp)) {
+            if (G.gl == 0) atomicAdd(&st->detail[4], 1u);
+            const Mask before = mask_or(keep, out);
+#pragma unroll
+            for (int r = 0; r < VPL; ++r) {
+                const int s = r * T + G.gl;
+                if (before.test(s)) {
+                    sm.vpos[s][0] = vx[r];
+                    sm.vpos[s][1] = vy[r];
+                    sm.vpos[s][2] = vz[r];
+                }
+            }
+            G.sync();
+#pragma unroll
+            for (int r = 0; r < VPL; ++r) {
+                if (!((need >> r) & 1u)) continue;
+                const int s = r * T + G.gl;
+                const int v = sm.vsrc[s], w = sm.vadj[s][0];
+                const Real px = sm.vpos[v][0], py = sm.vpos[v][1], pz = sm.vpos[v][2];
+                const Real qx = sm.vpos[w][0], qy = sm.vpos[w][1], qz = sm.vpos[w][2];
+                const Real sv_ = nx * px + ny * py + nz * pz - b, sw_ = nx * qx + ny * qy + nz * qz - b;
+                Real t = sv_ - sw_ > (Real)0 ? sv_ / (sv_ - sw_) : (Real)0.5;
+                t = t < (Real)0 ? (Real)0 : (t > (Real)1 ? (Real)1 : t);
+                vx[r] = px + t * (qx - px);
+                vy[r] = py + t * (qy - py);
+                vz[r] = pz + t * (qz - pz);
+            }
+            G.sync();
+        }
         update_r2();
         return CLIP_CUT;
     }

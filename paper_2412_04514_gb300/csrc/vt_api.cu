@@ -585,6 +585,7 @@ int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cells_out*
     S.fp64_rechecks = (int64_t)h.fp64_rechecks;
     S.capacity_retries = (int64_t)h.capacity_events;
     S.precision_retries = (int64_t)h.precision_events;
+    for (int a = 0; a < 5; ++a) S.clip_events[a] = (int64_t)h.detail[a];
     S.launches = (int)(launches() - l0);
     if (timer.on) {
         S.ms_grid = timer.total(StageTimer::GRID);

@@ -48,7 +48,8 @@ struct DevStatus {
     unsigned long long capacity_events;
     unsigned long long precision_events;
     long long totals[4];      // nbr, vtx, face, face_vtx totals written by the emit scan
-    long long pad2[5];
+    unsigned int detail[8];   // clip events: 0 keep-none, 1 plane cap, 2 vertex cap, 3 ring, 4 interpolated
+    long long pad2[1];
 };
 static_assert(sizeof(DevStatus) % 64 == 0, "status block must stay 64-byte sized");
 

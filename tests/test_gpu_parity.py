@@ -4,7 +4,8 @@ Tolerances (from the FP64 form's rounding and the stated FP32 target):
   * grid sort, FP64 kNN lists, FP64 neighbour sets: bit-exact;
   * FP64 volumes / centroids / second moments: 1e-12 relative;
   * FP32+FP64-recheck form: 1e-5 relative on volumes and centroids;
-    neighbour sets equal except faces the oracle measures below 1e-5 V^(2/3).
+    neighbour sets equal except faces the oracle measures below 1e-6 V^(2/3)
+    (a face that small is below float32 resolution of the cell).
 """
 import numpy as np
 import pytest
@@ -46,7 +47,7 @@ def check_fp64(cells, want, n_sample=None):
     assert np.array_equal(np_(cells.nbr), want["nbr"])
 
 
-def check_fp32(vol, cen, nbr_lists, want, cells_idx=None, max_bad_frac=2e-3):
+def check_fp32(vol, cen, nbr_lists, want, cells_idx=None, max_bad_frac=1e-3):
     np.testing.assert_allclose(vol, want["vol"], rtol=1e-5, atol=0)
     rel_c = np.linalg.norm(cen - want["cen"], axis=1) / np.linalg.norm(want["cen"], axis=1)
     assert rel_c.max() < 1e-5, rel_c.max()
@@ -57,8 +58,8 @@ def check_fp32(vol, cen, nbr_lists, want, cells_idx=None, max_bad_frac=2e-3):
             bad += 1
             i = a
             V = want["vol"][a]
-            for j in set(w.tolist()) - set(g.tolist()):
-                assert oracle_face_area(want, i, j) < 1e-5 * V ** (2 / 3)
+            for j in set(w.tolist()) ^ set(g.tolist()):
+                assert oracle_face_area(want, i, j) < 1e-6 * V ** (2 / 3), (i, j)
     assert bad <= max(2, max_bad_frac * len(wl)), bad
 
 
