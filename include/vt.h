@@ -173,6 +173,27 @@ VT_API int vt_grid_build(const float* pts, int64_t n, const vt_params* p, int G,
                   float* sorted, int32_t* perm, int32_t* cell_off,
                   void* ws, size_t ws_bytes, void* stream);
 
+/* The grid sort of vt_grid_build for callers that cannot allocate device
+ * memory: a host program whose device memory is handed out up front by an
+ * arena or pool it does not control, code running where a cudaMalloc would
+ * synchronise the device or break a capture in progress, or an embedding
+ * that must keep its device footprint fixed after start-up. Its scratch is a
+ * device array inside this library, 17 MiB on every GPU that loads the
+ * library, held until the process exits; inputs and outputs are still the
+ * caller's device buffers (same layout as vt_grid_build; no workspace).
+ * Limits: n <= 1,048,576 points and G^3 <= 1,048,576 grid cells; larger
+ * requests return VT_ERR_INVALID_ARG without launching anything.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and keeps it; make that first call before any stream
+ * capture begins. Every call reuses the same array and clears what must start
+ * at zero; calls whose work overlaps on a GPU (other streams, other host
+ * threads) race on it, so serialise them. Blocking: returns after the sort has
+ * finished on `stream`; a point that is not finite or outside the box gives
+ * VT_ERR_INVALID_ARG. The paper has no counterpart: this is a deployment
+ * variant of the grid-sort stage. */
+VT_API int vt_grid_build_static(const float* pts, int64_t n, const vt_params* p, int G,
+                                float* sorted, int32_t* perm, int32_t* cell_off, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* stage 2: k nearest neighbours (paper, Summary)                      */
 /* ------------------------------------------------------------------ */

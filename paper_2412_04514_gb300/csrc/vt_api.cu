@@ -63,6 +63,8 @@ int cuda_fail(cudaError_t e, const char* what)
 
 }  // namespace
 
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 

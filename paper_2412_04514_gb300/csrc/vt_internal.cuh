@@ -94,6 +94,7 @@ Layout make_layout(const vt_params* p, int64_t n);
 // ---------------------------------------------------------------------------
 // launch helpers shared by the translation units
 // ---------------------------------------------------------------------------
+int set_error(int code, const char* msg);  // records msg for vt_last_error, returns code
 void count_launch(int n = 1);
 int64_t launches();
 
