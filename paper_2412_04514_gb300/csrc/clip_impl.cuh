@@ -8,31 +8,36 @@
 //
 // Representation of the convex polyhedron (local frame of the generator, so
 // the generator is the origin):
-//  * planes  n.x <= b in shared memory (SoA), with the source of each plane
+//  * planes n.x <= b in shared memory (SoA), with the source of each plane
 //    (sorted index of the neighbour, or -1..-6 for the walls x-,x+,y-,y+,z-,z+);
 //  * vertices in VCAP slots. Slot s lives in lane s % T, register row s / T
 //    (positions in registers, so the per-plane sign pass touches no memory).
 //    In shared memory each slot holds the three planes meeting at the vertex,
-//    (a, b, c), ordered counter-clockwise seen from outside, and three
-//    adjacency links: the vertex across the polyhedron edge between faces
-//    a&b, b&c and c&a. A 128-bit mask marks the live slots.
+//    (a, b, c), counter-clockwise seen from outside, and three adjacency
+//    links: the vertex across the polyhedron edge between faces a&b, b&c and
+//    c&a. A 128-bit mask marks the live slots (group-uniform).
 //
 // Clipping by a plane h: every lane tests its live vertices; removed vertices
 // form a connected patch. Each edge (x -> y) of a removed vertex whose
 // neighbour w across it survives is a boundary edge and yields one new vertex
 // with planes (x, y, h) on the cut edge; its link across x&y is w, and the new
 // vertices chain around h through start_of[x] / end_of[y] tables (each face
-// x is cut at most once, so x starts exactly one boundary edge). New slots
-// take the lowest free slots; their positions are solved from the three
-// planes by the owning lanes.
+// x is cut at most once, so x starts exactly one boundary edge). New vertices
+// take the lowest slots free before the clip (removed slots are freed after
+// it), and their positions are solved from the three planes by the owners.
 //
-// FP32 form (variant 0): planes, vertices and sign tests in float32. A sign
-// test with |s| < 1e-6 |n| R is re-decided in FP64 from the vertex's three
-// planes rebuilt in FP64 from the input points; the security-radius test is
+// Passes: a cell that needs a longer neighbour list saves its polyhedron
+// (state) and the next pass resumes at the first unprocessed neighbour, so
+// the k-doubling re-queue never repeats a clip; the exhaustive pass resumes
+// from the k_max state and skips generators already in the list.
+//
+// FP32 form: planes, vertices and sign tests in float32. A sign test with
+// |s| < 1e-6 |n| R is re-decided in FP64 from the vertex's three planes
+// rebuilt in FP64 from the input points; the security-radius test is
 // re-decided in FP64 (vertices re-solved in FP64) when it is within 1e-5
 // relative of equality; volumes and moments accumulate per lane in float32 and
-// across lanes in FP64. A topology inconsistency (a face cut twice, a singular
-// vertex) sends the cell to the robust FP64 variant.
+// across lanes in FP64. A topology inconsistency (a face cut twice) sends the
+// cell to the robust FP64 variant.
 #pragma once
 #include <float.h>
 #include <limits.h>
@@ -49,7 +54,6 @@ namespace {
 struct Mask {
     uint64_t w[2];
     __device__ __forceinline__ bool test(int s) const { return (w[s >> 6] >> (s & 63)) & 1ull; }
-    __device__ __forceinline__ void set(int s) { w[s >> 6] |= 1ull << (s & 63); }
     __device__ __forceinline__ bool none() const { return (w[0] | w[1]) == 0; }
     __device__ __forceinline__ int count() const { return __popcll(w[0]) + __popcll(w[1]); }
     // number of set bits strictly below s
@@ -58,6 +62,8 @@ struct Mask {
         if (s < 64) return __popcll(w[0] & ((1ull << s) - 1ull));
         return __popcll(w[0]) + __popcll(w[1] & ((1ull << (s - 64)) - 1ull));
     }
+    // 1 + highest set bit (0 if empty)
+    __device__ __forceinline__ int top() const { return w[1] ? 128 - __clzll(w[1]) : (w[0] ? 64 - __clzll(w[0]) : 0); }
 };
 
 __device__ __forceinline__ Mask mask_and(Mask a, Mask b) { return {{a.w[0] & b.w[0], a.w[1] & b.w[1]}}; }
@@ -99,6 +105,15 @@ __device__ __forceinline__ Mask first_n(Mask m, int n)
     }
     return r;
 }
+// rows of lane gl whose slot (r*T + gl) is set in m
+template <int T, int VPL>
+__device__ __forceinline__ uint32_t lane_rows(Mask m, int gl)
+{
+    uint32_t b = 0;
+#pragma unroll
+    for (int r = 0; r < VPL; ++r) b |= (uint32_t)m.test(r * T + gl) << r;
+    return b;
+}
 
 // ---------------------------------------------------------------------------
 // group (T lanes of one warp) primitives
@@ -129,19 +144,6 @@ struct Group {
     {
 #pragma unroll
         for (int o = T / 2; o >= 1; o >>= 1) { V u = __shfl_xor_sync(mask, v, o, T); v = u > v ? u : v; }
-        return v;
-    }
-    template <typename V>
-    __device__ __forceinline__ V sum(V v) const
-    {
-#pragma unroll
-        for (int o = T / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(mask, v, o, T);
-        return v;
-    }
-    __device__ __forceinline__ uint64_t orr(uint64_t v) const
-    {
-#pragma unroll
-        for (int o = T / 2; o >= 1; o >>= 1) v |= __shfl_xor_sync(mask, v, o, T);
         return v;
     }
     // exclusive prefix sum and total
@@ -237,13 +239,13 @@ struct GroupSmem {
 enum ClipResult { CLIP_NONE = 0, CLIP_CUT = 1, CLIP_OVERFLOW = 2, CLIP_INCONSISTENT = 3 };
 enum CellEnd { END_VALID = 0, END_NEED_K = 1, END_OVERFLOW = 2, END_INCONSISTENT = 3 };
 
-template <typename Real>
-struct Tol;
 // A vertex counts as outside a plane n.x <= b when s = n.v - b exceeds
 // on_plane_rel * |n| * R (R = cell radius): round-off of FP64 vertex
 // positions at exactly degenerate inputs (lattices) must not cut slivers.
 // A 3x3 solve whose determinant is below cond_rel * |A||B||C| is replaced by
 // interpolation along the cut edge.
+template <typename Real>
+struct Tol;
 template <>
 struct Tol<float> {
     static constexpr bool fp32 = true;
@@ -258,68 +260,173 @@ struct Tol<double> {
 };
 constexpr double ON_PLANE_REL2 = 1e-28;  // (1e-14)^2
 
+// ---------------------------------------------------------------------------
+// saved polyhedron of a cell between passes (fixed stride per cell)
+// ---------------------------------------------------------------------------
+struct StateHdr {
+    uint64_t alive[2];
+    int32_t np;
+    int32_t last_orig;   // original index of the last list entry processed
+    double R2;
+    double last_d2;      // its squared distance (the kNN key)
+    int32_t pad[2];
+};
+static_assert(sizeof(StateHdr) == 48, "state header");
+
+template <typename Real, int VCAP, int PCAP>
+struct StateLayout {
+    static constexpr size_t PLANES = 64;                                // Real[4][PCAP]
+    static constexpr size_t PSRC = PLANES + 4 * sizeof(Real) * PCAP;    // int32[PCAP]
+    static constexpr size_t VID = PSRC + 4 * PCAP;                      // uint32[VCAP]
+    static constexpr size_t VADJ = VID + 4 * VCAP;                      // uint32[VCAP]
+    static constexpr size_t POS = (VADJ + 4 * VCAP + 15) / 16 * 16;     // Real[3][VCAP]
+    static constexpr size_t BYTES = (POS + 3 * sizeof(Real) * VCAP + 255) / 256 * 256;
+};
+
+// ---------------------------------------------------------------------------
+// rarely taken paths, kept out of line so the hot loop stays small
+// ---------------------------------------------------------------------------
+
+// FP64 re-decision of a sign test: the vertex re-solved from its planes
+template <typename S>
+__device__ __noinline__ bool outside64(const S& sm, int s, P64 h, const float4* __restrict__ sorted, float4 pi,
+                                       GridDesc g, double fx, double fy, double fz, double R2)
+{
+    const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
+    P64 A = plane64(sm.psrc[ids & 0xff], sorted, pi, g);
+    P64 B = plane64(sm.psrc[(ids >> 8) & 0xff], sorted, pi, g);
+    P64 C = plane64(sm.psrc[(ids >> 16) & 0xff], sorted, pi, g);
+    double x, y, z;
+    if (!vertex64(A, B, C, x, y, z)) { x = fx; y = fy; z = fz; }
+    const double sv = (h.x * x + h.y * y) + h.z * z - h.b;
+    return sv > 0.0 && sv * sv > ON_PLANE_REL2 * 2.0 * h.b * R2;
+}
+
+// FP64 squared distance of slot s's vertex, re-solved from its planes
+template <typename S>
+__device__ __noinline__ double vertex_r2_64(const S& sm, int s, const float4* __restrict__ sorted, float4 pi,
+                                            GridDesc g, double fx, double fy, double fz)
+{
+    const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
+    P64 A = plane64(sm.psrc[ids & 0xff], sorted, pi, g);
+    P64 B = plane64(sm.psrc[(ids >> 8) & 0xff], sorted, pi, g);
+    P64 C = plane64(sm.psrc[(ids >> 16) & 0xff], sorted, pi, g);
+    double x, y, z;
+    if (!vertex64(A, B, C, x, y, z)) { x = fx; y = fy; z = fz; }
+    return (x * x + y * y) + z * z;
+}
+
+// lowest plane id that no live vertex references (or -1)
+template <int T, typename S>
+__device__ __noinline__ int free_plane(const S& sm, Mask keep, int gl, unsigned gmask, int pcap, int vcap)
+{
+    uint64_t ref0 = 0, ref1 = 0;
+    for (int s = gl; s < vcap; s += T) {
+        if (!keep.test(s)) continue;
+        const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int pid = (ids >> (8 * e)) & 0xff;
+            if (pid < 64) ref0 |= 1ull << pid; else ref1 |= 1ull << (pid - 64);
+        }
+    }
+#pragma unroll
+    for (int o = T / 2; o >= 1; o >>= 1) {
+        ref0 |= __shfl_xor_sync(gmask, ref0, o, T);
+        ref1 |= __shfl_xor_sync(gmask, ref1, o, T);
+    }
+    return nth_set(mask_not(Mask{{ref0, ref1}}, pcap), 0);
+}
+
+// position of a new vertex by interpolation along its cut edge (the
+// pre-clip vertex positions are in sm.vpos)
+template <typename Real, typename S>
+__device__ __noinline__ void interp_vertex(const S& sm, int s, Real nx, Real ny, Real nz, Real b, Real* xyz)
+{
+    const int v = sm.vsrc[s], w = sm.vadj[s][0];
+    const Real px = sm.vpos[v][0], py = sm.vpos[v][1], pz = sm.vpos[v][2];
+    const Real qx = sm.vpos[w][0], qy = sm.vpos[w][1], qz = sm.vpos[w][2];
+    const Real sv = nx * px + ny * py + nz * pz - b, sw = nx * qx + ny * qy + nz * qz - b;
+    Real t = sv - sw > (Real)0 ? sv / (sv - sw) : (Real)0.5;
+    t = t < (Real)0 ? (Real)0 : (t > (Real)1 ? (Real)1 : t);
+    xyz[0] = px + t * (qx - px);
+    xyz[1] = py + t * (qy - py);
+    xyz[2] = pz + t * (qz - pz);
+}
+
+// ---------------------------------------------------------------------------
+// one cell: registers (positions, masks) + the group's shared memory
+// ---------------------------------------------------------------------------
 template <typename Real, int T, int VPL, int PCAP>
 struct Cell {
     static constexpr int VCAP = T * VPL;
     using S = GroupSmem<Real, VCAP, PCAP>;
+    using SL = StateLayout<Real, VCAP, PCAP>;
 
-    const Group<T>& G;
-    S& sm;
-    const float4* __restrict__ sorted;
-    const GridDesc& grid;
-    DevStatus* st;
-    float4 pi;
     Real vx[VPL], vy[VPL], vz[VPL];
-    Mask alive;
+    Mask alive;       // group-uniform
     int np;           // planes in use (ids < np)
+    int rows;         // register rows holding live slots
     uint32_t stamp;   // clip counter for the ring tables (keeps counting across cells)
     Real R2;          // max |v|^2 over live vertices
+    float4 pi;
 
-    __device__ Cell(const Group<T>& g_, S& sm_, const float4* s_, const GridDesc& gd, DevStatus* st_)
-        : G(g_), sm(sm_), sorted(s_), grid(gd), st(st_)
+    __device__ __forceinline__ void set_row(int r, Real x, Real y, Real z)
     {
+#pragma unroll
+        for (int rr = 0; rr < VPL; ++rr)
+            if (rr == r) { vx[rr] = x; vy[rr] = y; vz[rr] = z; }
+    }
+    __device__ __forceinline__ void get_row(int r, Real& x, Real& y, Real& z) const
+    {
+        x = vx[0]; y = vy[0]; z = vz[0];
+#pragma unroll
+        for (int rr = 1; rr < VPL; ++rr)
+            if (rr == r) { x = vx[rr]; y = vy[rr]; z = vz[rr]; }
     }
 
-    __device__ __forceinline__ void update_r2()
+    __device__ __forceinline__ void update_rows() { rows = (alive.top() + T - 1) / T; }
+
+    __device__ __forceinline__ void update_r2(const Group<T>& G)
     {
         Real m = 0;
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
-            const int s = r * T + G.gl;
-            Real d = vx[r] * vx[r] + vy[r] * vy[r] + vz[r] * vz[r];
-            if (alive.test(s) && d > m) m = d;
+            if (r < rows) {
+                const Real d = vx[r] * vx[r] + vy[r] * vy[r] + vz[r] * vz[r];
+                if (alive.test(r * T + G.gl) && d > m) m = d;
+            }
         }
         R2 = G.max(m);
     }
 
     // the box [lo, hi) in the frame of pi: walls 0..5, corners in slots 0..7
-    __device__ void init_box()
+    __device__ __forceinline__ void init_box(const Group<T>& G, S& sm, const GridDesc& grid)
     {
         const Real px = (Real)pi.x, py = (Real)pi.y, pz = (Real)pi.z;
-        const Real lo[3] = {(Real)grid.lo[0] - px, (Real)grid.lo[1] - py, (Real)grid.lo[2] - pz};
-        const Real hi[3] = {(Real)grid.hi[0] - px, (Real)grid.hi[1] - py, (Real)grid.hi[2] - pz};
+        const Real lx = (Real)grid.lo[0] - px, ly = (Real)grid.lo[1] - py, lz = (Real)grid.lo[2] - pz;
+        const Real hx = (Real)grid.hi[0] - px, hy = (Real)grid.hi[1] - py, hz = (Real)grid.hi[2] - pz;
         if (G.gl < 6) {
             const int w = G.gl, axis = w >> 1, upper = w & 1;
-            sm.pnx[w] = axis == 0 ? (upper ? (Real)1 : (Real)-1) : (Real)0;
-            sm.pny[w] = axis == 1 ? (upper ? (Real)1 : (Real)-1) : (Real)0;
-            sm.pnz[w] = axis == 2 ? (upper ? (Real)1 : (Real)-1) : (Real)0;
-            sm.pb[w] = upper ? hi[axis] : -lo[axis];
+            const Real one = upper ? (Real)1 : (Real)-1;
+            sm.pnx[w] = axis == 0 ? one : (Real)0;
+            sm.pny[w] = axis == 1 ? one : (Real)0;
+            sm.pnz[w] = axis == 2 ? one : (Real)0;
+            const Real lo_a = axis == 0 ? lx : (axis == 1 ? ly : lz);
+            const Real hi_a = axis == 0 ? hx : (axis == 1 ? hy : hz);
+            sm.pb[w] = upper ? hi_a : -lo_a;
             sm.psrc[w] = -(w + 1);
         }
         if (G.gl < 8) {
+            // corner c = 4 sx + 2 sy + sz; planes (x, y, z) in ccw order, swapped
+            // when an odd number of its walls are lower walls (mirror image)
             const int c = G.gl, sx = (c >> 2) & 1, sy = (c >> 1) & 1, sz = c & 1;
-            int P[3] = {sx, 2 + sy, 4 + sz};
-            const int nlo = (1 - sx) + (1 - sy) + (1 - sz);
-            if (nlo & 1) { int t = P[1]; P[1] = P[2]; P[2] = t; }
-#pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                sm.vid[c][e] = (uint8_t)P[e];
-                // neighbour across P[e] & P[e+1]: flip the axis of the third plane
-                const int axis = P[(e + 2) % 3] >> 1;
-                sm.vadj[c][e] = (uint8_t)(c ^ (4 >> axis));
-            }
-            sm.vid[c][3] = 0;
-            sm.vadj[c][3] = 0;
+            int p0 = sx, p1 = 2 + sy, p2 = 4 + sz;
+            if (((1 - sx) + (1 - sy) + (1 - sz)) & 1) { const int t = p1; p1 = p2; p2 = t; }
+            *reinterpret_cast<uint32_t*>(sm.vid[c]) = (uint32_t)p0 | ((uint32_t)p1 << 8) | ((uint32_t)p2 << 16);
+            // neighbour across (P[e], P[e+1]): flip the axis of the third plane
+            const uint32_t a0 = c ^ (4 >> (p2 >> 1)), a1 = c ^ (4 >> (p0 >> 1)), a2 = c ^ (4 >> (p1 >> 1));
+            *reinterpret_cast<uint32_t*>(sm.vadj[c]) = a0 | (a1 << 8) | (a2 << 16);
         }
         alive.w[0] = 0xffull;
         alive.w[1] = 0;
@@ -327,108 +434,159 @@ struct Cell {
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
             const int s = r * T + G.gl;
-            if (s < 8) {
-                vx[r] = ((s >> 2) & 1) ? hi[0] : lo[0];
-                vy[r] = ((s >> 1) & 1) ? hi[1] : lo[1];
-                vz[r] = (s & 1) ? hi[2] : lo[2];
-            } else {
-                vx[r] = vy[r] = vz[r] = 0;
-            }
+            vx[r] = ((s >> 2) & 1) ? hx : lx;
+            vy[r] = ((s >> 1) & 1) ? hy : ly;
+            vz[r] = (s & 1) ? hz : lz;
         }
+        update_rows();
         G.sync();
-        update_r2();
+        update_r2(G);
     }
 
-    // FP64 re-decision of a sign test: vertex re-solved from its planes
-    __device__ bool outside64(int s, const P64& h, int r)
+    // ---- save / restore between passes ------------------------------------
+    __device__ __forceinline__ void save(const Group<T>& G, const S& sm, uint8_t* st, double last_d2,
+                                         int last_orig) const
     {
-        uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-        P64 A = plane64(sm.psrc[ids & 0xff], sorted, pi, grid);
-        P64 B = plane64(sm.psrc[(ids >> 8) & 0xff], sorted, pi, grid);
-        P64 C = plane64(sm.psrc[(ids >> 16) & 0xff], sorted, pi, grid);
-        double x, y, z;
-        if (!vertex64(A, B, C, x, y, z)) { x = vx[r]; y = vy[r]; z = vz[r]; }
-        const double sv = (h.x * x + h.y * y) + h.z * z - h.b;
-        return sv > 0.0 && sv * sv > ON_PLANE_REL2 * 2.0 * h.b * (double)R2;
-    }
-
-    // FP64 security radius: vertices re-solved in FP64
-    __device__ double r2_64()
-    {
-        double m = 0;
+        Real* pl = reinterpret_cast<Real*>(st + SL::PLANES);
+        int32_t* ps = reinterpret_cast<int32_t*>(st + SL::PSRC);
+        for (int f = G.gl; f < np; f += T) {
+            pl[f] = sm.pnx[f];
+            pl[PCAP + f] = sm.pny[f];
+            pl[2 * PCAP + f] = sm.pnz[f];
+            pl[3 * PCAP + f] = sm.pb[f];
+            ps[f] = sm.psrc[f];
+        }
+        uint32_t* vi = reinterpret_cast<uint32_t*>(st + SL::VID);
+        uint32_t* va = reinterpret_cast<uint32_t*>(st + SL::VADJ);
+        Real* pos = reinterpret_cast<Real*>(st + SL::POS);
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
             const int s = r * T + G.gl;
-            if (alive.test(s)) {
-                uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-                P64 A = plane64(sm.psrc[ids & 0xff], sorted, pi, grid);
-                P64 B = plane64(sm.psrc[(ids >> 8) & 0xff], sorted, pi, grid);
-                P64 C = plane64(sm.psrc[(ids >> 16) & 0xff], sorted, pi, grid);
-                double x, y, z;
-                if (vertex64(A, B, C, x, y, z)) {
-                    double d = (x * x + y * y) + z * z;
-                    m = d > m ? d : m;
-                } else {
-                    double d = (double)vx[r] * vx[r] + (double)vy[r] * vy[r] + (double)vz[r] * vz[r];
-                    m = d > m ? d : m;
-                }
+            if (r < rows && alive.test(s)) {
+                vi[s] = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
+                va[s] = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
+                pos[s] = vx[r];
+                pos[VCAP + s] = vy[r];
+                pos[2 * VCAP + s] = vz[r];
             }
         }
-        return G.max(m);
+        if (G.gl == 0) {
+            StateHdr* h = reinterpret_cast<StateHdr*>(st);
+            h->alive[0] = alive.w[0];
+            h->alive[1] = alive.w[1];
+            h->np = np;
+            h->last_orig = last_orig;
+            h->R2 = (double)R2;
+            h->last_d2 = last_d2;
+        }
+    }
+
+    __device__ __forceinline__ void restore(const Group<T>& G, S& sm, const uint8_t* st, double& last_d2,
+                                            int& last_orig)
+    {
+        const StateHdr* h = reinterpret_cast<const StateHdr*>(st);
+        alive.w[0] = h->alive[0];
+        alive.w[1] = h->alive[1];
+        np = h->np;
+        R2 = (Real)h->R2;
+        last_d2 = h->last_d2;
+        last_orig = h->last_orig;
+        const Real* pl = reinterpret_cast<const Real*>(st + SL::PLANES);
+        const int32_t* ps = reinterpret_cast<const int32_t*>(st + SL::PSRC);
+        for (int f = G.gl; f < np; f += T) {
+            sm.pnx[f] = pl[f];
+            sm.pny[f] = pl[PCAP + f];
+            sm.pnz[f] = pl[2 * PCAP + f];
+            sm.pb[f] = pl[3 * PCAP + f];
+            sm.psrc[f] = ps[f];
+        }
+        update_rows();
+        const uint32_t* vi = reinterpret_cast<const uint32_t*>(st + SL::VID);
+        const uint32_t* va = reinterpret_cast<const uint32_t*>(st + SL::VADJ);
+        const Real* pos = reinterpret_cast<const Real*>(st + SL::POS);
+#pragma unroll
+        for (int r = 0; r < VPL; ++r) {
+            const int s = r * T + G.gl;
+            if (r < rows && alive.test(s)) {
+                *reinterpret_cast<uint32_t*>(sm.vid[s]) = vi[s];
+                *reinterpret_cast<uint32_t*>(sm.vadj[s]) = va[s];
+                vx[r] = pos[s];
+                vy[r] = pos[VCAP + s];
+                vz[r] = pos[2 * VCAP + s];
+            }
+        }
+        G.sync();
     }
 
     // true when no generator at squared distance >= dj can cut the cell
-    __device__ bool radius_ok(Real dj, int jsrc)
+    __device__ __forceinline__ bool radius_ok(const Group<T>& G, const S& sm, Real dj, int jsrc,
+                                              const float4* __restrict__ sorted, const GridDesc& grid, DevStatus* st)
     {
         if (!Tol<Real>::fp32) return (Real)4 * R2 <= dj;
         const float lhs = 4.0f * (float)R2, rhs = (float)dj;
         if (lhs <= rhs * (1.0f - 1e-5f)) return true;
         if (lhs > rhs * (1.0f + 1e-5f)) return false;
+        // within 1e-5 of equality: decide in FP64, every vertex re-solved in FP64
         if (G.gl == 0) atomicAdd(&st->fp64_rechecks, 1ull);
-        double d64 = 1e300;
-        if (jsrc >= 0) {
-            P64 h = plane64(jsrc, sorted, pi, grid);
-            d64 = 4.0 * h.b * 0.5;  // |n|^2 = 2b
-        } else {
-            d64 = (double)dj;
+        const double d64 = jsrc >= 0 ? 2.0 * plane64(jsrc, sorted, pi, grid).b : (double)dj;
+        double m = 0;
+        for (uint32_t rm = lane_rows<T, VPL>(alive, G.gl); rm; rm &= rm - 1) {
+            const int r = __ffs(rm) - 1;
+            Real fx, fy, fz;
+            get_row(r, fx, fy, fz);
+            const double d = vertex_r2_64(sm, r * T + G.gl, sorted, pi, grid, (double)fx, (double)fy, (double)fz);
+            m = d > m ? d : m;
         }
-        return 4.0 * r2_64() <= d64;
+        return 4.0 * G.max(m) <= d64;
     }
 
     // clip by n.x <= b (plane source src)
-    __device__ int clip(Real nx, Real ny, Real nz, Real b, int src)
+    __device__ __forceinline__ int clip(const Group<T>& G, S& sm, Real nx, Real ny, Real nz, Real b, int src,
+                                        const float4* __restrict__ sorted, const GridDesc& grid, DevStatus* st)
     {
         Mask out = {{0ull, 0ull}};
-        bool near = false;
-        Real sv[VPL];
+        uint32_t myout = 0, mynear = 0;
+        const double tol2 = Tol<Real>::fp32 ? 0.0 : ON_PLANE_REL2 * 2.0 * (double)b * (double)R2;
+        const float near2 = Tol<Real>::fp32 ? 2e-12f * (float)b * (float)R2 : 0.0f;
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
-            const int s = r * T + G.gl;
-            sv[r] = nx * vx[r] + ny * vy[r] + nz * vz[r] - b;
-            const bool al = alive.test(s);
-            const bool o = al && sv[r] > (Real)0 &&
-                           (Tol<Real>::fp32 || (double)sv[r] * sv[r] > ON_PLANE_REL2 * 2.0 * (double)b * (double)R2);
-            if (Tol<Real>::fp32 && al && (float)sv[r] * (float)sv[r] < 2e-12f * (float)b * (float)R2) near = true;
-            const uint64_t bits = G.ballot(o);
-            const int sh = r * T;
-            out.w[sh >> 6] |= bits << (sh & 63);
-        }
-        if (Tol<Real>::fp32 && G.any(near)) {
-            // re-decide the near-zero tests in FP64
-            P64 h = plane64(src, sorted, pi, grid);
-            out.w[0] = out.w[1] = 0;
-#pragma unroll
-            for (int r = 0; r < VPL; ++r) {
+            if (r < rows) {
                 const int s = r * T + G.gl;
+                const Real sv = nx * vx[r] + ny * vy[r] + nz * vz[r] - b;
                 const bool al = alive.test(s);
-                bool o = al && sv[r] > (Real)0;
-                if (al && (float)sv[r] * (float)sv[r] < 2e-12f * (float)b * (float)R2) {
-                    o = outside64(s, h, r);
-                    atomicAdd(&st->fp64_rechecks, 1ull);
+                bool o;
+                if (Tol<Real>::fp32) {
+                    o = al && sv > (Real)0;
+                    if (al && (float)sv * (float)sv < near2) mynear |= 1u << r;
+                } else {
+                    o = al && sv > (Real)0 && (double)sv * (double)sv > tol2;
                 }
+                myout |= (uint32_t)o << r;
                 const uint64_t bits = G.ballot(o);
                 const int sh = r * T;
                 out.w[sh >> 6] |= bits << (sh & 63);
+            }
+        }
+        if (Tol<Real>::fp32 && G.any(mynear != 0)) {
+            // re-decide the near-zero tests in FP64
+            const P64 h = plane64(src, sorted, pi, grid);
+            for (uint32_t m = mynear; m; m &= m - 1) {
+                const int r = __ffs(m) - 1;
+                Real fx, fy, fz;
+                get_row(r, fx, fy, fz);
+                const bool o = outside64(sm, r * T + G.gl, h, sorted, pi, grid, (double)fx, (double)fy, (double)fz,
+                                         (double)R2);
+                myout = o ? (myout | (1u << r)) : (myout & ~(1u << r));
+                atomicAdd(&st->fp64_rechecks, 1ull);
+            }
+            out.w[0] = out.w[1] = 0;
+#pragma unroll
+            for (int r = 0; r < VPL; ++r) {
+                if (r < rows) {
+                    const uint64_t bits = G.ballot((myout >> r) & 1u);
+                    const int sh = r * T;
+                    out.w[sh >> 6] |= bits << (sh & 63);
+                }
             }
         }
         if (out.none()) return CLIP_NONE;
@@ -437,43 +595,21 @@ struct Cell {
             if (G.gl == 0) atomicAdd(&st->detail[0], 1u);
             return CLIP_INCONSISTENT;
         }
-
         // plane id for h
         int h = np;
         if (np >= PCAP) {
-            uint64_t ref0 = 0, ref1 = 0;
-#pragma unroll
-            for (int r = 0; r < VPL; ++r) {
-                const int s = r * T + G.gl;
-                if (keep.test(s)) {
-                    uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const int pid = (ids >> (8 * e)) & 0xff;
-                        if (pid < 64) ref0 |= 1ull << pid; else ref1 |= 1ull << (pid - 64);
-                    }
-                }
-            }
-            ref0 = G.orr(ref0);
-            ref1 = G.orr(ref1);
-            Mask fr = mask_not(Mask{{ref0, ref1}}, PCAP);
-            h = nth_set(fr, 0);
+            h = free_plane<T>(sm, keep, G.gl, G.mask, PCAP, VCAP);
             if (h < 0) {
                 if (G.gl == 0) atomicAdd(&st->detail[1], 1u);
                 return CLIP_OVERFLOW;
             }
         }
-
         // boundary edges of the removed patch
         int mycnt = 0;
-#pragma unroll
-        for (int r = 0; r < VPL; ++r) {
-            const int s = r * T + G.gl;
-            if (out.test(s)) {
-                uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
-#pragma unroll
-                for (int e = 0; e < 3; ++e) mycnt += out.test((adj >> (8 * e)) & 0xff) ? 0 : 1;
-            }
+        for (uint32_t m = myout; m; m &= m - 1) {
+            const int s = (__ffs(m) - 1) * T + G.gl;
+            const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
+            mycnt += (int)!out.test(adj & 0xff) + (int)!out.test((adj >> 8) & 0xff) + (int)!out.test((adj >> 16) & 0xff);
         }
         int total;
         const int first = G.scan(mycnt, total);
@@ -487,36 +623,27 @@ struct Cell {
         const Mask newm = first_n(freem, total);
         ++stamp;
         const uint32_t tag = stamp << 8;
-
         // new vertices: topology and ring tables
         int idx = first;
-#pragma unroll
-        for (int r = 0; r < VPL; ++r) {
-            const int s = r * T + G.gl;
-            if (out.test(s)) {
-                const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-                const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
-#pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    const int w = (adj >> (8 * e)) & 0xff;
-                    if (out.test(w)) continue;
-                    const int d = nth_set(freem, idx++);
-                    const int x = (ids >> (8 * e)) & 0xff, y = (ids >> (8 * ((e + 1) % 3))) & 0xff;
-                    sm.vid[d][0] = (uint8_t)x;
-                    sm.vid[d][1] = (uint8_t)y;
-                    sm.vid[d][2] = (uint8_t)h;
-                    sm.vid[d][3] = 0;
-                    sm.vadj[d][0] = (uint8_t)w;
-                    sm.vsrc[d] = (uint8_t)s;
-                    sm.u.ring.start_of[x] = tag | (uint32_t)d;
-                    sm.u.ring.end_of[y] = tag | (uint32_t)d;
-                    // the survivor w: its link across y&x now points to d
-                    const uint32_t wid = *reinterpret_cast<const uint32_t*>(sm.vid[w]);
-#pragma unroll
-                    for (int e2 = 0; e2 < 3; ++e2)
-                        if ((int)((wid >> (8 * e2)) & 0xff) == y && (int)((wid >> (8 * ((e2 + 1) % 3))) & 0xff) == x)
-                            sm.vadj[w][e2] = (uint8_t)d;
-                }
+        for (uint32_t m = myout; m; m &= m - 1) {
+            const int s = (__ffs(m) - 1) * T + G.gl;
+            const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
+            const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
+            for (int e = 0; e < 3; ++e) {
+                const int w = (adj >> (8 * e)) & 0xff;
+                if (out.test(w)) continue;
+                const int d = nth_set(freem, idx++);
+                const int x = (ids >> (8 * e)) & 0xff, y = (ids >> (8 * (e == 2 ? 0 : e + 1))) & 0xff;
+                *reinterpret_cast<uint32_t*>(sm.vid[d]) = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)h << 16);
+                sm.vadj[d][0] = (uint8_t)w;
+                sm.vsrc[d] = (uint8_t)s;
+                sm.u.ring.start_of[x] = tag | (uint32_t)d;
+                sm.u.ring.end_of[y] = tag | (uint32_t)d;
+                // the survivor w: its link across y&x now points to d
+                const uint32_t wid = *reinterpret_cast<const uint32_t*>(sm.vid[w]);
+                const int w0 = wid & 0xff, w1 = (wid >> 8) & 0xff;
+                const int e2 = (w0 == y && w1 == x) ? 0 : ((w1 == y) ? 1 : 2);
+                sm.vadj[w][e2] = (uint8_t)d;
             }
         }
         if (G.gl == 0) {
@@ -530,24 +657,20 @@ struct Cell {
         // close the ring around h
         bool bad = false;
         idx = first;
-#pragma unroll
-        for (int r = 0; r < VPL; ++r) {
-            const int s = r * T + G.gl;
-            if (out.test(s)) {
-                const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-                const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
-#pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    const int w = (adj >> (8 * e)) & 0xff;
-                    if (out.test(w)) continue;
-                    const int d = nth_set(freem, idx++);
-                    const int x = (ids >> (8 * e)) & 0xff, y = (ids >> (8 * ((e + 1) % 3))) & 0xff;
-                    const uint32_t so = sm.u.ring.start_of[y], eo = sm.u.ring.end_of[x];
-                    if ((so & ~0xffu) != tag || (eo & ~0xffu) != tag || sm.u.ring.start_of[x] != (tag | (uint32_t)d))
-                        bad = true;
-                    sm.vadj[d][1] = (uint8_t)(so & 0xff);
-                    sm.vadj[d][2] = (uint8_t)(eo & 0xff);
-                }
+        for (uint32_t m = myout; m; m &= m - 1) {
+            const int s = (__ffs(m) - 1) * T + G.gl;
+            const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
+            const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
+            for (int e = 0; e < 3; ++e) {
+                const int w = (adj >> (8 * e)) & 0xff;
+                if (out.test(w)) continue;
+                const int d = nth_set(freem, idx++);
+                const int x = (ids >> (8 * e)) & 0xff, y = (ids >> (8 * (e == 2 ? 0 : e + 1))) & 0xff;
+                const uint32_t so = sm.u.ring.start_of[y], eo = sm.u.ring.end_of[x];
+                if ((so & ~0xffu) != tag || (eo & ~0xffu) != tag || sm.u.ring.start_of[x] != (tag | (uint32_t)d))
+                    bad = true;
+                sm.vadj[d][1] = (uint8_t)(so & 0xff);
+                sm.vadj[d][2] = (uint8_t)(eo & 0xff);
             }
         }
         if (G.any(bad)) {
@@ -555,60 +678,52 @@ struct Cell {
             return CLIP_INCONSISTENT;
         }
         if (h == np) ++np;
+        const Mask before = alive;
+        const int rows_before = rows;
         alive = mask_or(keep, newm);
+        update_rows();
         G.sync();
         // positions of the new vertices, solved from their planes by the owners;
         // an ill-conditioned solve falls back to interpolation along the cut edge
-        bool interp = false;
         uint32_t need = 0;
-#pragma unroll
-        for (int r = 0; r < VPL; ++r) {
+        for (uint32_t m = lane_rows<T, VPL>(newm, G.gl); m; m &= m - 1) {
+            const int r = __ffs(m) - 1;
             const int s = r * T + G.gl;
-            if (newm.test(s)) {
-                const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-                const int a = ids & 0xff, bb = (ids >> 8) & 0xff, c = (ids >> 16) & 0xff;
-                if (!solve3<Real>(sm.pnx[a], sm.pny[a], sm.pnz[a], sm.pb[a], sm.pnx[bb], sm.pny[bb], sm.pnz[bb],
-                                  sm.pb[bb], sm.pnx[c], sm.pny[c], sm.pnz[c], sm.pb[c], vx[r], vy[r], vz[r],
-                                  (Real)Tol<Real>::cond_rel)) {
-                    need |= 1u << r;
-                    interp = true;
-                }
-            }
+            const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
+            const int a = ids & 0xff, bb = (ids >> 8) & 0xff, c = (ids >> 16) & 0xff;
+            Real x, y, z;
+            if (solve3<Real>(sm.pnx[a], sm.pny[a], sm.pnz[a], sm.pb[a], sm.pnx[bb], sm.pny[bb], sm.pnz[bb], sm.pb[bb],
+                             sm.pnx[c], sm.pny[c], sm.pnz[c], sm.pb[c], x, y, z, (Real)Tol<Real>::cond_rel))
+                set_row(r, x, y, z);
+            else
+                need |= 1u << r;
         }
-        if (G.any(interp)) {
+        if (G.any(need != 0)) {
             if (G.gl == 0) atomicAdd(&st->detail[4], 1u);
-            const Mask before = mask_or(keep, out);
 #pragma unroll
             for (int r = 0; r < VPL; ++r) {
                 const int s = r * T + G.gl;
-                if (before.test(s)) {
+                if (r < rows_before && before.test(s)) {
                     sm.vpos[s][0] = vx[r];
                     sm.vpos[s][1] = vy[r];
                     sm.vpos[s][2] = vz[r];
                 }
             }
             G.sync();
-#pragma unroll
-            for (int r = 0; r < VPL; ++r) {
-                if (!((need >> r) & 1u)) continue;
-                const int s = r * T + G.gl;
-                const int v = sm.vsrc[s], w = sm.vadj[s][0];
-                const Real px = sm.vpos[v][0], py = sm.vpos[v][1], pz = sm.vpos[v][2];
-                const Real qx = sm.vpos[w][0], qy = sm.vpos[w][1], qz = sm.vpos[w][2];
-                const Real sv_ = nx * px + ny * py + nz * pz - b, sw_ = nx * qx + ny * qy + nz * qz - b;
-                Real t = sv_ - sw_ > (Real)0 ? sv_ / (sv_ - sw_) : (Real)0.5;
-                t = t < (Real)0 ? (Real)0 : (t > (Real)1 ? (Real)1 : t);
-                vx[r] = px + t * (qx - px);
-                vy[r] = py + t * (qy - py);
-                vz[r] = pz + t * (qz - pz);
+            for (uint32_t m = need; m; m &= m - 1) {
+                const int r = __ffs(m) - 1;
+                Real xyz[3];
+                interp_vertex<Real>(sm, r * T + G.gl, nx, ny, nz, b, xyz);
+                set_row(r, xyz[0], xyz[1], xyz[2]);
             }
             G.sync();
         }
-        update_r2();
+        update_r2(G);
         return CLIP_CUT;
     }
 
-    __device__ __forceinline__ int clip_point(float4 pj, int j)
+    __device__ __forceinline__ int clip_point(const Group<T>& G, S& sm, float4 pj, int j,
+                                              const float4* __restrict__ sorted, const GridDesc& grid, DevStatus* st)
     {
         Real nx, ny, nz;
         if (Tol<Real>::fp32) {
@@ -621,191 +736,246 @@ struct Cell {
             nz = (Real)pj.z - (Real)pi.z;
         }
         const Real b = (Real)0.5 * (nx * nx + ny * ny + nz * nz);
-        return clip(nx, ny, nz, b, j);
+        return clip(G, sm, nx, ny, nz, b, j, sorted, grid, st);
     }
 
-    // ---------------------------------------------------------------------
-    // moments, neighbours and geometry of a validated cell
-    // ---------------------------------------------------------------------
-    __device__ void finish(int64_t out_idx, const ClipArgs& A, int q)
+    __device__ __forceinline__ void dump_positions(const Group<T>& G, S& sm) const
     {
-        // positions to shared memory, tables reset
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
             const int s = r * T + G.gl;
-            sm.vpos[s][0] = vx[r];
-            sm.vpos[s][1] = vy[r];
-            sm.vpos[s][2] = vz[r];
-        }
-        for (int f = G.gl; f < np; f += T) {
-            sm.u.tail.area[f] = 0;
-            sm.u.tail.first[f] = -1;
-        }
-        G.sync();
-        // per (vertex, face) terms: tetrahedron (0, q_f, v, next(v around f)),
-        // q_f = foot of the perpendicular from the generator onto face f
-        Real vol = 0, mx = 0, my = 0, mz = 0, m2 = 0;
-#pragma unroll
-        for (int r = 0; r < VPL; ++r) {
-            const int s = r * T + G.gl;
-            if (!alive.test(s)) continue;
-            const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-            const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
-            const Real ax = vx[r], ay = vy[r], az = vz[r];
-            const Real a2 = ax * ax + ay * ay + az * az;
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const int f = (ids >> (8 * t)) & 0xff;
-                const int nx_ = (adj >> (8 * ((t + 2) % 3))) & 0xff;
-                const Real bx = sm.vpos[nx_][0], by = sm.vpos[nx_][1], bz = sm.vpos[nx_][2];
-                const Real fnx = sm.pnx[f], fny = sm.pny[f], fnz = sm.pnz[f], fb = sm.pb[f];
-                const Real nn = fnx * fnx + fny * fny + fnz * fnz;
-                const Real sc = fb / nn;
-                const Real qx = fnx * sc, qy = fny * sc, qz = fnz * sc;
-                // det[q a b]
-                const Real cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
-                const Real det = qx * cx + qy * cy + qz * cz;
-                const Real dv = det * (Real)(1.0 / 6.0);
-                const Real sx = qx + ax + bx, sy = qy + ay + by, sz = qz + az + bz;
-                vol += dv;
-                mx += dv * sx;
-                my += dv * sy;
-                mz += dv * sz;
-                m2 += dv * (qx * qx + qy * qy + qz * qz + a2 + bx * bx + by * by + bz * bz + sx * sx + sy * sy + sz * sz);
-                // face area: 0.5 * (a - q) x (b - q) . n / |n|
-                const Real ux = ax - qx, uy = ay - qy, uz = az - qz, wx = bx - qx, wy = by - qy, wz = bz - qz;
-                const Real ar = (Real)0.5 * ((uy * wz - uz * wy) * fnx + (uz * wx - ux * wz) * fny + (ux * wy - uy * wx) * fnz) /
-                                sqrt(nn);
-                atomicAdd(&sm.u.tail.area[f], ar);
-                sm.u.tail.first[f] = (int16_t)s;
+            if (r < rows && alive.test(s)) {
+                sm.vpos[s][0] = vx[r];
+                sm.vpos[s][1] = vy[r];
+                sm.vpos[s][2] = vz[r];
             }
         }
-        const double V = G.sum((double)vol);
-        const double MX = G.sum((double)mx) * 0.25, MY = G.sum((double)my) * 0.25, MZ = G.sum((double)mz) * 0.25;
-        const double M2 = G.sum((double)m2) * 0.05;
-        G.sync();
-        // neighbour keys: planes with a face of area above the threshold
-        const double tau = Tol<Real>::area_rel * cbrt(V * V);
-        for (int f = G.gl; f < np; f += T) {
-            const int src = sm.psrc[f];
-            const bool has = sm.u.tail.first[f] >= 0;
-            int key = INT_MAX;
-            if (src >= 0 && has && (double)sm.u.tail.area[f] > tau)
-                key = A.index_space == VT_INDEX_ORIGINAL ? __float_as_int(sorted[src].w) : src;
-            sm.u.tail.key[f] = key;
-        }
-        G.sync();
-        if (G.gl == 0) {
-            if (A.vol) A.vol[out_idx] = V;
-            if (A.cen) {
-                A.cen[3 * out_idx] = (double)pi.x + MX / V;
-                A.cen[3 * out_idx + 1] = (double)pi.y + MY / V;
-                A.cen[3 * out_idx + 2] = (double)pi.z + MZ / V;
-            }
-            if (A.m2) A.m2[out_idx] = M2;
-        }
-        if (!A.rec) return;
-        uint8_t* rec = A.rec + (size_t)out_idx * A.rec_stride;
-        int32_t* rnbr = reinterpret_cast<int32_t*>(rec + REC_NBR_OFF);
-        int nn_total = 0;
-        for (int f = G.gl; f < np; f += T) {
-            const int key = sm.u.tail.key[f];
-            if (key == INT_MAX) continue;
-            int rank = 0;
-            for (int g2 = 0; g2 < np; ++g2) rank += sm.u.tail.key[g2] < key ? 1 : 0;
-            if (rank < REC_FACES) rnbr[rank] = key;
-        }
-        {
-            int c = 0;
-            for (int f = G.gl; f < np; f += T) c += sm.u.tail.key[f] != INT_MAX ? 1 : 0;
-            nn_total = G.sum(c);
-        }
-        int nface = 0, nvtx = 0, nfv = 0;
-        if (A.emit & VT_EMIT_GEOM) {
-            nvtx = alive.count();
-            // degrees by walking each face
-            for (int f = G.gl; f < np; f += T) {
-                int deg = 0;
-                const int s0 = sm.u.tail.first[f];
-                if (s0 >= 0) {
-                    int cur = s0;
-                    do {
-                        const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[cur]);
-                        const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[cur]);
-                        int t = ((ids & 0xff) == (uint32_t)f) ? 0 : ((((ids >> 8) & 0xff) == (uint32_t)f) ? 1 : 2);
-                        cur = (adj >> (8 * ((t + 2) % 3))) & 0xff;
-                        ++deg;
-                    } while (cur != s0 && deg <= VCAP);
-                }
-                sm.u.tail.deg[f] = (uint8_t)(deg > 255 ? 255 : deg);
-            }
-            G.sync();
-            int32_t* rfn = reinterpret_cast<int32_t*>(rec + REC_FNBR_OFF);
-            uint8_t* rdeg = rec + REC_FDEG_OFF;
-            uint8_t* rfv = rec + REC_FVTX_OFF;
-            double* rv = reinterpret_cast<double*>(rec + REC_VTX_OFF);
-            for (int f = G.gl; f < np; f += T) {
-                const int deg = sm.u.tail.deg[f];
-                if (deg == 0) continue;
-                int fi = 0, pos = 0;
-                for (int g2 = 0; g2 < f; ++g2) {
-                    const int dg = sm.u.tail.deg[g2];
-                    fi += dg ? 1 : 0;
-                    pos += dg;
-                }
-                if (fi >= REC_FACES || pos + deg > 3 * REC_VERTS) continue;
-                const int src = sm.psrc[f];
-                rfn[fi] = src < 0 ? src : (A.index_space == VT_INDEX_ORIGINAL ? __float_as_int(sorted[src].w) : src);
-                rdeg[fi] = (uint8_t)deg;
-                int cur = sm.u.tail.first[f];
-                for (int t2 = 0; t2 < deg; ++t2) {
-                    rfv[pos + t2] = (uint8_t)alive.rank(cur);
-                    const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[cur]);
-                    const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[cur]);
-                    int t = ((ids & 0xff) == (uint32_t)f) ? 0 : ((((ids >> 8) & 0xff) == (uint32_t)f) ? 1 : 2);
-                    cur = (adj >> (8 * ((t + 2) % 3))) & 0xff;
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < VPL; ++r) {
-                const int s = r * T + G.gl;
-                if (alive.test(s)) {
-                    const int li = alive.rank(s);
-                    if (li < REC_VERTS) {
-                        rv[3 * li] = (double)pi.x + (double)vx[r];
-                        rv[3 * li + 1] = (double)pi.y + (double)vy[r];
-                        rv[3 * li + 2] = (double)pi.z + (double)vz[r];
-                    }
-                }
-            }
-            int fc = 0, fvc = 0;
-            for (int f = G.gl; f < np; f += T) {
-                fc += sm.u.tail.deg[f] ? 1 : 0;
-                fvc += sm.u.tail.deg[f];
-            }
-            nface = G.sum(fc);
-            nfv = G.sum(fvc);
-        }
-        if (G.gl == 0) {
-            bool over = nn_total > REC_FACES || nface > REC_FACES || nvtx > REC_VERTS || nfv > 3 * REC_VERTS;
-            if (over) atomicAdd((int*)&st->record_overflow, 1);
-            RecHeader* hd = reinterpret_cast<RecHeader*>(rec);
-            hd->nnbr = over ? 0 : nn_total;
-            hd->nface = over ? 0 : nface;
-            hd->nvtx = over ? 0 : nvtx;
-            hd->nfv = over ? 0 : nfv;
-        }
-        G.sync();
     }
 };
 
 // ---------------------------------------------------------------------------
-// kernel
+// moments, neighbours and geometry of a validated cell (shared memory only)
+// ---------------------------------------------------------------------------
+template <typename Real, int T, int VCAP, int PCAP>
+__device__ __noinline__ void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, Mask alive, int np, float4 pi, int gl,
+                                         unsigned gmask, int64_t out_idx, const ClipArgs& A)
+{
+    for (int f = gl; f < np; f += T) {
+        sm.u.tail.area[f] = 0;
+        sm.u.tail.first[f] = -1;
+    }
+    __syncwarp(gmask);
+    // per (vertex, face) terms: tetrahedron (0, q_f, v, next(v around f)),
+    // q_f = foot of the perpendicular from the generator onto face f
+    Real vol = 0, mx = 0, my = 0, mz = 0, m2 = 0;
+    for (int s = gl; s < VCAP; s += T) {
+        if (!alive.test(s)) continue;
+        const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
+        const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
+        const Real ax = sm.vpos[s][0], ay = sm.vpos[s][1], az = sm.vpos[s][2];
+        const Real a2 = ax * ax + ay * ay + az * az;
+        for (int t = 0; t < 3; ++t) {
+            const int f = (ids >> (8 * t)) & 0xff;
+            const int nv = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
+            const Real bx = sm.vpos[nv][0], by = sm.vpos[nv][1], bz = sm.vpos[nv][2];
+            const Real fnx = sm.pnx[f], fny = sm.pny[f], fnz = sm.pnz[f], fb = sm.pb[f];
+            const Real nn = fnx * fnx + fny * fny + fnz * fnz;
+            const Real sc = fb / nn;
+            const Real qx = fnx * sc, qy = fny * sc, qz = fnz * sc;
+            const Real cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+            const Real dv = (qx * cx + qy * cy + qz * cz) * (Real)(1.0 / 6.0);
+            const Real sx = qx + ax + bx, sy = qy + ay + by, sz = qz + az + bz;
+            vol += dv;
+            mx += dv * sx;
+            my += dv * sy;
+            mz += dv * sz;
+            m2 += dv * (qx * qx + qy * qy + qz * qz + a2 + bx * bx + by * by + bz * bz + sx * sx + sy * sy + sz * sz);
+            const Real ux = ax - qx, uy = ay - qy, uz = az - qz, wx = bx - qx, wy = by - qy, wz = bz - qz;
+            const Real ar = (Real)0.5 *
+                            ((uy * wz - uz * wy) * fnx + (uz * wx - ux * wz) * fny + (ux * wy - uy * wx) * fnz) / sqrt(nn);
+            atomicAdd(&sm.u.tail.area[f], ar);
+            sm.u.tail.first[f] = (int16_t)s;
+        }
+    }
+    double V = (double)vol, MX = (double)mx, MY = (double)my, MZ = (double)mz, M2 = (double)m2;
+#pragma unroll
+    for (int o = T / 2; o >= 1; o >>= 1) {
+        V += __shfl_xor_sync(gmask, V, o, T);
+        MX += __shfl_xor_sync(gmask, MX, o, T);
+        MY += __shfl_xor_sync(gmask, MY, o, T);
+        MZ += __shfl_xor_sync(gmask, MZ, o, T);
+        M2 += __shfl_xor_sync(gmask, M2, o, T);
+    }
+    MX *= 0.25;
+    MY *= 0.25;
+    MZ *= 0.25;
+    M2 *= 0.05;
+    __syncwarp(gmask);
+    // neighbour keys: planes with a face of area above the threshold
+    const double tau = Tol<Real>::area_rel * cbrt(V * V);
+    for (int f = gl; f < np; f += T) {
+        const int src = sm.psrc[f];
+        int key = INT_MAX;
+        if (src >= 0 && sm.u.tail.first[f] >= 0 && (double)sm.u.tail.area[f] > tau)
+            key = A.index_space == VT_INDEX_ORIGINAL ? __float_as_int(A.sorted[src].w) : src;
+        sm.u.tail.key[f] = key;
+    }
+    __syncwarp(gmask);
+    if (gl == 0) {
+        if (A.vol) A.vol[out_idx] = V;
+        if (A.cen) {
+            A.cen[3 * out_idx] = (double)pi.x + MX / V;
+            A.cen[3 * out_idx + 1] = (double)pi.y + MY / V;
+            A.cen[3 * out_idx + 2] = (double)pi.z + MZ / V;
+        }
+        if (A.m2) A.m2[out_idx] = M2;
+    }
+    if (!A.rec) return;
+    uint8_t* rec = A.rec + (size_t)out_idx * A.rec_stride;
+    int32_t* rnbr = reinterpret_cast<int32_t*>(rec + REC_NBR_OFF);
+    int c = 0;
+    for (int f = gl; f < np; f += T) {
+        const int key = sm.u.tail.key[f];
+        if (key == INT_MAX) continue;
+        ++c;
+        int rank = 0;
+        for (int g2 = 0; g2 < np; ++g2) rank += sm.u.tail.key[g2] < key ? 1 : 0;
+        if (rank < REC_FACES) rnbr[rank] = key;
+    }
+    int nn_total = c;
+#pragma unroll
+    for (int o = T / 2; o >= 1; o >>= 1) nn_total += __shfl_xor_sync(gmask, nn_total, o, T);
+    int nface = 0, nvtx = 0, nfv = 0;
+    if (A.emit & VT_EMIT_GEOM) {
+        nvtx = alive.count();
+        // degrees by walking each face
+        for (int f = gl; f < np; f += T) {
+            int deg = 0;
+            const int s0 = sm.u.tail.first[f];
+            if (s0 >= 0) {
+                int cur = s0;
+                do {
+                    const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[cur]);
+                    const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[cur]);
+                    const int t = ((ids & 0xff) == (uint32_t)f) ? 0 : ((((ids >> 8) & 0xff) == (uint32_t)f) ? 1 : 2);
+                    cur = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
+                    ++deg;
+                } while (cur != s0 && deg <= VCAP);
+            }
+            sm.u.tail.deg[f] = (uint8_t)(deg > 255 ? 255 : deg);
+        }
+        __syncwarp(gmask);
+        int32_t* rfn = reinterpret_cast<int32_t*>(rec + REC_FNBR_OFF);
+        uint8_t* rdeg = rec + REC_FDEG_OFF;
+        uint8_t* rfv = rec + REC_FVTX_OFF;
+        double* rv = reinterpret_cast<double*>(rec + REC_VTX_OFF);
+        int fc = 0, fvc = 0;
+        for (int f = gl; f < np; f += T) {
+            const int deg = sm.u.tail.deg[f];
+            if (deg == 0) continue;
+            ++fc;
+            fvc += deg;
+            int fi = 0, pos = 0;
+            for (int g2 = 0; g2 < f; ++g2) {
+                const int dg = sm.u.tail.deg[g2];
+                fi += dg ? 1 : 0;
+                pos += dg;
+            }
+            if (fi >= REC_FACES || pos + deg > 3 * REC_VERTS) continue;
+            const int src = sm.psrc[f];
+            rfn[fi] = src < 0 ? src : (A.index_space == VT_INDEX_ORIGINAL ? __float_as_int(A.sorted[src].w) : src);
+            rdeg[fi] = (uint8_t)deg;
+            int cur = sm.u.tail.first[f];
+            for (int t2 = 0; t2 < deg; ++t2) {
+                rfv[pos + t2] = (uint8_t)alive.rank(cur);
+                const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[cur]);
+                const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[cur]);
+                const int t = ((ids & 0xff) == (uint32_t)f) ? 0 : ((((ids >> 8) & 0xff) == (uint32_t)f) ? 1 : 2);
+                cur = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
+            }
+        }
+        for (int s = gl; s < VCAP; s += T) {
+            if (!alive.test(s)) continue;
+            const int li = alive.rank(s);
+            if (li < REC_VERTS) {
+                rv[3 * li] = (double)pi.x + (double)sm.vpos[s][0];
+                rv[3 * li + 1] = (double)pi.y + (double)sm.vpos[s][1];
+                rv[3 * li + 2] = (double)pi.z + (double)sm.vpos[s][2];
+            }
+        }
+        nface = fc;
+        nfv = fvc;
+#pragma unroll
+        for (int o = T / 2; o >= 1; o >>= 1) {
+            nface += __shfl_xor_sync(gmask, nface, o, T);
+            nfv += __shfl_xor_sync(gmask, nfv, o, T);
+        }
+    }
+    if (gl == 0) {
+        const bool over = nn_total > REC_FACES || nface > REC_FACES || nvtx > REC_VERTS || nfv > 3 * REC_VERTS;
+        if (over) atomicAdd((int*)&A.st->record_overflow, 1);
+        RecHeader* hd = reinterpret_cast<RecHeader*>(rec);
+        hd->nnbr = over ? 0 : nn_total;
+        hd->nface = over ? 0 : nface;
+        hd->nvtx = over ? 0 : nvtx;
+        hd->nfv = over ? 0 : nfv;
+    }
+    __syncwarp(gmask);
+}
+
+// one candidate range [a, b) of sorted points for the exhaustive walk: every
+// generator that can still cut the cell (4 R^2 > d^2) and that the resumed
+// list did not already process is clipped
+template <typename Real, int T, int VPL, int PCAP>
+__device__ __forceinline__ int exhaustive_range(Cell<Real, T, VPL, PCAP>& cell, const Group<T>& G,
+                                                typename Cell<Real, T, VPL, PCAP>::S& sm, const ClipArgs& A, int a,
+                                                int b, int q, double last_d2, int last_orig)
+{
+    const float4 pq = cell.pi;
+    for (int b0 = a; b0 < b; b0 += T) {
+        const int jj = b0 + G.gl;
+        float4 pc = make_float4(0.f, 0.f, 0.f, 0.f);
+        double d2 = 0.0;
+        bool need = false;
+        if (jj < b && jj != q) {
+            pc = A.sorted[jj];
+            const double ex = (double)pc.x - (double)pq.x, ey = (double)pc.y - (double)pq.y,
+                         ez = (double)pc.z - (double)pq.z;
+            d2 = (ex * ex + ey * ey) + ez * ez;
+            need = 4.0 * (double)cell.R2 * (1.0 + 1e-5) > d2;
+            if (need && last_orig >= 0) {  // already processed from the list?
+                const double kd = Tol<Real>::fp32 ? (double)knn_d2_f32(pq, pc) : knn_d2_f64(pq, pc);
+                const int ko = __float_as_int(pc.w);
+                if (kd < last_d2 || (kd == last_d2 && ko <= last_orig)) need = false;
+            }
+        }
+        unsigned mm = G.ballot(need);
+        while (mm) {
+            const int src = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const double bd2 = G.bcast(d2, src);
+            if (!(4.0 * (double)cell.R2 * (1.0 + 1e-5) > bd2)) continue;
+            const int j = G.bcast(jj, src);
+            float4 p;
+            p.x = G.bcast(pc.x, src);
+            p.y = G.bcast(pc.y, src);
+            p.z = G.bcast(pc.z, src);
+            p.w = 0.f;
+            const int r = cell.clip_point(G, sm, p, j, A.sorted, A.g, A.st);
+            if (r == CLIP_OVERFLOW) return END_OVERFLOW;
+            if (r == CLIP_INCONSISTENT) return END_INCONSISTENT;
+        }
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// kernels: list mode (k > 0) and exhaustive mode (k == 0)
 // ---------------------------------------------------------------------------
 constexpr int CLIP_BLOCK = 128;
 
-template <typename Real, int T, int VPL, int PCAP, bool ROBUST>
-__global__ void __launch_bounds__(CLIP_BLOCK) k_clip(ClipArgs A)
+template <typename Real, int T, int VPL, int PCAP, bool ROBUST, bool EXH>
+__global__ void __launch_bounds__(CLIP_BLOCK, 4) k_clip(ClipArgs A)
 {
     using C = Cell<Real, T, VPL, PCAP>;
     using S = typename C::S;
@@ -816,33 +986,61 @@ __global__ void __launch_bounds__(CLIP_BLOCK) k_clip(ClipArgs A)
     const int64_t ngroups = ((int64_t)gridDim.x * CLIP_BLOCK) / T;
     const int k = A.k;
     const int Gr = A.g.G;
+    const bool resume = !ROBUST && A.state && A.k_prev > 0;
+    C cell;
+    cell.stamp = 0;
 
-    uint32_t stamp = 0;
     for (int64_t c = gid; c < A.nq; c += ngroups) {
         const int q = A.queries ? A.queries[c] : (int)c;
-        C cell(G, sm, A.sorted, A.g, A.st);
-        cell.stamp = stamp;
         cell.pi = A.sorted[q];
         const int orig = __float_as_int(cell.pi.w);
         const int64_t out_idx = A.index_space == VT_INDEX_ORIGINAL ? (int64_t)orig : (int64_t)q;
-        cell.init_box();
+        uint8_t* stp = A.state ? A.state + (size_t)q * A.state_stride : nullptr;
+        double last_d2 = -1.0;
+        int last_orig = -1;
+        if (resume) cell.restore(G, sm, stp, last_d2, last_orig);
+        else cell.init_box(G, sm, A.g);
         int end = END_NEED_K;
-        if (k > 0) {
-            // neighbour list, nearest first
+        if (!EXH) {
+            // neighbour list, nearest first, from the first unprocessed entry;
+            // each lane holds one entry of the current chunk of T and prefetches
+            // its entry of the next chunk
             const int32_t* nb = A.nbr + c * (int64_t)k;
             const Real* dd = reinterpret_cast<const Real*>(A.d2) + c * (int64_t)k;
-            int m = 0;
-            for (; m < k; ++m) {
-                const int j = nb[m];
-                if (j < 0) break;  // the list holds every other generator
-                const Real dj = dd[m];
-                if (cell.radius_ok(dj, j)) { end = END_VALID; break; }
-                const int r = cell.clip_point(A.sorted[j], j);
-                if (r == CLIP_OVERFLOW) { end = END_OVERFLOW; break; }
-                if (r == CLIP_INCONSISTENT) { end = END_INCONSISTENT; break; }
+            const int m0 = resume ? A.k_prev : 0;
+            int nj = m0 + G.gl < k ? nb[m0 + G.gl] : -1;
+            Real nd = m0 + G.gl < k ? dd[m0 + G.gl] : (Real)0;
+            float4 np4 = nj >= 0 ? A.sorted[nj] : make_float4(0.f, 0.f, 0.f, 0.f);
+            bool stop = false;
+            for (int base = m0; base < k && !stop; base += T) {
+                const int cj = nj;
+                const Real cd = nd;
+                const float4 cp = np4;
+                const int nm = base + T + G.gl;
+                nj = nm < k ? nb[nm] : -1;
+                nd = nm < k ? dd[nm] : (Real)0;
+                np4 = nj >= 0 ? A.sorted[nj] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int cnt = k - base < T ? k - base : T;
+                for (int t = 0; t < cnt; ++t) {
+                    const int j = G.bcast(cj, t);
+                    if (j < 0) { end = END_VALID; stop = true; break; }  // the list holds every other generator
+                    const Real dj = G.bcast(cd, t);
+                    if (cell.radius_ok(G, sm, dj, j, A.sorted, A.g, A.st)) { end = END_VALID; stop = true; break; }
+                    float4 p;
+                    p.x = G.bcast(cp.x, t);
+                    p.y = G.bcast(cp.y, t);
+                    p.z = G.bcast(cp.z, t);
+                    p.w = 0.f;
+                    const int r = cell.clip_point(G, sm, p, j, A.sorted, A.g, A.st);
+                    if (r == CLIP_OVERFLOW) { end = END_OVERFLOW; stop = true; break; }
+                    if (r == CLIP_INCONSISTENT) { end = END_INCONSISTENT; stop = true; break; }
+                }
             }
-            if (m < k && end == END_NEED_K && nb[m] < 0) end = END_VALID;
-            if (m == k && end == END_NEED_K && cell.radius_ok(dd[k - 1], nb[k - 1])) end = END_VALID;
+            if (!stop && k > 0 && cell.radius_ok(G, sm, dd[k - 1], nb[k - 1], A.sorted, A.g, A.st)) end = END_VALID;
+            if (end == END_NEED_K && k > 0) {
+                last_d2 = (double)dd[k - 1];
+                last_orig = __float_as_int(A.sorted[nb[k - 1]].w);
+            }
         } else {
             // exhaustive: every generator closer than 2R, by a shell walk
             const float4 pq = cell.pi;
@@ -850,29 +1048,6 @@ __global__ void __launch_bounds__(CLIP_BLOCK) k_clip(ClipArgs A)
             const int iy = cell_coord(pq.y, A.g.lo[1], A.g.scale[1], Gr);
             const int iz = cell_coord(pq.z, A.g.lo[2], A.g.scale[2], Gr);
             int status = 0;
-            auto scan_range = [&](int a, int b) {
-                for (int base = a; base < b && status == 0; base += T) {
-                    const int jj = base + G.gl;
-                    float4 pc = make_float4(0, 0, 0, 0);
-                    bool need = false;
-                    if (jj < b && jj != q) {
-                        pc = A.sorted[jj];
-                        const double dx = (double)pc.x - (double)pq.x, dy = (double)pc.y - (double)pq.y,
-                                     dz = (double)pc.z - (double)pq.z;
-                        const double d2 = (dx * dx + dy * dy) + dz * dz;
-                        need = 4.0 * (double)cell.R2 * (1.0 + 1e-5) > d2;
-                    }
-                    unsigned m = G.ballot(need);
-                    while (m && status == 0) {
-                        const int src = __ffs(m) - 1;
-                        m &= m - 1;
-                        const int j = G.bcast(jj, src);
-                        const int r = cell.clip_point(A.sorted[j], j);
-                        if (r == CLIP_OVERFLOW) status = END_OVERFLOW;
-                        if (r == CLIP_INCONSISTENT) status = END_INCONSISTENT;
-                    }
-                }
-            };
             for (int s = 0; status == 0; ++s) {
                 for (int dx = -s; dx <= s && status == 0; ++dx) {
                     const int x = ix + dx;
@@ -880,18 +1055,20 @@ __global__ void __launch_bounds__(CLIP_BLOCK) k_clip(ClipArgs A)
                     for (int dy = -s; dy <= s && status == 0; ++dy) {
                         const int y = iy + dy;
                         if (y < 0 || y >= Gr) continue;
-                        const bool full = dx == -s || dx == s || dy == -s || dy == s;
-                        if (full) {
+                        if (dx == -s || dx == s || dy == -s || dy == s) {
                             const int z0 = max(iz - s, 0), z1 = min(iz + s, Gr - 1);
-                            scan_range(A.cell_off[cell_id(x, y, z0, Gr)], A.cell_off[cell_id(x, y, z1, Gr) + 1]);
+                            status = exhaustive_range(cell, G, sm, A, A.cell_off[cell_id(x, y, z0, Gr)],
+                                                      A.cell_off[cell_id(x, y, z1, Gr) + 1], q, last_d2, last_orig);
                         } else {
                             if (iz - s >= 0) {
                                 const int cc = cell_id(x, y, iz - s, Gr);
-                                scan_range(A.cell_off[cc], A.cell_off[cc + 1]);
+                                status = exhaustive_range(cell, G, sm, A, A.cell_off[cc], A.cell_off[cc + 1], q,
+                                                          last_d2, last_orig);
                             }
-                            if (iz + s < Gr) {
+                            if (status == 0 && iz + s < Gr) {
                                 const int cc = cell_id(x, y, iz + s, Gr);
-                                scan_range(A.cell_off[cc], A.cell_off[cc + 1]);
+                                status = exhaustive_range(cell, G, sm, A, A.cell_off[cc], A.cell_off[cc + 1], q,
+                                                          last_d2, last_orig);
                             }
                         }
                     }
@@ -900,30 +1077,31 @@ __global__ void __launch_bounds__(CLIP_BLOCK) k_clip(ClipArgs A)
                 const bool covers = ix - s <= 0 && iy - s <= 0 && iz - s <= 0 && ix + s >= Gr - 1 &&
                                     iy + s >= Gr - 1 && iz + s >= Gr - 1;
                 if (covers) { status = -1; break; }
-                const double qc[3] = {(double)pq.x, (double)pq.y, (double)pq.z};
-                const int ic[3] = {ix, iy, iz};
                 double gap = 1e300;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (ic[a] - s > 0) gap = fmin(gap, qc[a] - ((double)A.g.lo[a] + (ic[a] - s) * A.g.cw[a]) - A.g.margin);
-                    if (ic[a] + s + 1 < Gr)
-                        gap = fmin(gap, ((double)A.g.lo[a] + (ic[a] + s + 1) * A.g.cw[a]) - qc[a] - A.g.margin);
-                }
+                const double q0 = pq.x, q1 = pq.y, q2 = pq.z;
+                if (ix - s > 0) gap = fmin(gap, q0 - ((double)A.g.lo[0] + (ix - s) * A.g.cw[0]) - A.g.margin);
+                if (ix + s + 1 < Gr) gap = fmin(gap, ((double)A.g.lo[0] + (ix + s + 1) * A.g.cw[0]) - q0 - A.g.margin);
+                if (iy - s > 0) gap = fmin(gap, q1 - ((double)A.g.lo[1] + (iy - s) * A.g.cw[1]) - A.g.margin);
+                if (iy + s + 1 < Gr) gap = fmin(gap, ((double)A.g.lo[1] + (iy + s + 1) * A.g.cw[1]) - q1 - A.g.margin);
+                if (iz - s > 0) gap = fmin(gap, q2 - ((double)A.g.lo[2] + (iz - s) * A.g.cw[2]) - A.g.margin);
+                if (iz + s + 1 < Gr) gap = fmin(gap, ((double)A.g.lo[2] + (iz + s + 1) * A.g.cw[2]) - q2 - A.g.margin);
                 if (gap > 0 && 4.0 * (double)cell.R2 * (1.0 + 1e-5) <= gap * gap) { status = -1; break; }
             }
             end = status == -1 ? END_VALID : status;
         }
 
-        stamp = cell.stamp + 1;
         if (end == END_VALID) {
-            cell.finish(out_idx, A, q);
+            cell.dump_positions(G, sm);
+            G.sync();
+            finish_cell<Real, T, T * VPL, PCAP>(sm, cell.alive, cell.np, cell.pi, G.gl, G.mask, out_idx, A);
         } else {
+            if (end == END_NEED_K && !EXH && !ROBUST && A.state) cell.save(G, sm, stp, last_d2, last_orig);
             if (G.gl == 0) {
                 if (A.rec) {
                     RecHeader* hd = reinterpret_cast<RecHeader*>(A.rec + (size_t)out_idx * A.rec_stride);
                     hd->nnbr = hd->nface = hd->nvtx = hd->nfv = 0;
                 }
-                if (end == END_NEED_K && k > 0) {
+                if (end == END_NEED_K && !EXH) {
                     const int slot = atomicAdd(A.ctr_next, 1);
                     A.fail_next[slot] = q;
                 } else {
@@ -940,12 +1118,18 @@ __global__ void __launch_bounds__(CLIP_BLOCK) k_clip(ClipArgs A)
     }
 }
 
+template <typename Real, int T, int VPL, int PCAP>
+constexpr size_t state_bytes()
+{
+    return StateLayout<Real, T * VPL, PCAP>::BYTES;
+}
+
 template <typename Real, int T, int VPL, int PCAP, bool ROBUST>
 cudaError_t launch_variant(const ClipArgs& a, cudaStream_t s)
 {
     using S = GroupSmem<Real, T * VPL, PCAP>;
     const size_t smem = sizeof(S) * (CLIP_BLOCK / T);
-    auto kern = k_clip<Real, T, VPL, PCAP, ROBUST>;
+    auto kern = a.k == 0 ? k_clip<Real, T, VPL, PCAP, ROBUST, true> : k_clip<Real, T, VPL, PCAP, ROBUST, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int gpb = CLIP_BLOCK / T;

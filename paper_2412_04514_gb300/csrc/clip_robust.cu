@@ -8,6 +8,12 @@ namespace vt {
 cudaError_t launch_clip_f32(const ClipArgs& a, int t, cudaStream_t s);
 cudaError_t launch_clip_f64(const ClipArgs& a, int t, cudaStream_t s);
 
+size_t clip_state_bytes(int precision)
+{
+    // the regular variants all hold 64 vertex slots and 64 planes
+    return precision == VT_FP64 ? state_bytes<double, 8, 8, 64>() : state_bytes<float, 8, 8, 64>();
+}
+
 cudaError_t launch_clip(const ClipArgs& a, int variant, int threads_per_cell, cudaStream_t s)
 {
     if (a.nq <= 0) return cudaSuccess;

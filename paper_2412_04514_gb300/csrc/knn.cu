@@ -28,23 +28,13 @@ struct Dist;
 template <>
 struct Dist<double> {
     // the exact key of the FP64 form: ((dx*dx + dy*dy) + dz*dz), no contraction
-    static __device__ __forceinline__ double d2(float4 a, float4 b)
-    {
-        double dx = __dsub_rn((double)b.x, (double)a.x);
-        double dy = __dsub_rn((double)b.y, (double)a.y);
-        double dz = __dsub_rn((double)b.z, (double)a.z);
-        return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    }
+    static __device__ __forceinline__ double d2(float4 a, float4 b) { return knn_d2_f64(a, b); }
     static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
 };
 
 template <>
 struct Dist<float> {
-    static __device__ __forceinline__ float d2(float4 a, float4 b)
-    {
-        float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
-        return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    }
+    static __device__ __forceinline__ float d2(float4 a, float4 b) { return knn_d2_f32(a, b); }
     static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
 };
 
@@ -139,13 +129,25 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
                 bool valid = jj < b && jj != q;
                 Real cd = Dist<Real>::inf();
                 int co = INT_MAX;
+                bool cand = false;
                 if (valid) {
                     float4 pc = sorted[jj];
-                    cd = Dist<Real>::d2(pq, pc);
                     co = __float_as_int(pc.w);
                     if (pc.x == pq.x && pc.y == pq.y && pc.z == pq.z) dup = true;
+                    if (sizeof(Real) == 8) {
+                        // FP64 keys only for candidates whose float32 distance (relative
+                        // error < 1e-6) does not already rule them out: same list, less FP64
+                        const float c32 = knn_d2_f32(pq, pc);
+                        if (count < k || (double)c32 <= (double)kd * (1.0 + 1e-6)) {
+                            cd = Dist<Real>::d2(pq, pc);
+                            cand = count < k || key_less(cd, co, kd, ko);
+                        }
+                    } else {
+                        cd = Dist<Real>::d2(pq, pc);
+                        cand = count < k || key_less(cd, co, kd, ko);
+                    }
                 }
-                unsigned m = __ballot_sync(FULL, valid && (count < k || key_less(cd, co, kd, ko)));
+                unsigned m = __ballot_sync(FULL, cand);
                 while (m) {
                     const int src = __ffs(m) - 1;
                     m &= m - 1;

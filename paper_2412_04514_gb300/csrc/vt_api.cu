@@ -133,6 +133,8 @@ Layout make_layout(const vt_params* p, int64_t n)
     L.rec = take(L.rec_stride * (size_t)nn);
     L.cnt = take(sizeof(int32_t) * 4 * nn);
     L.off64 = take(sizeof(int64_t) * 4 * (nn + 1));
+    L.state_stride = clip_state_bytes(p->precision);
+    L.state = take(L.state_stride * (size_t)nn);
     L.total = off;
     return L;
 }
@@ -237,8 +239,8 @@ __global__ void k_iota(int32_t* a, int64_t n)
 
 // one clip pass over `list` (m cells): kNN with k in chunks that fit the
 // list buffer, then the clipper; k == 0 runs the exhaustive clipper
-int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, int k, int variant, int knn_prec,
-              vt_cells_out* out, int32_t* fail_next, int32_t* fail_robust)
+int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, int k, int k_prev, int variant,
+              int knn_prec, vt_cells_out* out, int32_t* fail_next, int32_t* fail_robust)
 {
     const Layout& L = c.L;
     ClipArgs a{};
@@ -258,6 +260,9 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
     a.fail_robust = fail_robust;
     a.ctr_next = &c.st->n_fail_next;
     a.ctr_robust = &c.st->n_fail_robust;
+    a.k_prev = k_prev;
+    a.state = c.at<uint8_t>(L.state);
+    a.state_stride = L.state_stride;
     a.st = c.st;
     const int tpc = p->threads_per_cell;
     StageTimer dummy;
@@ -524,6 +529,7 @@ int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cells_out*
     int64_t m_reg = n, m_rob = 0, n_unval = 0;
     bool implicit = true;  // the first pass runs over all cells without a list
     int k = p->k0;
+    int k_prev = 0;  // regular cells resume from their saved state after list entry k_prev
     int r = VT_OK;
     DevStatus h{};
     while (m_reg + m_rob > 0) {
@@ -544,8 +550,8 @@ int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cells_out*
                 count_launch();
                 implicit = false;
             }
-            r = clip_pass(c, p, implicit ? nullptr : reg_cur, m_reg, kk, variant_reg, p->precision, out, reg_nxt,
-                          rob_new);
+            r = clip_pass(c, p, implicit ? nullptr : reg_cur, m_reg, kk, k_prev, variant_reg, p->precision, out,
+                          reg_nxt, rob_new);
             if (r) return r;
             if ((r = read_status(c, h))) return r;
             if ((r = status_errors(h))) return r;
@@ -561,7 +567,7 @@ int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cells_out*
         int64_t rob_next = 0;
         if (m_rob > 0) {
             if ((r = zero_counters(c))) return r;
-            r = clip_pass(c, p, rob_cur, m_rob, kk, 2, VT_FP64, out, rob_nxt, unval + n_unval);
+            r = clip_pass(c, p, rob_cur, m_rob, kk, 0, 2, VT_FP64, out, rob_nxt, unval + n_unval);
             if (r) return r;
             if ((r = read_status(c, h))) return r;
             if ((r = status_errors(h))) return r;
@@ -576,6 +582,7 @@ int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cells_out*
             n_unval += m_reg + m_rob;  // cannot happen: the exhaustive pass always concludes
             break;
         }
+        k_prev = k;
         k *= 2;
     }
     S.unvalidated = n_unval;

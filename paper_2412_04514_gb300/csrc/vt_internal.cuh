@@ -33,6 +33,22 @@ __device__ __forceinline__ int cell_coord(float x, float lo, float scale, int G)
 
 __device__ __forceinline__ int cell_id(int ix, int iy, int iz, int G) { return (ix * G + iy) * G + iz; }
 
+// kNN ordering keys. FP64 form: ((dx*dx + dy*dy) + dz*dz) in double with
+// dx = double(x_j) - double(x_i), every operation separately rounded (no FMA),
+// so lists are exact and reproducible. FP32 form: the same in float32 with FMA.
+__device__ __forceinline__ double knn_d2_f64(float4 a, float4 b)
+{
+    const double dx = __dsub_rn((double)b.x, (double)a.x);
+    const double dy = __dsub_rn((double)b.y, (double)a.y);
+    const double dz = __dsub_rn((double)b.z, (double)a.z);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+__device__ __forceinline__ float knn_d2_f32(float4 a, float4 b)
+{
+    const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+    return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
 // ---------------------------------------------------------------------------
 // device status block at the start of every workspace
 // ---------------------------------------------------------------------------
@@ -86,7 +102,8 @@ struct Layout {
     int64_t knn_cap;            // entries of the neighbour-list buffer
     size_t rec_stride;
     size_t status, cid, ticket, counts, cell_off, big, scan_tmp, sorted, perm;
-    size_t list_a, list_b, list_r, knn_nbr, knn_d2, rec, cnt, off64;
+    size_t state_stride;
+    size_t list_a, list_b, list_r, knn_nbr, knn_d2, rec, cnt, off64, state;
     size_t total;
 };
 Layout make_layout(const vt_params* p, int64_t n);
@@ -134,10 +151,14 @@ struct ClipArgs {
                               // the robust variant itself, cells left unvalidated)
     int32_t* ctr_next;        // device counters of the two lists
     int32_t* ctr_robust;
+    int k_prev;               // > 0: resume saved cells; list entries [0, k_prev) are done
+    uint8_t* state;           // per-cell saved polyhedra (sorted index * state_stride), or NULL
+    size_t state_stride;
     DevStatus* st;
 };
 // variant: 0 = FP32 regular, 1 = FP64 regular, 2 = FP64 robust (bigger capacity)
 cudaError_t launch_clip(const ClipArgs& a, int variant, int threads_per_cell, cudaStream_t s);
+size_t clip_state_bytes(int precision);  // per-cell state of the regular variant
 
 struct EmitArgs {
     int64_t n;
