@@ -139,6 +139,7 @@ typedef struct vt_stats {
     int clip_launches;                   /* clipper launches among them */
     int knn_launches;                    /* kNN launches among them */
     double ms_grid, ms_knn, ms_clip, ms_emit; /* device time per stage (VT_FLAG_STAGE_TIMES), else 0 */
+    double ms_clip_pass[VT_MAX_PASSES];  /* clipper device time of each pass (VT_FLAG_STAGE_TIMES) */
     int64_t clip_events[5];              /* diagnostic counts of clip steps that: removed every vertex,
                                             hit the plane cap, hit the vertex cap, found an inconsistent
                                             ring, or placed a vertex by edge interpolation */

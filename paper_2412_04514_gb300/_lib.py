@@ -105,6 +105,7 @@ class VtStats(ctypes.Structure):
         ("ms_knn", ctypes.c_double),
         ("ms_clip", ctypes.c_double),
         ("ms_emit", ctypes.c_double),
+        ("ms_clip_pass", ctypes.c_double * VT_MAX_PASSES),
         ("clip_events", ctypes.c_int64 * 5),
     ]
 
@@ -128,6 +129,7 @@ class VtStats(ctypes.Structure):
             "ms_knn": self.ms_knn,
             "ms_clip": self.ms_clip,
             "ms_emit": self.ms_emit,
+            "ms_clip_pass": list(self.ms_clip_pass[:m]),
             "clip_events": list(self.clip_events),
         }
 

@@ -38,11 +38,12 @@ def _newest_input() -> float:
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     """Compile (if stale) and return the path of libvt.so."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input() and not extra:
+    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input() and not extra
+            and not os.environ.get("VT_NVCC_FLAGS")):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    extra = extra or []
+    extra = (extra or []) + os.environ.get("VT_NVCC_FLAGS", "").split()
 
     def one(src: str) -> str:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))

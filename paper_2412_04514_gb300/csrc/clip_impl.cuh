@@ -44,76 +44,139 @@
 
 #include "vt_internal.cuh"
 
+// rarely taken paths are out of line by default (smaller hot loop); building
+// with -DVT_INLINE_RARE inlines them (no call-site register spills)
+#ifdef VT_INLINE_RARE
+#define VT_RARE __forceinline__
+#else
+#define VT_RARE __noinline__
+#endif
+
 namespace vt {
 
 namespace {
 
 // ---------------------------------------------------------------------------
-// 128-bit slot mask
+// slot masks of W 64-bit words (W = 1 for 64 slots, 2 for 128)
 // ---------------------------------------------------------------------------
-struct Mask {
-    uint64_t w[2];
-    __device__ __forceinline__ bool test(int s) const { return (w[s >> 6] >> (s & 63)) & 1ull; }
-    __device__ __forceinline__ bool none() const { return (w[0] | w[1]) == 0; }
-    __device__ __forceinline__ int count() const { return __popcll(w[0]) + __popcll(w[1]); }
+template <int W>
+struct MaskW {
+    static constexpr int W_ = W;
+    uint64_t w[W];
+    __device__ __forceinline__ bool test(int s) const
+    {
+        if (W == 1) return (w[0] >> s) & 1ull;
+        return (w[s >> 6] >> (s & 63)) & 1ull;
+    }
+    __device__ __forceinline__ bool none() const
+    {
+        uint64_t o = 0;
+#pragma unroll
+        for (int i = 0; i < W; ++i) o |= w[i];
+        return o == 0;
+    }
+    __device__ __forceinline__ int count() const
+    {
+        int c = 0;
+#pragma unroll
+        for (int i = 0; i < W; ++i) c += __popcll(w[i]);
+        return c;
+    }
     // number of set bits strictly below s
     __device__ __forceinline__ int rank(int s) const
     {
+        if (W == 1) return __popcll(w[0] & ((1ull << s) - 1ull));
         if (s < 64) return __popcll(w[0] & ((1ull << s) - 1ull));
-        return __popcll(w[0]) + __popcll(w[1] & ((1ull << (s - 64)) - 1ull));
+        return __popcll(w[0]) + __popcll(w[W - 1] & ((1ull << (s - 64)) - 1ull));
     }
     // 1 + highest set bit (0 if empty)
-    __device__ __forceinline__ int top() const { return w[1] ? 128 - __clzll(w[1]) : (w[0] ? 64 - __clzll(w[0]) : 0); }
+    __device__ __forceinline__ int top() const
+    {
+        if (W == 1) return w[0] ? 64 - __clzll(w[0]) : 0;
+        return w[W - 1] ? 128 - __clzll(w[W - 1]) : (w[0] ? 64 - __clzll(w[0]) : 0);
+    }
+    __device__ __forceinline__ void clear()
+    {
+#pragma unroll
+        for (int i = 0; i < W; ++i) w[i] = 0;
+    }
+    __device__ __forceinline__ void or_bits(uint64_t bits, int sh)
+    {
+        if (W == 1) w[0] |= bits << sh;
+        else w[sh >> 6] |= bits << (sh & 63);
+    }
 };
 
-__device__ __forceinline__ Mask mask_and(Mask a, Mask b) { return {{a.w[0] & b.w[0], a.w[1] & b.w[1]}}; }
-__device__ __forceinline__ Mask mask_or(Mask a, Mask b) { return {{a.w[0] | b.w[0], a.w[1] | b.w[1]}}; }
-__device__ __forceinline__ Mask mask_not(Mask a, int cap)
-{
-    Mask m = {{~a.w[0], ~a.w[1]}};
-    if (cap < 128) m.w[1] &= cap > 64 ? ((1ull << (cap - 64)) - 1ull) : 0ull;
-    if (cap < 64) m.w[0] &= (1ull << cap) - 1ull;
-    return m;
-}
-// position of the i-th (0-based) set bit, or -1
-__device__ __forceinline__ int nth_set(Mask m, int i)
+template <int W>
+__device__ __forceinline__ MaskW<W> mask_and(MaskW<W> a, MaskW<W> b)
 {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        uint32_t lo = (uint32_t)m.w[h], hi = (uint32_t)(m.w[h] >> 32);
-        int cl = __popc(lo);
+    for (int i = 0; i < W; ++i) a.w[i] &= b.w[i];
+    return a;
+}
+template <int W>
+__device__ __forceinline__ MaskW<W> mask_or(MaskW<W> a, MaskW<W> b)
+{
+#pragma unroll
+    for (int i = 0; i < W; ++i) a.w[i] |= b.w[i];
+    return a;
+}
+template <int W>
+__device__ __forceinline__ MaskW<W> mask_not(MaskW<W> a, int cap)
+{
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        a.w[i] = ~a.w[i];
+        const int lim = cap - 64 * i;
+        if (lim <= 0) a.w[i] = 0;
+        else if (lim < 64) a.w[i] &= (1ull << lim) - 1ull;
+    }
+    return a;
+}
+// position of the i-th (0-based) set bit, or -1
+template <int W>
+__device__ __forceinline__ int nth_set(MaskW<W> m, int i)
+{
+#pragma unroll
+    for (int h = 0; h < W; ++h) {
+        const uint32_t lo = (uint32_t)m.w[h], hi = (uint32_t)(m.w[h] >> 32);
+        const int cl = __popc(lo);
         if (i < cl) return h * 64 + (int)__fns(lo, 0, i + 1);
         i -= cl;
-        int ch = __popc(hi);
+        const int ch = __popc(hi);
         if (i < ch) return h * 64 + 32 + (int)__fns(hi, 0, i + 1);
         i -= ch;
     }
     return -1;
 }
 // the first n set bits of m
-__device__ __forceinline__ Mask first_n(Mask m, int n)
+template <int W>
+__device__ __forceinline__ MaskW<W> first_n(MaskW<W> m, int n)
 {
-    if (n <= 0) return {{0ull, 0ull}};
-    int last = nth_set(m, n - 1);
-    Mask r = m;
-    if (last < 64) {
-        r.w[0] &= last == 63 ? ~0ull : ((1ull << (last + 1)) - 1ull);
-        r.w[1] = 0;
-    } else {
-        int l = last - 64;
-        r.w[1] &= l == 63 ? ~0ull : ((1ull << (l + 1)) - 1ull);
+    MaskW<W> r = m;
+    if (n <= 0) {
+        r.clear();
+        return r;
+    }
+    const int last = nth_set(m, n - 1);
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const int lim = last - 64 * i;  // keep bits <= lim in word i
+        if (lim < 0) r.w[i] = 0;
+        else if (lim < 63) r.w[i] &= (1ull << (lim + 1)) - 1ull;
     }
     return r;
 }
 // rows of lane gl whose slot (r*T + gl) is set in m
-template <int T, int VPL>
-__device__ __forceinline__ uint32_t lane_rows(Mask m, int gl)
+template <int T, int VPL, int W>
+__device__ __forceinline__ uint32_t lane_rows(MaskW<W> m, int gl)
 {
     uint32_t b = 0;
 #pragma unroll
     for (int r = 0; r < VPL; ++r) b |= (uint32_t)m.test(r * T + gl) << r;
     return b;
 }
+using Mask = MaskW<2>;
 
 // ---------------------------------------------------------------------------
 // group (T lanes of one warp) primitives
@@ -221,6 +284,8 @@ struct GroupSmem {
     uint8_t vid[VCAP][4];   // planes a, b, c (ccw from outside)
     uint8_t vadj[VCAP][4];  // neighbour across a&b, b&c, c&a
     uint8_t vsrc[VCAP];     // removed vertex whose cut edge created the slot (this clip)
+    uint16_t elist[VCAP];   // boundary edges of the current clip: slot | (edge << 8)
+    uint8_t dlist[VCAP];    // slot of the new vertex of each boundary edge
     union {
         struct {
             uint32_t start_of[PCAP];  // (stamp << 8) | slot
@@ -289,7 +354,7 @@ struct StateLayout {
 
 // FP64 re-decision of a sign test: the vertex re-solved from its planes
 template <typename S>
-__device__ __noinline__ bool outside64(const S& sm, int s, P64 h, const float4* __restrict__ sorted, float4 pi,
+__device__ VT_RARE bool outside64(const S& sm, int s, P64 h, const float4* __restrict__ sorted, float4 pi,
                                        GridDesc g, double fx, double fy, double fz, double R2)
 {
     const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
@@ -304,7 +369,7 @@ __device__ __noinline__ bool outside64(const S& sm, int s, P64 h, const float4* 
 
 // FP64 squared distance of slot s's vertex, re-solved from its planes
 template <typename S>
-__device__ __noinline__ double vertex_r2_64(const S& sm, int s, const float4* __restrict__ sorted, float4 pi,
+__device__ VT_RARE double vertex_r2_64(const S& sm, int s, const float4* __restrict__ sorted, float4 pi,
                                             GridDesc g, double fx, double fy, double fz)
 {
     const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
@@ -317,8 +382,8 @@ __device__ __noinline__ double vertex_r2_64(const S& sm, int s, const float4* __
 }
 
 // lowest plane id that no live vertex references (or -1)
-template <int T, typename S>
-__device__ __noinline__ int free_plane(const S& sm, Mask keep, int gl, unsigned gmask, int pcap, int vcap)
+template <int T, typename S, typename M>
+__device__ VT_RARE int free_plane(const S& sm, M keep, int gl, unsigned gmask, int pcap, int vcap)
 {
     uint64_t ref0 = 0, ref1 = 0;
     for (int s = gl; s < vcap; s += T) {
@@ -341,7 +406,7 @@ __device__ __noinline__ int free_plane(const S& sm, Mask keep, int gl, unsigned 
 // position of a new vertex by interpolation along its cut edge (the
 // pre-clip vertex positions are in sm.vpos)
 template <typename Real, typename S>
-__device__ __noinline__ void interp_vertex(const S& sm, int s, Real nx, Real ny, Real nz, Real b, Real* xyz)
+__device__ VT_RARE void interp_vertex(const S& sm, int s, Real nx, Real ny, Real nz, Real b, Real* xyz)
 {
     const int v = sm.vsrc[s], w = sm.vadj[s][0];
     const Real px = sm.vpos[v][0], py = sm.vpos[v][1], pz = sm.vpos[v][2];
@@ -362,9 +427,10 @@ struct Cell {
     static constexpr int VCAP = T * VPL;
     using S = GroupSmem<Real, VCAP, PCAP>;
     using SL = StateLayout<Real, VCAP, PCAP>;
+    using M = MaskW<(VCAP + 63) / 64>;
 
     Real vx[VPL], vy[VPL], vz[VPL];
-    Mask alive;       // group-uniform
+    M alive;          // group-uniform
     int np;           // planes in use (ids < np)
     int rows;         // register rows holding live slots
     uint32_t stamp;   // clip counter for the ring tables (keeps counting across cells)
@@ -400,6 +466,29 @@ struct Cell {
         R2 = G.max(m);
     }
 
+    // axis-aligned bounding box of the live vertices (local frame), for the
+    // exhaustive walk's support test
+    __device__ __forceinline__ void bbox(const Group<T>& G, float* lo3, float* hi3) const
+    {
+        float l0 = FLT_MAX, l1 = FLT_MAX, l2 = FLT_MAX, h0 = -FLT_MAX, h1 = -FLT_MAX, h2 = -FLT_MAX;
+#pragma unroll
+        for (int r = 0; r < VPL; ++r) {
+            if (r < rows && alive.test(r * T + G.gl)) {
+                l0 = fminf(l0, (float)vx[r]); h0 = fmaxf(h0, (float)vx[r]);
+                l1 = fminf(l1, (float)vy[r]); h1 = fmaxf(h1, (float)vy[r]);
+                l2 = fminf(l2, (float)vz[r]); h2 = fmaxf(h2, (float)vz[r]);
+            }
+        }
+#pragma unroll
+        for (int o = T / 2; o >= 1; o >>= 1) {
+            l0 = fminf(l0, __shfl_xor_sync(G.mask, l0, o, T)); h0 = fmaxf(h0, __shfl_xor_sync(G.mask, h0, o, T));
+            l1 = fminf(l1, __shfl_xor_sync(G.mask, l1, o, T)); h1 = fmaxf(h1, __shfl_xor_sync(G.mask, h1, o, T));
+            l2 = fminf(l2, __shfl_xor_sync(G.mask, l2, o, T)); h2 = fmaxf(h2, __shfl_xor_sync(G.mask, h2, o, T));
+        }
+        lo3[0] = l0; lo3[1] = l1; lo3[2] = l2;
+        hi3[0] = h0; hi3[1] = h1; hi3[2] = h2;
+    }
+
     // the box [lo, hi) in the frame of pi: walls 0..5, corners in slots 0..7
     __device__ __forceinline__ void init_box(const Group<T>& G, S& sm, const GridDesc& grid)
     {
@@ -428,8 +517,8 @@ struct Cell {
             const uint32_t a0 = c ^ (4 >> (p2 >> 1)), a1 = c ^ (4 >> (p0 >> 1)), a2 = c ^ (4 >> (p1 >> 1));
             *reinterpret_cast<uint32_t*>(sm.vadj[c]) = a0 | (a1 << 8) | (a2 << 16);
         }
+        alive.clear();
         alive.w[0] = 0xffull;
-        alive.w[1] = 0;
         np = 6;
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
@@ -473,7 +562,7 @@ struct Cell {
         if (G.gl == 0) {
             StateHdr* h = reinterpret_cast<StateHdr*>(st);
             h->alive[0] = alive.w[0];
-            h->alive[1] = alive.w[1];
+            h->alive[1] = M::W_ == 2 ? alive.w[M::W_ - 1] : 0ull;
             h->np = np;
             h->last_orig = last_orig;
             h->R2 = (double)R2;
@@ -486,7 +575,7 @@ struct Cell {
     {
         const StateHdr* h = reinterpret_cast<const StateHdr*>(st);
         alive.w[0] = h->alive[0];
-        alive.w[1] = h->alive[1];
+        if (M::W_ == 2) alive.w[M::W_ - 1] = h->alive[1];
         np = h->np;
         R2 = (Real)h->R2;
         last_d2 = h->last_d2;
@@ -544,7 +633,8 @@ struct Cell {
     __device__ __forceinline__ int clip(const Group<T>& G, S& sm, Real nx, Real ny, Real nz, Real b, int src,
                                         const float4* __restrict__ sorted, const GridDesc& grid, DevStatus* st)
     {
-        Mask out = {{0ull, 0ull}};
+        M out;
+        out.clear();
         uint32_t myout = 0, mynear = 0;
         const double tol2 = Tol<Real>::fp32 ? 0.0 : ON_PLANE_REL2 * 2.0 * (double)b * (double)R2;
         const float near2 = Tol<Real>::fp32 ? 2e-12f * (float)b * (float)R2 : 0.0f;
@@ -562,9 +652,7 @@ struct Cell {
                     o = al && sv > (Real)0 && (double)sv * (double)sv > tol2;
                 }
                 myout |= (uint32_t)o << r;
-                const uint64_t bits = G.ballot(o);
-                const int sh = r * T;
-                out.w[sh >> 6] |= bits << (sh & 63);
+                out.or_bits((uint64_t)G.ballot(o), r * T);
             }
         }
         if (Tol<Real>::fp32 && G.any(mynear != 0)) {
@@ -579,18 +667,13 @@ struct Cell {
                 myout = o ? (myout | (1u << r)) : (myout & ~(1u << r));
                 atomicAdd(&st->fp64_rechecks, 1ull);
             }
-            out.w[0] = out.w[1] = 0;
+            out.clear();
 #pragma unroll
-            for (int r = 0; r < VPL; ++r) {
-                if (r < rows) {
-                    const uint64_t bits = G.ballot((myout >> r) & 1u);
-                    const int sh = r * T;
-                    out.w[sh >> 6] |= bits << (sh & 63);
-                }
-            }
+            for (int r = 0; r < VPL; ++r)
+                if (r < rows) out.or_bits((uint64_t)G.ballot((myout >> r) & 1u), r * T);
         }
         if (out.none()) return CLIP_NONE;
-        const Mask keep = mask_and(alive, mask_not(out, 128));
+        const M keep = mask_and(alive, mask_not(out, VCAP));
         if (keep.none()) {  // the generator itself is always inside
             if (G.gl == 0) atomicAdd(&st->detail[0], 1u);
             return CLIP_INCONSISTENT;
@@ -604,47 +687,28 @@ struct Cell {
                 return CLIP_OVERFLOW;
             }
         }
-        // boundary edges of the removed patch
-        int mycnt = 0;
+        // boundary edges of the removed patch: edge e of a removed vertex whose
+        // neighbour across it survives (bit 3r+e of myedge)
+        uint32_t myedge = 0;
         for (uint32_t m = myout; m; m &= m - 1) {
-            const int s = (__ffs(m) - 1) * T + G.gl;
-            const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
-            mycnt += (int)!out.test(adj & 0xff) + (int)!out.test((adj >> 8) & 0xff) + (int)!out.test((adj >> 16) & 0xff);
+            const int r = __ffs(m) - 1;
+            const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[r * T + G.gl]);
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+                if (!out.test((adj >> (8 * e)) & 0xff)) myedge |= 1u << (3 * r + e);
         }
         int total;
-        const int first = G.scan(mycnt, total);
+        int idx = G.scan(__popc(myedge), total);
         // new vertices go to slots that were free before this clip, so the
         // removed vertices' topology stays readable until the ring is closed
-        const Mask freem = mask_not(alive, VCAP);
+        const M freem = mask_not(alive, VCAP);
         if (total > freem.count()) {
             if (G.gl == 0) atomicAdd(&st->detail[2], 1u);
             return CLIP_OVERFLOW;
         }
-        const Mask newm = first_n(freem, total);
-        ++stamp;
-        const uint32_t tag = stamp << 8;
-        // new vertices: topology and ring tables
-        int idx = first;
-        for (uint32_t m = myout; m; m &= m - 1) {
-            const int s = (__ffs(m) - 1) * T + G.gl;
-            const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-            const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
-            for (int e = 0; e < 3; ++e) {
-                const int w = (adj >> (8 * e)) & 0xff;
-                if (out.test(w)) continue;
-                const int d = nth_set(freem, idx++);
-                const int x = (ids >> (8 * e)) & 0xff, y = (ids >> (8 * (e == 2 ? 0 : e + 1))) & 0xff;
-                *reinterpret_cast<uint32_t*>(sm.vid[d]) = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)h << 16);
-                sm.vadj[d][0] = (uint8_t)w;
-                sm.vsrc[d] = (uint8_t)s;
-                sm.u.ring.start_of[x] = tag | (uint32_t)d;
-                sm.u.ring.end_of[y] = tag | (uint32_t)d;
-                // the survivor w: its link across y&x now points to d
-                const uint32_t wid = *reinterpret_cast<const uint32_t*>(sm.vid[w]);
-                const int w0 = wid & 0xff, w1 = (wid >> 8) & 0xff;
-                const int e2 = (w0 == y && w1 == x) ? 0 : ((w1 == y) ? 1 : 2);
-                sm.vadj[w][e2] = (uint8_t)d;
-            }
+        for (uint32_t m = myedge; m; m &= m - 1) {
+            const int bit = __ffs(m) - 1, r = bit / 3, e = bit - 3 * r;
+            sm.elist[idx++] = (uint16_t)((r * T + G.gl) | (e << 8));
         }
         if (G.gl == 0) {
             sm.pnx[h] = nx;
@@ -653,70 +717,95 @@ struct Cell {
             sm.pb[h] = b;
             sm.psrc[h] = src;
         }
+        ++stamp;
+        const uint32_t tag = stamp << 8;
         G.sync();
-        // close the ring around h
-        bool bad = false;
-        idx = first;
-        for (uint32_t m = myout; m; m &= m - 1) {
-            const int s = (__ffs(m) - 1) * T + G.gl;
+        // one boundary edge per lane: the new vertex (x, y, h) on the cut edge
+        for (int i = G.gl; i < total; i += T) {
+            const uint32_t ev = sm.elist[i];
+            const int s = ev & 0xff, e = ev >> 8;
             const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-            const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
-            for (int e = 0; e < 3; ++e) {
-                const int w = (adj >> (8 * e)) & 0xff;
-                if (out.test(w)) continue;
-                const int d = nth_set(freem, idx++);
-                const int x = (ids >> (8 * e)) & 0xff, y = (ids >> (8 * (e == 2 ? 0 : e + 1))) & 0xff;
-                const uint32_t so = sm.u.ring.start_of[y], eo = sm.u.ring.end_of[x];
-                if ((so & ~0xffu) != tag || (eo & ~0xffu) != tag || sm.u.ring.start_of[x] != (tag | (uint32_t)d))
-                    bad = true;
-                sm.vadj[d][1] = (uint8_t)(so & 0xff);
-                sm.vadj[d][2] = (uint8_t)(eo & 0xff);
+            const int w = sm.vadj[s][e];
+            const int x = (ids >> (8 * e)) & 0xff, y = (ids >> (8 * (e == 2 ? 0 : e + 1))) & 0xff;
+            const int d = nth_set(freem, i);
+            sm.dlist[i] = (uint8_t)d;
+            *reinterpret_cast<uint32_t*>(sm.vid[d]) = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)h << 16);
+            sm.vadj[d][0] = (uint8_t)w;
+            sm.vsrc[d] = (uint8_t)s;
+            sm.u.ring.start_of[x] = tag | (uint32_t)d;
+            sm.u.ring.end_of[y] = tag | (uint32_t)d;
+            // the survivor w: its link across y&x now points to d
+            const uint32_t wid = *reinterpret_cast<const uint32_t*>(sm.vid[w]);
+            const int w0 = wid & 0xff, w1 = (wid >> 8) & 0xff;
+            const int e2 = (w0 == y && w1 == x) ? 0 : ((w1 == y) ? 1 : 2);
+            sm.vadj[w][e2] = (uint8_t)d;
+        }
+        G.sync();
+        // close the ring around h and solve the new positions
+        bool bad = false, need = false;
+        for (int i = G.gl; i < total; i += T) {
+            const int d = sm.dlist[i];
+            const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[d]);
+            const int x = ids & 0xff, y = (ids >> 8) & 0xff;
+            const uint32_t so = sm.u.ring.start_of[y], eo = sm.u.ring.end_of[x];
+            if ((so & ~0xffu) != tag || (eo & ~0xffu) != tag || sm.u.ring.start_of[x] != (tag | (uint32_t)d))
+                bad = true;
+            sm.vadj[d][1] = (uint8_t)(so & 0xff);
+            sm.vadj[d][2] = (uint8_t)(eo & 0xff);
+            Real px, py, pz;
+            if (solve3<Real>(sm.pnx[x], sm.pny[x], sm.pnz[x], sm.pb[x], sm.pnx[y], sm.pny[y], sm.pnz[y], sm.pb[y], nx,
+                             ny, nz, b, px, py, pz, (Real)Tol<Real>::cond_rel)) {
+                sm.vpos[d][0] = px;
+                sm.vpos[d][1] = py;
+                sm.vpos[d][2] = pz;
+            } else {
+                sm.vpos[d][0] = (Real)NAN;  // marks an interpolated vertex
+                need = true;
             }
         }
         if (G.any(bad)) {
             if (G.gl == 0) atomicAdd(&st->detail[3], 1u);
             return CLIP_INCONSISTENT;
         }
-        if (h == np) ++np;
-        const Mask before = alive;
-        const int rows_before = rows;
-        alive = mask_or(keep, newm);
-        update_rows();
-        G.sync();
-        // positions of the new vertices, solved from their planes by the owners;
-        // an ill-conditioned solve falls back to interpolation along the cut edge
-        uint32_t need = 0;
-        for (uint32_t m = lane_rows<T, VPL>(newm, G.gl); m; m &= m - 1) {
-            const int r = __ffs(m) - 1;
-            const int s = r * T + G.gl;
-            const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-            const int a = ids & 0xff, bb = (ids >> 8) & 0xff, c = (ids >> 16) & 0xff;
-            Real x, y, z;
-            if (solve3<Real>(sm.pnx[a], sm.pny[a], sm.pnz[a], sm.pb[a], sm.pnx[bb], sm.pny[bb], sm.pnz[bb], sm.pb[bb],
-                             sm.pnx[c], sm.pny[c], sm.pnz[c], sm.pb[c], x, y, z, (Real)Tol<Real>::cond_rel))
-                set_row(r, x, y, z);
-            else
-                need |= 1u << r;
-        }
-        if (G.any(need != 0)) {
+        if (G.any(need)) {
+            // ill-conditioned solves: interpolate along the cut edge from the
+            // pre-clip positions (the new slots were free, so no overlap)
             if (G.gl == 0) atomicAdd(&st->detail[4], 1u);
 #pragma unroll
             for (int r = 0; r < VPL; ++r) {
                 const int s = r * T + G.gl;
-                if (r < rows_before && before.test(s)) {
+                if (r < rows && alive.test(s)) {
                     sm.vpos[s][0] = vx[r];
                     sm.vpos[s][1] = vy[r];
                     sm.vpos[s][2] = vz[r];
                 }
             }
             G.sync();
-            for (uint32_t m = need; m; m &= m - 1) {
-                const int r = __ffs(m) - 1;
-                Real xyz[3];
-                interp_vertex<Real>(sm, r * T + G.gl, nx, ny, nz, b, xyz);
-                set_row(r, xyz[0], xyz[1], xyz[2]);
+            for (int i = G.gl; i < total; i += T) {
+                const int d = sm.dlist[i];
+                if (isnan(sm.vpos[d][0])) {
+                    Real xyz[3];
+                    interp_vertex<Real>(sm, d, nx, ny, nz, b, xyz);
+                    sm.vpos[d][0] = xyz[0];
+                    sm.vpos[d][1] = xyz[1];
+                    sm.vpos[d][2] = xyz[2];
+                }
             }
-            G.sync();
+        }
+        if (h == np) ++np;
+        const M newm = first_n(freem, total);
+        alive = mask_or(keep, newm);
+        update_rows();
+        G.sync();
+        // owners take the new positions into their registers
+#pragma unroll
+        for (int r = 0; r < VPL; ++r) {
+            const int s = r * T + G.gl;
+            if (r < rows && newm.test(s)) {
+                vx[r] = sm.vpos[s][0];
+                vy[r] = sm.vpos[s][1];
+                vz[r] = sm.vpos[s][2];
+            }
         }
         update_r2(G);
         return CLIP_CUT;
@@ -756,8 +845,8 @@ struct Cell {
 // ---------------------------------------------------------------------------
 // moments, neighbours and geometry of a validated cell (shared memory only)
 // ---------------------------------------------------------------------------
-template <typename Real, int T, int VCAP, int PCAP>
-__device__ __noinline__ void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, Mask alive, int np, float4 pi, int gl,
+template <typename Real, int T, int VCAP, int PCAP, typename M>
+__device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, int np, float4 pi, int gl,
                                          unsigned gmask, int64_t out_idx, const ClipArgs& A)
 {
     for (int f = gl; f < np; f += T) {
@@ -923,26 +1012,31 @@ __device__ __noinline__ void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, Mask a
     __syncwarp(gmask);
 }
 
-// one candidate range [a, b) of sorted points for the exhaustive walk: every
-// generator that can still cut the cell (4 R^2 > d^2) and that the resumed
-// list did not already process is clipped
+// one candidate range [a, b) of sorted points for the exhaustive walk. A
+// generator q can cut the cell only if 4 R^2 > |q - p|^2 and its bisector
+// n.x <= b (n = q - p, b = |n|^2 / 2) reaches beyond the cell's bounding box
+// (sum_i max(n_i lo_i, n_i hi_i) > b); both tests run on every lane in float
+// with margins that only admit extra candidates, and the survivors are clipped
+// one at a time. Generators a resumed list already processed are skipped.
 template <typename Real, int T, int VPL, int PCAP>
 __device__ __forceinline__ int exhaustive_range(Cell<Real, T, VPL, PCAP>& cell, const Group<T>& G,
                                                 typename Cell<Real, T, VPL, PCAP>::S& sm, const ClipArgs& A, int a,
-                                                int b, int q, double last_d2, int last_orig)
+                                                int b, int q, double last_d2, int last_orig, float* lo3, float* hi3)
 {
     const float4 pq = cell.pi;
     for (int b0 = a; b0 < b; b0 += T) {
         const int jj = b0 + G.gl;
         float4 pc = make_float4(0.f, 0.f, 0.f, 0.f);
-        double d2 = 0.0;
         bool need = false;
         if (jj < b && jj != q) {
             pc = A.sorted[jj];
-            const double ex = (double)pc.x - (double)pq.x, ey = (double)pc.y - (double)pq.y,
-                         ez = (double)pc.z - (double)pq.z;
-            d2 = (ex * ex + ey * ey) + ez * ez;
-            need = 4.0 * (double)cell.R2 * (1.0 + 1e-5) > d2;
+            const float ex = pc.x - pq.x, ey = pc.y - pq.y, ez = pc.z - pq.z;
+            const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+            const float r4 = 4.0f * (float)cell.R2;
+            const float hb = fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) +
+                             fmaxf(ez * lo3[2], ez * hi3[2]);
+            need = r4 * (1.0f + 1e-4f) > d2 &&
+                   hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f;
             if (need && last_orig >= 0) {  // already processed from the list?
                 const double kd = Tol<Real>::fp32 ? (double)knn_d2_f32(pq, pc) : knn_d2_f64(pq, pc);
                 const int ko = __float_as_int(pc.w);
@@ -953,17 +1047,24 @@ __device__ __forceinline__ int exhaustive_range(Cell<Real, T, VPL, PCAP>& cell, 
         while (mm) {
             const int src = __ffs(mm) - 1;
             mm &= mm - 1;
-            const double bd2 = G.bcast(d2, src);
-            if (!(4.0 * (double)cell.R2 * (1.0 + 1e-5) > bd2)) continue;
-            const int j = G.bcast(jj, src);
             float4 p;
             p.x = G.bcast(pc.x, src);
             p.y = G.bcast(pc.y, src);
             p.z = G.bcast(pc.z, src);
             p.w = 0.f;
+            const int j = G.bcast(jj, src);
+            // re-test against the current (smaller) cell
+            const float ex = p.x - pq.x, ey = p.y - pq.y, ez = p.z - pq.z;
+            const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+            const float hb = fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) +
+                             fmaxf(ez * lo3[2], ez * hi3[2]);
+            if (!(4.0f * (float)cell.R2 * (1.0f + 1e-4f) > d2 &&
+                  hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f))
+                continue;
             const int r = cell.clip_point(G, sm, p, j, A.sorted, A.g, A.st);
             if (r == CLIP_OVERFLOW) return END_OVERFLOW;
             if (r == CLIP_INCONSISTENT) return END_INCONSISTENT;
+            if (r == CLIP_CUT) cell.bbox(G, lo3, hi3);
         }
     }
     return 0;
@@ -973,9 +1074,12 @@ __device__ __forceinline__ int exhaustive_range(Cell<Real, T, VPL, PCAP>& cell, 
 // kernels: list mode (k > 0) and exhaustive mode (k == 0)
 // ---------------------------------------------------------------------------
 constexpr int CLIP_BLOCK = 128;
+#ifndef VT_CLIP_MINB
+#define VT_CLIP_MINB 4  // resident blocks per SM the register budget aims for
+#endif
 
 template <typename Real, int T, int VPL, int PCAP, bool ROBUST, bool EXH>
-__global__ void __launch_bounds__(CLIP_BLOCK, 4) k_clip(ClipArgs A)
+__global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(ClipArgs A)
 {
     using C = Cell<Real, T, VPL, PCAP>;
     using S = typename C::S;
@@ -1047,6 +1151,8 @@ __global__ void __launch_bounds__(CLIP_BLOCK, 4) k_clip(ClipArgs A)
             const int ix = cell_coord(pq.x, A.g.lo[0], A.g.scale[0], Gr);
             const int iy = cell_coord(pq.y, A.g.lo[1], A.g.scale[1], Gr);
             const int iz = cell_coord(pq.z, A.g.lo[2], A.g.scale[2], Gr);
+            float lo3[3], hi3[3];
+            cell.bbox(G, lo3, hi3);
             int status = 0;
             for (int s = 0; status == 0; ++s) {
                 for (int dx = -s; dx <= s && status == 0; ++dx) {
@@ -1058,17 +1164,17 @@ __global__ void __launch_bounds__(CLIP_BLOCK, 4) k_clip(ClipArgs A)
                         if (dx == -s || dx == s || dy == -s || dy == s) {
                             const int z0 = max(iz - s, 0), z1 = min(iz + s, Gr - 1);
                             status = exhaustive_range(cell, G, sm, A, A.cell_off[cell_id(x, y, z0, Gr)],
-                                                      A.cell_off[cell_id(x, y, z1, Gr) + 1], q, last_d2, last_orig);
+                                                      A.cell_off[cell_id(x, y, z1, Gr) + 1], q, last_d2, last_orig, lo3, hi3);
                         } else {
                             if (iz - s >= 0) {
                                 const int cc = cell_id(x, y, iz - s, Gr);
                                 status = exhaustive_range(cell, G, sm, A, A.cell_off[cc], A.cell_off[cc + 1], q,
-                                                          last_d2, last_orig);
+                                                          last_d2, last_orig, lo3, hi3);
                             }
                             if (status == 0 && iz + s < Gr) {
                                 const int cc = cell_id(x, y, iz + s, Gr);
                                 status = exhaustive_range(cell, G, sm, A, A.cell_off[cc], A.cell_off[cc + 1], q,
-                                                          last_d2, last_orig);
+                                                          last_d2, last_orig, lo3, hi3);
                             }
                         }
                     }
@@ -1093,7 +1199,8 @@ __global__ void __launch_bounds__(CLIP_BLOCK, 4) k_clip(ClipArgs A)
         if (end == END_VALID) {
             cell.dump_positions(G, sm);
             G.sync();
-            finish_cell<Real, T, T * VPL, PCAP>(sm, cell.alive, cell.np, cell.pi, G.gl, G.mask, out_idx, A);
+            finish_cell<Real, T, T * VPL, PCAP, typename C::M>(sm, cell.alive, cell.np, cell.pi, G.gl, G.mask, out_idx,
+                                                               A);
         } else {
             if (end == END_NEED_K && !EXH && !ROBUST && A.state) cell.save(G, sm, stp, last_d2, last_orig);
             if (G.gl == 0) {

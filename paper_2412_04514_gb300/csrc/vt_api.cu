@@ -151,6 +151,8 @@ struct StageTimer {
     bool on = false;
     cudaStream_t s = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
+    std::vector<int> clip_pass;  // pass index of each CLIP event pair
+    int pass = 0;
     int open_stage = -1;
     void begin(int stage)
     {
@@ -160,7 +162,16 @@ struct StageTimer {
         cudaEventCreate(&b);
         cudaEventRecord(a, s);
         ev[stage].push_back({a, b});
+        if (stage == CLIP) clip_pass.push_back(pass);
         open_stage = stage;
+    }
+    void per_pass(double* out, int n)
+    {
+        for (size_t i = 0; i < ev[CLIP].size(); ++i) {
+            float ms = 0;
+            if (clip_pass[i] < n && cudaEventElapsedTime(&ms, ev[CLIP][i].first, ev[CLIP][i].second) == cudaSuccess)
+                out[clip_pass[i]] += ms;
+        }
     }
     void end()
     {
@@ -539,6 +550,7 @@ int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cells_out*
             S.k_of_pass[S.passes] = kk;
             S.cells_of_pass[S.passes] = m_reg + m_rob;
         }
+        timer.pass = S.passes;
         ++S.passes;
         if (exhaustive) S.exhaustive_cells = m_reg + m_rob;
         int64_t got_next = 0, got_rob = 0;
@@ -601,6 +613,7 @@ int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cells_out*
         S.ms_knn = timer.total(StageTimer::KNN);
         S.ms_clip = timer.total(StageTimer::CLIP);
         S.ms_emit = timer.total(StageTimer::EMIT);
+        timer.per_pass(S.ms_clip_pass, VT_MAX_PASSES);
     }
     if (stats) *stats = S;
     if (n_unval > 0) return fail(VT_ERR_UNVALIDATED, "%lld cells could not be validated", (long long)n_unval);
