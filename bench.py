@@ -30,7 +30,7 @@ METRIC = "Voronoi cells/sec at 1M & 8M pts, 1 GB300: FP32+FP64-recheck vs plain 
 WORKLOADS = {
     "mixed-1m": dict(n=1 << 20, seed=1, desc="1,048,576 float32 points in [0,1)^3: 524,288 uniform + 524,288 in "
                      "1,000 isotropic Gaussian clumps (centres uniform, sigma log-uniform in [1e-3,1e-2], "
-                     "out-of-box draws resampled), seed 1; k0=16 with doubling to 256 then the exhaustive pass; "
+                     "out-of-box draws resampled), seed 1; k0=16 with doubling to k_max then the exhaustive pass; "
                      "outputs neighbours (CSR, original ids) + volume + centroid + full geometry"),
     "mixed-8m": dict(n=1 << 23, seed=2, desc="8,388,608 float32 points, same recipe as mixed-1m, seed 2"),
 }
@@ -221,8 +221,8 @@ def run_gpu(args, rank: int, world: int, local: int):
         return ms, stats, launches, cells
 
     # warm up both forms, then time: FP32+recheck (headline) and plain FP64
-    p32 = vt.Params(precision="fp32", emit=emit)
-    p64 = vt.Params(precision="fp64", emit=emit)
+    p32 = vt.Params(precision="fp32", k0=16, k_max=args.k_max, threads_per_cell=32, emit=emit)
+    p64 = vt.Params(precision="fp64", k0=16, k_max=args.k_max, threads_per_cell=32, emit=emit)
     with Clocks(local) as clk:
         ms32, st32, launches32, cells = timed(p32, args.steps, args.warmup, stage_times=True)
     clocks = clk.summary()
@@ -265,7 +265,7 @@ def run_gpu(args, rank: int, world: int, local: int):
     clip_launches = statistics.mean(s["clip_launches"] for s in st32)
     achieved = n * flops_per_cell / (stage["ms_clip"] / 1e3) / 1e12
     roofline = {
-        "kernel": "k_clip<float,8,8,64> (all re-queue passes of one step)",
+        "kernel": "k_clip<float,32,2,64> (all passes of one step)",
         "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (unit counts and max SM clock)",
@@ -310,6 +310,7 @@ def main():
     ap.add_argument("--ref-cells", type=int, default=20_000)
     ap.add_argument("--flops-per-cell", type=float, default=25134.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--k-max", type=int, default=32)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

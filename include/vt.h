@@ -75,10 +75,11 @@ enum {
 
 typedef struct vt_params {
     int k0;                 /* initial k of the neighbour lists (default 16) */
-    int k_max;              /* largest k of the doubling passes, <= 256 (default 256) */
+    int k_max;              /* largest k of the doubling passes, <= 256 (default 32; the exhaustive
+                               pass that follows finishes every remaining cell exactly) */
     float grid_density;     /* target generators per grid cell rho; G = ceil(cbrt(n / rho)) (default 2) */
     int grid_res;           /* G override per axis (0 = derive from grid_density) */
-    int threads_per_cell;   /* lanes cooperating on one cell: 8, 16 or 32 (0 = default 8) */
+    int threads_per_cell;   /* lanes cooperating on one cell: 8, 16 or 32 (0 = default 32) */
     int precision;          /* VT_FP64 or VT_FP32_RECHECK */
     int emit;               /* VT_EMIT_* bitmask */
     int index_space;        /* VT_INDEX_ORIGINAL (default) or VT_INDEX_SORTED */

@@ -24,7 +24,7 @@ class Params:
     clipping with FP64 rechecks) or ``"fp64"`` (plain FP64)."""
 
     k0: int = 16
-    k_max: int = 256
+    k_max: int = 32
     grid_density: float = 2.0
     grid_res: int = 0
     threads_per_cell: int = 0

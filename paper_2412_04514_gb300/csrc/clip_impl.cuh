@@ -1019,53 +1019,50 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
 // with margins that only admit extra candidates, and the survivors are clipped
 // one at a time. Generators a resumed list already processed are skipped.
 template <typename Real, int T, int VPL, int PCAP>
-__device__ __forceinline__ int exhaustive_range(Cell<Real, T, VPL, PCAP>& cell, const Group<T>& G,
-                                                typename Cell<Real, T, VPL, PCAP>::S& sm, const ClipArgs& A, int a,
-                                                int b, int q, double last_d2, int last_orig, float* lo3, float* hi3)
+__device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, const Group<T>& G,
+                                                typename Cell<Real, T, VPL, PCAP>::S& sm, const ClipArgs& A, bool valid,
+                                                int jj, double last_d2, int last_orig, float* lo3, float* hi3)
 {
     const float4 pq = cell.pi;
-    for (int b0 = a; b0 < b; b0 += T) {
-        const int jj = b0 + G.gl;
-        float4 pc = make_float4(0.f, 0.f, 0.f, 0.f);
-        bool need = false;
-        if (jj < b && jj != q) {
-            pc = A.sorted[jj];
-            const float ex = pc.x - pq.x, ey = pc.y - pq.y, ez = pc.z - pq.z;
-            const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-            const float r4 = 4.0f * (float)cell.R2;
-            const float hb = fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) +
-                             fmaxf(ez * lo3[2], ez * hi3[2]);
-            need = r4 * (1.0f + 1e-4f) > d2 &&
-                   hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f;
-            if (need && last_orig >= 0) {  // already processed from the list?
-                const double kd = Tol<Real>::fp32 ? (double)knn_d2_f32(pq, pc) : knn_d2_f64(pq, pc);
-                const int ko = __float_as_int(pc.w);
-                if (kd < last_d2 || (kd == last_d2 && ko <= last_orig)) need = false;
-            }
+    float4 pc = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool need = false;
+    if (valid) {
+        pc = A.sorted[jj];
+        const float ex = pc.x - pq.x, ey = pc.y - pq.y, ez = pc.z - pq.z;
+        const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+        const float r4 = 4.0f * (float)cell.R2;
+        const float hb =
+            fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) + fmaxf(ez * lo3[2], ez * hi3[2]);
+        need = r4 * (1.0f + 1e-4f) > d2 &&
+               hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f;
+        if (need && last_orig >= 0) {  // already processed from the list?
+            const double kd = Tol<Real>::fp32 ? (double)knn_d2_f32(pq, pc) : knn_d2_f64(pq, pc);
+            const int ko = __float_as_int(pc.w);
+            if (kd < last_d2 || (kd == last_d2 && ko <= last_orig)) need = false;
         }
-        unsigned mm = G.ballot(need);
-        while (mm) {
-            const int src = __ffs(mm) - 1;
-            mm &= mm - 1;
-            float4 p;
-            p.x = G.bcast(pc.x, src);
-            p.y = G.bcast(pc.y, src);
-            p.z = G.bcast(pc.z, src);
-            p.w = 0.f;
-            const int j = G.bcast(jj, src);
-            // re-test against the current (smaller) cell
-            const float ex = p.x - pq.x, ey = p.y - pq.y, ez = p.z - pq.z;
-            const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-            const float hb = fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) +
-                             fmaxf(ez * lo3[2], ez * hi3[2]);
-            if (!(4.0f * (float)cell.R2 * (1.0f + 1e-4f) > d2 &&
-                  hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f))
-                continue;
-            const int r = cell.clip_point(G, sm, p, j, A.sorted, A.g, A.st);
-            if (r == CLIP_OVERFLOW) return END_OVERFLOW;
-            if (r == CLIP_INCONSISTENT) return END_INCONSISTENT;
-            if (r == CLIP_CUT) cell.bbox(G, lo3, hi3);
-        }
+    }
+    unsigned mm = G.ballot(need);
+    while (mm) {
+        const int src = __ffs(mm) - 1;
+        mm &= mm - 1;
+        float4 p;
+        p.x = G.bcast(pc.x, src);
+        p.y = G.bcast(pc.y, src);
+        p.z = G.bcast(pc.z, src);
+        p.w = 0.f;
+        const int j = G.bcast(jj, src);
+        // re-test against the current (smaller) cell
+        const float ex = p.x - pq.x, ey = p.y - pq.y, ez = p.z - pq.z;
+        const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+        const float hb =
+            fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) + fmaxf(ez * lo3[2], ez * hi3[2]);
+        if (!(4.0f * (float)cell.R2 * (1.0f + 1e-4f) > d2 &&
+              hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f))
+            continue;
+        const int r = cell.clip_point(G, sm, p, j, A.sorted, A.g, A.st);
+        if (r == CLIP_OVERFLOW) return END_OVERFLOW;
+        if (r == CLIP_INCONSISTENT) return END_INCONSISTENT;
+        if (r == CLIP_CUT) cell.bbox(G, lo3, hi3);
     }
     return 0;
 }
@@ -1155,28 +1152,24 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(ClipArgs A)
             cell.bbox(G, lo3, hi3);
             int status = 0;
             for (int s = 0; status == 0; ++s) {
-                for (int dx = -s; dx <= s && status == 0; ++dx) {
-                    const int x = ix + dx;
-                    if (x < 0 || x >= Gr) continue;
-                    for (int dy = -s; dy <= s && status == 0; ++dy) {
-                        const int y = iy + dy;
-                        if (y < 0 || y >= Gr) continue;
-                        if (dx == -s || dx == s || dy == -s || dy == s) {
-                            const int z0 = max(iz - s, 0), z1 = min(iz + s, Gr - 1);
-                            status = exhaustive_range(cell, G, sm, A, A.cell_off[cell_id(x, y, z0, Gr)],
-                                                      A.cell_off[cell_id(x, y, z1, Gr) + 1], q, last_d2, last_orig, lo3, hi3);
-                        } else {
-                            if (iz - s >= 0) {
-                                const int cc = cell_id(x, y, iz - s, Gr);
-                                status = exhaustive_range(cell, G, sm, A, A.cell_off[cc], A.cell_off[cc + 1], q,
-                                                          last_d2, last_orig, lo3, hi3);
-                            }
-                            if (status == 0 && iz + s < Gr) {
-                                const int cc = cell_id(x, y, iz + s, Gr);
-                                status = exhaustive_range(cell, G, sm, A, A.cell_off[cc], A.cell_off[cc + 1], q,
-                                                          last_d2, last_orig, lo3, hi3);
-                            }
-                        }
+                // the shell's segments, T at a time, candidates spread over the lanes
+                const int nseg = 2 * (2 * s + 1) * (2 * s + 1);
+                for (int e0 = 0; e0 < nseg && status == 0; e0 += T) {
+                    int sa = 0, sb = 0;
+                    if (e0 + G.gl < nseg) shell_segment(e0 + G.gl, s, ix, iy, iz, Gr, A.cell_off, sa, sb);
+                    const int len = sb - sa;
+                    int total;
+                    const int start = G.scan(len, total);
+                    const int incl = start + len;
+                    for (int c0 = 0; c0 < total && status == 0; c0 += T) {
+                        const int i = c0 + G.gl;
+                        int seg = 0;  // segments ending at or before i
+#pragma unroll
+                        for (int step = T / 2; step >= 1; step >>= 1)
+                            if (G.bcast(incl, (seg + step - 1) & (T - 1)) <= i) seg += step;
+                        const int aj = G.bcast(sa, seg & (T - 1)), sj = G.bcast(start, seg & (T - 1));
+                        const int jj = aj + (i - sj);
+                        status = exhaustive_batch(cell, G, sm, A, i < total && jj != q, jj, last_d2, last_orig, lo3, hi3);
                     }
                 }
                 if (status) break;

@@ -17,7 +17,7 @@ size_t clip_state_bytes(int precision)
 cudaError_t launch_clip(const ClipArgs& a, int variant, int threads_per_cell, cudaStream_t s)
 {
     if (a.nq <= 0) return cudaSuccess;
-    const int t = threads_per_cell == 0 ? 8 : threads_per_cell;
+    const int t = threads_per_cell == 0 ? 32 : threads_per_cell;
     if (variant == 2) return launch_variant<double, 32, 4, 128, true>(a, s);
     if (variant == 0) return launch_clip_f32(a, t, s);
     return launch_clip_f64(a, t, s);

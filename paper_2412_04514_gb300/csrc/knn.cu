@@ -123,64 +123,61 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
         int ko = INT_MAX;
         bool dup = false;
 
-        auto scan_range = [&](int a, int b) {
-            for (int base = a; base < b; base += 32) {
-                const int jj = base + lane;
-                bool valid = jj < b && jj != q;
-                Real cd = Dist<Real>::inf();
-                int co = INT_MAX;
-                bool cand = false;
-                if (valid) {
-                    float4 pc = sorted[jj];
-                    co = __float_as_int(pc.w);
-                    if (pc.x == pq.x && pc.y == pq.y && pc.z == pq.z) dup = true;
-                    if (sizeof(Real) == 8) {
-                        // FP64 keys only for candidates whose float32 distance (relative
-                        // error < 1e-6) does not already rule them out: same list, less FP64
-                        const float c32 = knn_d2_f32(pq, pc);
-                        if (count < k || (double)c32 <= (double)kd * (1.0 + 1e-6)) {
+        for (int s = 0;; ++s) {
+            // the shell's segments, 32 at a time: lanes load segment bounds in
+            // parallel, then the segments' candidates are spread over all lanes
+            const int nseg = 2 * (2 * s + 1) * (2 * s + 1);
+            for (int e0 = 0; e0 < nseg; e0 += 32) {
+                int sa = 0, sb = 0;
+                if (e0 + lane < nseg) shell_segment(e0 + lane, s, ix, iy, iz, G, cell_off, sa, sb);
+                const int len = sb - sa;
+                int incl = len;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int u = __shfl_up_sync(FULL, incl, d);
+                    if (lane >= d) incl += u;
+                }
+                const int total = __shfl_sync(FULL, incl, 31);
+                const int start = incl - len;
+                for (int c0 = 0; c0 < total; c0 += 32) {
+                    const int i = c0 + lane;
+                    int seg = 0;  // number of segments ending at or before i
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1)
+                        if (__shfl_sync(FULL, incl, (seg + step - 1) & 31) <= i) seg += step;
+                    const int aj = __shfl_sync(FULL, sa, seg & 31), sj = __shfl_sync(FULL, start, seg & 31);
+                    const int jj = aj + (i - sj);
+                    const bool valid = i < total && jj != q;
+                    Real cd = Dist<Real>::inf();
+                    int co = INT_MAX;
+                    bool cand = false;
+                    if (valid) {
+                        const float4 pc = sorted[jj];
+                        co = __float_as_int(pc.w);
+                        if (pc.x == pq.x && pc.y == pq.y && pc.z == pq.z) dup = true;
+                        if (sizeof(Real) == 8) {
+                            // FP64 keys only for candidates whose float32 distance (relative
+                            // error < 1e-6) does not already rule them out: same list, less FP64
+                            const float c32 = knn_d2_f32(pq, pc);
+                            if (count < k || (double)c32 <= (double)kd * (1.0 + 1e-6)) {
+                                cd = Dist<Real>::d2(pq, pc);
+                                cand = count < k || key_less(cd, co, kd, ko);
+                            }
+                        } else {
                             cd = Dist<Real>::d2(pq, pc);
                             cand = count < k || key_less(cd, co, kd, ko);
                         }
-                    } else {
-                        cd = Dist<Real>::d2(pq, pc);
-                        cand = count < k || key_less(cd, co, kd, ko);
                     }
-                }
-                unsigned m = __ballot_sync(FULL, cand);
-                while (m) {
-                    const int src = __ffs(m) - 1;
-                    m &= m - 1;
-                    Real bd = __shfl_sync(FULL, cd, src);
-                    int bo = __shfl_sync(FULL, co, src);
-                    int bj = __shfl_sync(FULL, jj, src);
-                    L.insert(bd, bo, bj, k, lane);
-                    if (count < k) ++count;
-                    if (count == k) L.entry(k - 1, kd, ko);
-                }
-            }
-        };
-
-        for (int s = 0;; ++s) {
-            for (int dx = -s; dx <= s; ++dx) {
-                const int x = ix + dx;
-                if (x < 0 || x >= G) continue;
-                for (int dy = -s; dy <= s; ++dy) {
-                    const int y = iy + dy;
-                    if (y < 0 || y >= G) continue;
-                    const bool full = dx == -s || dx == s || dy == -s || dy == s;
-                    if (full) {
-                        const int z0 = max(iz - s, 0), z1 = min(iz + s, G - 1);
-                        scan_range(cell_off[cell_id(x, y, z0, G)], cell_off[cell_id(x, y, z1, G) + 1]);
-                    } else {
-                        if (iz - s >= 0) {
-                            const int cc = cell_id(x, y, iz - s, G);
-                            scan_range(cell_off[cc], cell_off[cc + 1]);
-                        }
-                        if (iz + s < G) {
-                            const int cc = cell_id(x, y, iz + s, G);
-                            scan_range(cell_off[cc], cell_off[cc + 1]);
-                        }
+                    unsigned m = __ballot_sync(FULL, cand);
+                    while (m) {
+                        const int src = __ffs(m) - 1;
+                        m &= m - 1;
+                        const Real bd = __shfl_sync(FULL, cd, src);
+                        const int bo = __shfl_sync(FULL, co, src);
+                        const int bj = __shfl_sync(FULL, jj, src);
+                        L.insert(bd, bo, bj, k, lane);
+                        if (count < k) ++count;
+                        if (count == k) L.entry(k - 1, kd, ko);
                     }
                 }
             }

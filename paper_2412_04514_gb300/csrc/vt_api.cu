@@ -391,7 +391,7 @@ void vt_params_default(vt_params* p)
     if (!p) return;
     std::memset(p, 0, sizeof(*p));
     p->k0 = 16;
-    p->k_max = 256;
+    p->k_max = 32;
     p->grid_density = 2.0f;
     p->grid_res = 0;
     p->threads_per_cell = 0;

@@ -33,6 +33,36 @@ __device__ __forceinline__ int cell_coord(float x, float lo, float scale, int G)
 
 __device__ __forceinline__ int cell_id(int ix, int iy, int iz, int G) { return (ix * G + iy) * G + iz; }
 
+// Segment e of Chebyshev shell s around grid cell (ix, iy, iz): a contiguous
+// range [a, b) of the sorted points (empty when outside the grid). Row
+// (dx, dy), dx, dy in [-s, s], owns segments 2*row and 2*row + 1: a row on the
+// shell's rim (|dx| = s or |dy| = s) contributes the z-range [iz-s, iz+s] as
+// its first segment; an inner row contributes the two cells z = iz-s and
+// z = iz+s. A shell has 2 (2s+1)^2 segments, s = 0 has the cell itself.
+__device__ __forceinline__ void shell_segment(int e, int s, int ix, int iy, int iz, int G,
+                                              const int32_t* __restrict__ cell_off, int& a, int& b)
+{
+    const int W = 2 * s + 1;
+    const int row = e >> 1, half = e & 1;
+    const int dx = row / W - s, dy = row - (row / W) * W - s;
+    const int x = ix + dx, y = iy + dy;
+    a = b = 0;
+    if (x < 0 || x >= G || y < 0 || y >= G) return;
+    const bool rim = dx == -s || dx == s || dy == -s || dy == s;
+    const int base = (x * G + y) * G;
+    if (rim) {
+        if (half) return;
+        const int z0 = iz - s < 0 ? 0 : iz - s, z1 = iz + s > G - 1 ? G - 1 : iz + s;
+        a = cell_off[base + z0];
+        b = cell_off[base + z1 + 1];
+    } else {
+        const int z = half ? iz + s : iz - s;
+        if (z < 0 || z >= G) return;
+        a = cell_off[base + z];
+        b = cell_off[base + z + 1];
+    }
+}
+
 // kNN ordering keys. FP64 form: ((dx*dx + dy*dy) + dz*dz) in double with
 // dx = double(x_j) - double(x_i), every operation separately rounded (no FMA),
 // so lists are exact and reproducible. FP32 form: the same in float32 with FMA.

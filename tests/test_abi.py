@@ -39,7 +39,7 @@ def test_host_only_calls():
     lib = L.load()
     p = L.VtParams()
     lib.vt_params_default(ctypes.byref(p))
-    assert (p.k0, p.k_max, p.precision) == (16, 256, L.VT_FP32_RECHECK)
+    assert (p.k0, p.k_max, p.precision) == (16, 32, L.VT_FP32_RECHECK)
     assert lib.vt_grid_resolution(ctypes.byref(p), 1 << 20) == 81
     assert lib.vt_grid_resolution(ctypes.byref(p), 1 << 23) == 162
     b = ctypes.c_size_t()

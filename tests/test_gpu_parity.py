@@ -182,11 +182,18 @@ def clustered():
 
 def test_fp64_clustered_runs_every_pass(clustered):
     pts, want = clustered
-    cells = vt.tessellate(dev(pts), vt.Params(precision="fp64", emit=("nbr", "vol", "cen", "m2")))
+    cells = vt.tessellate(dev(pts), vt.Params(precision="fp64", k_max=256, emit=("nbr", "vol", "cen", "m2")))
     check_fp64(cells, want)
     st = cells.stats
     assert st["k_of_pass"][:5] == [16, 32, 64, 128, 256]
     assert st["exhaustive_cells"] > 0 and st["k_of_pass"][-1] == 0
+
+
+@pytest.mark.parametrize("k0,k_max", [(16, 16), (16, 32), (32, 64)])
+def test_pass_policies_agree(clustered, k0, k_max):
+    pts, want = clustered
+    cells = vt.tessellate(dev(pts), vt.Params(precision="fp64", k0=k0, k_max=k_max, emit=("nbr", "vol", "cen")))
+    check_fp64(cells, want)
 
 
 def test_fp32_clustered(clustered):
