@@ -33,11 +33,29 @@ WORKLOADS = {
                      "out-of-box draws resampled), seed 1; k0=16 with doubling to k_max then the exhaustive pass; "
                      "outputs neighbours (CSR, original ids) + volume + centroid + full geometry"),
     "mixed-8m": dict(n=1 << 23, seed=2, desc="8,388,608 float32 points, same recipe as mixed-1m, seed 2"),
+    "mixed-300k": dict(n=300_000, seed=1, clumps=300, desc="300,000 float32 points, the mixed-1m recipe with 300 "
+                       "clumps (a small case for profiler captures)"),
 }
 # FP32 FMA peak from the unit counts and the maximum SM clock: 152 SMs x 128
 # FP32 lanes x 2 flops x 2.070 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
+
+
+def _clip_traffic(n_cells: int):
+    """DRAM bytes of the clip stage per step from a committed ncu capture,
+    scaled to n_cells; None when the kernel source changed since the capture."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "clip_traffic.json")) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2412_04514_gb300", "csrc", "clip_impl.cuh"), "rb").read()
+    except OSError:
+        return None
+    if hashlib.sha256(src).hexdigest() != rec.get("clip_impl_sha256"):
+        return None
+    return rec["bytes_per_cell"] * n_cells
 
 
 def _peaks():
@@ -154,7 +172,7 @@ def run_reference(args, rank: int, world: int):
     from paper_2412_04514_gb300 import workloads as W
 
     wl = WORKLOADS[args.workload]
-    pts = W.mixed(wl["n"], wl["seed"])
+    pts = W.mixed(wl["n"], wl["seed"], n_clumps=wl.get("clumps", 1000))
     per_step = args.ref_cells
     for i in range(args.warmup):
         cpu_oracle_rate(pts, min(2000, per_step), seed=100 + i)
@@ -189,7 +207,7 @@ def run_gpu(args, rank: int, world: int, local: int):
     torch.cuda.set_device(dev)
     wl = WORKLOADS[args.workload]
     n = wl["n"]
-    pts_np = W.mixed(n, wl["seed"] + 1000 * rank)
+    pts_np = W.mixed(n, wl["seed"] + 1000 * rank, n_clumps=wl.get("clumps", 1000))
     pts = torch.from_numpy(pts_np).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     emit = ("nbr", "vol", "cen", "geom")
@@ -226,19 +244,20 @@ def run_gpu(args, rank: int, world: int, local: int):
     with Clocks(local) as clk:
         ms32, st32, launches32, cells = timed(p32, args.steps, args.warmup, stage_times=True)
     clocks = clk.summary()
-    ms64, st64, _, _ = timed(p64, max(1, args.steps_fp64), max(3, min(args.warmup, 3)), stage_times=True)
+    if args.steps_fp64 > 0:
+        ms64, st64, _, _ = timed(p64, args.steps_fp64, 3, stage_times=True)
+        tot64 = dist_max(sum(ms64), world)
+        value64 = n * world * len(ms64) / (tot64 / 1e3)
 
     tot32 = dist_max(sum(ms32), world)
-    tot64 = dist_max(sum(ms64), world)
     value = n * world * len(ms32) / (tot32 / 1e3)
-    value64 = n * world * len(ms64) / (tot64 / 1e3)
 
     # end to end through the public API with host buffers
     host = torch.from_numpy(pts_np).pin_memory()
     e2e_ms = []
     h2d = host.numel() * 4
     d2h = 0
-    for i in range(args.warmup + args.steps):
+    for i in range(args.warmup + args.steps if not args.no_e2e else 0):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -249,8 +268,8 @@ def run_gpu(args, rank: int, world: int, local: int):
         d2h = sum(getattr(out, f).numel() * getattr(out, f).element_size()
                   for f in ("vol", "cen", "nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx_off",
                             "face_vtx") if getattr(out, f) is not None)
-    e2e_tot = dist_max(sum(e2e_ms), world)
-    e2e_value = n * world * len(e2e_ms) / (e2e_tot / 1e3)
+    e2e_tot = dist_max(sum(e2e_ms), world) if e2e_ms else 0.0
+    e2e_value = n * world * len(e2e_ms) / (e2e_tot / 1e3) if e2e_ms else None
 
     if rank != 0:
         return
@@ -267,7 +286,7 @@ def run_gpu(args, rank: int, world: int, local: int):
     roofline = {
         "kernel": "k_clip<float,32,2,64> (all passes of one step)",
         "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": _clip_traffic(n),
         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (unit counts and max SM clock)",
         "units": f"{n} validated cells x {flops_per_cell:.0f} algorithmic FP32 flops/cell over {clip_launches:.1f} "
                  f"clip launches",
@@ -280,12 +299,13 @@ def run_gpu(args, rank: int, world: int, local: int):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["desc"], "n_points": n, "precision": "fp32+fp64-recheck",
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world} (independent clouds)"},
-        "fp64_form": {"value": value64, "unit": "cells/s", "ms_per_step": tot64 / len(ms64), "steps": len(ms64),
-                      "stage_ms": {k: statistics.mean(s[k] for s in st64) for k in ("ms_grid", "ms_knn", "ms_clip",
-                                                                                    "ms_emit")},
-                      "fp32_speedup": value / value64},
-        "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": e2e_tot / len(e2e_ms)},
+        "fp64_form": None if args.steps_fp64 <= 0 else {
+            "value": value64, "unit": "cells/s", "ms_per_step": tot64 / len(ms64), "steps": len(ms64),
+            "stage_ms": {k: statistics.mean(s[k] for s in st64) for k in ("ms_grid", "ms_knn", "ms_clip", "ms_emit")},
+            "fp32_speedup": value / value64},
+        "e2e": None if not e2e_ms else {
+            "value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": e2e_tot / len(e2e_ms)},
         "roofline": roofline,
         "cpu_baseline": None if cpu is None else {"value": cpu["value"], "unit": "cells/s", "cores": cpu["cores"],
                                                   "kind": "oracle", "sample": cpu["sample"]},
@@ -311,6 +331,7 @@ def main():
     ap.add_argument("--flops-per-cell", type=float, default=25134.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--k-max", type=int, default=32)
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
