@@ -258,6 +258,27 @@ VT_API int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cel
                   vt_stats* stats, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ */
+/* adjoint of the cell moments (for Lloyd relaxation and cell losses)  */
+/* ------------------------------------------------------------------ */
+
+/* Vector-Jacobian product of the cell volumes V_i, centroids c_i and second
+ * moments M2_i (integral over C_i of |x - p_i|^2) with respect to the
+ * generators: grad[k] = sum_i gV_i dV_i/dp_k + gC_i . dc_i/dp_k + gM_i dM2_i/dp_k.
+ * The cells move through their bisector faces (a face between p_i and p_j
+ * moves along its normal with speed (x - p_i).dp_i / |p_j - p_i| and
+ * (p_j - x).dp_j / |p_j - p_i|; walls are fixed), so the product is a sum of
+ * exact face integrals of cubic polynomials plus 2 gM_k V_k (p_k - c_k).
+ * pts[n*3]: the generators of the tessellation (original order).
+ * cells: vol, cen and the geometry (vtx_off, vtx, face_off, face_nbr,
+ * face_vtx_off, face_vtx) of a vt_tessellate call on pts with
+ * VT_EMIT_VOL|VT_EMIT_CEN|VT_EMIT_GEOM and VT_INDEX_ORIGINAL.
+ * gV[n], gC[n*3], gM[n]: upstream gradients, each may be NULL (zero).
+ * grad[n*3] (FP64) is overwritten. Deterministic: each generator's gradient
+ * is summed by one warp in a fixed order. Asynchronous on `stream`. */
+VT_API int vt_moments_adjoint(const float* pts, int64_t n, const vt_cells_out* cells, const double* gV,
+                              const double* gC, const double* gM, double* grad, void* stream);
+
+/* ------------------------------------------------------------------ */
 /* diagnostics                                                         */
 /* ------------------------------------------------------------------ */
 

@@ -42,7 +42,7 @@ STATUS_NAMES = {
 EXPORTS = [
     "vt_params_default", "vt_grid_resolution", "vt_workspace_size", "vt_grid_build", "vt_knn", "vt_clip_cells",
     "vt_emit", "vt_tessellate", "vt_read_status", "vt_last_error", "vt_launch_count", "vt_version",
-    "vt_grid_build_static",
+    "vt_grid_build_static", "vt_moments_adjoint",
 ]
 
 
@@ -185,6 +185,8 @@ def load() -> ctypes.CDLL:
         L.vt_version.restype = ctypes.c_char_p
         L.vt_grid_build_static.argtypes = [P, I64, pp, I, P, P, P, P]
         L.vt_grid_build_static.restype = I
+        L.vt_moments_adjoint.argtypes = [P, I64, po, P, P, P, P, P]
+        L.vt_moments_adjoint.restype = I
         _lib = L
         return L
 

@@ -319,3 +319,85 @@ def launch_count() -> int:
 
 def version() -> str:
     return L.load().vt_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# adjoint of the cell moments, autograd and Lloyd relaxation
+# ---------------------------------------------------------------------------
+
+def moments_adjoint(points: torch.Tensor, cells: Cells, gV: torch.Tensor | None = None,
+                    gC: torch.Tensor | None = None, gM: torch.Tensor | None = None) -> torch.Tensor:
+    """d(sum gV.V + gC.c + gM.M2)/d(points) as float64 [n, 3] (vt_moments_adjoint).
+
+    ``cells`` must come from :func:`tessellate` on ``points`` with emit
+    including vol, cen and geom in the original index space."""
+    pts = _check_points(points)
+    n = pts.shape[0]
+    dev = pts.device
+    grad = torch.empty((max(n, 1), 3), dtype=torch.float64, device=dev)
+    o = _out_struct(cells)
+
+    def f64(t):
+        return None if t is None else t.to(device=dev, dtype=torch.float64).contiguous()
+
+    gV, gC, gM = f64(gV), f64(gC), f64(gM)
+    L.check(L.load().vt_moments_adjoint(_ptr(pts), n, ctypes.byref(o), _ptr(gV), _ptr(gC), _ptr(gM), _ptr(grad),
+                                        _stream(dev)))
+    return grad[:n]
+
+
+class VoronoiMoments(torch.autograd.Function):
+    """(V, c, M2) of every Voronoi cell of ``points``, differentiable in the points.
+
+    forward: one tessellation (emit vol, cen, m2 and the geometry the adjoint
+    needs). backward: the hand-written adjoint kernel (vt_moments_adjoint)."""
+
+    @staticmethod
+    def forward(ctx, points: torch.Tensor, params: Params | None = None):
+        p = params or Params()
+        p = Params(**{**p.__dict__, "emit": ("vol", "cen", "m2", "geom"), "index_space": "original"})
+        cells = tessellate(points.detach(), p)
+        ctx.cells = cells
+        ctx.save_for_backward(points)
+        return cells.vol, cells.cen, cells.m2
+
+    @staticmethod
+    def backward(ctx, gV, gC, gM):
+        (points,) = ctx.saved_tensors
+        g = moments_adjoint(points.detach(), ctx.cells, gV, gC, gM)
+        return g.to(points.dtype), None
+
+
+def voronoi_moments(points: torch.Tensor, params: Params | None = None):
+    return VoronoiMoments.apply(points, params)
+
+
+def lloyd(points: torch.Tensor, iterations: int, params: Params | None = None, checkpoint: str | None = None,
+          checkpoint_every: int = 10, resume: bool = False, callback=None) -> torch.Tensor:
+    """Lloyd relaxation: minimises sum_i M2_i by p <- p - g / (2 V), g the
+    adjoint gradient of the loss (the step lands on the cell centroids).
+
+    With ``checkpoint`` the points and the iteration are saved every
+    ``checkpoint_every`` iterations; ``resume=True`` continues from the file.
+    The pipeline is deterministic, so a resumed run reproduces the points of
+    an uninterrupted one bit for bit."""
+    p = points.detach().clone()
+    start = 0
+    if resume and checkpoint:
+        state = torch.load(checkpoint, map_location=p.device)
+        p = state["points"].to(p.device)
+        start = int(state["iteration"])
+    for it in range(start, iterations):
+        q = p.clone().requires_grad_(True)
+        vol, cen, m2 = voronoi_moments(q, params)
+        loss = m2.sum()
+        loss.backward()
+        with torch.no_grad():
+            g = q.grad.to(torch.float64)
+            step = p.to(torch.float64) - g / (2.0 * vol.detach()[:, None])
+            p = step.to(torch.float32)
+        if callback is not None:
+            callback(it, float(loss.detach()))
+        if checkpoint and ((it + 1) % checkpoint_every == 0 or it + 1 == iterations):
+            torch.save({"points": p.cpu(), "iteration": it + 1}, checkpoint)
+    return p

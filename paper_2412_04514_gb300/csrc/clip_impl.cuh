@@ -294,7 +294,7 @@ struct GroupSmem {
         struct {
             Real area[PCAP];
             int32_t key[PCAP];
-            int16_t first[PCAP];
+            int32_t first[PCAP];  // lowest live slot on the face (a face's walk starts there)
             uint8_t deg[PCAP];
         } tail;
     } u;
@@ -849,10 +849,7 @@ template <typename Real, int T, int VCAP, int PCAP, typename M>
 __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, int np, float4 pi, int gl,
                                          unsigned gmask, int64_t out_idx, const ClipArgs& A)
 {
-    for (int f = gl; f < np; f += T) {
-        sm.u.tail.area[f] = 0;
-        sm.u.tail.first[f] = -1;
-    }
+    for (int f = gl; f < np; f += T) sm.u.tail.first[f] = INT_MAX;
     __syncwarp(gmask);
     // per (vertex, face) terms: tetrahedron (0, q_f, v, next(v around f)),
     // q_f = foot of the perpendicular from the generator onto face f
@@ -868,8 +865,7 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
             const int nv = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
             const Real bx = sm.vpos[nv][0], by = sm.vpos[nv][1], bz = sm.vpos[nv][2];
             const Real fnx = sm.pnx[f], fny = sm.pny[f], fnz = sm.pnz[f], fb = sm.pb[f];
-            const Real nn = fnx * fnx + fny * fny + fnz * fnz;
-            const Real sc = fb / nn;
+            const Real sc = fb / (fnx * fnx + fny * fny + fnz * fnz);
             const Real qx = fnx * sc, qy = fny * sc, qz = fnz * sc;
             const Real cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
             const Real dv = (qx * cx + qy * cy + qz * cz) * (Real)(1.0 / 6.0);
@@ -879,12 +875,39 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
             my += dv * sy;
             mz += dv * sz;
             m2 += dv * (qx * qx + qy * qy + qz * qz + a2 + bx * bx + by * by + bz * bz + sx * sx + sy * sy + sz * sz);
-            const Real ux = ax - qx, uy = ay - qy, uz = az - qz, wx = bx - qx, wy = by - qy, wz = bz - qz;
-            const Real ar = (Real)0.5 *
-                            ((uy * wz - uz * wy) * fnx + (uz * wx - ux * wz) * fny + (ux * wy - uy * wx) * fnz) / sqrt(nn);
-            atomicAdd(&sm.u.tail.area[f], ar);
-            sm.u.tail.first[f] = (int16_t)s;
+            atomicMin(&sm.u.tail.first[f], s);
         }
+    }
+    __syncwarp(gmask);
+    // face areas (and degrees) by walking each face from its lowest slot, so
+    // the sums and the emitted loops do not depend on thread timing
+    for (int f = gl; f < np; f += T) {
+        Real area = 0;
+        int deg = 0;
+        const int s0 = sm.u.tail.first[f];
+        if (s0 != INT_MAX) {
+            const Real fnx = sm.pnx[f], fny = sm.pny[f], fnz = sm.pnz[f], fb = sm.pb[f];
+            const Real nn = fnx * fnx + fny * fny + fnz * fnz;
+            const Real sc = fb / nn;
+            const Real qx = fnx * sc, qy = fny * sc, qz = fnz * sc;
+            int cur = s0;
+            do {
+                const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[cur]);
+                const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[cur]);
+                const int t = ((ids & 0xff) == (uint32_t)f) ? 0 : ((((ids >> 8) & 0xff) == (uint32_t)f) ? 1 : 2);
+                const int nxt = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
+                const Real ux = sm.vpos[cur][0] - qx, uy = sm.vpos[cur][1] - qy, uz = sm.vpos[cur][2] - qz;
+                const Real wx = sm.vpos[nxt][0] - qx, wy = sm.vpos[nxt][1] - qy, wz = sm.vpos[nxt][2] - qz;
+                area += (uy * wz - uz * wy) * fnx + (uz * wx - ux * wz) * fny + (ux * wy - uy * wx) * fnz;
+                cur = nxt;
+                ++deg;
+            } while (cur != s0 && deg <= VCAP);
+            area *= (Real)0.5 / sqrt(nn);
+        } else {
+            sm.u.tail.first[f] = -1;
+        }
+        sm.u.tail.area[f] = area;
+        sm.u.tail.deg[f] = (uint8_t)(deg > 255 ? 255 : deg);
     }
     double V = (double)vol, MX = (double)mx, MY = (double)my, MZ = (double)mz, M2 = (double)m2;
 #pragma unroll
@@ -937,22 +960,6 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
     int nface = 0, nvtx = 0, nfv = 0;
     if (A.emit & VT_EMIT_GEOM) {
         nvtx = alive.count();
-        // degrees by walking each face
-        for (int f = gl; f < np; f += T) {
-            int deg = 0;
-            const int s0 = sm.u.tail.first[f];
-            if (s0 >= 0) {
-                int cur = s0;
-                do {
-                    const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[cur]);
-                    const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[cur]);
-                    const int t = ((ids & 0xff) == (uint32_t)f) ? 0 : ((((ids >> 8) & 0xff) == (uint32_t)f) ? 1 : 2);
-                    cur = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
-                    ++deg;
-                } while (cur != s0 && deg <= VCAP);
-            }
-            sm.u.tail.deg[f] = (uint8_t)(deg > 255 ? 255 : deg);
-        }
         __syncwarp(gmask);
         int32_t* rfn = reinterpret_cast<int32_t*>(rec + REC_FNBR_OFF);
         uint8_t* rdeg = rec + REC_FDEG_OFF;
