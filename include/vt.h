@@ -90,8 +90,15 @@ typedef struct vt_params {
 
 /* vt_params.flags */
 enum {
-    VT_FLAG_STAGE_TIMES = 1 /* time every kernel group with CUDA events on the call's stream
+    VT_FLAG_STAGE_TIMES = 1, /* time every kernel group with CUDA events on the call's stream
                                (vt_stats.ms_*); costs one event pair per launch group */
+    VT_FLAG_NO_SYNC = 2      /* fixed schedule: passes k0, 2k0, ... <= k_max, then the exhaustive
+                               pass, each launched over the worst-case cell count and reading its
+                               true count from device memory. The call never waits on the device,
+                               so it can be captured in a CUDA graph; errors and output sizes are
+                               read afterwards with vt_read_stats. Outputs that do not fit the
+                               caller's capacities are not written (VT_ERR_CAPACITY there). The
+                               neighbour-list buffer grows to n * k_max entries. */
 };
 
 /* Fills *p with the defaults above, unit box, FP32_RECHECK, emit NBR|VOL|CEN. */
@@ -123,6 +130,19 @@ typedef struct vt_cells_out {
     /* filled by vt_tessellate / vt_emit (host memory, inside this struct) */
     int64_t needed_nbr, needed_vtx, needed_face, needed_face_vtx;
 } vt_cells_out;
+
+/* Grid of one point set of a batch, made on the host by vt_batch_plan and
+ * copied to device memory by the caller before vt_tessellate_batch. */
+typedef struct vt_set_desc {
+    int G;                  /* grid cells per axis of this set */
+    float lo[3], hi[3];     /* the set's box */
+    float scale[3];         /* float32(G) / (hi - lo) */
+    double cw[3];           /* cell width */
+    double margin;          /* rounding margin of the shell-walk stop rule */
+    int64_t cell_base;      /* first global grid cell of this set */
+    int64_t pt_begin;       /* first point of this set in the concatenated input */
+    int64_t npts;           /* points in this set */
+} vt_set_desc;
 
 #define VT_MAX_PASSES 16
 
@@ -258,6 +278,41 @@ VT_API int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cel
                   vt_stats* stats, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ */
+/* batches of independent point sets                                   */
+/* ------------------------------------------------------------------ */
+
+/* Batches (the paper treats one point set at a time; many independent sets
+ * of uneven sizes run here as one tessellation over a concatenated input).
+ * Every set has its own uniform grid over the box of p and is tessellated on
+ * its own: its cells see only its own generators. Each stage runs as one
+ * launch over the cells of all sets, so small sets share the GPU with large
+ * ones.
+ *
+ * vt_batch_plan (host, no device work): set_off[n_sets+1] (host) are the
+ * point offsets of the sets in the concatenated input (set_off[0] = 0,
+ * non-decreasing); grid_res[n_sets] (host, may be NULL) overrides G per set
+ * (0 = from p->grid_density and the set's size). Writes plan[n_sets] (host)
+ * and *total_cells, the grid cells of all sets together. The caller copies
+ * plan and set_off to device memory for vt_tessellate_batch. */
+VT_API int vt_batch_plan(const int64_t* set_off, int n_sets, const vt_params* p, const int* grid_res,
+                         vt_set_desc* plan, int64_t* total_cells);
+
+/* Workspace bytes of a batch of n_total points whose grids have total_cells
+ * cells (from vt_batch_plan). */
+VT_API int vt_batch_workspace_size(const vt_params* p, int64_t n_total, int64_t total_cells, size_t* bytes);
+
+/* Tessellates every set of a batch. pts[n_total*3] (device), plan[n_sets] and
+ * set_off[n_sets+1] (device copies of vt_batch_plan's plan and offsets).
+ * Outputs as vt_tessellate over the concatenated input: cell i is point i of
+ * the concatenation (VT_INDEX_ORIGINAL) and neighbour ids are indices into it,
+ * so they never leave the cell's own set. With VT_FLAG_NO_SYNC the call only
+ * enqueues work (capturable in a CUDA graph; read errors and sizes with
+ * vt_read_stats); otherwise it behaves like vt_tessellate. */
+VT_API int vt_tessellate_batch(const float* pts, int64_t n_total, const vt_set_desc* plan,
+                               const int64_t* set_off, int n_sets, int64_t total_cells, const vt_params* p,
+                               vt_cells_out* out, vt_stats* stats, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
 /* adjoint of the cell moments (for Lloyd relaxation and cell losses)  */
 /* ------------------------------------------------------------------ */
 
@@ -285,6 +340,15 @@ VT_API int vt_moments_adjoint(const float* pts, int64_t n, const vt_cells_out* c
 /* Reads the device status flags of the workspace (blocking on `stream`):
  * returns VT_OK, VT_ERR_INVALID_ARG (bad point) or VT_ERR_DUPLICATE_POINTS. */
 VT_API int vt_read_status(void* ws, size_t ws_bytes, void* stream);
+
+/* After a VT_FLAG_NO_SYNC call (or any call) on workspace ws (blocking on
+ * `stream`): fills the device-counted fields of *stats (fp64_rechecks,
+ * capacity_retries, precision_retries, unvalidated, clip_events; other fields
+ * are left as they are) and out->needed_* (either may be NULL). Returns the
+ * call's error: VT_ERR_INVALID_ARG / VT_ERR_DUPLICATE_POINTS for bad input,
+ * VT_ERR_CAPACITY when an output did not fit (nothing of that output was
+ * written), VT_ERR_UNVALIDATED when cells stayed unvalidated, else VT_OK. */
+VT_API int vt_read_stats(void* ws, size_t ws_bytes, vt_stats* stats, vt_cells_out* out, void* stream);
 
 /* Message of the last failure on this host thread ("" if none). */
 VT_API const char* vt_last_error(void);

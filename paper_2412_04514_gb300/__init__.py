@@ -4,10 +4,10 @@ The computation runs in the CUDA library ``libvt.so`` (C ABI in
 ``include/vt.h``); :mod:`.api` is a thin PyTorch binding over it and
 :mod:`.workloads` draws the seeded synthetic point clouds.
 """
-from .api import (Cells, Params, VoronoiMoments, Workspace, clip_cells, emit, grid_build, grid_resolution, knn,
-                  launch_count, lloyd, moments_adjoint, tessellate, tessellate_host, version, voronoi_moments,
-                  workspace_size)
+from .api import (Batch, Cells, Params, VoronoiMoments, Workspace, batch_plan, clip_cells, emit, grid_build,
+                  grid_resolution, knn, launch_count, lloyd, moments_adjoint, tessellate, tessellate_batch,
+                  tessellate_host, version, voronoi_moments, workspace_size)
 
-__all__ = ["Cells", "Params", "VoronoiMoments", "Workspace", "clip_cells", "emit", "grid_build", "grid_resolution",
-           "knn", "launch_count", "lloyd", "moments_adjoint", "tessellate", "tessellate_host", "version",
-           "voronoi_moments", "workspace_size"]
+__all__ = ["Batch", "Cells", "Params", "VoronoiMoments", "Workspace", "batch_plan", "clip_cells", "emit",
+           "grid_build", "grid_resolution", "knn", "launch_count", "lloyd", "moments_adjoint", "tessellate",
+           "tessellate_batch", "tessellate_host", "version", "voronoi_moments", "workspace_size"]

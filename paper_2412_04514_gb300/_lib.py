@@ -32,6 +32,7 @@ VT_EMIT_M2 = 8
 VT_EMIT_GEOM = 16
 VT_MAX_PASSES = 16
 VT_FLAG_STAGE_TIMES = 1
+VT_FLAG_NO_SYNC = 2
 
 STATUS_NAMES = {
     0: "VT_OK", 1: "VT_ERR_INVALID_ARG", 2: "VT_ERR_CUDA", 3: "VT_ERR_CAPACITY", 4: "VT_ERR_UNVALIDATED",
@@ -42,7 +43,8 @@ STATUS_NAMES = {
 EXPORTS = [
     "vt_params_default", "vt_grid_resolution", "vt_workspace_size", "vt_grid_build", "vt_knn", "vt_clip_cells",
     "vt_emit", "vt_tessellate", "vt_read_status", "vt_last_error", "vt_launch_count", "vt_version",
-    "vt_grid_build_static", "vt_moments_adjoint",
+    "vt_grid_build_static", "vt_moments_adjoint", "vt_batch_plan", "vt_batch_workspace_size",
+    "vt_tessellate_batch", "vt_read_stats",
 ]
 
 
@@ -84,6 +86,20 @@ class VtCellsOut(ctypes.Structure):
         ("needed_vtx", ctypes.c_int64),
         ("needed_face", ctypes.c_int64),
         ("needed_face_vtx", ctypes.c_int64),
+    ]
+
+
+class VtSetDesc(ctypes.Structure):
+    _fields_ = [
+        ("G", ctypes.c_int),
+        ("lo", ctypes.c_float * 3),
+        ("hi", ctypes.c_float * 3),
+        ("scale", ctypes.c_float * 3),
+        ("cw", ctypes.c_double * 3),
+        ("margin", ctypes.c_double),
+        ("cell_base", ctypes.c_int64),
+        ("pt_begin", ctypes.c_int64),
+        ("npts", ctypes.c_int64),
     ]
 
 
@@ -187,6 +203,15 @@ def load() -> ctypes.CDLL:
         L.vt_grid_build_static.restype = I
         L.vt_moments_adjoint.argtypes = [P, I64, po, P, P, P, P, P]
         L.vt_moments_adjoint.restype = I
+        ps = ctypes.POINTER(VtStats)
+        L.vt_batch_plan.argtypes = [P, I, pp, P, P, ctypes.POINTER(I64)]
+        L.vt_batch_plan.restype = I
+        L.vt_batch_workspace_size.argtypes = [pp, I64, I64, ctypes.POINTER(ctypes.c_size_t)]
+        L.vt_batch_workspace_size.restype = I
+        L.vt_tessellate_batch.argtypes = [P, I64, P, P, I, I64, pp, po, ps, P, ctypes.c_size_t, P]
+        L.vt_tessellate_batch.restype = I
+        L.vt_read_stats.argtypes = [P, ctypes.c_size_t, ps, po, P]
+        L.vt_read_stats.restype = I
         _lib = L
         return L
 

@@ -34,6 +34,7 @@ class Params:
     box_lo: tuple = (0.0, 0.0, 0.0)
     box_hi: tuple = (1.0, 1.0, 1.0)
     stage_times: bool = False
+    no_sync: bool = False
 
     def c(self) -> L.VtParams:
         p = L.VtParams()
@@ -49,7 +50,7 @@ class Params:
         for a in range(3):
             p.box_lo[a] = self.box_lo[a]
             p.box_hi[a] = self.box_hi[a]
-        p.flags = L.VT_FLAG_STAGE_TIMES if self.stage_times else 0
+        p.flags = (L.VT_FLAG_STAGE_TIMES if self.stage_times else 0) | (L.VT_FLAG_NO_SYNC if self.no_sync else 0)
         return p
 
 
@@ -188,6 +189,10 @@ def tessellate(points: torch.Tensor, params: Params | None = None, workspace: Wo
     s = _stream(dev)
     code = lib.vt_tessellate(_ptr(pts), n, ctypes.byref(pc), ctypes.byref(o), ctypes.byref(st), _ptr(ws.buf),
                              ws.buf.numel(), s)
+    if code == L.VT_OK and params.no_sync:  # the call only enqueued: read status and sizes now
+        code = lib.vt_read_stats(_ptr(ws.buf), ws.buf.numel(), ctypes.byref(st), ctypes.byref(o), s)
+        if code == L.VT_ERR_CAPACITY:
+            pc = Params(**{**params.__dict__, "no_sync": False}).c()
     if code == L.VT_ERR_CAPACITY and o.needed_nbr >= 0:
         guess = {"nbr": o.needed_nbr, "vtx": o.needed_vtx, "face": o.needed_face, "face_vtx": o.needed_face_vtx}
         fresh = _alloc(Params(**{**params.__dict__, "emit": tuple(x for x in params.emit if x in ("nbr", "geom"))}),
@@ -218,6 +223,141 @@ def tessellate_host(points, params: Params | None = None, device="cuda") -> Cell
         v = getattr(cells, name)
         setattr(out, name, None if v is None else v.to("cpu"))
     return out
+
+
+# ---------------------------------------------------------------------------
+# batches of independent point sets (vt_batch_plan, vt_tessellate_batch)
+# ---------------------------------------------------------------------------
+
+def batch_plan(set_off, params: Params | None = None, grid_res=None):
+    """Host plan of a batch: (plan as a list of L.VtSetDesc, total grid cells).
+    ``set_off`` holds the n_sets + 1 point offsets of the sets in the
+    concatenated input; ``grid_res`` optionally fixes G per set (0 = derive)."""
+    params = params or Params()
+    off = [int(x) for x in set_off]
+    ns = len(off) - 1
+    if ns < 1:
+        raise ValueError("a batch needs at least one set")
+    offs = (ctypes.c_int64 * len(off))(*off)
+    gr = None if grid_res is None else (ctypes.c_int * ns)(*[int(g) for g in grid_res])
+    plan = (L.VtSetDesc * ns)()
+    cells = ctypes.c_int64()
+    L.check(L.load().vt_batch_plan(offs, ns, ctypes.byref(params.c()), gr, plan, ctypes.byref(cells)))
+    return plan, cells.value
+
+
+class Batch:
+    """A batch of independent point sets tessellated as one run.
+
+    ``points`` is the concatenation of the sets (float32 CUDA tensor (N, 3)),
+    ``set_off`` the n_sets + 1 offsets (host). Every set gets its own grid
+    (``grid_res`` per set, else from ``params.grid_density``); cells see only
+    the generators of their own set and neighbour ids index the concatenation.
+
+    The plan, workspace and output buffers are made once. :meth:`run`
+    enqueues the whole path with the fixed no-sync schedule (no host wait), so
+    it can be recorded by :meth:`capture` into a CUDA graph and replayed with
+    :meth:`replay` after new coordinates are copied into :attr:`points`.
+    :meth:`result` then reads the status and returns the cells.
+    """
+
+    def __init__(self, points: torch.Tensor, set_off, params: Params | None = None, grid_res=None,
+                 nbr_per_cell: int = 20, geom_guess: dict | None = None):
+        base = params or Params()
+        self.params = Params(**{**base.__dict__, "no_sync": True, "stage_times": False})
+        self.points = _check_points(points).clone()
+        n = self.points.shape[0]
+        self.n = n
+        dev = self.points.device
+        self.set_off_host = [int(x) for x in set_off]
+        if self.set_off_host[-1] != n:
+            raise ValueError("set_off[-1] must equal the number of points")
+        self.n_sets = len(self.set_off_host) - 1
+        plan, self.total_cells = batch_plan(self.set_off_host, self.params, grid_res)
+        raw = torch.frombuffer(bytearray(bytes(plan)), dtype=torch.uint8)
+        self.plan = raw.to(dev)
+        self.set_off = torch.tensor(self.set_off_host, dtype=torch.int64, device=dev)
+        self.grid_res = [plan[i].G for i in range(self.n_sets)]
+        b = ctypes.c_size_t()
+        L.check(L.load().vt_batch_workspace_size(ctypes.byref(self.params.c()), n, self.total_cells, ctypes.byref(b)))
+        self.ws = torch.empty(max(b.value, 256), dtype=torch.uint8, device=dev)
+        guess = {"nbr": nbr_per_cell * n + 64, **(geom_guess or {})}
+        self.cells = _alloc(self.params, n, dev, False, guess)
+        self.graph = None
+        self._pc = self.params.c()
+
+    def run(self) -> None:
+        """Enqueue one tessellation of :attr:`points` on the current stream."""
+        o = _out_struct(self.cells)
+        st = L.VtStats()
+        L.check(L.load().vt_tessellate_batch(_ptr(self.points), self.n, _ptr(self.plan), _ptr(self.set_off),
+                                             self.n_sets, self.total_cells, ctypes.byref(self._pc), ctypes.byref(o),
+                                             ctypes.byref(st), _ptr(self.ws), self.ws.numel(),
+                                             _stream(self.points.device)))
+        self.launch_stats = st.as_dict()
+
+    def capture(self) -> None:
+        """Record :meth:`run` in a CUDA graph (after one eager warm-up run)."""
+        self.run()
+        torch.cuda.synchronize(self.points.device)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(self.points.device)
+        s.wait_stream(torch.cuda.current_stream(self.points.device))
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.run()
+        torch.cuda.current_stream(self.points.device).wait_stream(s)
+        self.graph = g
+
+    def replay(self) -> None:
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+
+    def result(self, strict: bool = True) -> Cells:
+        """Status of the last run (blocking) and the cells as views of the
+        batch's buffers. Raises VtError on bad input, unvalidated cells
+        (``strict``) or outputs that did not fit (VT_ERR_CAPACITY: call
+        :meth:`grow` and run again)."""
+        o = _out_struct(self.cells)
+        st = L.VtStats()
+        code = L.load().vt_read_stats(_ptr(self.ws), self.ws.numel(), ctypes.byref(st), ctypes.byref(o),
+                                      _stream(self.points.device))
+        self.needed = {"nbr": o.needed_nbr, "vtx": o.needed_vtx, "face": o.needed_face,
+                       "face_vtx": o.needed_face_vtx}
+        if code not in (L.VT_OK, L.VT_ERR_UNVALIDATED) or (strict and code != L.VT_OK):
+            L.check(code)
+        out = Cells(**{k: getattr(self.cells, k) for k in ("vol", "cen", "m2", "nbr_off", "nbr", "vtx_off", "vtx",
+                                                         "face_off", "face_nbr", "face_vtx_off", "face_vtx")})
+        stats = dict(self.launch_stats)
+        for k in ("fp64_rechecks", "capacity_retries", "precision_retries", "unvalidated"):
+            stats[k] = getattr(st, k)
+        stats["clip_events"] = list(st.clip_events)
+        stats["status"] = L.STATUS_NAMES.get(code, code)
+        out.stats = stats
+        _trim(out, o)
+        return out
+
+    def grow(self) -> None:
+        """Reallocate the variable-length outputs to the sizes the last run
+        needed (drops a captured graph, whose pointers would be stale)."""
+        self.cells = _alloc(self.params, self.n, self.points.device, False, self.needed)
+        self.graph = None
+
+
+def tessellate_batch(points: torch.Tensor, set_off, params: Params | None = None, grid_res=None,
+                     strict: bool = True) -> Cells:
+    """One-shot batch: plan, run, and grow the outputs once if they were too small."""
+    b = Batch(points, set_off, params, grid_res)
+    b.run()
+    try:
+        return b.result(strict)
+    except L.VtError as e:
+        if e.code != L.VT_ERR_CAPACITY:
+            raise
+    b.grow()
+    b.run()
+    return b.result(strict)
 
 
 # ---------------------------------------------------------------------------

@@ -1027,8 +1027,9 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
 // one at a time. Generators a resumed list already processed are skipped.
 template <typename Real, int T, int VPL, int PCAP>
 __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, const Group<T>& G,
-                                                typename Cell<Real, T, VPL, PCAP>::S& sm, const ClipArgs& A, bool valid,
-                                                int jj, double last_d2, int last_orig, float* lo3, float* hi3)
+                                                typename Cell<Real, T, VPL, PCAP>::S& sm, const ClipArgs& A,
+                                                const GridDesc& grid, bool valid, int jj, double last_d2,
+                                                int last_orig, float* lo3, float* hi3)
 {
     const float4 pq = cell.pi;
     float4 pc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1066,7 +1067,7 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, 
         if (!(4.0f * (float)cell.R2 * (1.0f + 1e-4f) > d2 &&
               hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f))
             continue;
-        const int r = cell.clip_point(G, sm, p, j, A.sorted, A.g, A.st);
+        const int r = cell.clip_point(G, sm, p, j, A.sorted, grid, A.st);
         if (r == CLIP_OVERFLOW) return END_OVERFLOW;
         if (r == CLIP_INCONSISTENT) return END_INCONSISTENT;
         if (r == CLIP_CUT) cell.bbox(G, lo3, hi3);
@@ -1083,7 +1084,7 @@ constexpr int CLIP_BLOCK = 128;
 #endif
 
 template <typename Real, int T, int VPL, int PCAP, bool ROBUST, bool EXH>
-__global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(ClipArgs A)
+__global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_constant__ ClipArgs A)
 {
     using C = Cell<Real, T, VPL, PCAP>;
     using S = typename C::S;
@@ -1093,13 +1094,14 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(ClipArgs A)
     const int64_t gid = ((int64_t)blockIdx.x * CLIP_BLOCK + threadIdx.x) / T;
     const int64_t ngroups = ((int64_t)gridDim.x * CLIP_BLOCK) / T;
     const int k = A.k;
-    const int Gr = A.g.G;
     const bool resume = !ROBUST && A.state && A.k_prev > 0;
+    const int64_t nq = A.nq_dev ? (int64_t)*A.nq_dev : A.nq;
     C cell;
     cell.stamp = 0;
 
-    for (int64_t c = gid; c < A.nq; c += ngroups) {
+    for (int64_t c = gid; c < nq; c += ngroups) {
         const int q = A.queries ? A.queries[c] : (int)c;
+        const GridDesc& grid = grid_of(A.g, A.sets, A.set_of, q);
         cell.pi = A.sorted[q];
         const int orig = __float_as_int(cell.pi.w);
         const int64_t out_idx = A.index_space == VT_INDEX_ORIGINAL ? (int64_t)orig : (int64_t)q;
@@ -1107,7 +1109,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(ClipArgs A)
         double last_d2 = -1.0;
         int last_orig = -1;
         if (resume) cell.restore(G, sm, stp, last_d2, last_orig);
-        else cell.init_box(G, sm, A.g);
+        else cell.init_box(G, sm, grid);
         int end = END_NEED_K;
         if (!EXH) {
             // neighbour list, nearest first, from the first unprocessed entry;
@@ -1133,18 +1135,18 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(ClipArgs A)
                     const int j = G.bcast(cj, t);
                     if (j < 0) { end = END_VALID; stop = true; break; }  // the list holds every other generator
                     const Real dj = G.bcast(cd, t);
-                    if (cell.radius_ok(G, sm, dj, j, A.sorted, A.g, A.st)) { end = END_VALID; stop = true; break; }
+                    if (cell.radius_ok(G, sm, dj, j, A.sorted, grid, A.st)) { end = END_VALID; stop = true; break; }
                     float4 p;
                     p.x = G.bcast(cp.x, t);
                     p.y = G.bcast(cp.y, t);
                     p.z = G.bcast(cp.z, t);
                     p.w = 0.f;
-                    const int r = cell.clip_point(G, sm, p, j, A.sorted, A.g, A.st);
+                    const int r = cell.clip_point(G, sm, p, j, A.sorted, grid, A.st);
                     if (r == CLIP_OVERFLOW) { end = END_OVERFLOW; stop = true; break; }
                     if (r == CLIP_INCONSISTENT) { end = END_INCONSISTENT; stop = true; break; }
                 }
             }
-            if (!stop && k > 0 && cell.radius_ok(G, sm, dd[k - 1], nb[k - 1], A.sorted, A.g, A.st)) end = END_VALID;
+            if (!stop && k > 0 && cell.radius_ok(G, sm, dd[k - 1], nb[k - 1], A.sorted, grid, A.st)) end = END_VALID;
             if (end == END_NEED_K && k > 0) {
                 last_d2 = (double)dd[k - 1];
                 last_orig = __float_as_int(A.sorted[nb[k - 1]].w);
@@ -1152,9 +1154,11 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(ClipArgs A)
         } else {
             // exhaustive: every generator closer than 2R, by a shell walk
             const float4 pq = cell.pi;
-            const int ix = cell_coord(pq.x, A.g.lo[0], A.g.scale[0], Gr);
-            const int iy = cell_coord(pq.y, A.g.lo[1], A.g.scale[1], Gr);
-            const int iz = cell_coord(pq.z, A.g.lo[2], A.g.scale[2], Gr);
+            const int Gr = grid.G;
+            const int32_t* coff = A.cell_off + grid.cell_base;
+            const int ix = cell_coord(pq.x, grid.lo[0], grid.scale[0], Gr);
+            const int iy = cell_coord(pq.y, grid.lo[1], grid.scale[1], Gr);
+            const int iz = cell_coord(pq.z, grid.lo[2], grid.scale[2], Gr);
             float lo3[3], hi3[3];
             cell.bbox(G, lo3, hi3);
             int status = 0;
@@ -1163,7 +1167,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(ClipArgs A)
                 const int nseg = 2 * (2 * s + 1) * (2 * s + 1);
                 for (int e0 = 0; e0 < nseg && status == 0; e0 += T) {
                     int sa = 0, sb = 0;
-                    if (e0 + G.gl < nseg) shell_segment(e0 + G.gl, s, ix, iy, iz, Gr, A.cell_off, sa, sb);
+                    if (e0 + G.gl < nseg) shell_segment(e0 + G.gl, s, ix, iy, iz, Gr, coff, sa, sb);
                     const int len = sb - sa;
                     int total;
                     const int start = G.scan(len, total);
@@ -1176,21 +1180,15 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(ClipArgs A)
                             if (G.bcast(incl, (seg + step - 1) & (T - 1)) <= i) seg += step;
                         const int aj = G.bcast(sa, seg & (T - 1)), sj = G.bcast(start, seg & (T - 1));
                         const int jj = aj + (i - sj);
-                        status = exhaustive_batch(cell, G, sm, A, i < total && jj != q, jj, last_d2, last_orig, lo3, hi3);
+                        status = exhaustive_batch(cell, G, sm, A, grid, i < total && jj != q, jj, last_d2, last_orig,
+                                                  lo3, hi3);
                     }
                 }
                 if (status) break;
                 const bool covers = ix - s <= 0 && iy - s <= 0 && iz - s <= 0 && ix + s >= Gr - 1 &&
                                     iy + s >= Gr - 1 && iz + s >= Gr - 1;
                 if (covers) { status = -1; break; }
-                double gap = 1e300;
-                const double q0 = pq.x, q1 = pq.y, q2 = pq.z;
-                if (ix - s > 0) gap = fmin(gap, q0 - ((double)A.g.lo[0] + (ix - s) * A.g.cw[0]) - A.g.margin);
-                if (ix + s + 1 < Gr) gap = fmin(gap, ((double)A.g.lo[0] + (ix + s + 1) * A.g.cw[0]) - q0 - A.g.margin);
-                if (iy - s > 0) gap = fmin(gap, q1 - ((double)A.g.lo[1] + (iy - s) * A.g.cw[1]) - A.g.margin);
-                if (iy + s + 1 < Gr) gap = fmin(gap, ((double)A.g.lo[1] + (iy + s + 1) * A.g.cw[1]) - q1 - A.g.margin);
-                if (iz - s > 0) gap = fmin(gap, q2 - ((double)A.g.lo[2] + (iz - s) * A.g.cw[2]) - A.g.margin);
-                if (iz + s + 1 < Gr) gap = fmin(gap, ((double)A.g.lo[2] + (iz + s + 1) * A.g.cw[2]) - q2 - A.g.margin);
+                const double gap = shell_gap(grid, pq, ix, iy, iz, s);
                 if (gap > 0 && 4.0 * (double)cell.R2 * (1.0 + 1e-5) <= gap * gap) { status = -1; break; }
             }
             end = status == -1 ? END_VALID : status;

@@ -33,7 +33,7 @@ __global__ void k_emit_totals(const int64_t* __restrict__ off, int64_t n, int ge
 }
 
 __global__ void k_emit_write(const uint8_t* __restrict__ rec, size_t stride, int64_t n, int emit,
-                             const int64_t* __restrict__ off, vt_cells_out out)
+                             const int64_t* __restrict__ off, vt_cells_out out, DevStatus* st)
 {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -45,6 +45,15 @@ __global__ void k_emit_write(const uint8_t* __restrict__ rec, size_t stride, int
     for (int64_t i = wid; i < n; i += nw) {
         const uint8_t* r = rec + (size_t)i * stride;
         const RecHeader h = *reinterpret_cast<const RecHeader*>(r);
+        // capacities are checked here as well, so a run that never synchronises
+        // (a captured graph) cannot write past the caller's buffers
+        const bool nbr_fits = !(emit & VT_EMIT_NBR) || o_nbr[n] <= out.nbr_cap;
+        const bool geo_fits = !(emit & VT_EMIT_GEOM) ||
+                              (o_vtx[n] <= out.vtx_cap && o_face[n] <= out.face_cap && o_fv[n] <= out.face_vtx_cap);
+        if (!nbr_fits || !geo_fits) {
+            if (lane == 0 && i == 0) atomicExch((int*)&st->cap_overflow, 1);
+            continue;
+        }
         if (emit & VT_EMIT_NBR) {
             const int64_t b = o_nbr[i];
             const int32_t* src = reinterpret_cast<const int32_t*>(r + REC_NBR_OFF);
@@ -105,7 +114,7 @@ cudaError_t launch_emit_write(const EmitArgs& a, const vt_cells_out& out, cudaSt
     if (a.n <= 0) return cudaSuccess;
     int64_t blocks = (a.n + 7) / 8;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    k_emit_write<<<(unsigned)blocks, 256, 0, s>>>(a.rec, a.rec_stride, a.n, a.emit, a.off64, out);
+    k_emit_write<<<(unsigned)blocks, 256, 0, s>>>(a.rec, a.rec_stride, a.n, a.emit, a.off64, out, a.st);
     count_launch();
     return cudaGetLastError();
 }

@@ -17,18 +17,32 @@ namespace {
 
 constexpr int SMALL_CELL = 32;
 
-__global__ void k_grid_count(const float* __restrict__ pts, int64_t n, GridDesc g, int32_t* __restrict__ cid,
+// set of input point i: the last s with set_off[s] <= i (binary search)
+__device__ __forceinline__ int set_of_point(const int64_t* __restrict__ set_off, int nsets, int64_t i)
+{
+    int lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (set_off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_grid_count(const float* __restrict__ pts, int64_t n, GridDesc g0, const GridDesc* __restrict__ sets,
+                             const int64_t* __restrict__ set_off, int nsets, int32_t* __restrict__ cid,
                              int32_t* __restrict__ ticket, int32_t* __restrict__ counts, DevStatus* st)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const GridDesc& g = sets ? sets[set_of_point(set_off, nsets, i)] : g0;
         float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
         bool ok = (x >= g.lo[0]) & (x < g.hi[0]) & (y >= g.lo[1]) & (y < g.hi[1]) & (z >= g.lo[2]) & (z < g.hi[2]);
         if (!ok) {  // NaN fails every comparison
             atomicCAS((int*)&st->bad_point, 0, (int)(i + 1));
             x = g.lo[0]; y = g.lo[1]; z = g.lo[2];
         }
-        int c = cell_id(cell_coord(x, g.lo[0], g.scale[0], g.G), cell_coord(y, g.lo[1], g.scale[1], g.G),
-                        cell_coord(z, g.lo[2], g.scale[2], g.G), g.G);
+        int c = (int)g.cell_base + cell_id(cell_coord(x, g.lo[0], g.scale[0], g.G),
+                                           cell_coord(y, g.lo[1], g.scale[1], g.G),
+                                           cell_coord(z, g.lo[2], g.scale[2], g.G), g.G);
         cid[i] = c;
         ticket[i] = atomicAdd(&counts[c], 1);
     }
@@ -114,10 +128,14 @@ __global__ void k_grid_fix_big(float4* __restrict__ sorted, const int32_t* __res
     }
 }
 
-__global__ void k_grid_perm(const float4* __restrict__ sorted, int64_t n, int32_t* __restrict__ perm)
+__global__ void k_grid_perm(const float4* __restrict__ sorted, int64_t n, int32_t* __restrict__ perm,
+                            const int64_t* __restrict__ set_off, int nsets, int32_t* __restrict__ set_of)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        perm[i] = __float_as_int(sorted[i].w);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int o = __float_as_int(sorted[i].w);
+        perm[i] = o;
+        if (set_of) set_of[i] = set_of_point(set_off, nsets, o);
+    }
 }
 
 unsigned blocks_for(int64_t n, int threads)
@@ -132,13 +150,17 @@ unsigned blocks_for(int64_t n, int threads)
 
 cudaError_t launch_grid_build(const float* pts, int64_t n, const GridDesc& g, float4* sorted, int32_t* perm,
                               int32_t* cell_off, int32_t* cid, int32_t* ticket, int32_t* counts, int32_t* big,
-                              void* scan_tmp, DevStatus* st, cudaStream_t s)
+                              void* scan_tmp, DevStatus* st, cudaStream_t s, const BatchArgs* batch, int64_t g3)
 {
-    const int64_t g3 = (int64_t)g.G * g.G * g.G;
+    if (g3 < 0) g3 = (int64_t)g.G * g.G * g.G;
+    const GridDesc* sets = batch ? batch->sets : nullptr;
+    const int64_t* set_off = batch ? batch->set_off : nullptr;
+    const int nsets = batch ? batch->nsets : 1;
+    int32_t* set_of = batch ? batch->set_of : nullptr;
     cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)g3 * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     if (n > 0) {
-        k_grid_count<<<blocks_for(n, 256), 256, 0, s>>>(pts, n, g, cid, ticket, counts, st);
+        k_grid_count<<<blocks_for(n, 256), 256, 0, s>>>(pts, n, g, sets, set_off, nsets, cid, ticket, counts, st);
         count_launch();
     }
     exclusive_scan_i32(counts, cell_off, g3, scan_tmp, s);
@@ -146,7 +168,7 @@ cudaError_t launch_grid_build(const float* pts, int64_t n, const GridDesc& g, fl
     k_grid_scatter<<<blocks_for(n, 256), 256, 0, s>>>(pts, n, cid, ticket, cell_off, sorted);
     k_grid_fix<<<blocks_for(g3, 128), 128, 0, s>>>(sorted, cell_off, g3, big, st);
     k_grid_fix_big<<<152 * 2, 512, 0, s>>>(sorted, cell_off, big, st);
-    k_grid_perm<<<blocks_for(n, 256), 256, 0, s>>>(sorted, n, perm);
+    k_grid_perm<<<blocks_for(n, 256), 256, 0, s>>>(sorted, n, perm, set_off, nsets, set_of);
     count_launch(4);
     return cudaGetLastError();
 }

@@ -102,17 +102,22 @@ struct WarpList {
 };
 
 template <typename Real, int KPL>
-__global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, const int32_t* __restrict__ cell_off,
-                                             GridDesc g, const int32_t* __restrict__ queries, int64_t nq, int k,
+__global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, const int32_t* __restrict__ cell_off0,
+                                             const __grid_constant__ GridDesc g0, const GridDesc* __restrict__ sets,
+                                             const int32_t* __restrict__ set_of, const int32_t* __restrict__ queries,
+                                             int64_t nq_host, const int32_t* __restrict__ nq_dev, int k,
                                              int32_t* __restrict__ nbr, Real* __restrict__ d2out, DevStatus* st)
 {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int G = g.G;
+    const int64_t nq = nq_dev ? (int64_t)*nq_dev : nq_host;
     for (int64_t c = wid; c < nq; c += nw) {
         const int q = queries ? queries[c] : (int)c;
         const float4 pq = sorted[q];
+        const GridDesc& g = grid_of(g0, sets, set_of, q);
+        const int G = g.G;
+        const int32_t* cell_off = cell_off0 + g.cell_base;
         const int ix = cell_coord(pq.x, g.lo[0], g.scale[0], G);
         const int iy = cell_coord(pq.y, g.lo[1], g.scale[1], G);
         const int iz = cell_coord(pq.z, g.lo[2], g.scale[2], G);
@@ -186,15 +191,7 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
                                 iz + s >= G - 1;
             if (covers) break;
             if (count == k) {
-                const double qc[3] = {(double)pq.x, (double)pq.y, (double)pq.z};
-                const int ic[3] = {ix, iy, iz};
-                double gap = 1e300;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (ic[a] - s > 0) gap = fmin(gap, qc[a] - ((double)g.lo[a] + (ic[a] - s) * g.cw[a]) - g.margin);
-                    if (ic[a] + s + 1 < G)
-                        gap = fmin(gap, ((double)g.lo[a] + (ic[a] + s + 1) * g.cw[a]) - qc[a] - g.margin);
-                }
+                const double gap = shell_gap(g, pq, ix, iy, iz, s);
                 if (gap > 0 && (double)kd <= gap * gap * (1.0 - 1e-6)) break;
             }
         }
@@ -211,17 +208,22 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
 }
 
 template <typename Real>
-cudaError_t launch_knn_t(const float4* sorted, const int32_t* cell_off, const GridDesc& g, const int32_t* queries,
-                         int64_t nq, int k, int32_t* nbr, Real* d2, DevStatus* st, cudaStream_t s)
+cudaError_t launch_knn_t(const float4* sorted, const int32_t* cell_off, const GridDesc& g, const GridDesc* sets,
+                         const int32_t* set_of, const int32_t* queries, int64_t nq, const int32_t* nq_dev, int k,
+                         int32_t* nbr, Real* d2, DevStatus* st, cudaStream_t s)
 {
     if (nq <= 0) return cudaSuccess;
     int64_t blocks = (nq + 7) / 8;
     if (blocks > 152 * 32) blocks = 152 * 32;
     dim3 grid((unsigned)blocks), block(256);
-    if (k <= 32) k_knn<Real, 1><<<grid, block, 0, s>>>(sorted, cell_off, g, queries, nq, k, nbr, d2, st);
-    else if (k <= 64) k_knn<Real, 2><<<grid, block, 0, s>>>(sorted, cell_off, g, queries, nq, k, nbr, d2, st);
-    else if (k <= 128) k_knn<Real, 4><<<grid, block, 0, s>>>(sorted, cell_off, g, queries, nq, k, nbr, d2, st);
-    else k_knn<Real, 8><<<grid, block, 0, s>>>(sorted, cell_off, g, queries, nq, k, nbr, d2, st);
+    if (k <= 32)
+        k_knn<Real, 1><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, k, nbr, d2, st);
+    else if (k <= 64)
+        k_knn<Real, 2><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, k, nbr, d2, st);
+    else if (k <= 128)
+        k_knn<Real, 4><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, k, nbr, d2, st);
+    else
+        k_knn<Real, 8><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, k, nbr, d2, st);
     count_launch();
     return cudaGetLastError();
 }
@@ -230,13 +232,15 @@ cudaError_t launch_knn_t(const float4* sorted, const int32_t* cell_off, const Gr
 
 cudaError_t launch_knn(const float4* sorted, const int32_t* cell_off, const GridDesc& g, int64_t n,
                        const int32_t* queries, int64_t nq, int k, int precision, int32_t* nbr, void* d2,
-                       DevStatus* st, cudaStream_t s)
+                       DevStatus* st, cudaStream_t s, const GridDesc* sets, const int32_t* set_of,
+                       const int32_t* nq_dev)
 {
     (void)n;
     if (k < 1 || k > 256) return cudaErrorInvalidValue;
     if (precision == VT_FP64)
-        return launch_knn_t<double>(sorted, cell_off, g, queries, nq, k, nbr, (double*)d2, st, s);
-    return launch_knn_t<float>(sorted, cell_off, g, queries, nq, k, nbr, (float*)d2, st, s);
+        return launch_knn_t<double>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, k, nbr, (double*)d2, st,
+                                    s);
+    return launch_knn_t<float>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, k, nbr, (float*)d2, st, s);
 }
 
 }  // namespace vt

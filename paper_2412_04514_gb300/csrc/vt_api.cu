@@ -48,6 +48,8 @@ int check_params(const vt_params* p)
         return fail(VT_ERR_INVALID_ARG, "precision must be VT_FP64 or VT_FP32_RECHECK");
     if (p->index_space != VT_INDEX_ORIGINAL && p->index_space != VT_INDEX_SORTED)
         return fail(VT_ERR_INVALID_ARG, "index_space must be VT_INDEX_ORIGINAL or VT_INDEX_SORTED");
+    if (p->flags & ~(VT_FLAG_STAGE_TIMES | VT_FLAG_NO_SYNC))
+        return fail(VT_ERR_INVALID_ARG, "unknown flag bits 0x%x", p->flags);
     if (p->emit & ~(VT_EMIT_NBR | VT_EMIT_VOL | VT_EMIT_CEN | VT_EMIT_M2 | VT_EMIT_GEOM))
         return fail(VT_ERR_INVALID_ARG, "unknown emit bits 0x%x", p->emit);
     for (int a = 0; a < 3; ++a)
@@ -96,17 +98,23 @@ GridDesc make_grid(const vt_params* p, int G)
     // cell assignment in float32 may differ from exact arithmetic by a few
     // ulps of the scaled coordinate; the shell-walk stop rule stays clear of it
     g.margin = 16.0 * ext_max * std::ldexp(1.0, -24);
+    g.cell_base = 0;
+    g.pt_begin = 0;
+    g.npts = 0;
     return g;
 }
 
-Layout make_layout(const vt_params* p, int64_t n)
+Layout make_layout(const vt_params* p, int64_t n, int64_t cells, bool batch)
 {
     Layout L{};
     L.G = grid_res_for(p, n);
     L.n = n;
-    L.g3 = (int64_t)L.G * L.G * L.G;
+    L.g3 = cells >= 0 ? cells : (int64_t)L.G * L.G * L.G;
     const int64_t nn = n > 0 ? n : 1;
-    int64_t cap = nn * (int64_t)p->k0;
+    // list-mode passes run in chunks of knn_cap / k cells; the no-sync schedule
+    // runs each pass in one launch, so its buffer holds n * k_max entries
+    const bool nosync = (p->flags & VT_FLAG_NO_SYNC) != 0;
+    int64_t cap = nn * (int64_t)(nosync ? p->k_max : p->k0);
     if (cap < (int64_t)p->k_max * 64) cap = (int64_t)p->k_max * 64;
     L.knn_cap = cap;
     const bool recs = (p->emit & (VT_EMIT_NBR | VT_EMIT_GEOM)) != 0;
@@ -117,24 +125,29 @@ Layout make_layout(const vt_params* p, int64_t n)
         off += align256(bytes);
         return o;
     };
+    // the regions vt_emit reads come first: their offsets depend only on n
+    // and the emit bits, so vt_emit works after single-set and batch runs alike
     L.status = take(sizeof(DevStatus));
+    L.rec = take(L.rec_stride * (size_t)nn);
+    L.cnt = take(sizeof(int32_t) * 4 * nn);
+    L.off64 = take(sizeof(int64_t) * 4 * (nn + 1));
+    L.scan_emit = take(scan_tmp_bytes(nn));
     L.cid = take(sizeof(int32_t) * nn);
     L.ticket = take(sizeof(int32_t) * nn);
+    L.sorted = take(sizeof(float4) * nn);
+    L.perm = take(sizeof(int32_t) * nn);
+    L.list_a = take(sizeof(int32_t) * nn * 6);  // six cell lists of n entries
+    L.state_stride = clip_state_bytes(p->precision);
+    L.state = take(L.state_stride * (size_t)nn);
     L.counts = take(sizeof(int32_t) * (L.g3 + 1));
     L.cell_off = take(sizeof(int32_t) * (L.g3 + 1));
     L.big = take(sizeof(int32_t) * (L.g3 + 1));
     size_t st1 = scan_tmp_bytes(L.g3), st2 = scan_tmp_bytes(nn);
     L.scan_tmp = take(st1 > st2 ? st1 : st2);
-    L.sorted = take(sizeof(float4) * nn);
-    L.perm = take(sizeof(int32_t) * nn);
-    L.list_a = take(sizeof(int32_t) * nn * 6);  // six cell lists of n entries
     L.knn_nbr = take(sizeof(int32_t) * L.knn_cap);
     L.knn_d2 = take(sizeof(double) * L.knn_cap);
-    L.rec = take(L.rec_stride * (size_t)nn);
-    L.cnt = take(sizeof(int32_t) * 4 * nn);
-    L.off64 = take(sizeof(int64_t) * 4 * (nn + 1));
-    L.state_stride = clip_state_bytes(p->precision);
-    L.state = take(L.state_stride * (size_t)nn);
+    L.set_of = batch ? take(sizeof(int32_t) * nn) : 0;
+    L.ctr = take(sizeof(int32_t) * (3 * VT_MAX_PASSES + 8));
     L.total = off;
     return L;
 }
@@ -205,19 +218,25 @@ struct Ctx {
     cudaStream_t s;
     DevStatus* st;
     GridDesc g;
+    // batches (null for a single point set)
+    const GridDesc* sets = nullptr;
+    const int64_t* set_off = nullptr;
+    int nsets = 1;
     StageTimer* timer = nullptr;
     int* clip_launches = nullptr;
     int* knn_launches = nullptr;
     template <typename X>
     X* at(size_t off) const { return reinterpret_cast<X*>(base + off); }
+    int32_t* set_of() const { return sets ? at<int32_t>(L.set_of) : nullptr; }
 };
 
-int make_ctx(const vt_params* p, int64_t n, void* ws, size_t ws_bytes, void* stream, Ctx& c)
+int make_ctx(const vt_params* p, int64_t n, void* ws, size_t ws_bytes, void* stream, Ctx& c, int64_t cells = -1,
+             bool batch = false)
 {
     int e = check_params(p);
     if (e) return e;
     if (n < 0 || n > (int64_t)INT32_MAX / 2) return fail(VT_ERR_INVALID_ARG, "n out of range: %lld", (long long)n);
-    c.L = make_layout(p, n);
+    c.L = make_layout(p, n, cells, batch);
     if (!ws) return fail(VT_ERR_WORKSPACE, "workspace is NULL");
     if (ws_bytes < c.L.total)
         return fail(VT_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu bytes needed", ws_bytes, c.L.total);
@@ -225,6 +244,7 @@ int make_ctx(const vt_params* p, int64_t n, void* ws, size_t ws_bytes, void* str
     c.s = (cudaStream_t)stream;
     c.st = c.at<DevStatus>(c.L.status);
     c.g = make_grid(p, c.L.G);
+    c.g.npts = n;
     return VT_OK;
 }
 
@@ -248,16 +268,21 @@ __global__ void k_iota(int32_t* a, int64_t n)
         a[i] = (int32_t)i;
 }
 
-// one clip pass over `list` (m cells): kNN with k in chunks that fit the
-// list buffer, then the clipper; k == 0 runs the exhaustive clipper
-int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, int k, int k_prev, int variant,
-              int knn_prec, vt_cells_out* out, int32_t* fail_next, int32_t* fail_robust)
+// one clip pass over `list` (m cells, or *m_dev cells when m_dev is set): kNN
+// with k in chunks that fit the list buffer, then the clipper; k == 0 runs
+// the exhaustive clipper. Failures go to the given lists and counters.
+int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, const int32_t* m_dev, int k,
+              int k_prev, int variant, int knn_prec, vt_cells_out* out, int32_t* fail_next, int32_t* ctr_next,
+              int32_t* fail_robust, int32_t* ctr_robust)
 {
     const Layout& L = c.L;
     ClipArgs a{};
     a.sorted = c.at<float4>(L.sorted);
     a.cell_off = c.at<int32_t>(L.cell_off);
     a.g = c.g;
+    a.sets = c.sets;
+    a.set_of = c.set_of();
+    a.nq_dev = m_dev;
     a.n = L.n;
     a.k = k;
     a.emit = p->emit;
@@ -269,8 +294,8 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
     a.rec_stride = L.rec_stride;
     a.fail_next = fail_next;
     a.fail_robust = fail_robust;
-    a.ctr_next = &c.st->n_fail_next;
-    a.ctr_robust = &c.st->n_fail_robust;
+    a.ctr_next = ctr_next;
+    a.ctr_robust = ctr_robust;
     a.k_prev = k_prev;
     a.state = c.at<uint8_t>(L.state);
     a.state_stride = L.state_stride;
@@ -288,13 +313,14 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
         return e == cudaSuccess ? VT_OK : cuda_fail(e, "clip launch");
     }
     const int64_t chunk = L.knn_cap / k;
+    if (m_dev && m > chunk) return fail(VT_ERR_INVALID_ARG, "internal: device-counted pass needs one chunk");
     for (int64_t o = 0; o < m; o += chunk) {
         const int64_t cnt = (m - o) < chunk ? (m - o) : chunk;
         const int32_t* q = list ? list + o : nullptr;
         if (!list && o > 0) return fail(VT_ERR_INVALID_ARG, "internal: implicit list needs one chunk");
         T.begin(StageTimer::KNN);
         cudaError_t e = launch_knn(a.sorted, a.cell_off, c.g, L.n, q, cnt, k, knn_prec, c.at<int32_t>(L.knn_nbr),
-                                   c.at<void>(L.knn_d2), c.st, c.s);
+                                   c.at<void>(L.knn_d2), c.st, c.s, c.sets, c.set_of(), m_dev);
         T.end();
         if (c.knn_launches) ++*c.knn_launches;
         if (e != cudaSuccess) return cuda_fail(e, "knn launch");
@@ -324,6 +350,8 @@ int emit_outputs(const Ctx& c, const vt_params* p, vt_cells_out* out)
     const Layout& L = c.L;
     const int64_t n = L.n;
     if (!(p->emit & (VT_EMIT_NBR | VT_EMIT_GEOM))) return VT_OK;
+    const bool nosync = (p->flags & VT_FLAG_NO_SYNC) != 0;
+    if (n == 0 && nosync) return VT_OK;
     if (n == 0) {
         int64_t z = 0;
         if ((p->emit & VT_EMIT_NBR) && out->nbr_off)
@@ -344,14 +372,25 @@ int emit_outputs(const Ctx& c, const vt_params* p, vt_cells_out* out)
     e.rec_stride = L.rec_stride;
     e.cnt = c.at<int32_t>(L.cnt);
     e.off64 = c.at<int64_t>(L.off64);
-    e.scan_tmp = c.at<void>(L.scan_tmp);
+    e.scan_tmp = c.at<void>(L.scan_emit);
     e.st = c.st;
+    // a buffer may be NULL only when its capacity is 0
+    if ((p->emit & VT_EMIT_NBR) && (!out->nbr_off || (!out->nbr && out->nbr_cap > 0)))
+        return fail(VT_ERR_INVALID_ARG, "VT_EMIT_NBR needs nbr_off and nbr");
+    if ((p->emit & VT_EMIT_GEOM) &&
+        (!out->vtx_off || !out->face_off || !out->face_vtx_off || (!out->vtx && out->vtx_cap > 0) ||
+         (!out->face_nbr && out->face_cap > 0) || (!out->face_vtx && out->face_vtx_cap > 0)))
+        return fail(VT_ERR_INVALID_ARG, "VT_EMIT_GEOM needs every geometry pointer");
     StageTimer dummy;
     StageTimer& T = c.timer ? *c.timer : dummy;
     T.begin(StageTimer::EMIT);
     cudaError_t ce = launch_emit_count(e, c.s);
     T.end();
     if (ce != cudaSuccess) return cuda_fail(ce, "emit count");
+    if (nosync) {  // capacities are checked on the device; vt_read_stats reports them
+        ce = launch_emit_write(e, *out, c.s);
+        return ce == cudaSuccess ? VT_OK : cuda_fail(ce, "emit write");
+    }
     DevStatus h;
     int r = read_status(c, h);
     if (r) return r;
@@ -361,14 +400,10 @@ int emit_outputs(const Ctx& c, const vt_params* p, vt_cells_out* out)
     out->needed_face_vtx = h.totals[3];
     if (h.record_overflow) return fail(VT_ERR_CAPACITY, "%d cells exceed the per-cell record size", h.record_overflow);
     if (p->emit & VT_EMIT_NBR) {
-        if (!out->nbr_off || (!out->nbr && h.totals[0] > 0))
-            return fail(VT_ERR_INVALID_ARG, "VT_EMIT_NBR needs nbr_off and nbr");
         if (out->nbr_cap < h.totals[0])
             return fail(VT_ERR_CAPACITY, "nbr_cap %lld < needed %lld", (long long)out->nbr_cap, (long long)h.totals[0]);
     }
     if (p->emit & VT_EMIT_GEOM) {
-        if (!out->vtx_off || !out->vtx || !out->face_off || !out->face_nbr || !out->face_vtx_off || !out->face_vtx)
-            return fail(VT_ERR_INVALID_ARG, "VT_EMIT_GEOM needs every geometry pointer");
         if (out->vtx_cap < h.totals[1] || out->face_cap < h.totals[2] || out->face_vtx_cap < h.totals[3])
             return fail(VT_ERR_CAPACITY, "geometry buffers too small (need vtx %lld, faces %lld, face_vtx %lld)",
                         (long long)h.totals[1], (long long)h.totals[2], (long long)h.totals[3]);
@@ -377,6 +412,183 @@ int emit_outputs(const Ctx& c, const vt_params* p, vt_cells_out* out)
     ce = launch_emit_write(e, *out, c.s);
     T.end();
     if (ce != cudaSuccess) return cuda_fail(ce, "emit write");
+    return VT_OK;
+}
+
+
+// the whole path on an initialised context (single set or batch)
+int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_cells_out* out, vt_stats* stats)
+{
+    if (!out) return fail(VT_ERR_INVALID_ARG, "out is NULL");
+    if (n > 0 && !pts) return fail(VT_ERR_INVALID_ARG, "pts is NULL");
+    if ((p->emit & VT_EMIT_VOL) && n > 0 && !out->vol) return fail(VT_ERR_INVALID_ARG, "VT_EMIT_VOL needs vol");
+    if ((p->emit & VT_EMIT_CEN) && n > 0 && !out->cen) return fail(VT_ERR_INVALID_ARG, "VT_EMIT_CEN needs cen");
+    if ((p->emit & VT_EMIT_M2) && n > 0 && !out->m2) return fail(VT_ERR_INVALID_ARG, "VT_EMIT_M2 needs m2");
+    const bool nosync = (p->flags & VT_FLAG_NO_SYNC) != 0;
+    if (nosync && (p->flags & VT_FLAG_STAGE_TIMES))
+        return fail(VT_ERR_INVALID_ARG, "VT_FLAG_STAGE_TIMES needs the synchronising schedule");
+    const int64_t l0 = launches();
+    vt_stats S{};
+    S.grid_res = c.sets ? 0 : c.L.G;
+    const Layout& L = c.L;
+    StageTimer timer;
+    timer.on = (p->flags & VT_FLAG_STAGE_TIMES) != 0;
+    timer.s = c.s;
+    c.timer = &timer;
+    c.clip_launches = &S.clip_launches;
+    c.knn_launches = &S.knn_launches;
+    cudaError_t ce = cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c.at<int32_t>(L.ctr), 0, sizeof(int32_t) * (3 * VT_MAX_PASSES + 8), c.s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "status reset");
+    if (n > 0) {
+        timer.begin(StageTimer::GRID);
+        BatchArgs b{c.sets, c.set_off, c.nsets, c.set_of()};
+        ce = launch_grid_build(pts, n, c.g, c.at<float4>(L.sorted), c.at<int32_t>(L.perm), c.at<int32_t>(L.cell_off),
+                               c.at<int32_t>(L.cid), c.at<int32_t>(L.ticket), c.at<int32_t>(L.counts),
+                               c.at<int32_t>(L.big), c.at<void>(L.scan_tmp), c.st, c.s, c.sets ? &b : nullptr, L.g3);
+        timer.end();
+        if (ce != cudaSuccess) return cuda_fail(ce, "grid build");
+        if (out->perm) {
+            ce = cudaMemcpyAsync(out->perm, c.at<int32_t>(L.perm), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c.s);
+            if (ce != cudaSuccess) return cuda_fail(ce, "perm copy");
+        }
+    }
+    // six lists of n cells: regular current/next, robust current/next, robust new, unvalidated
+    int32_t* lists = c.at<int32_t>(L.list_a);
+    int32_t* reg_cur = lists;
+    int32_t* reg_nxt = lists + n;
+    int32_t* rob_cur = lists + 2 * n;
+    int32_t* rob_nxt = lists + 3 * n;
+    int32_t* rob_new = lists + 4 * n;
+    int32_t* unval = lists + 5 * n;
+    const int variant_reg = p->precision == VT_FP64 ? 1 : 0;
+    int r = VT_OK;
+    DevStatus h{};
+
+    if (nosync && n > 0) {
+        // fixed schedule, counts stay on the device: capturable in a CUDA graph.
+        // Pass i reads its regular cells from the list pass i-1 appended to
+        // (count ctr_reg[i-1]); robust cells of pass i are the new ones
+        // (ctr_new[i]) and the ones carried from pass i-1 (ctr_rob[i-1]).
+        int32_t* ctr_reg = c.at<int32_t>(L.ctr);
+        int32_t* ctr_new = ctr_reg + VT_MAX_PASSES;
+        int32_t* ctr_rob = ctr_new + VT_MAX_PASSES;
+        int32_t* regl[2] = {reg_cur, reg_nxt};
+        int32_t* robl[2] = {rob_cur, rob_nxt};
+        int ks[VT_MAX_PASSES];
+        int np_ = 0;
+        for (int k = p->k0; k <= p->k_max && np_ < VT_MAX_PASSES - 1; k *= 2) ks[np_++] = k;
+        ks[np_++] = 0;
+        int k_prev = 0;
+        for (int pi = 0; pi < np_; ++pi) {
+            const int kk = ks[pi];
+            if (pi < VT_MAX_PASSES) S.k_of_pass[pi] = kk;
+            ++S.passes;
+            const int32_t* q = pi == 0 ? nullptr : regl[pi % 2];
+            const int32_t* qn = pi == 0 ? nullptr : &ctr_reg[pi - 1];
+            // the exhaustive pass always concludes; anything it still hands on
+            // is counted as unvalidated rather than dropped
+            const bool last = kk == 0;
+            int32_t* rn = last ? unval : regl[(pi + 1) % 2];
+            int32_t* rc = last ? &c.st->n_unval : &ctr_reg[pi];
+            int32_t* bn = last ? unval : robl[(pi + 1) % 2];
+            int32_t* bc = last ? &c.st->n_unval : &ctr_rob[pi];
+            r = clip_pass(c, p, q, n, qn, kk, k_prev, variant_reg, p->precision, out, rn, rc, rob_new, &ctr_new[pi]);
+            if (r) return r;
+            r = clip_pass(c, p, rob_new, n, &ctr_new[pi], kk, 0, 2, VT_FP64, out, bn, bc, unval, &c.st->n_unval);
+            if (r) return r;
+            if (pi > 0) {
+                r = clip_pass(c, p, robl[pi % 2], n, &ctr_rob[pi - 1], kk, 0, 2, VT_FP64, out, bn, bc, unval,
+                              &c.st->n_unval);
+                if (r) return r;
+            }
+            if (kk) k_prev = kk;
+        }
+        r = emit_outputs(c, p, out);
+        S.launches = (int)(launches() - l0);
+        if (stats) *stats = S;
+        return r;
+    }
+
+    int64_t m_reg = n, m_rob = 0, n_unval = 0;
+    bool implicit = true;  // the first pass runs over all cells without a list
+    int k = p->k0;
+    int k_prev = 0;  // regular cells resume from their saved state after list entry k_prev
+    while (m_reg + m_rob > 0) {
+        const bool exhaustive = k > p->k_max;
+        const int kk = exhaustive ? 0 : k;
+        if (S.passes < VT_MAX_PASSES) {
+            S.k_of_pass[S.passes] = kk;
+            S.cells_of_pass[S.passes] = m_reg + m_rob;
+        }
+        timer.pass = S.passes;
+        ++S.passes;
+        if (exhaustive) S.exhaustive_cells = m_reg + m_rob;
+        int64_t got_next = 0, got_rob = 0;
+        if (m_reg > 0) {
+            if ((r = zero_counters(c))) return r;
+            if (implicit && (int64_t)kk * m_reg > L.knn_cap) {
+                k_iota<<<(unsigned)((m_reg + 255) / 256 < 152 * 64 ? (m_reg + 255) / 256 : 152 * 64), 256, 0, c.s>>>(
+                    reg_cur, m_reg);
+                count_launch();
+                implicit = false;
+            }
+            r = clip_pass(c, p, implicit ? nullptr : reg_cur, m_reg, nullptr, kk, k_prev, variant_reg, p->precision,
+                          out, reg_nxt, &c.st->n_fail_next, rob_new, &c.st->n_fail_robust);
+            if (r) return r;
+            if ((r = read_status(c, h))) return r;
+            if ((r = status_errors(h))) return r;
+            got_next = h.n_fail_next;
+            got_rob = h.n_fail_robust;
+        }
+        implicit = false;
+        if (got_rob > 0) {
+            ce = cudaMemcpyAsync(rob_cur + m_rob, rob_new, sizeof(int32_t) * got_rob, cudaMemcpyDeviceToDevice, c.s);
+            if (ce != cudaSuccess) return cuda_fail(ce, "list copy");
+            m_rob += got_rob;
+        }
+        int64_t rob_next = 0;
+        if (m_rob > 0) {
+            if ((r = zero_counters(c))) return r;
+            r = clip_pass(c, p, rob_cur, m_rob, nullptr, kk, 0, 2, VT_FP64, out, rob_nxt, &c.st->n_fail_next,
+                          unval + n_unval, &c.st->n_fail_robust);
+            if (r) return r;
+            if ((r = read_status(c, h))) return r;
+            if ((r = status_errors(h))) return r;
+            rob_next = h.n_fail_next;
+            n_unval += h.n_fail_robust;
+        }
+        std::swap(reg_cur, reg_nxt);
+        std::swap(rob_cur, rob_nxt);
+        m_reg = got_next;
+        m_rob = rob_next;
+        if (exhaustive) {
+            n_unval += m_reg + m_rob;  // cannot happen: the exhaustive pass always concludes
+            break;
+        }
+        k_prev = k;
+        k *= 2;
+    }
+    S.unvalidated = n_unval;
+    r = emit_outputs(c, p, out);
+    if ((r = r ? r : read_status(c, h))) {
+        if (stats) *stats = S;
+        return r;
+    }
+    S.fp64_rechecks = (int64_t)h.fp64_rechecks;
+    S.capacity_retries = (int64_t)h.capacity_events;
+    S.precision_retries = (int64_t)h.precision_events;
+    for (int a = 0; a < 5; ++a) S.clip_events[a] = (int64_t)h.detail[a];
+    S.launches = (int)(launches() - l0);
+    if (timer.on) {
+        S.ms_grid = timer.total(StageTimer::GRID);
+        S.ms_knn = timer.total(StageTimer::KNN);
+        S.ms_clip = timer.total(StageTimer::CLIP);
+        S.ms_emit = timer.total(StageTimer::EMIT);
+        timer.per_pass(S.ms_clip_pass, VT_MAX_PASSES);
+    }
+    if (stats) *stats = S;
+    if (n_unval > 0) return fail(VT_ERR_UNVALIDATED, "%lld cells could not be validated", (long long)n_unval);
     return VT_OK;
 }
 
@@ -499,125 +711,56 @@ int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cells_out*
     Ctx c;
     int e = make_ctx(p, n, ws, ws_bytes, stream, c);
     if (e) return e;
-    if (!out) return fail(VT_ERR_INVALID_ARG, "out is NULL");
-    if (n > 0 && !pts) return fail(VT_ERR_INVALID_ARG, "pts is NULL");
-    if ((p->emit & VT_EMIT_VOL) && n > 0 && !out->vol) return fail(VT_ERR_INVALID_ARG, "VT_EMIT_VOL needs vol");
-    if ((p->emit & VT_EMIT_CEN) && n > 0 && !out->cen) return fail(VT_ERR_INVALID_ARG, "VT_EMIT_CEN needs cen");
-    if ((p->emit & VT_EMIT_M2) && n > 0 && !out->m2) return fail(VT_ERR_INVALID_ARG, "VT_EMIT_M2 needs m2");
-    const int64_t l0 = launches();
-    vt_stats S{};
-    S.grid_res = c.L.G;
-    const Layout& L = c.L;
-    StageTimer timer;
-    timer.on = (p->flags & VT_FLAG_STAGE_TIMES) != 0;
-    timer.s = c.s;
-    c.timer = &timer;
-    c.clip_launches = &S.clip_launches;
-    c.knn_launches = &S.knn_launches;
-    cudaError_t ce = cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s);
-    if (ce != cudaSuccess) return cuda_fail(ce, "status reset");
-    if (n > 0) {
-        timer.begin(StageTimer::GRID);
-        ce = launch_grid_build(pts, n, c.g, c.at<float4>(L.sorted), c.at<int32_t>(L.perm), c.at<int32_t>(L.cell_off),
-                               c.at<int32_t>(L.cid), c.at<int32_t>(L.ticket), c.at<int32_t>(L.counts),
-                               c.at<int32_t>(L.big), c.at<void>(L.scan_tmp), c.st, c.s);
-        timer.end();
-        if (ce != cudaSuccess) return cuda_fail(ce, "grid build");
-        if (out->perm) {
-            ce = cudaMemcpyAsync(out->perm, c.at<int32_t>(L.perm), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c.s);
-            if (ce != cudaSuccess) return cuda_fail(ce, "perm copy");
-        }
+    return tessellate_run(c, pts, n, p, out, stats);
+}
+
+int vt_batch_plan(const int64_t* set_off, int n_sets, const vt_params* p, const int* grid_res, vt_set_desc* plan,
+                  int64_t* total_cells)
+{
+    int e = check_params(p);
+    if (e) return e;
+    if (n_sets < 1 || !set_off || !plan || !total_cells) return fail(VT_ERR_INVALID_ARG, "bad batch plan arguments");
+    if (set_off[0] != 0) return fail(VT_ERR_INVALID_ARG, "set_off[0] must be 0");
+    int64_t cells = 0;
+    for (int sidx = 0; sidx < n_sets; ++sidx) {
+        const int64_t ns = set_off[sidx + 1] - set_off[sidx];
+        if (ns < 0) return fail(VT_ERR_INVALID_ARG, "set_off must be non-decreasing");
+        int G = grid_res && grid_res[sidx] > 0 ? grid_res[sidx] : grid_res_for(p, ns);
+        if (G > 1024) return fail(VT_ERR_INVALID_ARG, "grid resolution of set %d above 1024", sidx);
+        GridDesc g = make_grid(p, G);
+        g.cell_base = cells;
+        g.pt_begin = set_off[sidx];
+        g.npts = ns;
+        std::memcpy(&plan[sidx], &g, sizeof(g));
+        cells += (int64_t)G * G * G;
     }
-    // six lists of n cells: regular current/next, robust current/next, robust new, unvalidated
-    int32_t* lists = c.at<int32_t>(L.list_a);
-    int32_t* reg_cur = lists;
-    int32_t* reg_nxt = lists + n;
-    int32_t* rob_cur = lists + 2 * n;
-    int32_t* rob_nxt = lists + 3 * n;
-    int32_t* rob_new = lists + 4 * n;
-    int32_t* unval = lists + 5 * n;
-    const int variant_reg = p->precision == VT_FP64 ? 1 : 0;
-    int64_t m_reg = n, m_rob = 0, n_unval = 0;
-    bool implicit = true;  // the first pass runs over all cells without a list
-    int k = p->k0;
-    int k_prev = 0;  // regular cells resume from their saved state after list entry k_prev
-    int r = VT_OK;
-    DevStatus h{};
-    while (m_reg + m_rob > 0) {
-        const bool exhaustive = k > p->k_max;
-        const int kk = exhaustive ? 0 : k;
-        if (S.passes < VT_MAX_PASSES) {
-            S.k_of_pass[S.passes] = kk;
-            S.cells_of_pass[S.passes] = m_reg + m_rob;
-        }
-        timer.pass = S.passes;
-        ++S.passes;
-        if (exhaustive) S.exhaustive_cells = m_reg + m_rob;
-        int64_t got_next = 0, got_rob = 0;
-        if (m_reg > 0) {
-            if ((r = zero_counters(c))) return r;
-            if (implicit && (int64_t)kk * m_reg > L.knn_cap) {
-                k_iota<<<(unsigned)((m_reg + 255) / 256 < 152 * 64 ? (m_reg + 255) / 256 : 152 * 64), 256, 0, c.s>>>(
-                    reg_cur, m_reg);
-                count_launch();
-                implicit = false;
-            }
-            r = clip_pass(c, p, implicit ? nullptr : reg_cur, m_reg, kk, k_prev, variant_reg, p->precision, out,
-                          reg_nxt, rob_new);
-            if (r) return r;
-            if ((r = read_status(c, h))) return r;
-            if ((r = status_errors(h))) return r;
-            got_next = h.n_fail_next;
-            got_rob = h.n_fail_robust;
-        }
-        implicit = false;
-        if (got_rob > 0) {
-            ce = cudaMemcpyAsync(rob_cur + m_rob, rob_new, sizeof(int32_t) * got_rob, cudaMemcpyDeviceToDevice, c.s);
-            if (ce != cudaSuccess) return cuda_fail(ce, "list copy");
-            m_rob += got_rob;
-        }
-        int64_t rob_next = 0;
-        if (m_rob > 0) {
-            if ((r = zero_counters(c))) return r;
-            r = clip_pass(c, p, rob_cur, m_rob, kk, 0, 2, VT_FP64, out, rob_nxt, unval + n_unval);
-            if (r) return r;
-            if ((r = read_status(c, h))) return r;
-            if ((r = status_errors(h))) return r;
-            rob_next = h.n_fail_next;
-            n_unval += h.n_fail_robust;
-        }
-        std::swap(reg_cur, reg_nxt);
-        std::swap(rob_cur, rob_nxt);
-        m_reg = got_next;
-        m_rob = rob_next;
-        if (exhaustive) {
-            n_unval += m_reg + m_rob;  // cannot happen: the exhaustive pass always concludes
-            break;
-        }
-        k_prev = k;
-        k *= 2;
-    }
-    S.unvalidated = n_unval;
-    r = emit_outputs(c, p, out);
-    if ((r = r ? r : read_status(c, h))) {
-        if (stats) *stats = S;
-        return r;
-    }
-    S.fp64_rechecks = (int64_t)h.fp64_rechecks;
-    S.capacity_retries = (int64_t)h.capacity_events;
-    S.precision_retries = (int64_t)h.precision_events;
-    for (int a = 0; a < 5; ++a) S.clip_events[a] = (int64_t)h.detail[a];
-    S.launches = (int)(launches() - l0);
-    if (timer.on) {
-        S.ms_grid = timer.total(StageTimer::GRID);
-        S.ms_knn = timer.total(StageTimer::KNN);
-        S.ms_clip = timer.total(StageTimer::CLIP);
-        S.ms_emit = timer.total(StageTimer::EMIT);
-        timer.per_pass(S.ms_clip_pass, VT_MAX_PASSES);
-    }
-    if (stats) *stats = S;
-    if (n_unval > 0) return fail(VT_ERR_UNVALIDATED, "%lld cells could not be validated", (long long)n_unval);
+    if (cells > (int64_t)INT32_MAX / 2) return fail(VT_ERR_INVALID_ARG, "too many grid cells in the batch");
+    *total_cells = cells;
     return VT_OK;
+}
+
+int vt_batch_workspace_size(const vt_params* p, int64_t n_total, int64_t total_cells, size_t* bytes)
+{
+    int e = check_params(p);
+    if (e) return e;
+    if (n_total < 0 || total_cells < 1 || !bytes) return fail(VT_ERR_INVALID_ARG, "bad batch sizes");
+    *bytes = make_layout(p, n_total, total_cells, true).total;
+    return VT_OK;
+}
+
+int vt_tessellate_batch(const float* pts, int64_t n_total, const vt_set_desc* plan, const int64_t* set_off,
+                        int n_sets, int64_t total_cells, const vt_params* p, vt_cells_out* out, vt_stats* stats,
+                        void* ws, size_t ws_bytes, void* stream)
+{
+    if (n_sets < 1 || !plan || !set_off || total_cells < 1)
+        return fail(VT_ERR_INVALID_ARG, "a batch needs its device plan, set offsets and cell count");
+    Ctx c;
+    int e = make_ctx(p, n_total, ws, ws_bytes, stream, c, total_cells, true);
+    if (e) return e;
+    c.sets = reinterpret_cast<const GridDesc*>(plan);
+    c.set_off = set_off;
+    c.nsets = n_sets;
+    return tessellate_run(c, pts, n_total, p, out, stats);
 }
 
 int vt_moments_adjoint(const float* pts, int64_t n, const vt_cells_out* cells, const double* gV, const double* gC,
@@ -644,6 +787,36 @@ int vt_read_status(void* ws, size_t ws_bytes, void* stream)
     int r = read_status(c, h);
     if (r) return r;
     return status_errors(h);
+}
+
+int vt_read_stats(void* ws, size_t ws_bytes, vt_stats* stats, vt_cells_out* out, void* stream)
+{
+    if (!ws || ws_bytes < sizeof(DevStatus)) return fail(VT_ERR_WORKSPACE, "workspace too small");
+    Ctx c;
+    c.base = (uint8_t*)ws;
+    c.s = (cudaStream_t)stream;
+    c.st = (DevStatus*)ws;
+    DevStatus h;
+    int r = read_status(c, h);
+    if (r) return r;
+    if (stats) {
+        stats->fp64_rechecks = (int64_t)h.fp64_rechecks;
+        stats->capacity_retries = (int64_t)h.capacity_events;
+        stats->precision_retries = (int64_t)h.precision_events;
+        stats->unvalidated = h.n_unval;
+        for (int a = 0; a < 5; ++a) stats->clip_events[a] = (int64_t)h.detail[a];
+    }
+    if (out) {
+        out->needed_nbr = h.totals[0];
+        out->needed_vtx = h.totals[1];
+        out->needed_face = h.totals[2];
+        out->needed_face_vtx = h.totals[3];
+    }
+    if ((r = status_errors(h))) return r;
+    if (h.record_overflow) return fail(VT_ERR_CAPACITY, "%d cells exceed the per-cell record size", h.record_overflow);
+    if (h.cap_overflow) return fail(VT_ERR_CAPACITY, "an output buffer was too small (needed_* hold the sizes)");
+    if (h.n_unval) return fail(VT_ERR_UNVALIDATED, "%d cells could not be validated", h.n_unval);
+    return VT_OK;
 }
 
 const char* vt_last_error(void) { return g_err.c_str(); }

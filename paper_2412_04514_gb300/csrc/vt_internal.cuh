@@ -18,7 +18,35 @@ struct GridDesc {
     float scale[3];   // float32(G) / (hi - lo), rounded once on the host
     double cw[3];     // cell width (hi - lo) / G in double (stop-rule geometry only)
     double margin;    // safety margin of the shell-walk stop rule (coordinates)
+    int64_t cell_base;  // first global grid cell of this point set (batches)
+    int64_t pt_begin;   // first input point of this point set
+    int64_t npts;       // points in this point set
 };
+static_assert(sizeof(GridDesc) == sizeof(vt_set_desc), "vt_set_desc mirrors GridDesc");
+
+// grid of the point set that sorted point q belongs to
+__device__ __forceinline__ const GridDesc& grid_of(const GridDesc& g0, const GridDesc* sets, const int32_t* set_of,
+                                                   int q)
+{
+    return sets ? sets[set_of[q]] : g0;
+}
+
+// distance from q (in grid cell (ix, iy, iz)) to the outside of the block of
+// shells 0..s, minus the rounding margin; 1e300 when the block reaches every
+// wall of the box (no generator lies beyond it)
+__device__ __forceinline__ double shell_gap(const GridDesc& g, float4 q, int ix, int iy, int iz, int s)
+{
+    const int G = g.G;
+    const double q0 = q.x, q1 = q.y, q2 = q.z;
+    double gap = 1e300;
+    if (ix - s > 0) gap = fmin(gap, q0 - ((double)g.lo[0] + (ix - s) * g.cw[0]) - g.margin);
+    if (ix + s + 1 < G) gap = fmin(gap, ((double)g.lo[0] + (ix + s + 1) * g.cw[0]) - q0 - g.margin);
+    if (iy - s > 0) gap = fmin(gap, q1 - ((double)g.lo[1] + (iy - s) * g.cw[1]) - g.margin);
+    if (iy + s + 1 < G) gap = fmin(gap, ((double)g.lo[1] + (iy + s + 1) * g.cw[1]) - q1 - g.margin);
+    if (iz - s > 0) gap = fmin(gap, q2 - ((double)g.lo[2] + (iz - s) * g.cw[2]) - g.margin);
+    if (iz + s + 1 < G) gap = fmin(gap, ((double)g.lo[2] + (iz + s + 1) * g.cw[2]) - q2 - g.margin);
+    return gap;
+}
 
 GridDesc make_grid(const vt_params* p, int G);
 
@@ -89,7 +117,8 @@ struct DevStatus {
     int32_t n_fail_robust;    // cells that need the robust variant (capacity / precision)
     int32_t n_big_cells;      // grid cells too large for the per-thread fix-up sort
     int32_t record_overflow;  // cells whose final polyhedron does not fit an output record
-    int32_t pad[2];
+    int32_t cap_overflow;     // an output buffer was too small for the emitted data (device check)
+    int32_t n_unval;          // cells left unvalidated (no-sync schedule)
     unsigned long long fp64_rechecks;
     unsigned long long capacity_events;
     unsigned long long precision_events;
@@ -133,10 +162,11 @@ struct Layout {
     size_t rec_stride;
     size_t status, cid, ticket, counts, cell_off, big, scan_tmp, sorted, perm;
     size_t state_stride;
-    size_t list_a, list_b, list_r, knn_nbr, knn_d2, rec, cnt, off64, state;
+    size_t list_a, list_b, list_r, knn_nbr, knn_d2, rec, cnt, off64, scan_emit, state, set_of, ctr;
     size_t total;
 };
-Layout make_layout(const vt_params* p, int64_t n);
+// cells < 0: the single-set grid of p; otherwise the total grid cells of a batch
+Layout make_layout(const vt_params* p, int64_t n, int64_t cells = -1, bool batch = false);
 
 // ---------------------------------------------------------------------------
 // launch helpers shared by the translation units
@@ -151,13 +181,24 @@ void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, void* tmp, c
 void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s);
 
 // stage launchers (return cudaError_t of the launch)
+// batches: sets (device, nsets descriptors), set_off (device, nsets + 1 point
+// offsets), g3 = total grid cells of all sets; set_of receives the set of each
+// sorted point. A single set passes sets = set_off = set_of = nullptr.
+struct BatchArgs {
+    const GridDesc* sets;
+    const int64_t* set_off;
+    int nsets;
+    int32_t* set_of;
+};
 cudaError_t launch_grid_build(const float* pts, int64_t n, const GridDesc& g, float4* sorted, int32_t* perm,
                               int32_t* cell_off, int32_t* cid, int32_t* ticket, int32_t* counts, int32_t* big,
-                              void* scan_tmp, DevStatus* st, cudaStream_t s);
+                              void* scan_tmp, DevStatus* st, cudaStream_t s, const BatchArgs* batch = nullptr,
+                              int64_t g3 = -1);
 
 cudaError_t launch_knn(const float4* sorted, const int32_t* cell_off, const GridDesc& g, int64_t n,
                        const int32_t* queries, int64_t nq, int k, int precision, int32_t* nbr, void* d2,
-                       DevStatus* st, cudaStream_t s);
+                       DevStatus* st, cudaStream_t s, const GridDesc* sets = nullptr, const int32_t* set_of = nullptr,
+                       const int32_t* nq_dev = nullptr);
 
 struct ClipArgs {
     const float4* sorted;
@@ -181,6 +222,9 @@ struct ClipArgs {
                               // the robust variant itself, cells left unvalidated)
     int32_t* ctr_next;        // device counters of the two lists
     int32_t* ctr_robust;
+    const GridDesc* sets;     // per-set grids of a batch (NULL: the single grid g)
+    const int32_t* set_of;    // set of each sorted point (batches)
+    const int32_t* nq_dev;    // when set, the cell count is read from device memory
     int k_prev;               // > 0: resume saved cells; list entries [0, k_prev) are done
     uint8_t* state;           // per-cell saved polyhedra (sorted index * state_stride), or NULL
     size_t state_stride;
@@ -201,7 +245,7 @@ struct EmitArgs {
     DevStatus* st;
 };
 cudaError_t launch_emit_count(const EmitArgs& a, cudaStream_t s);  // counts + scans + totals
-cudaError_t launch_emit_write(const EmitArgs& a, const vt_cells_out& out, cudaStream_t s);
+cudaError_t launch_emit_write(const EmitArgs& a, const vt_cells_out& out, cudaStream_t s);  // device-checked caps
 cudaError_t launch_adjoint(const float* pts, int64_t n, const vt_cells_out& c, const double* gV, const double* gC,
                            const double* gM, double* grad, cudaStream_t s);
 
