@@ -35,7 +35,13 @@ WORKLOADS = {
     "mixed-8m": dict(n=1 << 23, seed=2, desc="8,388,608 float32 points, same recipe as mixed-1m, seed 2"),
     "mixed-300k": dict(n=300_000, seed=1, clumps=300, desc="300,000 float32 points, the mixed-1m recipe with 300 "
                        "clumps (a small case for profiler captures)"),
+    "batch-512": dict(batch=True, seed=3, desc="512 independent point sets in [0,1)^3, sizes floor(10^U(3, log10 2e5)) "
+                      "(about 18M points), each uniform or mixed-recipe clustered by a seeded coin flip, seed 3; "
+                      "one CUDA graph per step (no-sync schedule), threads-per-cell / k0 / k_max / per-class grid "
+                      "density autotuned on 64 seeded sets before the timed region; outputs neighbours + volume + "
+                      "centroid"),
 }
+BATCH_SPACE = {"tpc": [16, 32], "k0": [12, 16, 24], "kmax_mult": [2], "rho": [1.0, 2.0, 3.0, 4.0, 6.0], "reps": 2}
 # FP32 FMA peak from the unit counts and the maximum SM clock: 152 SMs x 128
 # FP32 lanes x 2 flops x 2.070 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -206,6 +212,8 @@ def run_gpu(args, rank: int, world: int, local: int):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     wl = WORKLOADS[args.workload]
+    if wl.get("batch"):
+        return run_batch(args, rank, world, local)
     n = wl["n"]
     pts_np = W.mixed(n, wl["seed"] + 1000 * rank, n_clumps=wl.get("clumps", 1000))
     pts = torch.from_numpy(pts_np).to(dev)
@@ -314,6 +322,112 @@ def run_gpu(args, rank: int, world: int, local: int):
         "passes": {"k_of_pass": st32[-1]["k_of_pass"], "cells_of_pass": st32[-1]["cells_of_pass"],
                    "fp64_rechecks": st32[-1]["fp64_rechecks"], "precision_retries": st32[-1]["precision_retries"],
                    "capacity_retries": st32[-1]["capacity_retries"], "unvalidated": st32[-1]["unvalidated"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args, rank: int, world: int, local: int):
+    """The batch workload: the whole batch as one CUDA-graph replay per step."""
+    import torch
+
+    import paper_2412_04514_gb300 as vt
+    from paper_2412_04514_gb300 import workloads as W
+
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[args.workload]
+    pts_np, off, coin = W.batch_sets(seed=wl["seed"] + 1000 * rank)
+    n = len(pts_np)
+    pts = torch.from_numpy(pts_np).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    prm = vt.Params(precision="fp32", emit=("nbr", "vol", "cen"))
+    t0 = time.perf_counter()
+    b = vt.tuned_batch(pts, off, prm, space=BATCH_SPACE, sample_sets=64, seed=7)
+    tune_s = time.perf_counter() - t0
+    l0 = vt.launch_count()
+    b.capture()
+    per_replay = (vt.launch_count() - l0) // 2  # capture() runs once eagerly, then records
+    for _ in range(args.warmup):
+        b.replay()
+    b.result()
+    stream = torch.cuda.current_stream(dev)
+    ms = []
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            b.replay()
+            e.record(stream)
+            e.synchronize()
+            ms.append(a.elapsed_time(e))
+    clocks = clk.summary()
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    cells = b.result()
+    tot = dist_max(sum(ms), world)
+    value = n * world * len(ms) / (tot / 1e3)
+
+    # end to end: pinned host points in, replay, results back to pinned host memory
+    host = torch.from_numpy(pts_np).pin_memory()
+    outs = {k: torch.empty(getattr(cells, k).shape, dtype=getattr(cells, k).dtype, pin_memory=True)
+            for k in ("vol", "cen", "nbr_off")}
+    e2e_ms, d2h = [], 0
+    for i in range(args.warmup + args.steps if not args.no_e2e else 0):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        b.points.copy_(host, non_blocking=True)
+        b.replay()
+        c = b.result()
+        nbr_h = c.nbr.to("cpu")
+        for k, v in outs.items():
+            v.copy_(getattr(c, k), non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t1))
+        d2h = nbr_h.numel() * 4 + sum(v.numel() * v.element_size() for v in outs.values())
+    e2e_tot = dist_max(sum(e2e_ms), world) if e2e_ms else 0.0
+    if rank != 0:
+        return
+    # stage split and roofline from one stage-timed run of the same tuned batch (synchronising schedule)
+    sync = vt.tessellate_batch(pts, off, vt.Params(**{**b.params.__dict__, "no_sync": False, "stage_times": True}),
+                               grid_res=b.grid_res).stats
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        big = int(np.argmax(np.diff(off)))
+        sub = pts_np[off[big]:off[big + 1]]
+        cpu = cpu_oracle_rate(sub, min(args.cpu_cells, len(sub)))
+        cpu["sample"] += f" (set {big} of the batch, {len(sub)} points)"
+    flops_per_cell = cpu["flops_per_cell"] if cpu else args.flops_per_cell
+    achieved = n * flops_per_cell / (sync["ms_clip"] / 1e3) / 1e12
+    tr = b.tune_report
+    line = {
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": len(ms),
+        "warmup": args.warmup, "ms_per_step": tot / len(ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "n_points": n, "n_sets": len(off) - 1, "precision": "fp32+fp64-recheck",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}",
+                   "tuned": {"threads_per_cell": b.params.threads_per_cell, "k0": b.params.k0,
+                             "k_max": b.params.k_max, "density_of_class": tr["density_of_class"],
+                             "class_counts": tr["class_counts"], "tune_seconds": tune_s,
+                             "candidates": tr["n_tried"]}},
+        "e2e": None if not e2e_ms else {
+            "value": n * world * len(e2e_ms) / (e2e_tot / 1e3), "unit": "cells/s", "h2d_bytes_per_step": n * 12,
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_tot / len(e2e_ms)},
+        "roofline": {
+            "kernel": f"k_clip<float,{b.params.threads_per_cell},...> (all passes, stage-timed synchronising run)",
+            "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (unit counts and max SM clock)",
+            "stage_ms": {k: sync[k] for k in ("ms_grid", "ms_knn", "ms_clip", "ms_emit")}},
+        "cpu_baseline": None if cpu is None else {"value": cpu["value"], "unit": "cells/s", "cores": cpu["cores"],
+                                                  "kind": "oracle", "sample": cpu["sample"]},
+        "gpu_launches": int(per_replay * len(ms)),
+        "clocks": clocks,
+        "status": cells.stats["status"],
     }
     print(json.dumps(line), flush=True)
 

@@ -313,6 +313,84 @@ VT_API int vt_tessellate_batch(const float* pts, int64_t n_total, const vt_set_d
                                vt_cells_out* out, vt_stats* stats, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ */
+/* autotuning of threads per cell, k0, k_max and grid density          */
+/* ------------------------------------------------------------------ */
+
+/* The paper sets its launch parameters by hand for one GPU; these calls pick
+ * them by timing the whole path (grid, kNN, clipping, re-queue, emit) with
+ * CUDA events on the caller's points, one parameter at a time: grid density,
+ * k0, the k_max multiple, threads per cell. */
+
+#define VT_TUNE_CLASSES 4
+#define VT_TUNE_MAX_TRIED 64
+
+/* Morisita index of each set on its grid: I = G^3 * sum_c n_c (n_c - 1) /
+ * (n (n - 1)) over the grid cells c (n_c generators each), about 1 for
+ * uniform i.i.d. points, above 1 when clustered, 0 for n < 2. plan = NULL:
+ * one set over the grid of p (workspace of vt_workspace_size); else the
+ * device plan and set_off of a batch (workspace of vt_batch_workspace_size).
+ * index[n_sets] is host memory. Blocking; VT_ERR_INVALID_ARG for points
+ * outside the box. */
+VT_API int vt_cluster_index(const float* pts, int64_t n_total, const vt_set_desc* plan, const int64_t* set_off,
+                            int n_sets, int64_t total_cells, const vt_params* p, double* index, void* ws,
+                            size_t ws_bytes, void* stream);
+
+/* Clustering class of a Morisita index: 0 below 2, 1 below 8, 2 below 32, else 3. */
+VT_API int vt_cluster_class(double index);
+
+typedef struct vt_tune_space {
+    int n_tpc, tpc[4];          /* threads-per-cell candidates (8, 16, 32) */
+    int n_k0, k0[8];            /* initial k candidates */
+    int n_kmax, kmax_mult[4];   /* k_max = min(256, k0 * mult) candidates */
+    int n_rho;                  /* grid-density candidates */
+    float rho[8];
+    int reps;                   /* timed runs per candidate after one untimed run */
+} vt_tune_space;
+
+typedef struct vt_tune_trial {
+    int threads_per_cell, k0, k_max, cls;   /* cls: the class whose density was varied */
+    float grid_density;
+    int status;                             /* VT_OK or the run's error */
+    double ms;                              /* minimum over reps, -1 if it failed */
+} vt_tune_trial;
+
+typedef struct vt_tune_result {
+    vt_params best;                         /* base with the tuned fields */
+    float density_of_class[VT_TUNE_CLASSES];/* batches: grid density per clustering class */
+    double best_ms;
+    int n_tried;                            /* candidates timed (tried[] keeps the first 64) */
+    vt_tune_trial tried[VT_TUNE_MAX_TRIED];
+} vt_tune_result;
+
+/* Default space: tpc {8,16,32}, k0 {8,12,16,24,32}, mult {1,2,4}, rho {1,2,3,4,6}, reps 3. */
+VT_API void vt_tune_space_default(vt_tune_space* s);
+
+/* Workspace bytes for vt_autotune on n points (the widest candidate). */
+VT_API int vt_autotune_workspace_size(const vt_params* base, const vt_tune_space* s, int64_t n, size_t* bytes);
+
+/* Tunes one point set pts[n*3] (device) starting from base (whose emit,
+ * precision, box and flags every candidate keeps); out holds output buffers
+ * for n cells (capacities as for vt_tessellate). res->best is the fastest
+ * candidate that completed with VT_OK. Blocking. */
+VT_API int vt_autotune(const float* pts, int64_t n, const vt_params* base, const vt_tune_space* s,
+                       vt_cells_out* out, vt_tune_result* res, void* ws, size_t ws_bytes, void* stream);
+
+/* Workspace bytes for vt_autotune_batch (the widest candidate). */
+VT_API int vt_autotune_batch_workspace_size(const int64_t* set_off, int n_sets, const vt_params* base,
+                                            const vt_tune_space* s, size_t* bytes);
+
+/* Tunes a batch: one grid density per clustering class (set_class[n_sets],
+ * host, from vt_cluster_class), and k0, k_max, threads per cell for the whole
+ * batch. set_off_host / set_off_dev are the offsets on the host and device;
+ * plan_dev (device, n_sets descriptors) is overwritten by each candidate's
+ * plan. The schedule of base->flags (VT_FLAG_NO_SYNC or not) is the one
+ * timed. Blocking. */
+VT_API int vt_autotune_batch(const float* pts, const int64_t* set_off_host, const int64_t* set_off_dev, int n_sets,
+                             const int* set_class, const vt_params* base, const vt_tune_space* s,
+                             vt_set_desc* plan_dev, vt_cells_out* out, vt_tune_result* res, void* ws,
+                             size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
 /* adjoint of the cell moments (for Lloyd relaxation and cell losses)  */
 /* ------------------------------------------------------------------ */
 

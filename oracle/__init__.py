@@ -8,7 +8,9 @@ or runs it, and this package imports nothing from the product.
 Contents
 --------
 * :func:`grid_sort` -- the grid counting sort written out in NumPy (paper,
-  Summary: "the input set of points is sorted into a grid").
+  Summary: the generators are first binned into a uniform grid).
+* :func:`morisita_index` -- the clustering statistic the autotuner keys on:
+  the Morisita index of the generators on that grid.
 * :func:`knn` -- exact k nearest neighbours (C kd-tree), ordered by
   ``(d2, index)`` with ``d2`` in double from the float32 inputs.
 * :func:`tessellate` -- Voronoi cells by nearest-first bisector clipping of
@@ -175,6 +177,22 @@ def grid_sort(points, G: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)) -> dict:
     off[1:] = np.cumsum(counts)
     perm = np.argsort(cid, kind="stable")
     return {"cid": cid, "cell_off": off, "perm": perm.astype(np.int64), "sorted": p[perm]}
+
+
+def morisita_index(points, G: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)) -> float:
+    """Morisita's index of dispersion of the points over the G^3 grid cells:
+    I = Q * sum_c n_c (n_c - 1) / (n (n - 1)) with Q = G^3 cells holding n_c
+    points each (Morisita 1959). It is the ratio of the observed probability
+    that two distinct points share a cell to the one under a uniform
+    distribution: 1 in expectation for i.i.d. uniform points, 0 when no cell
+    holds two points, Q when all points share one cell. 0 for n < 2."""
+    p = _pts(points)
+    n = len(p)
+    if n < 2:
+        return 0.0
+    counts = np.bincount(grid_cell_ids(p, G, lo, hi), minlength=G**3).astype(np.int64)
+    pairs = int(np.sum(counts * (counts - 1)))
+    return float(G**3) * float(pairs) / (float(n) * (float(n) - 1.0))
 
 
 def grid_resolution(n: int, rho: float) -> int:

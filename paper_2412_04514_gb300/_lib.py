@@ -44,8 +44,11 @@ EXPORTS = [
     "vt_params_default", "vt_grid_resolution", "vt_workspace_size", "vt_grid_build", "vt_knn", "vt_clip_cells",
     "vt_emit", "vt_tessellate", "vt_read_status", "vt_last_error", "vt_launch_count", "vt_version",
     "vt_grid_build_static", "vt_moments_adjoint", "vt_batch_plan", "vt_batch_workspace_size",
-    "vt_tessellate_batch", "vt_read_stats",
+    "vt_tessellate_batch", "vt_read_stats", "vt_cluster_index", "vt_cluster_class", "vt_tune_space_default",
+    "vt_autotune_workspace_size", "vt_autotune", "vt_autotune_batch_workspace_size", "vt_autotune_batch",
 ]
+VT_TUNE_CLASSES = 4
+VT_TUNE_MAX_TRIED = 64
 
 
 class VtParams(ctypes.Structure):
@@ -100,6 +103,42 @@ class VtSetDesc(ctypes.Structure):
         ("cell_base", ctypes.c_int64),
         ("pt_begin", ctypes.c_int64),
         ("npts", ctypes.c_int64),
+    ]
+
+
+class VtTuneSpace(ctypes.Structure):
+    _fields_ = [
+        ("n_tpc", ctypes.c_int),
+        ("tpc", ctypes.c_int * 4),
+        ("n_k0", ctypes.c_int),
+        ("k0", ctypes.c_int * 8),
+        ("n_kmax", ctypes.c_int),
+        ("kmax_mult", ctypes.c_int * 4),
+        ("n_rho", ctypes.c_int),
+        ("rho", ctypes.c_float * 8),
+        ("reps", ctypes.c_int),
+    ]
+
+
+class VtTuneTrial(ctypes.Structure):
+    _fields_ = [
+        ("threads_per_cell", ctypes.c_int),
+        ("k0", ctypes.c_int),
+        ("k_max", ctypes.c_int),
+        ("cls", ctypes.c_int),
+        ("grid_density", ctypes.c_float),
+        ("status", ctypes.c_int),
+        ("ms", ctypes.c_double),
+    ]
+
+
+class VtTuneResult(ctypes.Structure):
+    _fields_ = [
+        ("best", VtParams),
+        ("density_of_class", ctypes.c_float * VT_TUNE_CLASSES),
+        ("best_ms", ctypes.c_double),
+        ("n_tried", ctypes.c_int),
+        ("tried", VtTuneTrial * VT_TUNE_MAX_TRIED),
     ]
 
 
@@ -212,6 +251,22 @@ def load() -> ctypes.CDLL:
         L.vt_tessellate_batch.restype = I
         L.vt_read_stats.argtypes = [P, ctypes.c_size_t, ps, po, P]
         L.vt_read_stats.restype = I
+        pts_ = ctypes.POINTER(VtTuneSpace)
+        ptr_ = ctypes.POINTER(VtTuneResult)
+        L.vt_cluster_index.argtypes = [P, I64, P, P, I, I64, pp, P, P, ctypes.c_size_t, P]
+        L.vt_cluster_index.restype = I
+        L.vt_cluster_class.argtypes = [ctypes.c_double]
+        L.vt_cluster_class.restype = I
+        L.vt_tune_space_default.argtypes = [pts_]
+        L.vt_tune_space_default.restype = None
+        L.vt_autotune_workspace_size.argtypes = [pp, pts_, I64, ctypes.POINTER(ctypes.c_size_t)]
+        L.vt_autotune_workspace_size.restype = I
+        L.vt_autotune.argtypes = [P, I64, pp, pts_, po, ptr_, P, ctypes.c_size_t, P]
+        L.vt_autotune.restype = I
+        L.vt_autotune_batch_workspace_size.argtypes = [P, I, pp, pts_, ctypes.POINTER(ctypes.c_size_t)]
+        L.vt_autotune_batch_workspace_size.restype = I
+        L.vt_autotune_batch.argtypes = [P, P, P, I, P, pp, pts_, P, po, ptr_, P, ctypes.c_size_t, P]
+        L.vt_autotune_batch.restype = I
         _lib = L
         return L
 

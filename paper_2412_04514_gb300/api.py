@@ -347,17 +347,57 @@ class Batch:
 
 def tessellate_batch(points: torch.Tensor, set_off, params: Params | None = None, grid_res=None,
                      strict: bool = True) -> Cells:
-    """One-shot batch: plan, run, and grow the outputs once if they were too small."""
-    b = Batch(points, set_off, params, grid_res)
-    b.run()
-    try:
+    """One-shot batch. With the default synchronising schedule this is
+    vt_tessellate_batch with the per-pass re-queue and the stage times of
+    ``params.stage_times``; with ``params.no_sync`` it runs a :class:`Batch`.
+    Variable-length outputs that do not fit are reallocated from the exact
+    counts and written again by vt_emit."""
+    params = params or Params()
+    if params.no_sync:
+        b = Batch(points, set_off, params, grid_res)
+        b.run()
+        try:
+            return b.result(strict)
+        except L.VtError as e:
+            if e.code != L.VT_ERR_CAPACITY:
+                raise
+        b.grow()
+        b.run()
         return b.result(strict)
-    except L.VtError as e:
-        if e.code != L.VT_ERR_CAPACITY:
-            raise
-    b.grow()
-    b.run()
-    return b.result(strict)
+    pts = _check_points(points)
+    n = pts.shape[0]
+    dev = pts.device
+    lib = L.load()
+    off = [int(x) for x in set_off]
+    if off[-1] != n:
+        raise ValueError("set_off[-1] must equal the number of points")
+    plan, total = batch_plan(off, params, grid_res)
+    plan_d = torch.frombuffer(bytearray(bytes(plan)), dtype=torch.uint8).to(dev)
+    off_d = torch.tensor(off, dtype=torch.int64, device=dev)
+    b = ctypes.c_size_t()
+    pc = params.c()
+    L.check(lib.vt_batch_workspace_size(ctypes.byref(pc), n, total, ctypes.byref(b)))
+    ws = torch.empty(max(b.value, 256), dtype=torch.uint8, device=dev)
+    cells = _alloc(params, n, dev, False)
+    o = _out_struct(cells)
+    st = L.VtStats()
+    s = _stream(dev)
+    code = lib.vt_tessellate_batch(_ptr(pts), n, _ptr(plan_d), _ptr(off_d), len(off) - 1, total, ctypes.byref(pc),
+                                   ctypes.byref(o), ctypes.byref(st), _ptr(ws), ws.numel(), s)
+    if code == L.VT_ERR_CAPACITY:
+        guess = {"nbr": o.needed_nbr, "vtx": o.needed_vtx, "face": o.needed_face, "face_vtx": o.needed_face_vtx}
+        fresh = _alloc(Params(**{**params.__dict__, "emit": tuple(x for x in params.emit if x in ("nbr", "geom"))}),
+                       n, dev, False, guess)
+        for name in ("nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx_off", "face_vtx"):
+            setattr(cells, name, getattr(fresh, name))
+        o = _out_struct(cells)
+        code = lib.vt_emit(n, ctypes.byref(pc), ctypes.byref(o), _ptr(ws), ws.numel(), s)
+    cells.stats = st.as_dict()
+    cells.stats["status"] = L.STATUS_NAMES.get(code, code)
+    if code not in (L.VT_OK, L.VT_ERR_UNVALIDATED) or (strict and code != L.VT_OK):
+        L.check(code)
+    _trim(cells, o)
+    return cells
 
 
 # ---------------------------------------------------------------------------

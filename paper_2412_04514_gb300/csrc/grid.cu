@@ -146,7 +146,38 @@ unsigned blocks_for(int64_t n, int threads)
     return (unsigned)b;
 }
 
+// sum over grid cells of n_c (n_c - 1), per set (exact 64-bit integer sums);
+// the set of global cell c is the last s with cell_base <= c
+__global__ void k_pair_counts(const int32_t* __restrict__ cell_off, int64_t g3, const GridDesc* __restrict__ sets,
+                              int nsets, unsigned long long* __restrict__ acc)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g3; c += (int64_t)gridDim.x * blockDim.x) {
+        const long long m = (long long)cell_off[c + 1] - cell_off[c];
+        if (m < 2) continue;
+        int s = 0;
+        if (sets) {
+            int lo = 0, hi = nsets - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sets[mid].cell_base <= c) lo = mid; else hi = mid - 1;
+            }
+            s = lo;
+        }
+        atomicAdd(&acc[s], (unsigned long long)(m * (m - 1)));
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_pair_counts(const int32_t* cell_off, int64_t g3, const GridDesc* sets, int nsets,
+                               unsigned long long* acc, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (nsets > 0 ? nsets : 1), s);
+    if (e != cudaSuccess) return e;
+    k_pair_counts<<<blocks_for(g3, 256), 256, 0, s>>>(cell_off, g3, sets, nsets, acc);
+    count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_grid_build(const float* pts, int64_t n, const GridDesc& g, float4* sorted, int32_t* perm,
                               int32_t* cell_off, int32_t* cid, int32_t* ticket, int32_t* counts, int32_t* big,

@@ -789,6 +789,63 @@ int vt_read_status(void* ws, size_t ws_bytes, void* stream)
     return status_errors(h);
 }
 
+int vt_cluster_index(const float* pts, int64_t n_total, const vt_set_desc* plan, const int64_t* set_off, int n_sets,
+                     int64_t total_cells, const vt_params* p, double* index, void* ws, size_t ws_bytes, void* stream)
+{
+    if (!index || n_sets < 1) return fail(VT_ERR_INVALID_ARG, "index is NULL or n_sets < 1");
+    if (!plan && n_sets != 1) return fail(VT_ERR_INVALID_ARG, "several sets need a plan");
+    Ctx c;
+    int e = plan ? make_ctx(p, n_total, ws, ws_bytes, stream, c, total_cells, true)
+                 : make_ctx(p, n_total, ws, ws_bytes, stream, c);
+    if (e) return e;
+    if (n_total > 0 && !pts) return fail(VT_ERR_INVALID_ARG, "pts is NULL");
+    if (plan) {
+        if (!set_off) return fail(VT_ERR_INVALID_ARG, "a plan needs set_off");
+        c.sets = reinterpret_cast<const GridDesc*>(plan);
+        c.set_off = set_off;
+        c.nsets = n_sets;
+    }
+    const Layout& L = c.L;
+    if ((int64_t)n_sets > L.knn_cap) return fail(VT_ERR_INVALID_ARG, "more sets than the workspace can count");
+    std::vector<GridDesc> h_sets(n_sets);
+    cudaError_t ce = cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "status reset");
+    if (plan) {
+        ce = cudaMemcpyAsync(h_sets.data(), plan, sizeof(GridDesc) * n_sets, cudaMemcpyDeviceToHost, c.s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "plan read");
+    } else {
+        h_sets[0] = c.g;
+        h_sets[0].npts = n_total;
+    }
+    unsigned long long* acc = c.at<unsigned long long>(L.knn_d2);
+    if (n_total > 0) {
+        BatchArgs b{c.sets, c.set_off, c.nsets, c.set_of()};
+        ce = launch_grid_build(pts, n_total, c.g, c.at<float4>(L.sorted), c.at<int32_t>(L.perm),
+                               c.at<int32_t>(L.cell_off), c.at<int32_t>(L.cid), c.at<int32_t>(L.ticket),
+                               c.at<int32_t>(L.counts), c.at<int32_t>(L.big), c.at<void>(L.scan_tmp), c.st, c.s,
+                               c.sets ? &b : nullptr, L.g3);
+        if (ce == cudaSuccess)
+            ce = launch_pair_counts(c.at<int32_t>(L.cell_off), L.g3, c.sets, c.sets ? n_sets : 1, acc, c.s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "grid build");
+    } else {
+        ce = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * n_sets, c.s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "clear");
+    }
+    std::vector<unsigned long long> h_acc(n_sets);
+    ce = cudaMemcpyAsync(h_acc.data(), acc, sizeof(unsigned long long) * n_sets, cudaMemcpyDeviceToHost, c.s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "count read");
+    DevStatus h;
+    int r = read_status(c, h);
+    if (r) return r;
+    if ((r = status_errors(h))) return r;
+    for (int sidx = 0; sidx < n_sets; ++sidx) {
+        const double ns = (double)h_sets[sidx].npts;
+        const double g3 = (double)h_sets[sidx].G * h_sets[sidx].G * h_sets[sidx].G;
+        index[sidx] = ns < 2 ? 0.0 : g3 * (double)h_acc[sidx] / (ns * (ns - 1.0));
+    }
+    return VT_OK;
+}
+
 int vt_read_stats(void* ws, size_t ws_bytes, vt_stats* stats, vt_cells_out* out, void* stream)
 {
     if (!ws || ws_bytes < sizeof(DevStatus)) return fail(VT_ERR_WORKSPACE, "workspace too small");

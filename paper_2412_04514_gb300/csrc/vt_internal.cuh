@@ -195,6 +195,10 @@ cudaError_t launch_grid_build(const float* pts, int64_t n, const GridDesc& g, fl
                               void* scan_tmp, DevStatus* st, cudaStream_t s, const BatchArgs* batch = nullptr,
                               int64_t g3 = -1);
 
+// acc[s] = sum over the grid cells of set s of n_c (n_c - 1) (sets = nullptr: one set)
+cudaError_t launch_pair_counts(const int32_t* cell_off, int64_t g3, const GridDesc* sets, int nsets,
+                               unsigned long long* acc, cudaStream_t s);
+
 cudaError_t launch_knn(const float4* sorted, const int32_t* cell_off, const GridDesc& g, int64_t n,
                        const int32_t* queries, int64_t nq, int k, int precision, int32_t* nbr, void* d2,
                        DevStatus* st, cudaStream_t s, const GridDesc* sets = nullptr, const int32_t* set_of = nullptr,

@@ -53,10 +53,10 @@ def split(cells, off, s):
     return np_(cells.vol)[a:b], np_(cells.cen)[a:b], np_(cells.m2)[a:b], lists
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_batch_matches_the_oracle_per_set(batch, prec):
+@pytest.mark.parametrize("prec,no_sync", [("fp64", False), ("fp64", True), ("fp32", False), ("fp32", True)])
+def test_batch_matches_the_oracle_per_set(batch, prec, no_sync):
     pts, off, parts, want = batch
-    cells = vt.tessellate_batch(dev(pts), off, vt.Params(precision=prec, emit=EMIT))
+    cells = vt.tessellate_batch(dev(pts), off, vt.Params(precision=prec, emit=EMIT, no_sync=no_sync))
     assert cells.stats["status"] == "VT_OK"
     for s, w in enumerate(want):
         if w is None:
@@ -81,7 +81,7 @@ def test_batch_is_bit_identical_to_single_set_runs(batch, prec):
     pts, off, parts, _ = batch
     G = [vt.grid_resolution(vt.Params(), max(len(p), 1)) for p in parts]
     prm = vt.Params(precision=prec, emit=EMIT)
-    cells = vt.tessellate_batch(dev(pts), off, prm, grid_res=G)
+    cells = vt.tessellate_batch(dev(pts), off, vt.Params(precision=prec, emit=EMIT, no_sync=True), grid_res=G)
     for s, p in enumerate(parts):
         if not len(p):
             continue
@@ -113,7 +113,7 @@ def test_graph_replay_equals_eager_runs(batch):
     b.points.copy_(dev(other))
     b.replay()
     got = b.result()
-    want = vt.tessellate_batch(dev(other), off, vt.Params(precision="fp32", emit=EMIT))
+    want = vt.tessellate_batch(dev(other), off, vt.Params(precision="fp32", emit=EMIT))  # synchronising schedule
     for name in ("vol", "cen", "m2", "nbr_off", "nbr"):
         assert torch.equal(getattr(got, name), getattr(want, name)), name
     snap = {k: getattr(got, k).clone() for k in ("vol", "nbr")}
@@ -146,6 +146,16 @@ def test_no_sync_reports_bad_points():
     with pytest.raises(L.VtError) as e:
         b.result()
     assert e.value.code == L.VT_ERR_INVALID_ARG
+
+
+def test_sync_batch_grows_small_outputs_and_reports_passes(batch):
+    pts, off, parts, want = batch
+    cells = vt.tessellate_batch(dev(pts), off, vt.Params(precision="fp64", emit=EMIT + ("geom",), stage_times=True))
+    assert cells.stats["passes"] >= 2 and cells.stats["ms_clip"] > 0
+    vol, cen, m2, lists = split(cells, off, 5)
+    np.testing.assert_allclose(vol, want[5]["vol"], rtol=1e-12)
+    nv = np.diff(cells.vtx_off.cpu().numpy())
+    assert nv.sum() == cells.vtx.shape[0]
 
 
 def test_batch_plan_grids():
