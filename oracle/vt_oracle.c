@@ -450,6 +450,94 @@ static void bisector(const float* pi, const float* pj, vec3* n, double* b)
 }
 
 /* ------------------------------------------------------------------ */
+/* vertex positions from their planes                                  */
+/* ------------------------------------------------------------------ */
+
+#define SNAP_INC 8  /* faces remembered per vertex */
+
+/* solve the 3x3 system n_r . x = b_r by Gaussian elimination with partial
+ * pivoting; returns 0 if a pivot vanishes */
+static int solve_planes(const vec3* n, const double* b, vec3* x)
+{
+    double A[3][4] = {{n[0].x, n[0].y, n[0].z, b[0]}, {n[1].x, n[1].y, n[1].z, b[1]}, {n[2].x, n[2].y, n[2].z, b[2]}};
+    for (int c = 0; c < 3; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 3; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (A[piv][c] == 0) return 0;
+        if (piv != c)
+            for (int k = 0; k < 4; ++k) { double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+        for (int r = c + 1; r < 3; ++r) {
+            double f = A[r][c] / A[c][c];
+            for (int k = c; k < 4; ++k) A[r][k] -= f * A[c][k];
+        }
+    }
+    double z = A[2][3] / A[2][2];
+    double y = (A[1][3] - A[1][2] * z) / A[1][1];
+    double xx = (A[0][3] - A[0][1] * y - A[0][2] * z) / A[0][0];
+    *x = v3(xx, y, z);
+    return 1;
+}
+
+/* Every vertex of the final cell is the common point of the planes of the
+ * faces that meet there (the cell is the box cut by bisector planes). The
+ * clipper reaches it by interpolating along edges, whose rounding scales with
+ * the length of the edge it cut -- up to the size of the box, far above the
+ * size of a small cell. Each vertex (vertices closer than 1e-12 V^(1/3) are
+ * one) is therefore recomputed from the triple of its face planes with the
+ * largest |det| of unit normals, when that is at least 1e-6; otherwise the
+ * interpolated position stays. */
+static void snap_vertices(poly_t* P, vec3* uniq, int* vid, int* inc, int* ninc)
+{
+    double vol = 0;
+    for (int f = 0; f < P->nf; ++f)
+        for (int i = 1; i + 1 < P->f[f].nv; ++i) vol += vdet(P->f[f].v[0], P->f[f].v[i], P->f[f].v[i + 1]) / 6.0;
+    double tol = 1e-12 * cbrt(fabs(vol));
+    int nu = 0, pos = 0;
+    for (int f = 0; f < P->nf; ++f)
+        for (int i = 0; i < P->f[f].nv; ++i) {
+            vec3 v = P->f[f].v[i];
+            int id = -1;
+            for (int u = 0; u < nu && id < 0; ++u)
+                if (fabs(uniq[u].x - v.x) <= tol && fabs(uniq[u].y - v.y) <= tol && fabs(uniq[u].z - v.z) <= tol)
+                    id = u;
+            if (id < 0) { uniq[nu] = v; ninc[nu] = 0; id = nu++; }
+            vid[pos++] = id;
+            int seen = 0;
+            for (int t = 0; t < ninc[id] && t < SNAP_INC; ++t) seen |= inc[id * SNAP_INC + t] == f;
+            if (!seen && ninc[id] < SNAP_INC) inc[id * SNAP_INC + ninc[id]++] = f;
+        }
+    for (int u = 0; u < nu; ++u) {
+        int m = ninc[u];
+        if (m < 3) continue;
+        double best = 0;
+        int ba = -1, bb = -1, bc = -1;
+        vec3 h[SNAP_INC];
+        for (int t = 0; t < m; ++t) {
+            vec3 nn = P->f[inc[u * SNAP_INC + t]].n;
+            h[t] = vscale(nn, 1.0 / sqrt(vdot(nn, nn)));
+        }
+        for (int a = 0; a < m; ++a)
+            for (int b = a + 1; b < m; ++b)
+                for (int c = b + 1; c < m; ++c) {
+                    double d = fabs(vdet(h[a], h[b], h[c]));
+                    if (d > best) { best = d; ba = a; bb = b; bc = c; }
+                }
+        if (best < 1e-6) continue;
+        const face_t* Fa = &P->f[inc[u * SNAP_INC + ba]];
+        const face_t* Fb = &P->f[inc[u * SNAP_INC + bb]];
+        const face_t* Fc = &P->f[inc[u * SNAP_INC + bc]];
+        vec3 nrm[3] = {Fa->n, Fb->n, Fc->n};
+        double rhs[3] = {Fa->b, Fb->b, Fc->b};
+        vec3 x;
+        if (solve_planes(nrm, rhs, &x)) uniq[u] = x;
+    }
+    pos = 0;
+    for (int f = 0; f < P->nf; ++f)
+        for (int i = 0; i < P->f[f].nv; ++i) P->f[f].v[i] = uniq[vid[pos++]];
+}
+
+/* ------------------------------------------------------------------ */
 /* per-cell measures                                                   */
 /* ------------------------------------------------------------------ */
 
@@ -664,6 +752,8 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
         int* loop = (int*)malloc((size_t)MAXF * MAXFV * sizeof(int));
         int* lsize = (int*)malloc((size_t)MAXF * sizeof(int));
         char* used = (char*)malloc((size_t)MAXF * MAXFV);
+        int* sinc = (int*)malloc((size_t)MAXF * MAXFV * SNAP_INC * sizeof(int));
+        int* sninc = (int*)malloc((size_t)MAXF * MAXFV * sizeof(int));
 #pragma omp for schedule(dynamic, 16)
         for (int64_t c = 0; c < nc; ++c) {
             int64_t i = cells ? cells[c] : c;
@@ -676,6 +766,7 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
             rc->work_nbrs = S->work_nbrs;
             if (rc->status != VTO_OK) continue;
             vec3 p = v3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+            snap_vertices(P, uniq, loop, sinc, sninc);
             measure(P, p, &rc->M, farea, fcen, uniq, loop, lsize, used);
             double tau = 1e-12 * pow(rc->M.vol, 2.0 / 3.0);
             int nf = rc->M.nfaces;
@@ -715,6 +806,7 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
             qsort(rc->nbr, (size_t)rc->nnbr, sizeof(int32_t), cmp_i32);
         }
         free(S->knn); free(S); free(farea); free(fcen); free(uniq); free(loop); free(lsize); free(used);
+        free(sinc); free(sninc);
     }
 
     /* gather into flat arrays */

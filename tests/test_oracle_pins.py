@@ -8,6 +8,8 @@ A plausible bug anywhere in the oracle -- a dropped clip, a wrong sign in the
 bisector offset, a mis-oriented face, a bad security-radius stop, a broken
 kNN tie order -- fails at least one of them.
 """
+from fractions import Fraction as F
+
 import numpy as np
 import pytest
 
@@ -307,3 +309,38 @@ def test_random_samples_fall_in_nearest_generators_cell():
     assert big.sum() > 200
     z = (counts[big] - expect[big]) / np.sqrt(expect[big] * (1 - r["vol"][big]))
     assert np.abs(z).max() < 6.0
+
+
+# --------------------------------------------------------------------------
+# exact rational arithmetic: the oracle's FP64 volumes against the same
+# cells solved exactly (vertices from three face planes, rational fan sums),
+# on uniform cells and on tiny cells inside a dense clump, where rounding
+# relative to the cell size matters most; every exact vertex also satisfies
+# every face half-space of its cell
+# --------------------------------------------------------------------------
+
+def _clump_cloud():
+    rng = np.random.default_rng(31)
+    sparse = rng.random((6000, 3))
+    dense = 0.5 + 1e-3 * rng.standard_normal((8000, 3))
+    pts = np.unique(np.concatenate([sparse, dense]).astype(np.float32), axis=0)
+    return pts[rng.permutation(len(pts))]
+
+
+@pytest.mark.parametrize("which", ["uniform", "clump"])
+def test_volumes_match_exact_rational_arithmetic(which):
+    from exact_cells import exact_cell
+
+    if which == "uniform":
+        pts = W.uniform(3000, 12)
+        cells = [3, 100, 2999]
+    else:
+        pts = _clump_cloud()
+        cells = [419, 1048, 1088, 5]
+    res = oracle.tessellate(pts, cells=cells, geometry=True)
+    for a, i in enumerate(cells):
+        vol, loops, planes = exact_cell(pts, i, res, a)
+        assert abs(float((F(res["vol"][a]) - vol) / vol)) < 1e-14
+        for loop in loops:
+            for v in loop:
+                assert all(sum(n[k] * v[k] for k in range(3)) <= b for n, b in planes)
