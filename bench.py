@@ -32,7 +32,9 @@ WORKLOADS = {
                      "1,000 isotropic Gaussian clumps (centres uniform, sigma log-uniform in [1e-3,1e-2], "
                      "out-of-box draws resampled), seed 1; k0=16 with doubling to k_max then the exhaustive pass; "
                      "outputs neighbours (CSR, original ids) + volume + centroid + full geometry"),
-    "mixed-8m": dict(n=1 << 23, seed=2, desc="8,388,608 float32 points, same recipe as mixed-1m, seed 2"),
+    "mixed-8m": dict(n=1 << 23, seed=2, sub_box=True, desc="8,388,608 float32 points, same recipe as mixed-1m, "
+                     "seed 2; per-result errors of both forms against the FP64 oracle on the cells of a seeded "
+                     "sub-box of about 65,536 generators"),
     "mixed-300k": dict(n=300_000, seed=1, clumps=300, desc="300,000 float32 points, the mixed-1m recipe with 300 "
                        "clumps (a small case for profiler captures)"),
     "batch-512": dict(batch=True, seed=3, desc="512 independent point sets in [0,1)^3, sizes floor(10^U(3, log10 2e5)) "
@@ -40,6 +42,10 @@ WORKLOADS = {
                       "one CUDA graph per step (no-sync schedule), threads-per-cell / k0 / k_max / per-class grid "
                       "density autotuned on 64 seeded sets before the timed region; outputs neighbours + volume + "
                       "centroid"),
+    "lloyd-1m": dict(lloyd=True, n=1 << 20, seed=4, desc="Lloyd relaxation of 1,048,576 uniform float32 points in "
+                     "[0,1)^3 (seed 4); one step = one iteration: FP32-form tessellation with geometry, the moments "
+                     "adjoint of sum_i M2_i (hand-written kernel through torch.autograd), and the update p <- p - "
+                     "g / (2 V)"),
 }
 BATCH_SPACE = {"tpc": [16, 32], "k0": [12, 16, 24], "kmax_mult": [2], "rho": [1.0, 2.0, 3.0, 4.0, 6.0], "reps": 2}
 # FP32 FMA peak from the unit counts and the maximum SM clock: 152 SMs x 128
@@ -156,19 +162,43 @@ def dist_barrier(world: int):
         dist.barrier()
 
 
-def cpu_oracle_rate(pts: np.ndarray, sample_cells: int, seed: int = 12345) -> dict:
-    """Times the FP64 CPU oracle on a random sample of the workload's cells."""
+def cpu_oracle_rate(pts: np.ndarray, sample_cells: int, seed: int = 12345, sub_box: bool = False) -> dict:
+    """Times the FP64 CPU oracle on a sample of the workload's cells: random
+    cells, or (sub_box) the cells of a seeded cube holding about that many
+    generators. Returns the rate and the oracle's result for the sample."""
     import oracle
 
-    idx = np.sort(np.random.default_rng(seed).choice(len(pts), sample_cells, replace=False))
+    if sub_box:
+        from paper_2412_04514_gb300 import workloads as W
+
+        idx = W.sub_box_cells(pts, sample_cells, seed)
+        what = f"the {len(idx)} cells of a seeded sub-box"
+    else:
+        idx = np.sort(np.random.default_rng(seed).choice(len(pts), sample_cells, replace=False))
+        what = f"{sample_cells} random cells"
     cores = oracle.default_threads()
     oracle.tessellate(pts[:2000], k0=16)  # load the library, warm the allocator
     t0 = time.perf_counter()
     r = oracle.tessellate(pts, k0=16, cells=idx, threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": sample_cells / dt, "seconds": dt, "cores": cores, "flops_per_cell": float(oracle.clip_flops(r).mean()),
-            "sample": f"{sample_cells} random cells of the same {len(pts)}-point workload (kd-tree build included), "
-                      f"FP64 oracle, {cores} threads"}
+    return {"value": len(idx) / dt, "seconds": dt, "cores": cores, "flops_per_cell": float(oracle.clip_flops(r).mean()),
+            "idx": idx, "result": r,
+            "sample": f"{what} of the same {len(pts)}-point workload (kd-tree build included), FP64 oracle, "
+                      f"{cores} threads"}
+
+
+def errors_vs_oracle(cells, cpu: dict) -> dict:
+    """Per-result error of a GPU tessellation on the oracle's sampled cells."""
+    idx, w = cpu["idx"], cpu["result"]
+    vol = cells.vol.cpu().numpy()[idx]
+    cen = cells.cen.cpu().numpy()[idx]
+    rv = np.abs(vol - w["vol"]) / w["vol"]
+    rc = np.linalg.norm(cen - w["cen"], axis=1) / np.linalg.norm(w["cen"], axis=1)
+    off, nbr = cells.nbr_off.cpu().numpy(), cells.nbr.cpu().numpy()
+    bad = sum(not np.array_equal(nbr[off[i]:off[i + 1]], w["nbr"][w["nbr_off"][a]:w["nbr_off"][a + 1]])
+              for a, i in enumerate(idx))
+    return {"cells": int(len(idx)), "vol_rel_max": float(rv.max()), "vol_rel_median": float(np.median(rv)),
+            "cen_rel_max": float(rc.max()), "cen_rel_median": float(np.median(rc)), "nbr_mismatch_cells": int(bad)}
 
 
 def run_reference(args, rank: int, world: int):
@@ -214,6 +244,8 @@ def run_gpu(args, rank: int, world: int, local: int):
     wl = WORKLOADS[args.workload]
     if wl.get("batch"):
         return run_batch(args, rank, world, local)
+    if wl.get("lloyd"):
+        return run_lloyd(args, rank, world, local)
     n = wl["n"]
     pts_np = W.mixed(n, wl["seed"] + 1000 * rank, n_clumps=wl.get("clumps", 1000))
     pts = torch.from_numpy(pts_np).to(dev)
@@ -252,8 +284,9 @@ def run_gpu(args, rank: int, world: int, local: int):
     with Clocks(local) as clk:
         ms32, st32, launches32, cells = timed(p32, args.steps, args.warmup, stage_times=True)
     clocks = clk.summary()
+    cells64 = None
     if args.steps_fp64 > 0:
-        ms64, st64, _, _ = timed(p64, args.steps_fp64, 3, stage_times=True)
+        ms64, st64, _, cells64 = timed(p64, args.steps_fp64, 3, stage_times=True)
         tot64 = dist_max(sum(ms64), world)
         value64 = n * world * len(ms64) / (tot64 / 1e3)
 
@@ -286,8 +319,14 @@ def run_gpu(args, rank: int, world: int, local: int):
     stage = {k: statistics.mean(s[k] for s in st32) for k in ("ms_grid", "ms_knn", "ms_clip", "ms_emit")}
     peaks = _peaks()
     cpu = None
+    errors = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(pts_np, args.cpu_cells)
+        sub = wl.get("sub_box", False)
+        cpu = cpu_oracle_rate(pts_np, 65536 if sub else args.cpu_cells, seed=17 if sub else 12345, sub_box=sub)
+        errors = {"fp32_recheck": errors_vs_oracle(cells, cpu)}
+        if cells64 is not None:
+            errors["fp64"] = errors_vs_oracle(cells64, cpu)
+        errors["sample"] = cpu["sample"]
     flops_per_cell = cpu["flops_per_cell"] if cpu else args.flops_per_cell
     clip_launches = statistics.mean(s["clip_launches"] for s in st32)
     achieved = n * flops_per_cell / (stage["ms_clip"] / 1e3) / 1e12
@@ -319,6 +358,7 @@ def run_gpu(args, rank: int, world: int, local: int):
                                                   "kind": "oracle", "sample": cpu["sample"]},
         "gpu_launches": int(launches32),
         "clocks": clocks,
+        "errors_vs_oracle": errors,
         "passes": {"k_of_pass": st32[-1]["k_of_pass"], "cells_of_pass": st32[-1]["cells_of_pass"],
                    "fp64_rechecks": st32[-1]["fp64_rechecks"], "precision_retries": st32[-1]["precision_retries"],
                    "capacity_retries": st32[-1]["capacity_retries"], "unvalidated": st32[-1]["unvalidated"]},
@@ -428,6 +468,90 @@ def run_batch(args, rank: int, world: int, local: int):
         "gpu_launches": int(per_replay * len(ms)),
         "clocks": clocks,
         "status": cells.stats["status"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_lloyd(args, rank: int, world: int, local: int):
+    """Lloyd iterations through the public API (vt.lloyd), one per step."""
+    import torch
+
+    import paper_2412_04514_gb300 as vt
+    from paper_2412_04514_gb300 import workloads as W
+
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[args.workload]
+    n = wl["n"]
+    pts_np = W.uniform(n, wl["seed"] + 1000 * rank)
+    p = torch.from_numpy(pts_np).to(dev)
+    prm = vt.Params(precision="fp32")
+    energies = []
+    for _ in range(args.warmup):
+        p = vt.lloyd(p, 1, prm, callback=lambda it, e: energies.append(e))
+    stream = torch.cuda.current_stream(dev)
+    ms = []
+    l0 = vt.launch_count()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            p = vt.lloyd(p, 1, prm, callback=lambda it, en: energies.append(en))
+            e.record(stream)
+            e.synchronize()
+            ms.append(a.elapsed_time(e))
+    clocks = clk.summary()
+    launches = vt.launch_count() - l0
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    tot = dist_max(sum(ms), world)
+    value = n * world * len(ms) / (tot / 1e3)
+    # end to end: host points in, one iteration, new points and the loss back on the host
+    host = torch.from_numpy(p.cpu().numpy()).pin_memory()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps if not args.no_e2e else 0):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        d = host.to(dev, non_blocking=True)
+        loss = []
+        out = vt.lloyd(d, 1, prm, callback=lambda it, en: loss.append(en)).to("cpu")
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t1))
+    e2e_tot = dist_max(sum(e2e_ms), world) if e2e_ms else 0.0
+    if rank != 0:
+        return
+    # stage split of the forward tessellation of the current points (stage-timed)
+    st = vt.tessellate(p, vt.Params(precision="fp32", emit=("vol", "cen", "m2", "geom"), stage_times=True)).stats
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(p.cpu().numpy(), args.cpu_cells)
+    flops_per_cell = cpu["flops_per_cell"] if cpu else args.flops_per_cell
+    achieved = n * flops_per_cell / (st["ms_clip"] / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": len(ms),
+        "warmup": args.warmup, "ms_per_step": tot / len(ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "n_points": n, "precision": "fp32+fp64-recheck",
+                   "l2": "inputs larger than L2 (geometry of 1M cells, ~1 GB per step)",
+                   "parallelism": f"replicas x{world}"},
+        "lloyd": {"energy_first": energies[0], "energy_last": energies[-1], "iterations": len(energies),
+                  "monotone": all(b <= a * (1 + 1e-9) for a, b in zip(energies, energies[1:]))},
+        "e2e": None if not e2e_ms else {
+            "value": n * world * len(e2e_ms) / (e2e_tot / 1e3), "unit": "cells/s", "h2d_bytes_per_step": n * 12,
+            "d2h_bytes_per_step": n * 12 + 8, "ms_per_step": e2e_tot / len(e2e_ms)},
+        "roofline": {
+            "kernel": "k_clip<float,32,2,64> of the forward tessellation (stage-timed run)",
+            "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (unit counts and max SM clock)",
+            "stage_ms": {k: st[k] for k in ("ms_grid", "ms_knn", "ms_clip", "ms_emit")}},
+        "cpu_baseline": None if cpu is None else {"value": cpu["value"], "unit": "cells/s", "cores": cpu["cores"],
+                                                  "kind": "oracle", "sample": cpu["sample"] + " (tessellation only)"},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 

@@ -1095,7 +1095,16 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
     const int64_t ngroups = ((int64_t)gridDim.x * CLIP_BLOCK) / T;
     const int k = A.k;
     const bool resume = !ROBUST && A.state && A.k_prev > 0;
-    const int64_t nq = A.nq_dev ? (int64_t)*A.nq_dev : A.nq;
+    // the robust exhaustive variant first clips by a nearest-first list, so
+    // that its walk meets an almost final cell (the regular one resumes the
+    // saved polyhedron of the last list pass instead)
+    constexpr bool LIST = !EXH || ROBUST;
+    int64_t nq = A.nq;
+    if (A.nq_dev) {
+        const int64_t want = *A.nq_dev;
+        if (want > A.nq_cap && threadIdx.x == 0 && blockIdx.x == 0) atomicExch((int*)&A.st->list_overflow, 1);
+        nq = want < A.nq_cap ? want : A.nq_cap;
+    }
     C cell;
     cell.stamp = 0;
 
@@ -1111,7 +1120,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
         if (resume) cell.restore(G, sm, stp, last_d2, last_orig);
         else cell.init_box(G, sm, grid);
         int end = END_NEED_K;
-        if (!EXH) {
+        if (LIST && k > 0) {
             // neighbour list, nearest first, from the first unprocessed entry;
             // each lane holds one entry of the current chunk of T and prefetches
             // its entry of the next chunk
@@ -1151,7 +1160,8 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
                 last_d2 = (double)dd[k - 1];
                 last_orig = __float_as_int(A.sorted[nb[k - 1]].w);
             }
-        } else {
+        }
+        if (EXH && end == END_NEED_K) {
             // exhaustive: every generator closer than 2R, by a shell walk
             const float4 pq = cell.pi;
             const int Gr = grid.G;
@@ -1234,7 +1244,7 @@ cudaError_t launch_variant(const ClipArgs& a, cudaStream_t s)
 {
     using S = GroupSmem<Real, T * VPL, PCAP>;
     const size_t smem = sizeof(S) * (CLIP_BLOCK / T);
-    auto kern = a.k == 0 ? k_clip<Real, T, VPL, PCAP, ROBUST, true> : k_clip<Real, T, VPL, PCAP, ROBUST, false>;
+    auto kern = a.exhaustive ? k_clip<Real, T, VPL, PCAP, ROBUST, true> : k_clip<Real, T, VPL, PCAP, ROBUST, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int gpb = CLIP_BLOCK / T;

@@ -111,7 +111,12 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nq = nq_dev ? (int64_t)*nq_dev : nq_host;
+    int64_t nq = nq_host;
+    if (nq_dev) {  // device-counted: at most nq_host queries fit the output
+        const int64_t want = *nq_dev;
+        if (want > nq_host && threadIdx.x == 0 && blockIdx.x == 0) atomicExch((int*)&st->list_overflow, 1);
+        nq = want < nq_host ? want : nq_host;
+    }
     for (int64_t c = wid; c < nq; c += nw) {
         const int q = queries ? queries[c] : (int)c;
         const float4 pq = sorted[q];

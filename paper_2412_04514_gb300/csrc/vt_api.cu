@@ -158,6 +158,9 @@ using namespace vt;
 
 namespace vt_host {
 
+// list length of the robust variant's exhaustive pass (nearest first, then the walk)
+constexpr int ROBUST_EXH_K = 128;
+
 // CUDA-event timing of kernel groups on the call's stream (VT_FLAG_STAGE_TIMES)
 struct StageTimer {
     enum { GRID = 0, KNN = 1, CLIP = 2, EMIT = 3 };
@@ -268,12 +271,14 @@ __global__ void k_iota(int32_t* a, int64_t n)
         a[i] = (int32_t)i;
 }
 
-// one clip pass over `list` (m cells, or *m_dev cells when m_dev is set): kNN
-// with k in chunks that fit the list buffer, then the clipper; k == 0 runs
-// the exhaustive clipper. Failures go to the given lists and counters.
+// one clip pass over `list` (m cells, or *m_dev cells when m_dev is set):
+// kNN with k in chunks that fit the list buffer, then the clipper. With
+// `exhaustive` the clipper then walks every generator within 2R (k = 0: no
+// list, the regular variant resumes its saved state instead). Failures go to
+// the given lists and counters.
 int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, const int32_t* m_dev, int k,
-              int k_prev, int variant, int knn_prec, vt_cells_out* out, int32_t* fail_next, int32_t* ctr_next,
-              int32_t* fail_robust, int32_t* ctr_robust)
+              bool exhaustive, int k_prev, int variant, int knn_prec, vt_cells_out* out, int32_t* fail_next,
+              int32_t* ctr_next, int32_t* fail_robust, int32_t* ctr_robust)
 {
     const Layout& L = c.L;
     ClipArgs a{};
@@ -285,6 +290,7 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
     a.nq_dev = m_dev;
     a.n = L.n;
     a.k = k;
+    a.exhaustive = exhaustive ? 1 : 0;
     a.emit = p->emit;
     a.index_space = p->index_space;
     a.vol = (p->emit & VT_EMIT_VOL) ? out->vol : nullptr;
@@ -306,6 +312,7 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
     if (k == 0) {
         a.queries = list;
         a.nq = m;
+        a.nq_cap = m;
         T.begin(StageTimer::CLIP);
         cudaError_t e = launch_clip(a, variant, tpc, c.s);
         T.end();
@@ -313,9 +320,10 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
         return e == cudaSuccess ? VT_OK : cuda_fail(e, "clip launch");
     }
     const int64_t chunk = L.knn_cap / k;
-    if (m_dev && m > chunk) return fail(VT_ERR_INVALID_ARG, "internal: device-counted pass needs one chunk");
-    for (int64_t o = 0; o < m; o += chunk) {
-        const int64_t cnt = (m - o) < chunk ? (m - o) : chunk;
+    // a device-counted pass runs as one launch over at most `chunk` cells
+    const int64_t mm = (m_dev && m > chunk) ? chunk : m;
+    for (int64_t o = 0; o < mm; o += chunk) {
+        const int64_t cnt = (mm - o) < chunk ? (mm - o) : chunk;
         const int32_t* q = list ? list + o : nullptr;
         if (!list && o > 0) return fail(VT_ERR_INVALID_ARG, "internal: implicit list needs one chunk");
         T.begin(StageTimer::KNN);
@@ -326,6 +334,7 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
         if (e != cudaSuccess) return cuda_fail(e, "knn launch");
         a.queries = q;
         a.nq = cnt;
+        a.nq_cap = cnt;
         a.nbr = c.at<int32_t>(L.knn_nbr);
         a.d2 = c.at<void>(L.knn_d2);
         T.begin(StageTimer::CLIP);
@@ -342,6 +351,9 @@ int status_errors(const DevStatus& h)
     if (h.bad_point)
         return fail(VT_ERR_INVALID_ARG, "point %d is not finite or not inside [box_lo, box_hi)", h.bad_point - 1);
     if (h.duplicate) return fail(VT_ERR_DUPLICATE_POINTS, "two generators coincide");
+    if (h.list_overflow)
+        return fail(VT_ERR_WORKSPACE, "more cells needed the robust list pass than the no-sync list buffer holds; "
+                                      "use the synchronising schedule");
     return VT_OK;
 }
 
@@ -493,12 +505,15 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
             int32_t* rc = last ? &c.st->n_unval : &ctr_reg[pi];
             int32_t* bn = last ? unval : robl[(pi + 1) % 2];
             int32_t* bc = last ? &c.st->n_unval : &ctr_rob[pi];
-            r = clip_pass(c, p, q, n, qn, kk, k_prev, variant_reg, p->precision, out, rn, rc, rob_new, &ctr_new[pi]);
+            const int kr = last ? ROBUST_EXH_K : kk;  // the robust variant's list
+            r = clip_pass(c, p, q, n, qn, kk, last, k_prev, variant_reg, p->precision, out, rn, rc, rob_new,
+                          &ctr_new[pi]);
             if (r) return r;
-            r = clip_pass(c, p, rob_new, n, &ctr_new[pi], kk, 0, 2, VT_FP64, out, bn, bc, unval, &c.st->n_unval);
+            r = clip_pass(c, p, rob_new, n, &ctr_new[pi], kr, last, 0, 2, VT_FP64, out, bn, bc, unval,
+                          &c.st->n_unval);
             if (r) return r;
             if (pi > 0) {
-                r = clip_pass(c, p, robl[pi % 2], n, &ctr_rob[pi - 1], kk, 0, 2, VT_FP64, out, bn, bc, unval,
+                r = clip_pass(c, p, robl[pi % 2], n, &ctr_rob[pi - 1], kr, last, 0, 2, VT_FP64, out, bn, bc, unval,
                               &c.st->n_unval);
                 if (r) return r;
             }
@@ -533,8 +548,8 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
                 count_launch();
                 implicit = false;
             }
-            r = clip_pass(c, p, implicit ? nullptr : reg_cur, m_reg, nullptr, kk, k_prev, variant_reg, p->precision,
-                          out, reg_nxt, &c.st->n_fail_next, rob_new, &c.st->n_fail_robust);
+            r = clip_pass(c, p, implicit ? nullptr : reg_cur, m_reg, nullptr, kk, exhaustive, k_prev, variant_reg,
+                          p->precision, out, reg_nxt, &c.st->n_fail_next, rob_new, &c.st->n_fail_robust);
             if (r) return r;
             if ((r = read_status(c, h))) return r;
             if ((r = status_errors(h))) return r;
@@ -550,8 +565,8 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
         int64_t rob_next = 0;
         if (m_rob > 0) {
             if ((r = zero_counters(c))) return r;
-            r = clip_pass(c, p, rob_cur, m_rob, nullptr, kk, 0, 2, VT_FP64, out, rob_nxt, &c.st->n_fail_next,
-                          unval + n_unval, &c.st->n_fail_robust);
+            r = clip_pass(c, p, rob_cur, m_rob, nullptr, exhaustive ? ROBUST_EXH_K : kk, exhaustive, 0, 2, VT_FP64,
+                          out, rob_nxt, &c.st->n_fail_next, unval + n_unval, &c.st->n_fail_robust);
             if (r) return r;
             if ((r = read_status(c, h))) return r;
             if ((r = status_errors(h))) return r;
@@ -680,6 +695,8 @@ int vt_clip_cells(const float* sorted, const int32_t* cell_off, int G, int64_t n
     a.nbr = nbr;
     a.d2 = d2;
     a.k = k;
+    a.exhaustive = k == 0 ? 1 : 0;
+    a.nq_cap = nq;
     a.emit = p->emit;
     a.index_space = p->index_space;
     a.vol = (p->emit & VT_EMIT_VOL) ? out->vol : nullptr;

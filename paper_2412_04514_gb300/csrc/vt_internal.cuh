@@ -124,7 +124,8 @@ struct DevStatus {
     unsigned long long precision_events;
     long long totals[4];      // nbr, vtx, face, face_vtx totals written by the emit scan
     unsigned int detail[8];   // clip events: 0 keep-none, 1 plane cap, 2 vertex cap, 3 ring, 4 interpolated
-    long long pad2[1];
+    int32_t list_overflow;    // a device-counted pass had more cells than its list buffers hold
+    int32_t pad2;
 };
 static_assert(sizeof(DevStatus) % 64 == 0, "status block must stay 64-byte sized");
 
@@ -199,6 +200,8 @@ cudaError_t launch_grid_build(const float* pts, int64_t n, const GridDesc& g, fl
 cudaError_t launch_pair_counts(const int32_t* cell_off, int64_t g3, const GridDesc* sets, int nsets,
                                unsigned long long* acc, cudaStream_t s);
 
+// nq_dev: the query count is read from device memory, clamped to nq (more sets
+// st->list_overflow)
 cudaError_t launch_knn(const float4* sorted, const int32_t* cell_off, const GridDesc& g, int64_t n,
                        const int32_t* queries, int64_t nq, int k, int precision, int32_t* nbr, void* d2,
                        DevStatus* st, cudaStream_t s, const GridDesc* sets = nullptr, const int32_t* set_of = nullptr,
@@ -213,7 +216,8 @@ struct ClipArgs {
     int64_t nq;
     const int32_t* nbr;       // [nq*k] (k > 0)
     const void* d2;           // [nq*k] float or double
-    int k;                    // 0 = exhaustive mode
+    int k;                    // list entries per cell (0 = no list)
+    int exhaustive;           // 1: after the list (or the resumed state), walk every generator within 2R
     int emit;
     int index_space;
     double* vol;
@@ -229,6 +233,8 @@ struct ClipArgs {
     const GridDesc* sets;     // per-set grids of a batch (NULL: the single grid g)
     const int32_t* set_of;    // set of each sorted point (batches)
     const int32_t* nq_dev;    // when set, the cell count is read from device memory
+    int64_t nq_cap;           // with nq_dev: at most this many cells fit the list buffers (more sets
+                              // DevStatus::list_overflow and the rest is not processed)
     int k_prev;               // > 0: resume saved cells; list entries [0, k_prev) are done
     uint8_t* state;           // per-cell saved polyhedra (sorted index * state_stride), or NULL
     size_t state_stride;

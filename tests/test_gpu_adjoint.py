@@ -113,3 +113,14 @@ def test_lloyd_energy_decreases_and_resume_is_bit_identical(tmp_path):
     vt.lloyd(p, 2, vt.Params(precision="fp32"), checkpoint=ck, checkpoint_every=1)
     resumed = vt.lloyd(p, 4, vt.Params(precision="fp32"), checkpoint=ck, resume=True)
     assert torch.equal(full, resumed)
+
+
+def test_lloyd_1m_uniform_50_iterations_decreases_the_energy():
+    # the differentiation workload at full size: 1,048,576 uniform points, 50 iterations
+    p = dev(W.uniform(1 << 20, 4))
+    energies = []
+    out = vt.lloyd(p, 50, vt.Params(precision="fp32"), callback=lambda it, e: energies.append(e))
+    assert len(energies) == 50
+    assert all(b <= a * (1 + 1e-9) for a, b in zip(energies, energies[1:]))
+    assert energies[-1] < 0.97 * energies[0]
+    assert bool(((out >= 0) & (out < 1)).all())

@@ -354,3 +354,35 @@ def test_bench_workload_fp32_sampled(bench_1m):
     lists = csr_lists(np_(cells.nbr_off), np_(cells.nbr))
     check_fp32(np_(cells.vol)[sample], np_(cells.cen)[sample], [lists[i] for i in sample], want)
     assert abs(np_(cells.vol).sum() - 1.0) < 1e-6
+
+
+# --------------------------------------------------------------------------
+# sparse cells next to a dense clump: thousands of generators lie within
+# twice their radius, so they reach the exhaustive pass, and clipped in walk
+# order the clump's bisectors would overflow the polyhedron; the robust
+# variant clips by a nearest-first list before its walk
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def clump_cloud():
+    rng = np.random.default_rng(31)
+    sparse = rng.random((6000, 3))
+    dense = 0.5 + 1e-3 * rng.standard_normal((8000, 3))
+    pts = np.unique(np.concatenate([sparse, dense]).astype(np.float32), axis=0)
+    pts = pts[rng.permutation(len(pts))]
+    return pts, oracle.tessellate(pts)
+
+
+@pytest.mark.parametrize("no_sync", [False, True])
+def test_sparse_cells_next_to_a_dense_clump_fp64(clump_cloud, no_sync):
+    pts, want = clump_cloud
+    assert want["k_used"].max() >= 1024  # the workload has the hard cells
+    cells = vt.tessellate(dev(pts), vt.Params(precision="fp64", emit=("nbr", "vol", "cen", "m2"), no_sync=no_sync))
+    assert cells.stats["unvalidated"] == 0
+    check_fp64(cells, want)
+
+
+def test_sparse_cells_next_to_a_dense_clump_fp32(clump_cloud):
+    pts, want = clump_cloud
+    cells = vt.tessellate(dev(pts), vt.Params(precision="fp32"))
+    check_fp32(np_(cells.vol), np_(cells.cen), csr_lists(np_(cells.nbr_off), np_(cells.nbr)), want)
