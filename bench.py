@@ -279,8 +279,10 @@ def run_gpu(args, rank: int, world: int, local: int):
         return ms, stats, launches, cells
 
     # warm up both forms, then time: FP32+recheck (headline) and plain FP64
-    p32 = vt.Params(precision="fp32", k0=16, k_max=args.k_max, threads_per_cell=32, emit=emit)
-    p64 = vt.Params(precision="fp64", k0=16, k_max=args.k_max, threads_per_cell=32, emit=emit)
+    p32 = vt.Params(precision="fp32", k0=args.k0, k_max=args.k_max, threads_per_cell=32, emit=emit,
+                    grid_density=args.rho)
+    p64 = vt.Params(precision="fp64", k0=args.k0, k_max=args.k_max, threads_per_cell=32, emit=emit,
+                    grid_density=args.rho)
     with Clocks(local) as clk:
         ms32, st32, launches32, cells = timed(p32, args.steps, args.warmup, stage_times=True)
     clocks = clk.summary()
@@ -345,6 +347,7 @@ def run_gpu(args, rank: int, world: int, local: int):
         "warmup": args.warmup, "ms_per_step": tot32 / len(ms32), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["desc"], "n_points": n, "precision": "fp32+fp64-recheck",
+                   "k0": args.k0, "k_max": args.k_max, "grid_density": args.rho, "threads_per_cell": 32,
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world} (independent clouds)"},
         "fp64_form": None if args.steps_fp64 <= 0 else {
             "value": value64, "unit": "cells/s", "ms_per_step": tot64 / len(ms64), "steps": len(ms64),
@@ -360,6 +363,8 @@ def run_gpu(args, rank: int, world: int, local: int):
         "clocks": clocks,
         "errors_vs_oracle": errors,
         "passes": {"k_of_pass": st32[-1]["k_of_pass"], "cells_of_pass": st32[-1]["cells_of_pass"],
+                   "clip_ms_of_pass": [statistics.mean(s["ms_clip_pass"][i] for s in st32)
+                                       for i in range(len(st32[-1]["ms_clip_pass"]))],
                    "fp64_rechecks": st32[-1]["fp64_rechecks"], "precision_retries": st32[-1]["precision_retries"],
                    "capacity_retries": st32[-1]["capacity_retries"], "unvalidated": st32[-1]["unvalidated"]},
     }
@@ -568,7 +573,9 @@ def main():
     ap.add_argument("--ref-cells", type=int, default=20_000)
     ap.add_argument("--flops-per-cell", type=float, default=25134.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--k0", type=int, default=16)
     ap.add_argument("--k-max", type=int, default=32)
+    ap.add_argument("--rho", type=float, default=2.0)
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -54,6 +54,17 @@
 
 namespace vt {
 
+#ifdef VT_PROFILE
+// section clocks and event counts of the clip kernels (diagnostic builds only):
+// [8 * EXH + i], i = 0 cells, 1 setup cycles, 2 list/walk cycles, 3 clip
+// cycles, 4 clip calls, 5 cuts, 6 finish cycles, 7 walk candidates; walk:
+// 16 shells, 17 segment groups, 18 candidate batches, 19 raw candidates
+static __device__ unsigned long long g_vt_prof[32];  // one copy per translation unit
+#define VT_PROF_ADD(i, v) atomicAdd(&g_vt_prof[(i)], (unsigned long long)(v))
+#else
+#define VT_PROF_ADD(i, v) ((void)0)
+#endif
+
 namespace {
 
 // ---------------------------------------------------------------------------
@@ -326,21 +337,12 @@ struct Tol<double> {
 constexpr double ON_PLANE_REL2 = 1e-28;  // (1e-14)^2
 
 // ---------------------------------------------------------------------------
-// saved polyhedron of a cell between passes (fixed stride per cell)
+// saved polyhedron of a cell between passes (fixed stride per cell): the
+// StateHdr, then planes, topology and positions
 // ---------------------------------------------------------------------------
-struct StateHdr {
-    uint64_t alive[2];
-    int32_t np;
-    int32_t last_orig;   // original index of the last list entry processed
-    double R2;
-    double last_d2;      // its squared distance (the kNN key)
-    int32_t pad[2];
-};
-static_assert(sizeof(StateHdr) == 48, "state header");
-
 template <typename Real, int VCAP, int PCAP>
 struct StateLayout {
-    static constexpr size_t PLANES = 64;                                // Real[4][PCAP]
+    static constexpr size_t PLANES = 128;                               // Real[4][PCAP]
     static constexpr size_t PSRC = PLANES + 4 * sizeof(Real) * PCAP;    // int32[PCAP]
     static constexpr size_t VID = PSRC + 4 * PCAP;                      // uint32[VCAP]
     static constexpr size_t VADJ = VID + 4 * VCAP;                      // uint32[VCAP]
@@ -559,8 +561,12 @@ struct Cell {
                 pos[2 * VCAP + s] = vz[r];
             }
         }
+        float lo3[3], hi3[3];
+        bbox(G, lo3, hi3);
         if (G.gl == 0) {
             StateHdr* h = reinterpret_cast<StateHdr*>(st);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) { h->bb_lo[a] = lo3[a]; h->bb_hi[a] = hi3[a]; }
             h->alive[0] = alive.w[0];
             h->alive[1] = M::W_ == 2 ? alive.w[M::W_ - 1] : 0ull;
             h->np = np;
@@ -923,12 +929,19 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
     MZ *= 0.25;
     M2 *= 0.05;
     __syncwarp(gmask);
-    // neighbour keys: planes with a face of area above the threshold
-    const double tau = Tol<Real>::area_rel * cbrt(V * V);
+    // neighbour keys: planes with a face of area above the threshold (the
+    // threshold of the FP32 form in float32: the FP64 pipe is scarce)
+    Real tau;
+    if (Tol<Real>::fp32) {
+        const float cv = cbrtf((float)V);
+        tau = (Real)((float)Tol<Real>::area_rel * cv * cv);
+    } else {
+        tau = (Real)(Tol<Real>::area_rel * cbrt(V * V));
+    }
     for (int f = gl; f < np; f += T) {
         const int src = sm.psrc[f];
         int key = INT_MAX;
-        if (src >= 0 && sm.u.tail.first[f] >= 0 && (double)sm.u.tail.area[f] > tau)
+        if (src >= 0 && sm.u.tail.first[f] >= 0 && sm.u.tail.area[f] > tau)
             key = A.index_space == VT_INDEX_ORIGINAL ? __float_as_int(A.sorted[src].w) : src;
         sm.u.tail.key[f] = key;
     }
@@ -936,9 +949,10 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
     if (gl == 0) {
         if (A.vol) A.vol[out_idx] = V;
         if (A.cen) {
-            A.cen[3 * out_idx] = (double)pi.x + MX / V;
-            A.cen[3 * out_idx + 1] = (double)pi.y + MY / V;
-            A.cen[3 * out_idx + 2] = (double)pi.z + MZ / V;
+            const double iv = 1.0 / V;
+            A.cen[3 * out_idx] = (double)pi.x + MX * iv;
+            A.cen[3 * out_idx + 1] = (double)pi.y + MY * iv;
+            A.cen[3 * out_idx + 2] = (double)pi.z + MZ * iv;
         }
         if (A.m2) A.m2[out_idx] = M2;
     }
@@ -1044,12 +1058,20 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, 
         need = r4 * (1.0f + 1e-4f) > d2 &&
                hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f;
         if (need && last_orig >= 0) {  // already processed from the list?
-            const double kd = Tol<Real>::fp32 ? (double)knn_d2_f32(pq, pc) : knn_d2_f64(pq, pc);
             const int ko = __float_as_int(pc.w);
-            if (kd < last_d2 || (kd == last_d2 && ko <= last_orig)) need = false;
+            if (Tol<Real>::fp32) {  // float keys compare in float (last_d2 holds a float)
+                const float kd = knn_d2_f32(pq, pc), ld = (float)last_d2;
+                if (kd < ld || (kd == ld && ko <= last_orig)) need = false;
+            } else {
+                const double kd = knn_d2_f64(pq, pc);
+                if (kd < last_d2 || (kd == last_d2 && ko <= last_orig)) need = false;
+            }
         }
     }
     unsigned mm = G.ballot(need);
+#ifdef VT_PROFILE
+    if (G.gl == 0) VT_PROF_ADD(8 + 7, __popc(mm));
+#endif
     while (mm) {
         const int src = __ffs(mm) - 1;
         mm &= mm - 1;
@@ -1067,7 +1089,17 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, 
         if (!(4.0f * (float)cell.R2 * (1.0f + 1e-4f) > d2 &&
               hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f))
             continue;
+#ifdef VT_PROFILE
+        const long long t0 = clock64();
+#endif
         const int r = cell.clip_point(G, sm, p, j, A.sorted, grid, A.st);
+#ifdef VT_PROFILE
+        if (G.gl == 0) {
+            VT_PROF_ADD(8 + 3, clock64() - t0);
+            VT_PROF_ADD(8 + 4, 1);
+            if (r == CLIP_CUT) VT_PROF_ADD(8 + 5, 1);
+        }
+#endif
         if (r == CLIP_OVERFLOW) return END_OVERFLOW;
         if (r == CLIP_INCONSISTENT) return END_INCONSISTENT;
         if (r == CLIP_CUT) cell.bbox(G, lo3, hi3);
@@ -1094,7 +1126,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
     const int64_t gid = ((int64_t)blockIdx.x * CLIP_BLOCK + threadIdx.x) / T;
     const int64_t ngroups = ((int64_t)gridDim.x * CLIP_BLOCK) / T;
     const int k = A.k;
-    const bool resume = !ROBUST && A.state && A.k_prev > 0;
+    const bool resume = !ROBUST && A.state && (A.k_prev > 0 || A.restore);
     // the robust exhaustive variant first clips by a nearest-first list, so
     // that its walk meets an almost final cell (the regular one resumes the
     // saved polyhedron of the last list pass instead)
@@ -1109,6 +1141,8 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
     cell.stamp = 0;
 
     for (int64_t c = gid; c < nq; c += ngroups) {
+        const int kc = A.klen ? A.klen[c] : k;  // this cell's list length
+        if (kc < 0) continue;                    // no list: the cell is handled elsewhere
         const int q = A.queries ? A.queries[c] : (int)c;
         const GridDesc& grid = grid_of(A.g, A.sets, A.set_of, q);
         cell.pi = A.sorted[q];
@@ -1117,8 +1151,19 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
         uint8_t* stp = A.state ? A.state + (size_t)q * A.state_stride : nullptr;
         double last_d2 = -1.0;
         int last_orig = -1;
+#ifdef VT_PROFILE
+        long long tp0 = clock64();
+        const int pb = EXH ? 8 : (A.complete ? 24 : 0);
+#endif
         if (resume) cell.restore(G, sm, stp, last_d2, last_orig);
         else cell.init_box(G, sm, grid);
+#ifdef VT_PROFILE
+        long long tp1 = clock64();
+        if (G.gl == 0) {
+            VT_PROF_ADD(pb + 0, 1);
+            VT_PROF_ADD(pb + 1, tp1 - tp0);
+        }
+#endif
         int end = END_NEED_K;
         if (LIST && k > 0) {
             // neighbour list, nearest first, from the first unprocessed entry;
@@ -1126,20 +1171,20 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
             // its entry of the next chunk
             const int32_t* nb = A.nbr + c * (int64_t)k;
             const Real* dd = reinterpret_cast<const Real*>(A.d2) + c * (int64_t)k;
-            const int m0 = resume ? A.k_prev : 0;
-            int nj = m0 + G.gl < k ? nb[m0 + G.gl] : -1;
-            Real nd = m0 + G.gl < k ? dd[m0 + G.gl] : (Real)0;
+            const int m0 = (resume && !A.restore) ? A.k_prev : 0;
+            int nj = m0 + G.gl < kc ? nb[m0 + G.gl] : -1;
+            Real nd = m0 + G.gl < kc ? dd[m0 + G.gl] : (Real)0;
             float4 np4 = nj >= 0 ? A.sorted[nj] : make_float4(0.f, 0.f, 0.f, 0.f);
             bool stop = false;
-            for (int base = m0; base < k && !stop; base += T) {
+            for (int base = m0; base < kc && !stop; base += T) {
                 const int cj = nj;
                 const Real cd = nd;
                 const float4 cp = np4;
                 const int nm = base + T + G.gl;
-                nj = nm < k ? nb[nm] : -1;
-                nd = nm < k ? dd[nm] : (Real)0;
+                nj = nm < kc ? nb[nm] : -1;
+                nd = nm < kc ? dd[nm] : (Real)0;
                 np4 = nj >= 0 ? A.sorted[nj] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const int cnt = k - base < T ? k - base : T;
+                const int cnt = kc - base < T ? kc - base : T;
                 for (int t = 0; t < cnt; ++t) {
                     const int j = G.bcast(cj, t);
                     if (j < 0) { end = END_VALID; stop = true; break; }  // the list holds every other generator
@@ -1150,15 +1195,31 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
                     p.y = G.bcast(cp.y, t);
                     p.z = G.bcast(cp.z, t);
                     p.w = 0.f;
+#ifdef VT_PROFILE
+                    const long long t0 = clock64();
+#endif
                     const int r = cell.clip_point(G, sm, p, j, A.sorted, grid, A.st);
+#ifdef VT_PROFILE
+                    if (G.gl == 0) {
+                        VT_PROF_ADD(pb + 3, clock64() - t0);
+                        VT_PROF_ADD(pb + 4, 1);
+                        if (r == CLIP_CUT) VT_PROF_ADD(pb + 5, 1);
+                    }
+#endif
                     if (r == CLIP_OVERFLOW) { end = END_OVERFLOW; stop = true; break; }
                     if (r == CLIP_INCONSISTENT) { end = END_INCONSISTENT; stop = true; break; }
                 }
             }
-            if (!stop && k > 0 && cell.radius_ok(G, sm, dd[k - 1], nb[k - 1], A.sorted, grid, A.st)) end = END_VALID;
-            if (end == END_NEED_K && k > 0) {
-                last_d2 = (double)dd[k - 1];
-                last_orig = __float_as_int(A.sorted[nb[k - 1]].w);
+            if (!stop) {
+                // a complete list leaves nothing that can cut; otherwise the
+                // last entry bounds every generator the list does not hold
+                if (A.complete) end = END_VALID;
+                else if (kc > 0 && cell.radius_ok(G, sm, dd[kc - 1], nb[kc - 1], A.sorted, grid, A.st))
+                    end = END_VALID;
+            }
+            if (end == END_NEED_K && kc > 0) {
+                last_d2 = (double)dd[kc - 1];
+                last_orig = __float_as_int(A.sorted[nb[kc - 1]].w);
             }
         }
         if (EXH && end == END_NEED_K) {
@@ -1171,18 +1232,35 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
             const int iz = cell_coord(pq.z, grid.lo[2], grid.scale[2], Gr);
             float lo3[3], hi3[3];
             cell.bbox(G, lo3, hi3);
+            const float r_in2 = last_orig >= 0 ? (float)last_d2 * (1.0f - 1e-4f) : -1.0f;
             int status = 0;
             for (int s = 0; status == 0; ++s) {
                 // the shell's segments, T at a time, candidates spread over the lanes
                 const int nseg = 2 * (2 * s + 1) * (2 * s + 1);
+#ifdef VT_PROFILE
+                if (G.gl == 0) VT_PROF_ADD(16, 1);
+#endif
                 for (int e0 = 0; e0 < nseg && status == 0; e0 += T) {
+#ifdef VT_PROFILE
+                    if (G.gl == 0) VT_PROF_ADD(17, 1);
+#endif
+                    // only grid cells that reach into the ball of radius 2R and are
+                    // not wholly inside the ball the list already covered
                     int sa = 0, sb = 0;
-                    if (e0 + G.gl < nseg) shell_segment(e0 + G.gl, s, ix, iy, iz, Gr, coff, sa, sb);
+                    const float r_out2 = 4.0f * (float)cell.R2 * (1.0f + 2e-4f);
+                    if (e0 + G.gl < nseg)
+                        shell_segment_ball(e0 + G.gl, s, ix, iy, iz, grid, coff, pq, r_out2, r_in2, sa, sb);
                     const int len = sb - sa;
                     int total;
                     const int start = G.scan(len, total);
                     const int incl = start + len;
+#ifdef VT_PROFILE
+                    if (G.gl == 0) VT_PROF_ADD(19, total);
+#endif
                     for (int c0 = 0; c0 < total && status == 0; c0 += T) {
+#ifdef VT_PROFILE
+                        if (G.gl == 0) VT_PROF_ADD(18, 1);
+#endif
                         const int i = c0 + G.gl;
                         int seg = 0;  // segments ending at or before i
 #pragma unroll
@@ -1198,17 +1276,24 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
                 const bool covers = ix - s <= 0 && iy - s <= 0 && iz - s <= 0 && ix + s >= Gr - 1 &&
                                     iy + s >= Gr - 1 && iz + s >= Gr - 1;
                 if (covers) { status = -1; break; }
-                const double gap = shell_gap(grid, pq, ix, iy, iz, s);
-                if (gap > 0 && 4.0 * (double)cell.R2 * (1.0 + 1e-5) <= gap * gap) { status = -1; break; }
+                const float gap = shell_gap(grid, pq, ix, iy, iz, s);
+                if (gap > 0.0f && 4.0f * (float)cell.R2 * (1.0f + 2e-5f) <= gap * gap) { status = -1; break; }
             }
             end = status == -1 ? END_VALID : status;
         }
 
+#ifdef VT_PROFILE
+        long long tp2 = clock64();
+        if (G.gl == 0) VT_PROF_ADD(pb + 2, tp2 - tp1);
+#endif
         if (end == END_VALID) {
             cell.dump_positions(G, sm);
             G.sync();
             finish_cell<Real, T, T * VPL, PCAP, typename C::M>(sm, cell.alive, cell.np, cell.pi, G.gl, G.mask, out_idx,
                                                                A);
+#ifdef VT_PROFILE
+            if (G.gl == 0) VT_PROF_ADD(pb + 6, clock64() - tp2);
+#endif
         } else {
             if (end == END_NEED_K && !EXH && !ROBUST && A.state) cell.save(G, sm, stp, last_d2, last_orig);
             if (G.gl == 0) {

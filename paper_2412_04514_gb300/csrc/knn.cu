@@ -138,8 +138,16 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
             // parallel, then the segments' candidates are spread over all lanes
             const int nseg = 2 * (2 * s + 1) * (2 * s + 1);
             for (int e0 = 0; e0 < nseg; e0 += 32) {
+                // once the list is full, only grid cells that reach into the
+                // ball of the current k-th distance can hold a better candidate
                 int sa = 0, sb = 0;
-                if (e0 + lane < nseg) shell_segment(e0 + lane, s, ix, iy, iz, G, cell_off, sa, sb);
+                if (e0 + lane < nseg) {
+                    if (count == k)
+                        shell_segment_ball(e0 + lane, s, ix, iy, iz, g, cell_off, pq, (float)kd * (1.0f + 1e-5f),
+                                           -1.0f, sa, sb);
+                    else
+                        shell_segment(e0 + lane, s, ix, iy, iz, G, cell_off, sa, sb);
+                }
                 const int len = sb - sa;
                 int incl = len;
 #pragma unroll
@@ -196,8 +204,8 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
                                 iz + s >= G - 1;
             if (covers) break;
             if (count == k) {
-                const double gap = shell_gap(g, pq, ix, iy, iz, s);
-                if (gap > 0 && (double)kd <= gap * gap * (1.0 - 1e-6)) break;
+                const float gap = shell_gap(g, pq, ix, iy, iz, s);
+                if (gap > 0.0f && (float)kd * (1.0f + 1e-6f) <= gap * gap * (1.0f - 1e-5f)) break;
             }
         }
         if (__any_sync(FULL, dup) && lane == 0) atomicExch((int*)&st->duplicate, 1);

@@ -1,0 +1,193 @@
+// range.cu -- candidate lists for the last clipping pass.
+//
+// After the k_max list pass a cell that is not yet validated has clipped by
+// its k_max nearest neighbours; it can still be cut only by a generator q
+// beyond the list (key above the last list key) with |q - p|^2 < 4 R^2 (the
+// security radius, Summary section of the paper) whose bisector reaches the
+// cell's bounding box. This kernel gathers exactly those generators for each
+// such cell -- one warp per cell walks the grid shells around it, restricted
+// to grid cells that meet the ball of radius 2R and are not inside the ball
+// the list already covered -- and writes them sorted by the kNN key, so the
+// clipper can process them nearest first and stop by the security radius.
+// R, the bounding box and the last list key come from the cell's saved
+// state. A cell with more than `cap` candidates is handed to the clipper's
+// own exhaustive walk instead (overflow list).
+#include <float.h>
+#include <limits.h>
+
+#include "vt_internal.cuh"
+
+namespace vt {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int RANGE_BLOCK = 256;
+
+template <typename Real>
+struct RangeKey;
+template <>
+struct RangeKey<float> {
+    static __device__ __forceinline__ float d2(float4 a, float4 b) { return knn_d2_f32(a, b); }
+};
+template <>
+struct RangeKey<double> {
+    static __device__ __forceinline__ double d2(float4 a, float4 b) { return knn_d2_f64(a, b); }
+};
+
+template <typename Real>
+__global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict__ sorted,
+                                                       const int32_t* __restrict__ cell_off0,
+                                                       const __grid_constant__ GridDesc g0,
+                                                       const GridDesc* __restrict__ sets,
+                                                       const int32_t* __restrict__ set_of,
+                                                       const int32_t* __restrict__ queries, int64_t nq_host,
+                                                       const int32_t* __restrict__ nq_dev,
+                                                       const uint8_t* __restrict__ state, size_t state_stride,
+                                                       int cap, int32_t* __restrict__ rnbr, Real* __restrict__ rd2,
+                                                       int32_t* __restrict__ rlen, int32_t* __restrict__ over_list,
+                                                       int32_t* __restrict__ over_ctr, DevStatus* st)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    Real* bk = reinterpret_cast<Real*>(smem_raw) + warp * RANGE_CAP;
+    int32_t* bo = reinterpret_cast<int32_t*>(smem_raw + sizeof(Real) * RANGE_CAP * (RANGE_BLOCK / 32)) +
+                  warp * RANGE_CAP;
+    int32_t* bj = bo + RANGE_CAP * (RANGE_BLOCK / 32);
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t nq = nq_host;
+    if (nq_dev) {
+        const int64_t want = *nq_dev;
+        if (want > nq_host && threadIdx.x == 0 && blockIdx.x == 0) atomicExch((int*)&st->list_overflow, 1);
+        nq = want < nq_host ? want : nq_host;
+    }
+    for (int64_t c = wid; c < nq; c += nw) {
+        const int q = queries[c];
+        const float4 pq = sorted[q];
+        const GridDesc& g = grid_of(g0, sets, set_of, q);
+        const int G = g.G;
+        const int32_t* cell_off = cell_off0 + g.cell_base;
+        const StateHdr* h = reinterpret_cast<const StateHdr*>(state + (size_t)q * state_stride);
+        const float R2 = (float)h->R2;
+        const Real lkey = (Real)h->last_d2;  // exact: the key was stored from a Real
+        const int last_orig = h->last_orig;
+        const float lo3[3] = {h->bb_lo[0], h->bb_lo[1], h->bb_lo[2]};
+        const float hi3[3] = {h->bb_hi[0], h->bb_hi[1], h->bb_hi[2]};
+        const float r4 = 4.0f * R2 * (1.0f + 1e-4f);
+        const float r_out2 = 4.0f * R2 * (1.0f + 2e-4f);
+        const float r_in2 = last_orig >= 0 ? (float)lkey * (1.0f - 1e-4f) : -1.0f;
+        const int ix = cell_coord(pq.x, g.lo[0], g.scale[0], G);
+        const int iy = cell_coord(pq.y, g.lo[1], g.scale[1], G);
+        const int iz = cell_coord(pq.z, g.lo[2], g.scale[2], G);
+        int count = 0;
+        bool over = false;
+        for (int s = 0; !over; ++s) {
+            const int nseg = 2 * (2 * s + 1) * (2 * s + 1);
+            for (int e0 = 0; e0 < nseg && !over; e0 += 32) {
+                int sa = 0, sb = 0;
+                if (e0 + lane < nseg)
+                    shell_segment_ball(e0 + lane, s, ix, iy, iz, g, cell_off, pq, r_out2, r_in2, sa, sb);
+                const int len = sb - sa;
+                int incl = len;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int u = __shfl_up_sync(FULL, incl, d);
+                    if (lane >= d) incl += u;
+                }
+                const int total = __shfl_sync(FULL, incl, 31);
+                const int start = incl - len;
+                for (int c0 = 0; c0 < total && !over; c0 += 32) {
+                    const int i = c0 + lane;
+                    int seg = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1)
+                        if (__shfl_sync(FULL, incl, (seg + step - 1) & 31) <= i) seg += step;
+                    const int aj = __shfl_sync(FULL, sa, seg & 31), sj = __shfl_sync(FULL, start, seg & 31);
+                    const int jj = aj + (i - sj);
+                    bool keep = false;
+                    Real key = (Real)0;
+                    int ko = 0;
+                    if (i < total && jj != q) {
+                        const float4 pc = sorted[jj];
+                        const float ex = pc.x - pq.x, ey = pc.y - pq.y, ez = pc.z - pq.z;
+                        const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                        const float hb = fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) +
+                                         fmaxf(ez * lo3[2], ez * hi3[2]);
+                        keep = r4 > d2 && hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * R2) - 1e-30f;
+                        if (keep) {
+                            key = RangeKey<Real>::d2(pq, pc);
+                            ko = __float_as_int(pc.w);
+                            if (last_orig >= 0 && (key < lkey || (key == lkey && ko <= last_orig)))
+                                keep = false;  // the list already held it
+                        }
+                    }
+                    const unsigned m = __ballot_sync(FULL, keep);
+                    const int pos = count + __popc(m & ((1u << lane) - 1u));
+                    if (keep && pos < cap) {
+                        bk[pos] = key;
+                        bo[pos] = ko;
+                        bj[pos] = jj;
+                    }
+                    count += __popc(m);
+                    over = count > cap;
+                }
+            }
+            if (over) break;
+            const bool covers = ix - s <= 0 && iy - s <= 0 && iz - s <= 0 && ix + s >= G - 1 && iy + s >= G - 1 &&
+                                iz + s >= G - 1;
+            if (covers) break;
+            const float gap = shell_gap(g, pq, ix, iy, iz, s);
+            if (gap > 0.0f && 4.0f * R2 * (1.0f + 2e-5f) <= gap * gap) break;
+        }
+        if (over) {
+            if (lane == 0) {
+                rlen[c] = -1;
+                over_list[atomicAdd(over_ctr, 1)] = q;
+            }
+            __syncwarp();
+            continue;
+        }
+        __syncwarp();
+        // rank sort by (key, original index): keys are distinct
+        for (int e = lane; e < count; e += 32) {
+            const Real ke = bk[e];
+            const int oe = bo[e];
+            int rank = 0;
+            for (int f = 0; f < count; ++f) rank += (bk[f] < ke || (bk[f] == ke && bo[f] < oe)) ? 1 : 0;
+            rnbr[c * (int64_t)cap + rank] = bj[e];
+            rd2[c * (int64_t)cap + rank] = ke;
+        }
+        if (lane == 0) rlen[c] = count;
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+size_t range_smem_bytes(int precision)
+{
+    const size_t key = precision == VT_FP64 ? sizeof(double) : sizeof(float);
+    return (key + 2 * sizeof(int32_t)) * RANGE_CAP * (RANGE_BLOCK / 32);
+}
+
+cudaError_t launch_range(const RangeArgs& a, cudaStream_t s)
+{
+    if (a.nq <= 0) return cudaSuccess;
+    int64_t blocks = (a.nq + 7) / 8;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    const size_t smem = range_smem_bytes(a.precision);
+    if (a.precision == VT_FP64)
+        k_range<double><<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(
+            a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.state, a.state_stride,
+            RANGE_CAP, a.rnbr, (double*)a.rd2, a.rlen, a.over_list, a.over_ctr, a.st);
+    else
+        k_range<float><<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(
+            a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.state, a.state_stride,
+            RANGE_CAP, a.rnbr, (float*)a.rd2, a.rlen, a.over_list, a.over_ctr, a.st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace vt

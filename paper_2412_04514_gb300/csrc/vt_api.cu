@@ -112,9 +112,11 @@ Layout make_layout(const vt_params* p, int64_t n, int64_t cells, bool batch)
     L.g3 = cells >= 0 ? cells : (int64_t)L.G * L.G * L.G;
     const int64_t nn = n > 0 ? n : 1;
     // list-mode passes run in chunks of knn_cap / k cells; the no-sync schedule
-    // runs each pass in one launch, so its buffer holds n * k_max entries
+    // runs each pass in one launch, so its buffer holds n * max(k_max, the
+    // range-list capacity) entries
     const bool nosync = (p->flags & VT_FLAG_NO_SYNC) != 0;
-    int64_t cap = nn * (int64_t)(nosync ? p->k_max : p->k0);
+    const int kmx = p->k_max > RANGE_CAP ? p->k_max : RANGE_CAP;
+    int64_t cap = nn * (int64_t)(nosync ? kmx : p->k0);
     if (cap < (int64_t)p->k_max * 64) cap = (int64_t)p->k_max * 64;
     L.knn_cap = cap;
     const bool recs = (p->emit & (VT_EMIT_NBR | VT_EMIT_GEOM)) != 0;
@@ -148,6 +150,7 @@ Layout make_layout(const vt_params* p, int64_t n, int64_t cells, bool batch)
     L.knn_d2 = take(sizeof(double) * L.knn_cap);
     L.set_of = batch ? take(sizeof(int32_t) * nn) : 0;
     L.ctr = take(sizeof(int32_t) * (3 * VT_MAX_PASSES + 8));
+    L.rlen = take(sizeof(int32_t) * nn);
     L.total = off;
     return L;
 }
@@ -346,6 +349,88 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
     return VT_OK;
 }
 
+// the last pass for resumed regular cells (`list`, m cells or *m_dev): range
+// lists of every generator that can still cut, sorted nearest first, clipped
+// as complete lists; cells with more candidates than a list holds go to
+// over_list / over_ctr and the exhaustive walk. Failures go to fail_robust.
+int range_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, const int32_t* m_dev, int k_prev,
+               int variant, vt_cells_out* out, int32_t* over_list, int32_t* over_ctr, int32_t* fail_robust,
+               int32_t* ctr_robust, int32_t* unval, int32_t* ctr_unval)
+{
+    const Layout& L = c.L;
+    StageTimer dummy;
+    StageTimer& T = c.timer ? *c.timer : dummy;
+    cudaError_t e = cudaMemsetAsync(over_ctr, 0, sizeof(int32_t), c.s);
+    if (e != cudaSuccess) return cuda_fail(e, "counter reset");
+    const int64_t chunk = L.knn_cap / RANGE_CAP;
+    const int64_t mm = (m_dev && m > chunk) ? chunk : m;
+    for (int64_t o = 0; o < mm; o += chunk) {
+        const int64_t cnt = (mm - o) < chunk ? (mm - o) : chunk;
+        RangeArgs r{};
+        r.sorted = c.at<float4>(L.sorted);
+        r.cell_off = c.at<int32_t>(L.cell_off);
+        r.g = c.g;
+        r.sets = c.sets;
+        r.set_of = c.set_of();
+        r.queries = list + o;
+        r.nq = cnt;
+        r.nq_dev = m_dev;
+        r.state = c.at<uint8_t>(L.state);
+        r.state_stride = L.state_stride;
+        r.precision = p->precision;
+        r.rnbr = c.at<int32_t>(L.knn_nbr);
+        r.rd2 = c.at<void>(L.knn_d2);
+        r.rlen = c.at<int32_t>(L.rlen);
+        r.over_list = over_list;
+        r.over_ctr = over_ctr;
+        r.st = c.st;
+        T.begin(StageTimer::KNN);
+        e = launch_range(r, c.s);
+        T.end();
+        if (c.knn_launches) ++*c.knn_launches;
+        if (e != cudaSuccess) return cuda_fail(e, "range launch");
+        ClipArgs a{};
+        a.sorted = r.sorted;
+        a.cell_off = r.cell_off;
+        a.g = c.g;
+        a.sets = c.sets;
+        a.set_of = c.set_of();
+        a.nq_dev = m_dev;
+        a.n = L.n;
+        a.queries = r.queries;
+        a.nq = cnt;
+        a.nq_cap = cnt;
+        a.nbr = r.rnbr;
+        a.d2 = r.rd2;
+        a.k = RANGE_CAP;
+        a.klen = r.rlen;
+        a.complete = 1;
+        a.restore = 1;
+        a.emit = p->emit;
+        a.index_space = p->index_space;
+        a.vol = (p->emit & VT_EMIT_VOL) ? out->vol : nullptr;
+        a.cen = (p->emit & VT_EMIT_CEN) ? out->cen : nullptr;
+        a.m2 = (p->emit & VT_EMIT_M2) ? out->m2 : nullptr;
+        a.rec = L.rec_stride ? c.at<uint8_t>(L.rec) : nullptr;
+        a.rec_stride = L.rec_stride;
+        a.fail_next = unval;  // a complete list never asks for more
+        a.ctr_next = ctr_unval;
+        a.fail_robust = fail_robust;
+        a.ctr_robust = ctr_robust;
+        a.state = c.at<uint8_t>(L.state);
+        a.state_stride = L.state_stride;
+        a.st = c.st;
+        T.begin(StageTimer::CLIP);
+        e = launch_clip(a, variant, p->threads_per_cell, c.s);
+        T.end();
+        if (c.clip_launches) ++*c.clip_launches;
+        if (e != cudaSuccess) return cuda_fail(e, "clip launch");
+    }
+    // the overflowed cells: the clipper's own walk, resuming the saved state
+    return clip_pass(c, p, over_list, m, over_ctr, 0, true, k_prev, variant, p->precision, out, unval, ctr_unval,
+                     fail_robust, ctr_robust);
+}
+
 int status_errors(const DevStatus& h)
 {
     if (h.bad_point)
@@ -506,8 +591,12 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
             int32_t* bn = last ? unval : robl[(pi + 1) % 2];
             int32_t* bc = last ? &c.st->n_unval : &ctr_rob[pi];
             const int kr = last ? ROBUST_EXH_K : kk;  // the robust variant's list
-            r = clip_pass(c, p, q, n, qn, kk, last, k_prev, variant_reg, p->precision, out, rn, rc, rob_new,
-                          &ctr_new[pi]);
+            if (last && pi > 0)
+                r = range_pass(c, p, q, n, qn, k_prev, variant_reg, out, regl[(pi + 1) % 2], &ctr_reg[pi], rob_new,
+                               &ctr_new[pi], unval, &c.st->n_unval);
+            else
+                r = clip_pass(c, p, q, n, qn, kk, last, k_prev, variant_reg, p->precision, out, rn, rc, rob_new,
+                              &ctr_new[pi]);
             if (r) return r;
             r = clip_pass(c, p, rob_new, n, &ctr_new[pi], kr, last, 0, 2, VT_FP64, out, bn, bc, unval,
                           &c.st->n_unval);
@@ -548,8 +637,12 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
                 count_launch();
                 implicit = false;
             }
-            r = clip_pass(c, p, implicit ? nullptr : reg_cur, m_reg, nullptr, kk, exhaustive, k_prev, variant_reg,
-                          p->precision, out, reg_nxt, &c.st->n_fail_next, rob_new, &c.st->n_fail_robust);
+            if (exhaustive && k_prev > 0 && !implicit)
+                r = range_pass(c, p, reg_cur, m_reg, nullptr, k_prev, variant_reg, out, reg_nxt, &c.st->n_range_over,
+                               rob_new, &c.st->n_fail_robust, unval + n_unval, &c.st->n_fail_next);
+            else
+                r = clip_pass(c, p, implicit ? nullptr : reg_cur, m_reg, nullptr, kk, exhaustive, k_prev, variant_reg,
+                              p->precision, out, reg_nxt, &c.st->n_fail_next, rob_new, &c.st->n_fail_robust);
             if (r) return r;
             if ((r = read_status(c, h))) return r;
             if ((r = status_errors(h))) return r;

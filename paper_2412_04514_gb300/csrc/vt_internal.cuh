@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <float.h>
 #include <stdint.h>
 
 #include "vt.h"
@@ -32,20 +33,23 @@ __device__ __forceinline__ const GridDesc& grid_of(const GridDesc& g0, const Gri
 }
 
 // distance from q (in grid cell (ix, iy, iz)) to the outside of the block of
-// shells 0..s, minus the rounding margin; 1e300 when the block reaches every
+// shells 0..s, minus the rounding margin; FLT_MAX when the block reaches every
 // wall of the box (no generator lies beyond it)
-__device__ __forceinline__ double shell_gap(const GridDesc& g, float4 q, int ix, int iy, int iz, int s)
+__device__ __forceinline__ float shell_gap(const GridDesc& g, float4 q, int ix, int iy, int iz, int s)
 {
+    // float32 throughout (the FP64 pipe is scarce): the grid's rounding
+    // margin is taken twice, which also covers the float32 rounding of the
+    // block bounds (a few ulps of the box extent)
     const int G = g.G;
-    const double q0 = q.x, q1 = q.y, q2 = q.z;
-    double gap = 1e300;
-    if (ix - s > 0) gap = fmin(gap, q0 - ((double)g.lo[0] + (ix - s) * g.cw[0]) - g.margin);
-    if (ix + s + 1 < G) gap = fmin(gap, ((double)g.lo[0] + (ix + s + 1) * g.cw[0]) - q0 - g.margin);
-    if (iy - s > 0) gap = fmin(gap, q1 - ((double)g.lo[1] + (iy - s) * g.cw[1]) - g.margin);
-    if (iy + s + 1 < G) gap = fmin(gap, ((double)g.lo[1] + (iy + s + 1) * g.cw[1]) - q1 - g.margin);
-    if (iz - s > 0) gap = fmin(gap, q2 - ((double)g.lo[2] + (iz - s) * g.cw[2]) - g.margin);
-    if (iz + s + 1 < G) gap = fmin(gap, ((double)g.lo[2] + (iz + s + 1) * g.cw[2]) - q2 - g.margin);
-    return gap;
+    float gap = FLT_MAX;
+    const float c0 = (float)g.cw[0], c1 = (float)g.cw[1], c2 = (float)g.cw[2];
+    if (ix - s > 0) gap = fminf(gap, q.x - (g.lo[0] + (float)(ix - s) * c0));
+    if (ix + s + 1 < G) gap = fminf(gap, (g.lo[0] + (float)(ix + s + 1) * c0) - q.x);
+    if (iy - s > 0) gap = fminf(gap, q.y - (g.lo[1] + (float)(iy - s) * c1));
+    if (iy + s + 1 < G) gap = fminf(gap, (g.lo[1] + (float)(iy + s + 1) * c1) - q.y);
+    if (iz - s > 0) gap = fminf(gap, q.z - (g.lo[2] + (float)(iz - s) * c2));
+    if (iz + s + 1 < G) gap = fminf(gap, (g.lo[2] + (float)(iz + s + 1) * c2) - q.z);
+    return gap == FLT_MAX ? FLT_MAX : gap - 2.0f * (float)g.margin;
 }
 
 GridDesc make_grid(const vt_params* p, int G);
@@ -91,6 +95,71 @@ __device__ __forceinline__ void shell_segment(int e, int s, int ix, int iy, int 
     }
 }
 
+// The part of segment e of shell s (see shell_segment) whose grid cells reach
+// into the ball of squared radius r_out2 around q and are not wholly inside
+// the ball of squared radius r_in2 (r_in2 <= 0: none is skipped). A rim row's
+// z-run loses its inner cells as two pieces: the part below is its first
+// segment, the part above its second. Cell bounds are widened by the grid's
+// rounding margin, so a cell is dropped only when no point assigned to it can
+// lie in the annulus; callers pass radii that already carry their own margins.
+__device__ __forceinline__ void shell_segment_ball(int e, int s, int ix, int iy, int iz, const GridDesc& g,
+                                                   const int32_t* __restrict__ cell_off, float4 q, float r_out2,
+                                                   float r_in2, int& a, int& b)
+{
+    const int G = g.G;
+    const int W = 2 * s + 1;
+    const int row = e >> 1, half = e & 1;
+    const int dx = row / W - s, dy = row - (row / W) * W - s;
+    const int x = ix + dx, y = iy + dy;
+    a = b = 0;
+    if (x < 0 || x >= G || y < 0 || y >= G) return;
+    const float m = (float)g.margin;
+    const float cx = (float)g.cw[0], cy = (float)g.cw[1], cz = (float)g.cw[2];
+    const float x0 = g.lo[0] + (float)x * cx - m, x1 = g.lo[0] + (float)(x + 1) * cx + m;
+    const float y0 = g.lo[1] + (float)y * cy - m, y1 = g.lo[1] + (float)(y + 1) * cy + m;
+    const float dxn = fmaxf(fmaxf(x0 - q.x, q.x - x1), 0.0f), dyn = fmaxf(fmaxf(y0 - q.y, q.y - y1), 0.0f);
+    const float dxf = fmaxf(q.x - x0, x1 - q.x), dyf = fmaxf(q.y - y0, y1 - q.y);
+    const float dn2 = dxn * dxn + dyn * dyn, df2 = dxf * dxf + dyf * dyf;
+    if (dn2 > r_out2) return;
+    // cells of the row that meet the outer ball
+    const float zr = sqrtf(r_out2 - dn2);
+    // (index arithmetic in float32 carries 1e-3 of a cell width of slack,
+    // far above its rounding for G <= 1024)
+    const float gz = (float)G;
+    const int zlo = (int)floorf(fminf(fmaxf((q.z - zr - m - g.lo[2]) * g.scale[2] - 1e-3f, -2.0f), gz + 1.0f));
+    const int zhi = (int)floorf(fminf(fmaxf((q.z + zr + m - g.lo[2]) * g.scale[2] + 1e-3f, -2.0f), gz + 1.0f));
+    // cells of the row wholly inside the inner ball: [zi0, zi1]
+    int zi0 = 1, zi1 = 0;
+    if (r_in2 > df2) {
+        const float zi = sqrtf(r_in2 - df2);
+        zi0 = (int)ceilf(fminf(fmaxf((q.z - zi + m - g.lo[2]) * g.scale[2] + 1e-3f, -2.0f), gz + 1.0f));
+        zi1 = (int)floorf(fminf(fmaxf((q.z + zi - m - g.lo[2]) * g.scale[2] - 1e-3f, -2.0f), gz + 1.0f)) - 1;
+    }
+    const bool rim = dx == -s || dx == s || dy == -s || dy == s;
+    const int base = (x * G + y) * G;
+    int za, zb;
+    if (rim) {
+        za = iz - s > zlo ? iz - s : zlo;
+        zb = iz + s < zhi ? iz + s : zhi;
+        za = za < 0 ? 0 : za;
+        zb = zb > G - 1 ? G - 1 : zb;
+        if (za > zb) return;
+        if (zi0 <= zi1 && zi0 <= zb && zi1 >= za) {  // the inner cells split the run
+            if (half) za = zi1 + 1 > za ? zi1 + 1 : za;
+            else zb = zi0 - 1 < zb ? zi0 - 1 : zb;
+        } else if (half) {
+            return;
+        }
+    } else {
+        const int z = half ? iz + s : iz - s;
+        if (z < 0 || z >= G || z < zlo || z > zhi || (z >= zi0 && z <= zi1)) return;
+        za = zb = z;
+    }
+    if (za > zb) return;
+    a = cell_off[base + za];
+    b = cell_off[base + zb + 1];
+}
+
 // kNN ordering keys. FP64 form: ((dx*dx + dy*dy) + dz*dz) in double with
 // dx = double(x_j) - double(x_i), every operation separately rounded (no FMA),
 // so lists are exact and reproducible. FP32 form: the same in float32 with FMA.
@@ -106,6 +175,23 @@ __device__ __forceinline__ float knn_d2_f32(float4 a, float4 b)
     const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
     return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
 }
+
+// ---------------------------------------------------------------------------
+// header of a cell's saved polyhedron between passes (fixed stride per cell;
+// the planes, topology and positions follow at 128 bytes)
+// ---------------------------------------------------------------------------
+struct StateHdr {
+    uint64_t alive[2];
+    int32_t np;
+    int32_t last_orig;   // original index of the last list entry processed
+    double R2;           // max |v|^2 over the vertices (local frame)
+    double last_d2;      // the last list entry's kNN key
+    float bb_lo[3];      // bounding box of the vertices (local frame)
+    float bb_hi[3];
+    int32_t pad[4];
+};
+static_assert(sizeof(StateHdr) <= 128, "state header");
+
 
 // ---------------------------------------------------------------------------
 // device status block at the start of every workspace
@@ -125,9 +211,32 @@ struct DevStatus {
     long long totals[4];      // nbr, vtx, face, face_vtx totals written by the emit scan
     unsigned int detail[8];   // clip events: 0 keep-none, 1 plane cap, 2 vertex cap, 3 ring, 4 interpolated
     int32_t list_overflow;    // a device-counted pass had more cells than its list buffers hold
-    int32_t pad2;
+    int32_t n_range_over;     // cells of the last pass with more candidates than a range list holds
 };
 static_assert(sizeof(DevStatus) % 64 == 0, "status block must stay 64-byte sized");
+
+// candidate lists of the last pass (range.cu): at most RANGE_CAP per cell
+constexpr int RANGE_CAP = 64;
+struct RangeArgs {
+    const float4* sorted;
+    const int32_t* cell_off;
+    GridDesc g;
+    const GridDesc* sets;
+    const int32_t* set_of;
+    const int32_t* queries;  // sorted indices of the cells (saved states)
+    int64_t nq;              // cells (the bound when nq_dev is set)
+    const int32_t* nq_dev;
+    const uint8_t* state;
+    size_t state_stride;
+    int precision;           // key precision: VT_FP64 or VT_FP32_RECHECK
+    int32_t* rnbr;           // [nq * RANGE_CAP] sorted indices, nearest first
+    void* rd2;               // [nq * RANGE_CAP] their keys (float or double)
+    int32_t* rlen;           // [nq] list length, -1 when the cell overflowed
+    int32_t* over_list;      // overflowed cells (appended)
+    int32_t* over_ctr;
+    DevStatus* st;
+};
+cudaError_t launch_range(const RangeArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // per-cell output record (fixed stride, in the workspace)
@@ -163,7 +272,7 @@ struct Layout {
     size_t rec_stride;
     size_t status, cid, ticket, counts, cell_off, big, scan_tmp, sorted, perm;
     size_t state_stride;
-    size_t list_a, list_b, list_r, knn_nbr, knn_d2, rec, cnt, off64, scan_emit, state, set_of, ctr;
+    size_t list_a, list_b, list_r, knn_nbr, knn_d2, rec, cnt, off64, scan_emit, state, set_of, ctr, rlen;
     size_t total;
 };
 // cells < 0: the single-set grid of p; otherwise the total grid cells of a batch
@@ -216,8 +325,11 @@ struct ClipArgs {
     int64_t nq;
     const int32_t* nbr;       // [nq*k] (k > 0)
     const void* d2;           // [nq*k] float or double
-    int k;                    // list entries per cell (0 = no list)
+    int k;                    // list entries per cell (0 = no list; the stride of nbr/d2)
     int exhaustive;           // 1: after the list (or the resumed state), walk every generator within 2R
+    const int32_t* klen;      // per-cell list lengths (<= k), or NULL (every list has k entries)
+    int complete;             // 1: the lists hold every generator that can still cut (range lists)
+    int restore;              // 1: resume the saved state and start at list entry 0
     int emit;
     int index_space;
     double* vol;
