@@ -834,6 +834,25 @@ struct Cell {
         return clip(G, sm, nx, ny, nz, b, j, sorted, grid, st);
     }
 
+    // Per-lane test of one plane n.x <= |n|^2 / 2 (n = pj - pi) against every
+    // live vertex, positions read from sm.vpos: false only when each vertex is
+    // inside by more than 1e-5 |n| R, beyond the band the sign test re-decides
+    // in FP64, so a plane that fails cannot cut and clip() would do nothing.
+    __device__ __forceinline__ bool reaches(const S& sm, float nx, float ny, float nz) const
+    {
+        const float nn = nx * nx + ny * ny + nz * nz;
+        const float lim = 0.5f * nn - 1e-5f * sqrtf(nn * (float)R2) - 1e-30f;
+#pragma unroll
+        for (int w = 0; w < M::W_; ++w) {
+            for (uint64_t m = alive.w[w]; m; m &= m - 1ull) {
+                const int s = w * 64 + __ffsll((long long)m) - 1;
+                const float d = nx * (float)sm.vpos[s][0] + ny * (float)sm.vpos[s][1] + nz * (float)sm.vpos[s][2];
+                if (d > lim) return true;
+            }
+        }
+        return false;
+    }
+
     __device__ __forceinline__ void dump_positions(const Group<T>& G, S& sm) const
     {
 #pragma unroll
@@ -1056,7 +1075,7 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, 
         const float hb =
             fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) + fmaxf(ez * lo3[2], ez * hi3[2]);
         need = r4 * (1.0f + 1e-4f) > d2 &&
-               hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f;
+               hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f && cell.reaches(sm, ex, ey, ez);
         if (need && last_orig >= 0) {  // already processed from the list?
             const int ko = __float_as_int(pc.w);
             if (Tol<Real>::fp32) {  // float keys compare in float (last_d2 holds a float)
@@ -1132,10 +1151,9 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
     // saved polyhedron of the last list pass instead)
     constexpr bool LIST = !EXH || ROBUST;
     int64_t nq = A.nq;
-    if (A.nq_dev) {
-        const int64_t want = *A.nq_dev;
-        if (want > A.nq_cap && threadIdx.x == 0 && blockIdx.x == 0) atomicExch((int*)&A.st->list_overflow, 1);
-        nq = want < A.nq_cap ? want : A.nq_cap;
+    if (A.nq_dev) {  // device-counted: list entries [nq_off, nq_off + nq_cap)
+        const int64_t want = (int64_t)*A.nq_dev - A.nq_off;
+        nq = want < 0 ? 0 : (want < A.nq_cap ? want : A.nq_cap);
     }
     C cell;
     cell.stamp = 0;
@@ -1157,6 +1175,8 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
 #endif
         if (resume) cell.restore(G, sm, stp, last_d2, last_orig);
         else cell.init_box(G, sm, grid);
+        cell.dump_positions(G, sm);  // the per-lane cut tests read positions from shared memory
+        G.sync();
 #ifdef VT_PROFILE
         long long tp1 = clock64();
         if (G.gl == 0) {
@@ -1185,7 +1205,15 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
                 nd = nm < kc ? dd[nm] : (Real)0;
                 np4 = nj >= 0 ? A.sorted[nj] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const int cnt = kc - base < T ? kc - base : T;
-                for (int t = 0; t < cnt; ++t) {
+                // range lists: each lane tests its entry against the live vertices
+                // and only the entries that can cut are clipped, in list order
+                // (in k-nearest lists most entries cut, so every one is clipped)
+                bool want = false;
+                if (G.gl < cnt)
+                    want = !A.complete || cj < 0 ||
+                           cell.reaches(sm, cp.x - cell.pi.x, cp.y - cell.pi.y, cp.z - cell.pi.z);
+                for (unsigned todo = G.ballot(want); todo; todo &= todo - 1u) {
+                    const int t = __ffs(todo) - 1;
                     const int j = G.bcast(cj, t);
                     if (j < 0) { end = END_VALID; stop = true; break; }  // the list holds every other generator
                     const Real dj = G.bcast(cd, t);

@@ -105,17 +105,17 @@ template <typename Real, int KPL>
 __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, const int32_t* __restrict__ cell_off0,
                                              const __grid_constant__ GridDesc g0, const GridDesc* __restrict__ sets,
                                              const int32_t* __restrict__ set_of, const int32_t* __restrict__ queries,
-                                             int64_t nq_host, const int32_t* __restrict__ nq_dev, int k,
+                                             int64_t nq_host, const int32_t* __restrict__ nq_dev,
+                                             int64_t nq_off, int k,
                                              int32_t* __restrict__ nbr, Real* __restrict__ d2out, DevStatus* st)
 {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t nq = nq_host;
-    if (nq_dev) {  // device-counted: at most nq_host queries fit the output
-        const int64_t want = *nq_dev;
-        if (want > nq_host && threadIdx.x == 0 && blockIdx.x == 0) atomicExch((int*)&st->list_overflow, 1);
-        nq = want < nq_host ? want : nq_host;
+    if (nq_dev) {  // device-counted: this launch takes entries [nq_off, nq_off + nq_host) of the list
+        const int64_t want = (int64_t)*nq_dev - nq_off;
+        nq = want < 0 ? 0 : (want < nq_host ? want : nq_host);
     }
     for (int64_t c = wid; c < nq; c += nw) {
         const int q = queries ? queries[c] : (int)c;
@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
 
 template <typename Real>
 cudaError_t launch_knn_t(const float4* sorted, const int32_t* cell_off, const GridDesc& g, const GridDesc* sets,
-                         const int32_t* set_of, const int32_t* queries, int64_t nq, const int32_t* nq_dev, int k,
+                         const int32_t* set_of, const int32_t* queries, int64_t nq, const int32_t* nq_dev,
+                         int64_t nq_off, int k,
                          int32_t* nbr, Real* d2, DevStatus* st, cudaStream_t s)
 {
     if (nq <= 0) return cudaSuccess;
@@ -230,13 +231,13 @@ cudaError_t launch_knn_t(const float4* sorted, const int32_t* cell_off, const Gr
     if (blocks > 152 * 32) blocks = 152 * 32;
     dim3 grid((unsigned)blocks), block(256);
     if (k <= 32)
-        k_knn<Real, 1><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, k, nbr, d2, st);
+        k_knn<Real, 1><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, d2, st);
     else if (k <= 64)
-        k_knn<Real, 2><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, k, nbr, d2, st);
+        k_knn<Real, 2><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, d2, st);
     else if (k <= 128)
-        k_knn<Real, 4><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, k, nbr, d2, st);
+        k_knn<Real, 4><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, d2, st);
     else
-        k_knn<Real, 8><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, k, nbr, d2, st);
+        k_knn<Real, 8><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, d2, st);
     count_launch();
     return cudaGetLastError();
 }
@@ -246,14 +247,15 @@ cudaError_t launch_knn_t(const float4* sorted, const int32_t* cell_off, const Gr
 cudaError_t launch_knn(const float4* sorted, const int32_t* cell_off, const GridDesc& g, int64_t n,
                        const int32_t* queries, int64_t nq, int k, int precision, int32_t* nbr, void* d2,
                        DevStatus* st, cudaStream_t s, const GridDesc* sets, const int32_t* set_of,
-                       const int32_t* nq_dev)
+                       const int32_t* nq_dev, int64_t nq_off)
 {
     (void)n;
     if (k < 1 || k > 256) return cudaErrorInvalidValue;
     if (precision == VT_FP64)
-        return launch_knn_t<double>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, k, nbr, (double*)d2, st,
+        return launch_knn_t<double>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, (double*)d2, st,
                                     s);
-    return launch_knn_t<float>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, k, nbr, (float*)d2, st, s);
+    return launch_knn_t<float>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, (float*)d2, st,
+                               s);
 }
 
 }  // namespace vt

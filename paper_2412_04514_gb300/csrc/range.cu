@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
                                                        const GridDesc* __restrict__ sets,
                                                        const int32_t* __restrict__ set_of,
                                                        const int32_t* __restrict__ queries, int64_t nq_host,
-                                                       const int32_t* __restrict__ nq_dev,
+                                                       const int32_t* __restrict__ nq_dev, int64_t nq_off,
                                                        const uint8_t* __restrict__ state, size_t state_stride,
                                                        int cap, int32_t* __restrict__ rnbr, Real* __restrict__ rd2,
                                                        int32_t* __restrict__ rlen, int32_t* __restrict__ over_list,
@@ -58,10 +58,9 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t nq = nq_host;
-    if (nq_dev) {
-        const int64_t want = *nq_dev;
-        if (want > nq_host && threadIdx.x == 0 && blockIdx.x == 0) atomicExch((int*)&st->list_overflow, 1);
-        nq = want < nq_host ? want : nq_host;
+    if (nq_dev) {  // device-counted: list entries [nq_off, nq_off + nq_host)
+        const int64_t want = (int64_t)*nq_dev - nq_off;
+        nq = want < 0 ? 0 : (want < nq_host ? want : nq_host);
     }
     for (int64_t c = wid; c < nq; c += nw) {
         const int q = queries[c];
@@ -180,11 +179,11 @@ cudaError_t launch_range(const RangeArgs& a, cudaStream_t s)
     const size_t smem = range_smem_bytes(a.precision);
     if (a.precision == VT_FP64)
         k_range<double><<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(
-            a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.state, a.state_stride,
+            a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.nq_off, a.state, a.state_stride,
             RANGE_CAP, a.rnbr, (double*)a.rd2, a.rlen, a.over_list, a.over_ctr, a.st);
     else
         k_range<float><<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(
-            a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.state, a.state_stride,
+            a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.nq_off, a.state, a.state_stride,
             RANGE_CAP, a.rnbr, (float*)a.rd2, a.rlen, a.over_list, a.over_ctr, a.st);
     count_launch();
     return cudaGetLastError();

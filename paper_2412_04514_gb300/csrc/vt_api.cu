@@ -164,6 +164,7 @@ namespace vt_host {
 // list length of the robust variant's exhaustive pass (nearest first, then the walk)
 constexpr int ROBUST_EXH_K = 128;
 
+
 // CUDA-event timing of kernel groups on the call's stream (VT_FLAG_STAGE_TIMES)
 struct StageTimer {
     enum { GRID = 0, KNN = 1, CLIP = 2, EMIT = 3 };
@@ -322,22 +323,23 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
         if (c.clip_launches) ++*c.clip_launches;
         return e == cudaSuccess ? VT_OK : cuda_fail(e, "clip launch");
     }
+    // chunks of the list buffer; a device-counted pass runs the same chunks
+    // as launches that each clamp to the count they find (empty ones exit)
     const int64_t chunk = L.knn_cap / k;
-    // a device-counted pass runs as one launch over at most `chunk` cells
-    const int64_t mm = (m_dev && m > chunk) ? chunk : m;
-    for (int64_t o = 0; o < mm; o += chunk) {
-        const int64_t cnt = (mm - o) < chunk ? (mm - o) : chunk;
+    for (int64_t o = 0; o < m; o += chunk) {
+        const int64_t cnt = (m - o) < chunk ? (m - o) : chunk;
         const int32_t* q = list ? list + o : nullptr;
         if (!list && o > 0) return fail(VT_ERR_INVALID_ARG, "internal: implicit list needs one chunk");
         T.begin(StageTimer::KNN);
         cudaError_t e = launch_knn(a.sorted, a.cell_off, c.g, L.n, q, cnt, k, knn_prec, c.at<int32_t>(L.knn_nbr),
-                                   c.at<void>(L.knn_d2), c.st, c.s, c.sets, c.set_of(), m_dev);
+                                   c.at<void>(L.knn_d2), c.st, c.s, c.sets, c.set_of(), m_dev, o);
         T.end();
         if (c.knn_launches) ++*c.knn_launches;
         if (e != cudaSuccess) return cuda_fail(e, "knn launch");
         a.queries = q;
         a.nq = cnt;
         a.nq_cap = cnt;
+        a.nq_off = o;
         a.nbr = c.at<int32_t>(L.knn_nbr);
         a.d2 = c.at<void>(L.knn_d2);
         T.begin(StageTimer::CLIP);
@@ -363,9 +365,8 @@ int range_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m,
     cudaError_t e = cudaMemsetAsync(over_ctr, 0, sizeof(int32_t), c.s);
     if (e != cudaSuccess) return cuda_fail(e, "counter reset");
     const int64_t chunk = L.knn_cap / RANGE_CAP;
-    const int64_t mm = (m_dev && m > chunk) ? chunk : m;
-    for (int64_t o = 0; o < mm; o += chunk) {
-        const int64_t cnt = (mm - o) < chunk ? (mm - o) : chunk;
+    for (int64_t o = 0; o < m; o += chunk) {
+        const int64_t cnt = (m - o) < chunk ? (m - o) : chunk;
         RangeArgs r{};
         r.sorted = c.at<float4>(L.sorted);
         r.cell_off = c.at<int32_t>(L.cell_off);
@@ -375,6 +376,7 @@ int range_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m,
         r.queries = list + o;
         r.nq = cnt;
         r.nq_dev = m_dev;
+        r.nq_off = o;
         r.state = c.at<uint8_t>(L.state);
         r.state_stride = L.state_stride;
         r.precision = p->precision;
@@ -400,6 +402,7 @@ int range_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m,
         a.queries = r.queries;
         a.nq = cnt;
         a.nq_cap = cnt;
+        a.nq_off = o;
         a.nbr = r.rnbr;
         a.d2 = r.rd2;
         a.k = RANGE_CAP;
@@ -436,9 +439,6 @@ int status_errors(const DevStatus& h)
     if (h.bad_point)
         return fail(VT_ERR_INVALID_ARG, "point %d is not finite or not inside [box_lo, box_hi)", h.bad_point - 1);
     if (h.duplicate) return fail(VT_ERR_DUPLICATE_POINTS, "two generators coincide");
-    if (h.list_overflow)
-        return fail(VT_ERR_WORKSPACE, "more cells needed the robust list pass than the no-sync list buffer holds; "
-                                      "use the synchronising schedule");
     return VT_OK;
 }
 

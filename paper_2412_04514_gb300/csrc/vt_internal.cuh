@@ -210,7 +210,7 @@ struct DevStatus {
     unsigned long long precision_events;
     long long totals[4];      // nbr, vtx, face, face_vtx totals written by the emit scan
     unsigned int detail[8];   // clip events: 0 keep-none, 1 plane cap, 2 vertex cap, 3 ring, 4 interpolated
-    int32_t list_overflow;    // a device-counted pass had more cells than its list buffers hold
+    int32_t reserved0;
     int32_t n_range_over;     // cells of the last pass with more candidates than a range list holds
 };
 static_assert(sizeof(DevStatus) % 64 == 0, "status block must stay 64-byte sized");
@@ -223,9 +223,10 @@ struct RangeArgs {
     GridDesc g;
     const GridDesc* sets;
     const int32_t* set_of;
-    const int32_t* queries;  // sorted indices of the cells (saved states)
+    const int32_t* queries;  // sorted indices of the cells (saved states), from entry nq_off
     int64_t nq;              // cells (the bound when nq_dev is set)
     const int32_t* nq_dev;
+    int64_t nq_off;
     const uint8_t* state;
     size_t state_stride;
     int precision;           // key precision: VT_FP64 or VT_FP32_RECHECK
@@ -309,12 +310,12 @@ cudaError_t launch_grid_build(const float* pts, int64_t n, const GridDesc& g, fl
 cudaError_t launch_pair_counts(const int32_t* cell_off, int64_t g3, const GridDesc* sets, int nsets,
                                unsigned long long* acc, cudaStream_t s);
 
-// nq_dev: the query count is read from device memory, clamped to nq (more sets
-// st->list_overflow)
+// nq_dev: the query count is read from device memory; the launch takes list
+// entries [nq_off, nq_off + nq) (queries already points at entry nq_off)
 cudaError_t launch_knn(const float4* sorted, const int32_t* cell_off, const GridDesc& g, int64_t n,
                        const int32_t* queries, int64_t nq, int k, int precision, int32_t* nbr, void* d2,
                        DevStatus* st, cudaStream_t s, const GridDesc* sets = nullptr, const int32_t* set_of = nullptr,
-                       const int32_t* nq_dev = nullptr);
+                       const int32_t* nq_dev = nullptr, int64_t nq_off = 0);
 
 struct ClipArgs {
     const float4* sorted;
@@ -345,8 +346,8 @@ struct ClipArgs {
     const GridDesc* sets;     // per-set grids of a batch (NULL: the single grid g)
     const int32_t* set_of;    // set of each sorted point (batches)
     const int32_t* nq_dev;    // when set, the cell count is read from device memory
-    int64_t nq_cap;           // with nq_dev: at most this many cells fit the list buffers (more sets
-                              // DevStatus::list_overflow and the rest is not processed)
+    int64_t nq_cap;           // with nq_dev: at most this many cells per launch (the list buffers)
+    int64_t nq_off;           // with nq_dev: this launch takes list entries [nq_off, nq_off + nq_cap)
     int k_prev;               // > 0: resume saved cells; list entries [0, k_prev) are done
     uint8_t* state;           // per-cell saved polyhedra (sorted index * state_stride), or NULL
     size_t state_stride;
