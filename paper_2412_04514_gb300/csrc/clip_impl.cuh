@@ -1189,8 +1189,9 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
             // neighbour list, nearest first, from the first unprocessed entry;
             // each lane holds one entry of the current chunk of T and prefetches
             // its entry of the next chunk
-            const int32_t* nb = A.nbr + c * (int64_t)k;
-            const Real* dd = reinterpret_cast<const Real*>(A.d2) + c * (int64_t)k;
+            const int64_t li = (A.by_cell ? (int64_t)q : c) * (A.kstride ? A.kstride : k);
+            const int32_t* nb = A.nbr + li;
+            const Real* dd = reinterpret_cast<const Real*>(A.d2) + li;
             const int m0 = (resume && !A.restore) ? A.k_prev : 0;
             int nj = m0 + G.gl < kc ? nb[m0 + G.gl] : -1;
             Real nd = m0 + G.gl < kc ? dd[m0 + G.gl] : (Real)0;

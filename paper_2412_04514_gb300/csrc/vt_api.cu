@@ -115,10 +115,17 @@ Layout make_layout(const vt_params* p, int64_t n, int64_t cells, bool batch)
     // runs each pass in one launch, so its buffer holds n * max(k_max, the
     // range-list capacity) entries
     const bool nosync = (p->flags & VT_FLAG_NO_SYNC) != 0;
+    // the first pass computes the second pass's list too when k doubles
+    // within k_max (2 k0 entries per cell, all cells at once)
     const int kmx = p->k_max > RANGE_CAP ? p->k_max : RANGE_CAP;
-    int64_t cap = nn * (int64_t)(nosync ? kmx : p->k0);
+    const int kpre = 2 * p->k0 <= p->k_max ? 2 * p->k0 : p->k0;
+    int64_t cap = nn * (int64_t)(nosync ? (kmx > kpre ? kmx : kpre) : kpre);
     if (cap < (int64_t)p->k_max * 64) cap = (int64_t)p->k_max * 64;
     L.knn_cap = cap;
+    // the robust variant's lists have their own buffer (the regular lists of
+    // the first pass stay in place for the second): n / 8 cells of 128
+    int64_t rc = nn / 8 > 65536 ? nn / 8 : 65536;
+    L.rob_cap = rc * 128;
     const bool recs = (p->emit & (VT_EMIT_NBR | VT_EMIT_GEOM)) != 0;
     L.rec_stride = !recs ? 0 : ((p->emit & VT_EMIT_GEOM) ? REC_STRIDE_GEOM : REC_STRIDE_NBR);
     size_t off = 0;
@@ -148,6 +155,8 @@ Layout make_layout(const vt_params* p, int64_t n, int64_t cells, bool batch)
     L.scan_tmp = take(st1 > st2 ? st1 : st2);
     L.knn_nbr = take(sizeof(int32_t) * L.knn_cap);
     L.knn_d2 = take(sizeof(double) * L.knn_cap);
+    L.rob_nbr = take(sizeof(int32_t) * L.rob_cap);
+    L.rob_d2 = take(sizeof(double) * L.rob_cap);
     L.set_of = batch ? take(sizeof(int32_t) * nn) : 0;
     L.ctr = take(sizeof(int32_t) * (3 * VT_MAX_PASSES + 8));
     L.rlen = take(sizeof(int32_t) * nn);
@@ -282,7 +291,7 @@ __global__ void k_iota(int32_t* a, int64_t n)
 // the given lists and counters.
 int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, const int32_t* m_dev, int k,
               bool exhaustive, int k_prev, int variant, int knn_prec, vt_cells_out* out, int32_t* fail_next,
-              int32_t* ctr_next, int32_t* fail_robust, int32_t* ctr_robust)
+              int32_t* ctr_next, int32_t* fail_robust, int32_t* ctr_robust, int k_list = 0, bool reuse = false)
 {
     const Layout& L = c.L;
     ClipArgs a{};
@@ -323,27 +332,38 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
         if (c.clip_launches) ++*c.clip_launches;
         return e == cudaSuccess ? VT_OK : cuda_fail(e, "clip launch");
     }
+    // k_list > k: the kNN computes k_list entries per cell (the next pass's
+    // list too) and the clipper uses the first k; reuse: the lists of all
+    // cells are already in the buffer, indexed by sorted cell index
+    const int kl = k_list > k ? k_list : k;
+    a.kstride = kl;
+    a.by_cell = reuse ? 1 : 0;
+    const bool rob = variant == 2;  // the robust variant's lists have their own buffer
+    int32_t* lnbr = c.at<int32_t>(rob ? L.rob_nbr : L.knn_nbr);
+    void* ld2 = c.at<void>(rob ? L.rob_d2 : L.knn_d2);
     // chunks of the list buffer; a device-counted pass runs the same chunks
     // as launches that each clamp to the count they find (empty ones exit)
-    const int64_t chunk = L.knn_cap / k;
+    const int64_t chunk = reuse ? (m > 0 ? m : 1) : (rob ? L.rob_cap : L.knn_cap) / kl;
     for (int64_t o = 0; o < m; o += chunk) {
         const int64_t cnt = (m - o) < chunk ? (m - o) : chunk;
         const int32_t* q = list ? list + o : nullptr;
         if (!list && o > 0) return fail(VT_ERR_INVALID_ARG, "internal: implicit list needs one chunk");
-        T.begin(StageTimer::KNN);
-        cudaError_t e = launch_knn(a.sorted, a.cell_off, c.g, L.n, q, cnt, k, knn_prec, c.at<int32_t>(L.knn_nbr),
-                                   c.at<void>(L.knn_d2), c.st, c.s, c.sets, c.set_of(), m_dev, o);
-        T.end();
-        if (c.knn_launches) ++*c.knn_launches;
-        if (e != cudaSuccess) return cuda_fail(e, "knn launch");
+        if (!reuse) {
+            T.begin(StageTimer::KNN);
+            cudaError_t e = launch_knn(a.sorted, a.cell_off, c.g, L.n, q, cnt, kl, knn_prec, lnbr, ld2, c.st, c.s,
+                                       c.sets, c.set_of(), m_dev, o);
+            T.end();
+            if (c.knn_launches) ++*c.knn_launches;
+            if (e != cudaSuccess) return cuda_fail(e, "knn launch");
+        }
         a.queries = q;
         a.nq = cnt;
         a.nq_cap = cnt;
         a.nq_off = o;
-        a.nbr = c.at<int32_t>(L.knn_nbr);
-        a.d2 = c.at<void>(L.knn_d2);
+        a.nbr = lnbr;
+        a.d2 = ld2;
         T.begin(StageTimer::CLIP);
-        e = launch_clip(a, variant, tpc, c.s);
+        cudaError_t e = launch_clip(a, variant, tpc, c.s);
         T.end();
         if (c.clip_launches) ++*c.clip_launches;
         if (e != cudaSuccess) return cuda_fail(e, "clip launch");
@@ -591,12 +611,16 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
             int32_t* bn = last ? unval : robl[(pi + 1) % 2];
             int32_t* bc = last ? &c.st->n_unval : &ctr_rob[pi];
             const int kr = last ? ROBUST_EXH_K : kk;  // the robust variant's list
+            // pass 0 computes pass 1's list too when it is a list pass of 2 k0;
+            // pass 1 then clips from those lists (indexed by cell)
+            const int k_list = (pi == 0 && np_ > 1 && ks[1] == 2 * kk) ? ks[1] : 0;
+            const bool reuse = pi == 1 && ks[0] > 0 && kk == 2 * ks[0];
             if (last && pi > 0)
                 r = range_pass(c, p, q, n, qn, k_prev, variant_reg, out, regl[(pi + 1) % 2], &ctr_reg[pi], rob_new,
                                &ctr_new[pi], unval, &c.st->n_unval);
             else
                 r = clip_pass(c, p, q, n, qn, kk, last, k_prev, variant_reg, p->precision, out, rn, rc, rob_new,
-                              &ctr_new[pi]);
+                              &ctr_new[pi], k_list, reuse);
             if (r) return r;
             r = clip_pass(c, p, rob_new, n, &ctr_new[pi], kr, last, 0, 2, VT_FP64, out, bn, bc, unval,
                           &c.st->n_unval);
@@ -618,6 +642,7 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
     bool implicit = true;  // the first pass runs over all cells without a list
     int k = p->k0;
     int k_prev = 0;  // regular cells resume from their saved state after list entry k_prev
+    int prefetched = 0;  // the list length the previous pass left for every cell
     while (m_reg + m_rob > 0) {
         const bool exhaustive = k > p->k_max;
         const int kk = exhaustive ? 0 : k;
@@ -640,9 +665,16 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
             if (exhaustive && k_prev > 0 && !implicit)
                 r = range_pass(c, p, reg_cur, m_reg, nullptr, k_prev, variant_reg, out, reg_nxt, &c.st->n_range_over,
                                rob_new, &c.st->n_fail_robust, unval + n_unval, &c.st->n_fail_next);
-            else
+            else {
+                // the first pass computes the second's list too when k doubles
+                // within k_max and every cell's lists fit at once
+                const int k_list = implicit && 2 * kk <= p->k_max && (int64_t)2 * kk * m_reg <= L.knn_cap ? 2 * kk : 0;
+                const bool reuse = !implicit && prefetched == kk;
                 r = clip_pass(c, p, implicit ? nullptr : reg_cur, m_reg, nullptr, kk, exhaustive, k_prev, variant_reg,
-                              p->precision, out, reg_nxt, &c.st->n_fail_next, rob_new, &c.st->n_fail_robust);
+                              p->precision, out, reg_nxt, &c.st->n_fail_next, rob_new, &c.st->n_fail_robust, k_list,
+                              reuse);
+                prefetched = k_list;
+            }
             if (r) return r;
             if ((r = read_status(c, h))) return r;
             if ((r = status_errors(h))) return r;

@@ -270,10 +270,12 @@ struct Layout {
     int G;
     int64_t n, g3;
     int64_t knn_cap;            // entries of the neighbour-list buffer
+    int64_t rob_cap;            // entries of the robust variant's list buffer
     size_t rec_stride;
     size_t status, cid, ticket, counts, cell_off, big, scan_tmp, sorted, perm;
     size_t state_stride;
-    size_t list_a, list_b, list_r, knn_nbr, knn_d2, rec, cnt, off64, scan_emit, state, set_of, ctr, rlen;
+    size_t list_a, list_b, list_r, knn_nbr, knn_d2, rob_nbr, rob_d2, rec, cnt, off64, scan_emit, state, set_of, ctr,
+        rlen;
     size_t total;
 };
 // cells < 0: the single-set grid of p; otherwise the total grid cells of a batch
@@ -329,6 +331,8 @@ struct ClipArgs {
     int k;                    // list entries per cell (0 = no list; the stride of nbr/d2)
     int exhaustive;           // 1: after the list (or the resumed state), walk every generator within 2R
     const int32_t* klen;      // per-cell list lengths (<= k), or NULL (every list has k entries)
+    int kstride;              // entries per cell in nbr / d2 (0: k)
+    int by_cell;              // 1: lists are indexed by the cell's sorted index, not its position
     int complete;             // 1: the lists hold every generator that can still cut (range lists)
     int restore;              // 1: resume the saved state and start at list entry 0
     int emit;
