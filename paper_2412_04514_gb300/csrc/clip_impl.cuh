@@ -1159,7 +1159,10 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
     cell.stamp = 0;
 
     for (int64_t c = gid; c < nq; c += ngroups) {
-        const int kc = A.klen ? A.klen[c] : k;  // this cell's list length
+        // this cell's list length; with k_next the doubled list follows at once:
+        // validation is tested before every entry, so a cell that the first k
+        // entries validate stops at entry k exactly as a re-queue would
+        const int kc = A.klen ? A.klen[c] : (A.k_next > k ? A.k_next : k);
         if (kc < 0) continue;                    // no list: the cell is handled elsewhere
         const int q = A.queries ? A.queries[c] : (int)c;
         const GridDesc& grid = grid_of(A.g, A.sets, A.set_of, q);
@@ -1215,6 +1218,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_
                            cell.reaches(sm, cp.x - cell.pi.x, cp.y - cell.pi.y, cp.z - cell.pi.z);
                 for (unsigned todo = G.ballot(want); todo; todo &= todo - 1u) {
                     const int t = __ffs(todo) - 1;
+                    if (A.k_next > k && base + t == k && G.gl == 0) atomicAdd((int*)&A.st->n_second, 1);
                     const int j = G.bcast(cj, t);
                     if (j < 0) { end = END_VALID; stop = true; break; }  // the list holds every other generator
                     const Real dj = G.bcast(cd, t);

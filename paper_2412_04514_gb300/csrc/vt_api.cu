@@ -291,7 +291,8 @@ __global__ void k_iota(int32_t* a, int64_t n)
 // the given lists and counters.
 int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, const int32_t* m_dev, int k,
               bool exhaustive, int k_prev, int variant, int knn_prec, vt_cells_out* out, int32_t* fail_next,
-              int32_t* ctr_next, int32_t* fail_robust, int32_t* ctr_robust, int k_list = 0, bool reuse = false)
+              int32_t* ctr_next, int32_t* fail_robust, int32_t* ctr_robust, int k_list = 0, bool reuse = false,
+              int k_next = 0)
 {
     const Layout& L = c.L;
     ClipArgs a{};
@@ -337,6 +338,7 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
     // cells are already in the buffer, indexed by sorted cell index
     const int kl = k_list > k ? k_list : k;
     a.kstride = kl;
+    a.k_next = k_next > k && k_next <= kl ? k_next : 0;
     a.by_cell = reuse ? 1 : 0;
     const bool rob = variant == 2;  // the robust variant's lists have their own buffer
     int32_t* lnbr = c.at<int32_t>(rob ? L.rob_nbr : L.knn_nbr);
@@ -592,15 +594,21 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
         int32_t* ctr_rob = ctr_new + VT_MAX_PASSES;
         int32_t* regl[2] = {reg_cur, reg_nxt};
         int32_t* robl[2] = {rob_cur, rob_nxt};
+        // the first two list passes (k0 and 2 k0) run as one launch over the
+        // 2 k0 list when 2 k0 <= k_max (same cells as a re-queue: validation
+        // is tested before every entry)
         int ks[VT_MAX_PASSES];
         int np_ = 0;
-        for (int k = p->k0; k <= p->k_max && np_ < VT_MAX_PASSES - 1; k *= 2) ks[np_++] = k;
+        const bool merge = 2 * p->k0 <= p->k_max;
+        for (int k = merge ? 2 * p->k0 : p->k0; k <= p->k_max && np_ < VT_MAX_PASSES - 1; k *= 2) ks[np_++] = k;
         ks[np_++] = 0;
         int k_prev = 0;
+        int lp = 0;  // logical pass (stats)
+        if (merge) S.k_of_pass[lp++] = p->k0;
         for (int pi = 0; pi < np_; ++pi) {
             const int kk = ks[pi];
-            if (pi < VT_MAX_PASSES) S.k_of_pass[pi] = kk;
-            ++S.passes;
+            if (lp < VT_MAX_PASSES) S.k_of_pass[lp] = kk;
+            ++lp;
             const int32_t* q = pi == 0 ? nullptr : regl[pi % 2];
             const int32_t* qn = pi == 0 ? nullptr : &ctr_reg[pi - 1];
             // the exhaustive pass always concludes; anything it still hands on
@@ -611,16 +619,13 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
             int32_t* bn = last ? unval : robl[(pi + 1) % 2];
             int32_t* bc = last ? &c.st->n_unval : &ctr_rob[pi];
             const int kr = last ? ROBUST_EXH_K : kk;  // the robust variant's list
-            // pass 0 computes pass 1's list too when it is a list pass of 2 k0;
-            // pass 1 then clips from those lists (indexed by cell)
-            const int k_list = (pi == 0 && np_ > 1 && ks[1] == 2 * kk) ? ks[1] : 0;
-            const bool reuse = pi == 1 && ks[0] > 0 && kk == 2 * ks[0];
+            const bool merged = merge && pi == 0;
             if (last && pi > 0)
                 r = range_pass(c, p, q, n, qn, k_prev, variant_reg, out, regl[(pi + 1) % 2], &ctr_reg[pi], rob_new,
                                &ctr_new[pi], unval, &c.st->n_unval);
             else
-                r = clip_pass(c, p, q, n, qn, kk, last, k_prev, variant_reg, p->precision, out, rn, rc, rob_new,
-                              &ctr_new[pi], k_list, reuse);
+                r = clip_pass(c, p, q, n, qn, merged ? p->k0 : kk, last, k_prev, variant_reg, p->precision, out, rn,
+                              rc, rob_new, &ctr_new[pi], merged ? kk : 0, false, merged ? kk : 0);
             if (r) return r;
             r = clip_pass(c, p, rob_new, n, &ctr_new[pi], kr, last, 0, 2, VT_FP64, out, bn, bc, unval,
                           &c.st->n_unval);
@@ -632,6 +637,7 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
             }
             if (kk) k_prev = kk;
         }
+        S.passes = lp;
         r = emit_outputs(c, p, out);
         S.launches = (int)(launches() - l0);
         if (stats) *stats = S;
@@ -642,10 +648,11 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
     bool implicit = true;  // the first pass runs over all cells without a list
     int k = p->k0;
     int k_prev = 0;  // regular cells resume from their saved state after list entry k_prev
-    int prefetched = 0;  // the list length the previous pass left for every cell
+
     while (m_reg + m_rob > 0) {
         const bool exhaustive = k > p->k_max;
         const int kk = exhaustive ? 0 : k;
+        const bool merged = implicit && !exhaustive && 2 * k <= p->k_max && (int64_t)2 * k * m_reg <= L.knn_cap;
         if (S.passes < VT_MAX_PASSES) {
             S.k_of_pass[S.passes] = kk;
             S.cells_of_pass[S.passes] = m_reg + m_rob;
@@ -665,16 +672,14 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
             if (exhaustive && k_prev > 0 && !implicit)
                 r = range_pass(c, p, reg_cur, m_reg, nullptr, k_prev, variant_reg, out, reg_nxt, &c.st->n_range_over,
                                rob_new, &c.st->n_fail_robust, unval + n_unval, &c.st->n_fail_next);
-            else {
-                // the first pass computes the second's list too when k doubles
-                // within k_max and every cell's lists fit at once
-                const int k_list = implicit && 2 * kk <= p->k_max && (int64_t)2 * kk * m_reg <= L.knn_cap ? 2 * kk : 0;
-                const bool reuse = !implicit && prefetched == kk;
+            else
+                // the first two list passes (k and 2 k) run as one launch over
+                // the 2 k list when 2 k <= k_max: a cell the first k entries
+                // leave open continues at entry k (validation is tested before
+                // every entry, so the cells are those of a re-queue)
                 r = clip_pass(c, p, implicit ? nullptr : reg_cur, m_reg, nullptr, kk, exhaustive, k_prev, variant_reg,
-                              p->precision, out, reg_nxt, &c.st->n_fail_next, rob_new, &c.st->n_fail_robust, k_list,
-                              reuse);
-                prefetched = k_list;
-            }
+                              p->precision, out, reg_nxt, &c.st->n_fail_next, rob_new, &c.st->n_fail_robust,
+                              merged ? 2 * kk : 0, false, merged ? 2 * kk : 0);
             if (r) return r;
             if ((r = read_status(c, h))) return r;
             if ((r = status_errors(h))) return r;
@@ -690,8 +695,9 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
         int64_t rob_next = 0;
         if (m_rob > 0) {
             if ((r = zero_counters(c))) return r;
-            r = clip_pass(c, p, rob_cur, m_rob, nullptr, exhaustive ? ROBUST_EXH_K : kk, exhaustive, 0, 2, VT_FP64,
-                          out, rob_nxt, &c.st->n_fail_next, unval + n_unval, &c.st->n_fail_robust);
+            r = clip_pass(c, p, rob_cur, m_rob, nullptr, exhaustive ? ROBUST_EXH_K : (merged ? 2 * kk : kk),
+                          exhaustive, 0, 2, VT_FP64, out, rob_nxt, &c.st->n_fail_next, unval + n_unval,
+                          &c.st->n_fail_robust);
             if (r) return r;
             if ((r = read_status(c, h))) return r;
             if ((r = status_errors(h))) return r;
@@ -705,6 +711,14 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
         if (exhaustive) {
             n_unval += m_reg + m_rob;  // cannot happen: the exhaustive pass always concludes
             break;
+        }
+        if (merged) {  // the second list pass ran inside this one
+            if (S.passes < VT_MAX_PASSES) {
+                S.k_of_pass[S.passes] = 2 * k;
+                S.cells_of_pass[S.passes] = h.n_second;
+            }
+            ++S.passes;
+            k *= 2;
         }
         k_prev = k;
         k *= 2;

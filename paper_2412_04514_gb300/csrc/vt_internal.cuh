@@ -210,7 +210,7 @@ struct DevStatus {
     unsigned long long precision_events;
     long long totals[4];      // nbr, vtx, face, face_vtx totals written by the emit scan
     unsigned int detail[8];   // clip events: 0 keep-none, 1 plane cap, 2 vertex cap, 3 ring, 4 interpolated
-    int32_t reserved0;
+    int32_t n_second;         // cells of a merged first pass still open at entry k (stats)
     int32_t n_range_over;     // cells of the last pass with more candidates than a range list holds
 };
 static_assert(sizeof(DevStatus) % 64 == 0, "status block must stay 64-byte sized");
@@ -332,6 +332,8 @@ struct ClipArgs {
     int exhaustive;           // 1: after the list (or the resumed state), walk every generator within 2R
     const int32_t* klen;      // per-cell list lengths (<= k), or NULL (every list has k entries)
     int kstride;              // entries per cell in nbr / d2 (0: k)
+    int k_next;               // > k: a cell the first k entries leave open continues with
+                              // entries [k, k_next) in the same launch (the doubled list)
     int by_cell;              // 1: lists are indexed by the cell's sorted index, not its position
     int complete;             // 1: the lists hold every generator that can still cut (range lists)
     int restore;              // 1: resume the saved state and start at list entry 0
