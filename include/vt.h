@@ -406,10 +406,13 @@ VT_API int vt_autotune_batch(const float* pts, const int64_t* set_off_host, cons
  * face_vtx_off, face_vtx) of a vt_tessellate call on pts with
  * VT_EMIT_VOL|VT_EMIT_CEN|VT_EMIT_GEOM and VT_INDEX_ORIGINAL.
  * gV[n], gC[n*3], gM[n]: upstream gradients, each may be NULL (zero).
+ * precision: VT_FP64 integrates the faces in FP64; VT_FP32_RECHECK in
+ * float32 in each generator's frame (for cells of the FP32 form, whose
+ * vertices carry float32 round-off anyway; the per-generator sums stay FP64).
  * grad[n*3] (FP64) is overwritten. Deterministic: each generator's gradient
  * is summed by one warp in a fixed order. Asynchronous on `stream`. */
 VT_API int vt_moments_adjoint(const float* pts, int64_t n, const vt_cells_out* cells, const double* gV,
-                              const double* gC, const double* gM, double* grad, void* stream);
+                              const double* gC, const double* gM, int precision, double* grad, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* diagnostics                                                         */

@@ -240,7 +240,7 @@ def load() -> ctypes.CDLL:
         L.vt_version.restype = ctypes.c_char_p
         L.vt_grid_build_static.argtypes = [P, I64, pp, I, P, P, P, P]
         L.vt_grid_build_static.restype = I
-        L.vt_moments_adjoint.argtypes = [P, I64, po, P, P, P, P, P]
+        L.vt_moments_adjoint.argtypes = [P, I64, po, P, P, P, I, P, P]
         L.vt_moments_adjoint.restype = I
         ps = ctypes.POINTER(VtStats)
         L.vt_batch_plan.argtypes = [P, I, pp, P, P, ctypes.POINTER(I64)]

@@ -506,11 +506,14 @@ def version() -> str:
 # ---------------------------------------------------------------------------
 
 def moments_adjoint(points: torch.Tensor, cells: Cells, gV: torch.Tensor | None = None,
-                    gC: torch.Tensor | None = None, gM: torch.Tensor | None = None) -> torch.Tensor:
+                    gC: torch.Tensor | None = None, gM: torch.Tensor | None = None,
+                    precision: str = "fp64") -> torch.Tensor:
     """d(sum gV.V + gC.c + gM.M2)/d(points) as float64 [n, 3] (vt_moments_adjoint).
 
     ``cells`` must come from :func:`tessellate` on ``points`` with emit
-    including vol, cen and geom in the original index space."""
+    including vol, cen and geom in the original index space. ``precision``
+    ("fp64" or "fp32") is that of the face integrals: "fp32" for cells of the
+    FP32 form."""
     pts = _check_points(points)
     n = pts.shape[0]
     dev = pts.device
@@ -521,8 +524,8 @@ def moments_adjoint(points: torch.Tensor, cells: Cells, gV: torch.Tensor | None 
         return None if t is None else t.to(device=dev, dtype=torch.float64).contiguous()
 
     gV, gC, gM = f64(gV), f64(gC), f64(gM)
-    L.check(L.load().vt_moments_adjoint(_ptr(pts), n, ctypes.byref(o), _ptr(gV), _ptr(gC), _ptr(gM), _ptr(grad),
-                                        _stream(dev)))
+    L.check(L.load().vt_moments_adjoint(_ptr(pts), n, ctypes.byref(o), _ptr(gV), _ptr(gC), _ptr(gM),
+                                        _PREC[precision], _ptr(grad), _stream(dev)))
     return grad[:n]
 
 
@@ -538,13 +541,14 @@ class VoronoiMoments(torch.autograd.Function):
         p = Params(**{**p.__dict__, "emit": ("vol", "cen", "m2", "geom"), "index_space": "original"})
         cells = tessellate(points.detach(), p)
         ctx.cells = cells
+        ctx.precision = p.precision
         ctx.save_for_backward(points)
         return cells.vol, cells.cen, cells.m2
 
     @staticmethod
     def backward(ctx, gV, gC, gM):
         (points,) = ctx.saved_tensors
-        g = moments_adjoint(points.detach(), ctx.cells, gV, gC, gM)
+        g = moments_adjoint(points.detach(), ctx.cells, gV, gC, gM, precision=ctx.precision)
         return g.to(points.dtype), None
 
 

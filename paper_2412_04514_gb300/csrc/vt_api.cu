@@ -920,15 +920,17 @@ int vt_tessellate_batch(const float* pts, int64_t n_total, const vt_set_desc* pl
 }
 
 int vt_moments_adjoint(const float* pts, int64_t n, const vt_cells_out* cells, const double* gV, const double* gC,
-                       const double* gM, double* grad, void* stream)
+                       const double* gM, int precision, double* grad, void* stream)
 {
     if (n < 0) return fail(VT_ERR_INVALID_ARG, "n must be >= 0");
+    if (precision != VT_FP64 && precision != VT_FP32_RECHECK)
+        return fail(VT_ERR_INVALID_ARG, "precision must be VT_FP64 or VT_FP32_RECHECK");
     if (n == 0) return VT_OK;
     if (!pts || !cells || !grad) return fail(VT_ERR_INVALID_ARG, "NULL argument");
     if (!cells->vol || !cells->cen || !cells->vtx_off || !cells->vtx || !cells->face_off || !cells->face_nbr ||
         !cells->face_vtx_off || !cells->face_vtx)
         return fail(VT_ERR_INVALID_ARG, "the adjoint needs vol, cen and the geometry of the tessellation");
-    cudaError_t e = launch_adjoint(pts, n, *cells, gV, gC, gM, grad, (cudaStream_t)stream);
+    cudaError_t e = launch_adjoint(pts, n, *cells, gV, gC, gM, grad, precision, (cudaStream_t)stream);
     return e == cudaSuccess ? VT_OK : cuda_fail(e, "adjoint");
 }
 

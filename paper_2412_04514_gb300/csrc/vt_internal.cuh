@@ -376,6 +376,6 @@ struct EmitArgs {
 cudaError_t launch_emit_count(const EmitArgs& a, cudaStream_t s);  // counts + scans + totals
 cudaError_t launch_emit_write(const EmitArgs& a, const vt_cells_out& out, cudaStream_t s);  // device-checked caps
 cudaError_t launch_adjoint(const float* pts, int64_t n, const vt_cells_out& c, const double* gV, const double* gC,
-                           const double* gM, double* grad, cudaStream_t s);
+                           const double* gM, double* grad, int precision, cudaStream_t s);
 
 }  // namespace vt

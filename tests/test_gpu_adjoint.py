@@ -36,7 +36,7 @@ def test_adjoint_matches_oracle(small, prec, tol):
     p, (gV, gC, gM), want = small
     d = dev(p)
     cells = vt.tessellate(d, vt.Params(precision=prec, emit=EMIT))
-    got = vt.moments_adjoint(d, cells, dev(gV), dev(gC), dev(gM)).cpu().numpy()
+    got = vt.moments_adjoint(d, cells, dev(gV), dev(gC), dev(gM), precision=prec).cpu().numpy()
     scale = np.abs(want).max()
     assert np.abs(got - want).max() <= tol * scale
 
@@ -48,11 +48,11 @@ def test_lloyd_identity_and_conservation_on_the_bench_cloud(prec, tol):
     cells = vt.tessellate(d, vt.Params(precision=prec, emit=EMIT))
     n = len(p)
     ones = torch.ones(n, dtype=torch.float64, device="cuda")
-    g = vt.moments_adjoint(d, cells, gM=ones)
+    g = vt.moments_adjoint(d, cells, gM=ones, precision=prec)
     want = 2 * cells.vol[:, None] * (d.double() - cells.cen)
     scale = want.abs().max()
     assert float((g - want).abs().max()) <= tol * float(scale)
-    g = vt.moments_adjoint(d, cells, gV=ones)  # total volume does not move
+    g = vt.moments_adjoint(d, cells, gV=ones, precision=prec)  # total volume does not move
     assert float(g.abs().max()) <= tol * float(cells.vol.max()) ** (2 / 3)
 
 
