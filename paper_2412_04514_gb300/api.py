@@ -218,10 +218,18 @@ def tessellate_host(points, params: Params | None = None, device="cuda") -> Cell
     d = t.to(device, non_blocking=True)
     cells = tessellate(d, params)
     out = Cells(stats=cells.stats)
+    # device-to-host copies into pinned buffers (torch caches the pinned
+    # allocations across calls), all queued before one synchronisation
     for name in ("vol", "cen", "m2", "nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx_off",
                  "face_vtx", "perm"):
         v = getattr(cells, name)
-        setattr(out, name, None if v is None else v.to("cpu"))
+        if v is None:
+            setattr(out, name, None)
+            continue
+        h = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+        h.copy_(v, non_blocking=True)
+        setattr(out, name, h)
+    torch.cuda.current_stream(d.device).synchronize()
     return out
 
 
