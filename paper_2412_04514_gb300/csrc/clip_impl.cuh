@@ -1130,12 +1130,23 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, 
 // kernels: list mode (k > 0) and exhaustive mode (k == 0)
 // ---------------------------------------------------------------------------
 constexpr int CLIP_BLOCK = 128;
-#ifndef VT_CLIP_MINB
-#define VT_CLIP_MINB 4  // resident blocks per SM the register budget aims for
+// resident blocks per SM the register budget aims for: the FP32 regular
+// variants trade some spills for occupancy (7 blocks: 72 registers, measured
+// fastest on the mixed cloud); FP64 and robust keep 128 registers
+#ifndef VT_CLIP_MINB_F32
+#define VT_CLIP_MINB_F32 7
 #endif
+#ifndef VT_CLIP_MINB_F64
+#define VT_CLIP_MINB_F64 4
+#endif
+template <typename Real, bool ROBUST>
+constexpr int clip_minb()
+{
+    return (sizeof(Real) == 4 && !ROBUST) ? VT_CLIP_MINB_F32 : VT_CLIP_MINB_F64;
+}
 
 template <typename Real, int T, int VPL, int PCAP, bool ROBUST, bool EXH>
-__global__ void __launch_bounds__(CLIP_BLOCK, VT_CLIP_MINB) k_clip(const __grid_constant__ ClipArgs A)
+__global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_clip(const __grid_constant__ ClipArgs A)
 {
     using C = Cell<Real, T, VPL, PCAP>;
     using S = typename C::S;
