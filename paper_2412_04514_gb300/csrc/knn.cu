@@ -101,6 +101,95 @@ struct WarpList {
     }
 };
 
+// The FP64 form's list: entries keep the float32 key f (relative error below
+// 3e-7 of the exact distance) and the exact FP64 key d, computed only when
+// two float32 keys are too close to order (within 2e-6) or at the end (d is
+// NaN until then). Orders are the FP64 keys' (with ties by original index),
+// so the list equals one built from FP64 keys throughout, with far fewer
+// FP64 operations (the part's FP64 rate is 1/64 of float32).
+template <int KPL>
+struct WarpList64 {
+    float f[KPL];
+    double d[KPL];
+    int o[KPL];
+    int j[KPL];
+
+    __device__ void init()
+    {
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+            f[r] = __int_as_float(0x7f800000);
+            d[r] = __longlong_as_double(0x7ff0000000000000ll);
+            o[r] = INT_MAX;
+            j[r] = -1;
+        }
+    }
+
+    // inserts the candidate (float key cf, original index co, sorted index cj)
+    // if it ranks among the first k; warp-uniform call
+    __device__ void insert(float cf, int co, int cj, float4 pq, const float4* __restrict__ sorted, int k, int lane)
+    {
+        const double nanv = __longlong_as_double(0x7ff8000000000000ll);
+        double cd = nanv;  // the candidate's exact key, when needed
+        int p = 0;
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+            bool less = f[r] < cf * (1.0f - 2e-6f);
+            const bool amb = !less && f[r] <= cf * (1.0f + 2e-6f) && o[r] != INT_MAX;
+            if (__any_sync(FULL, amb)) {
+                if (isnan(cd)) cd = knn_d2_f64(pq, sorted[cj]);  // uniform
+                if (amb) {
+                    if (isnan(d[r])) d[r] = knn_d2_f64(pq, sorted[j[r]]);
+                    less = d[r] < cd || (d[r] == cd && o[r] < co);
+                }
+            }
+            p += __popc(__ballot_sync(FULL, less));
+        }
+        if (p >= k) return;
+        float nf[KPL];
+        double nd[KPL];
+        int no[KPL], nj[KPL];
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+            float uf = __shfl_up_sync(FULL, f[r], 1);
+            double ud = __shfl_up_sync(FULL, d[r], 1);
+            int uo = __shfl_up_sync(FULL, o[r], 1);
+            int uj = __shfl_up_sync(FULL, j[r], 1);
+            if (r > 0) {
+                const float wf = __shfl_sync(FULL, f[r - 1], 31);
+                const double wd = __shfl_sync(FULL, d[r - 1], 31);
+                const int wo = __shfl_sync(FULL, o[r - 1], 31), wj = __shfl_sync(FULL, j[r - 1], 31);
+                if (lane == 0) { uf = wf; ud = wd; uo = wo; uj = wj; }
+            }
+            const int e = r * 32 + lane;
+            nf[r] = e > p ? uf : (e == p ? cf : f[r]);
+            nd[r] = e > p ? ud : (e == p ? cd : d[r]);
+            no[r] = e > p ? uo : (e == p ? co : o[r]);
+            nj[r] = e > p ? uj : (e == p ? cj : j[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) { f[r] = nf[r]; d[r] = nd[r]; o[r] = no[r]; j[r] = nj[r]; }
+    }
+
+    // float key of entry e (warp-uniform e)
+    __device__ float key(int e) const
+    {
+        float ff = f[0];
+#pragma unroll
+        for (int r = 1; r < KPL; ++r)
+            if (r == e / 32) ff = f[r];
+        return __shfl_sync(FULL, ff, e % 32);
+    }
+
+    // every entry's exact key
+    __device__ void finish(float4 pq, const float4* __restrict__ sorted)
+    {
+#pragma unroll
+        for (int r = 0; r < KPL; ++r)
+            if (isnan(d[r]) && j[r] >= 0) d[r] = knn_d2_f64(pq, sorted[j[r]]);
+    }
+};
+
 template <typename Real, int KPL>
 __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, const int32_t* __restrict__ cell_off0,
                                              const __grid_constant__ GridDesc g0, const GridDesc* __restrict__ sets,
@@ -126,10 +215,12 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
         const int ix = cell_coord(pq.x, g.lo[0], g.scale[0], G);
         const int iy = cell_coord(pq.y, g.lo[1], g.scale[1], G);
         const int iz = cell_coord(pq.z, g.lo[2], g.scale[2], G);
-        WarpList<Real, KPL> L;
-        L.init();
+        constexpr bool F64 = sizeof(Real) == 8;
+        WarpList<float, KPL> L;    // FP32 form
+        WarpList64<KPL> L64;       // FP64 form
+        if (F64) L64.init(); else L.init();
         int count = 0;
-        Real kd = Dist<Real>::inf();
+        float kd = __int_as_float(0x7f800000);  // float key of the k-th entry once the list is full
         int ko = INT_MAX;
         bool dup = false;
 
@@ -143,8 +234,8 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
                 int sa = 0, sb = 0;
                 if (e0 + lane < nseg) {
                     if (count == k)
-                        shell_segment_ball(e0 + lane, s, ix, iy, iz, g, cell_off, pq, (float)kd * (1.0f + 1e-5f),
-                                           -1.0f, sa, sb);
+                        shell_segment_ball(e0 + lane, s, ix, iy, iz, g, cell_off, pq, kd * (1.0f + 1e-5f), -1.0f, sa,
+                                           sb);
                     else
                         shell_segment(e0 + lane, s, ix, iy, iz, G, cell_off, sa, sb);
                 }
@@ -166,36 +257,34 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
                     const int aj = __shfl_sync(FULL, sa, seg & 31), sj = __shfl_sync(FULL, start, seg & 31);
                     const int jj = aj + (i - sj);
                     const bool valid = i < total && jj != q;
-                    Real cd = Dist<Real>::inf();
+                    float cd = __int_as_float(0x7f800000);
                     int co = INT_MAX;
                     bool cand = false;
                     if (valid) {
                         const float4 pc = sorted[jj];
                         co = __float_as_int(pc.w);
                         if (pc.x == pq.x && pc.y == pq.y && pc.z == pq.z) dup = true;
-                        if (sizeof(Real) == 8) {
-                            // FP64 keys only for candidates whose float32 distance (relative
-                            // error < 1e-6) does not already rule them out: same list, less FP64
-                            const float c32 = knn_d2_f32(pq, pc);
-                            if (count < k || (double)c32 <= (double)kd * (1.0 + 1e-6)) {
-                                cd = Dist<Real>::d2(pq, pc);
-                                cand = count < k || key_less(cd, co, kd, ko);
-                            }
-                        } else {
-                            cd = Dist<Real>::d2(pq, pc);
-                            cand = count < k || key_less(cd, co, kd, ko);
-                        }
+                        cd = knn_d2_f32(pq, pc);
+                        // FP64 form: the float key only rules out candidates clearly
+                        // beyond the k-th entry; insert() orders the close ones exactly
+                        cand = count < k || (F64 ? cd <= kd * (1.0f + 2e-6f) : key_less(cd, co, kd, ko));
                     }
                     unsigned m = __ballot_sync(FULL, cand);
                     while (m) {
                         const int src = __ffs(m) - 1;
                         m &= m - 1;
-                        const Real bd = __shfl_sync(FULL, cd, src);
+                        const float bd = __shfl_sync(FULL, cd, src);
                         const int bo = __shfl_sync(FULL, co, src);
                         const int bj = __shfl_sync(FULL, jj, src);
-                        L.insert(bd, bo, bj, k, lane);
-                        if (count < k) ++count;
-                        if (count == k) L.entry(k - 1, kd, ko);
+                        if (F64) {
+                            L64.insert(bd, bo, bj, pq, sorted, k, lane);
+                            if (count < k) ++count;
+                            if (count == k) kd = L64.key(k - 1);
+                        } else {
+                            L.insert(bd, bo, bj, k, lane);
+                            if (count < k) ++count;
+                            if (count == k) L.entry(k - 1, kd, ko);
+                        }
                     }
                 }
             }
@@ -205,16 +294,17 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
             if (covers) break;
             if (count == k) {
                 const float gap = shell_gap(g, pq, ix, iy, iz, s);
-                if (gap > 0.0f && (float)kd * (1.0f + 1e-6f) <= gap * gap * (1.0f - 1e-5f)) break;
+                if (gap > 0.0f && kd * (1.0f + 2e-6f) <= gap * gap * (1.0f - 1e-5f)) break;
             }
         }
         if (__any_sync(FULL, dup) && lane == 0) atomicExch((int*)&st->duplicate, 1);
+        if (F64) L64.finish(pq, sorted);
 #pragma unroll
         for (int r = 0; r < KPL; ++r) {
             const int e = r * 32 + lane;
             if (e < k) {
-                nbr[c * k + e] = L.j[r];
-                if (d2out) d2out[c * k + e] = L.d[r];
+                nbr[c * k + e] = F64 ? L64.j[r] : L.j[r];
+                if (d2out) d2out[c * k + e] = F64 ? (Real)L64.d[r] : (Real)L.d[r];
             }
         }
     }
