@@ -7,6 +7,7 @@ namespace vt {
 
 cudaError_t launch_clip_f32(const ClipArgs& a, int t, cudaStream_t s);
 cudaError_t launch_clip_f64(const ClipArgs& a, int t, cudaStream_t s);
+cudaError_t launch_clip_big(const ClipArgs& a, cudaStream_t s);
 
 size_t clip_state_bytes(int precision)
 {
@@ -19,6 +20,7 @@ cudaError_t launch_clip(const ClipArgs& a, int variant, int threads_per_cell, cu
     if (a.nq <= 0) return cudaSuccess;
     const int t = threads_per_cell == 0 ? 32 : threads_per_cell;
     if (variant == 2) return launch_variant<double, 32, 4, 128, true>(a, s);
+    if (variant == 3) return launch_clip_big(a, s);
     if (variant == 0) return launch_clip_f32(a, t, s);
     return launch_clip_f64(a, t, s);
 }

@@ -145,7 +145,7 @@ Layout make_layout(const vt_params* p, int64_t n, int64_t cells, bool batch)
     L.ticket = take(sizeof(int32_t) * nn);
     L.sorted = take(sizeof(float4) * nn);
     L.perm = take(sizeof(int32_t) * nn);
-    L.list_a = take(sizeof(int32_t) * nn * 6);  // six cell lists of n entries
+    L.list_a = take(sizeof(int32_t) * nn * 7);  // seven cell lists of n entries
     L.state_stride = clip_state_bytes(p->precision);
     L.state = take(L.state_stride * (size_t)nn);
     L.counts = take(sizeof(int32_t) * (L.g3 + 1));
@@ -158,7 +158,7 @@ Layout make_layout(const vt_params* p, int64_t n, int64_t cells, bool batch)
     L.rob_nbr = take(sizeof(int32_t) * L.rob_cap);
     L.rob_d2 = take(sizeof(double) * L.rob_cap);
     L.set_of = batch ? take(sizeof(int32_t) * nn) : 0;
-    L.ctr = take(sizeof(int32_t) * (3 * VT_MAX_PASSES + 8));
+    L.ctr = take(sizeof(int32_t) * (4 * VT_MAX_PASSES + 8));
     L.rlen = take(sizeof(int32_t) * nn);
     L.total = off;
     return L;
@@ -340,7 +340,7 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
     a.kstride = kl;
     a.k_next = k_next > k && k_next <= kl ? k_next : 0;
     a.by_cell = reuse ? 1 : 0;
-    const bool rob = variant == 2;  // the robust variant's lists have their own buffer
+    const bool rob = variant >= 2;  // the robust variants' lists have their own buffer
     int32_t* lnbr = c.at<int32_t>(rob ? L.rob_nbr : L.knn_nbr);
     void* ld2 = c.at<void>(rob ? L.rob_d2 : L.knn_d2);
     // chunks of the list buffer; a device-counted pass runs the same chunks
@@ -557,7 +557,7 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
     c.clip_launches = &S.clip_launches;
     c.knn_launches = &S.knn_launches;
     cudaError_t ce = cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(c.at<int32_t>(L.ctr), 0, sizeof(int32_t) * (3 * VT_MAX_PASSES + 8), c.s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c.at<int32_t>(L.ctr), 0, sizeof(int32_t) * (4 * VT_MAX_PASSES + 8), c.s);
     if (ce != cudaSuccess) return cuda_fail(ce, "status reset");
     if (n > 0) {
         timer.begin(StageTimer::GRID);
@@ -580,6 +580,13 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
     int32_t* rob_nxt = lists + 3 * n;
     int32_t* rob_new = lists + 4 * n;
     int32_t* unval = lists + 5 * n;
+    // the FP32 form's robust cells run first in FP32 with the robust capacity
+    // (variant 3); what that cannot finish goes to the FP64 robust variant
+    // through this list
+    int32_t* rob64 = lists + 6 * n;
+    const bool fp32 = p->precision != VT_FP64;
+    const int variant_rob = fp32 ? 3 : 2;
+    const int prec_rob = fp32 ? p->precision : VT_FP64;
     const int variant_reg = p->precision == VT_FP64 ? 1 : 0;
     int r = VT_OK;
     DevStatus h{};
@@ -627,11 +634,18 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
                 r = clip_pass(c, p, q, n, qn, merged ? p->k0 : kk, last, k_prev, variant_reg, p->precision, out, rn,
                               rc, rob_new, &ctr_new[pi], merged ? kk : 0, false, merged ? kk : 0);
             if (r) return r;
-            r = clip_pass(c, p, rob_new, n, &ctr_new[pi], kr, last, 0, 2, VT_FP64, out, bn, bc, unval,
-                          &c.st->n_unval);
+            int32_t* ctr64 = ctr_rob + VT_MAX_PASSES;
+            int32_t* fl = fp32 ? rob64 : unval;
+            int32_t* fc = fp32 ? &ctr64[pi] : &c.st->n_unval;
+            r = clip_pass(c, p, rob_new, n, &ctr_new[pi], kr, last, 0, variant_rob, prec_rob, out, bn, bc, fl, fc);
             if (r) return r;
             if (pi > 0) {
-                r = clip_pass(c, p, robl[pi % 2], n, &ctr_rob[pi - 1], kr, last, 0, 2, VT_FP64, out, bn, bc, unval,
+                r = clip_pass(c, p, robl[pi % 2], n, &ctr_rob[pi - 1], kr, last, 0, variant_rob, prec_rob, out, bn, bc,
+                              fl, fc);
+                if (r) return r;
+            }
+            if (fp32) {
+                r = clip_pass(c, p, rob64, n, &ctr64[pi], kr, last, 0, 2, VT_FP64, out, bn, bc, unval,
                               &c.st->n_unval);
                 if (r) return r;
             }
@@ -693,16 +707,28 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
             m_rob += got_rob;
         }
         int64_t rob_next = 0;
+        const int kr = exhaustive ? ROBUST_EXH_K : (merged ? 2 * kk : kk);
         if (m_rob > 0) {
             if ((r = zero_counters(c))) return r;
-            r = clip_pass(c, p, rob_cur, m_rob, nullptr, exhaustive ? ROBUST_EXH_K : (merged ? 2 * kk : kk),
-                          exhaustive, 0, 2, VT_FP64, out, rob_nxt, &c.st->n_fail_next, unval + n_unval,
-                          &c.st->n_fail_robust);
+            r = clip_pass(c, p, rob_cur, m_rob, nullptr, kr, exhaustive, 0, variant_rob, prec_rob, out, rob_nxt,
+                          &c.st->n_fail_next, fp32 ? rob64 : unval + n_unval, &c.st->n_fail_robust);
             if (r) return r;
             if ((r = read_status(c, h))) return r;
             if ((r = status_errors(h))) return r;
             rob_next = h.n_fail_next;
-            n_unval += h.n_fail_robust;
+            const int64_t failed = h.n_fail_robust;
+            if (fp32 && failed > 0) {  // the FP64 robust variant for what FP32 could not finish
+                if ((r = zero_counters(c))) return r;
+                r = clip_pass(c, p, rob64, failed, nullptr, kr, exhaustive, 0, 2, VT_FP64, out, rob_nxt + rob_next,
+                              &c.st->n_fail_next, unval + n_unval, &c.st->n_fail_robust);
+                if (r) return r;
+                if ((r = read_status(c, h))) return r;
+                if ((r = status_errors(h))) return r;
+                rob_next += h.n_fail_next;
+                n_unval += h.n_fail_robust;
+            } else if (!fp32) {
+                n_unval += failed;
+            }
         }
         std::swap(reg_cur, reg_nxt);
         std::swap(rob_cur, rob_nxt);

@@ -359,7 +359,8 @@ struct ClipArgs {
     size_t state_stride;
     DevStatus* st;
 };
-// variant: 0 = FP32 regular, 1 = FP64 regular, 2 = FP64 robust (bigger capacity)
+// variant: 0 = FP32 regular, 1 = FP64 regular, 2 = FP64 robust (bigger capacity),
+// 3 = FP32 with the robust capacity (the FP32 form's first fallback)
 cudaError_t launch_clip(const ClipArgs& a, int variant, int threads_per_cell, cudaStream_t s);
 size_t clip_state_bytes(int precision);  // per-cell state of the regular variant
 

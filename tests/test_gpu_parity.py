@@ -108,6 +108,21 @@ def test_knn_fp64_is_exact(k):
     assert np.array_equal(np_(d2), wd2)
 
 
+@pytest.mark.parametrize("k", [6, 26, 64])
+def test_knn_fp64_exact_with_exact_ties(k):
+    # lattice points: many candidates at exactly equal FP64 distances, so the
+    # list order rests on the FP64 keys and the index tie-break, not on the
+    # float32 keys the kNN orders by first
+    pts = W.bcc_lattice(8)
+    p = vt.Params(precision="fp64")
+    sorted_, perm, off, G, ws = vt.grid_build(dev(pts), p)
+    nbr, d2 = vt.knn(sorted_, off, G, k, p, workspace=ws)
+    perm_ = np_(perm)
+    want, wd2 = oracle.knn(pts, k, queries=perm_)
+    assert np.array_equal(perm_[np_(nbr)], want)
+    assert np.array_equal(np_(d2), wd2)
+
+
 def test_knn_fp64_exact_on_clustered_points_with_query_list():
     pts = W.mixed(50_000, 2, n_clumps=50)
     p = vt.Params(precision="fp64")
