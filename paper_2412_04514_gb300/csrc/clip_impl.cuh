@@ -306,6 +306,7 @@ struct GroupSmem {
             Real area[PCAP];
             int32_t key[PCAP];
             int32_t first[PCAP];  // lowest live slot on the face (a face's walk starts there)
+            int32_t oid[PCAP];    // the output id of the face's neighbour (or its wall id)
             uint8_t deg[PCAP];
         } tail;
     } u;
@@ -934,19 +935,34 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
         sm.u.tail.area[f] = area;
         sm.u.tail.deg[f] = (uint8_t)(deg > 255 ? 255 : deg);
     }
-    double V = (double)vol, MX = (double)mx, MY = (double)my, MZ = (double)mz, M2 = (double)m2;
+    // FP64 sums across the lanes by reduce-scatter: the five sums (padded to
+    // eight slots) are halved between partners at the first three levels, so
+    // a group of 32 lanes adds 9 times instead of 25 (the FP64 pipe is 1/64
+    // of FP32); lane 4 b1 T/8 ... holds slot 4 b1 + 2 b2 + b3 at the end
+    double w;
+    {
+        const double s0[8] = {(double)vol, (double)mx, (double)my, (double)mz, (double)m2, 0.0, 0.0, 0.0};
+        double t4[4], t2[2];
+        const bool hi1 = (gl & (T / 2)) != 0, hi2 = (gl & (T / 4)) != 0, hi3 = (gl & (T / 8)) != 0;
 #pragma unroll
-    for (int o = T / 2; o >= 1; o >>= 1) {
-        V += __shfl_xor_sync(gmask, V, o, T);
-        MX += __shfl_xor_sync(gmask, MX, o, T);
-        MY += __shfl_xor_sync(gmask, MY, o, T);
-        MZ += __shfl_xor_sync(gmask, MZ, o, T);
-        M2 += __shfl_xor_sync(gmask, M2, o, T);
+        for (int i = 0; i < 4; ++i) {
+            const double send = hi1 ? s0[i] : s0[4 + i];
+            t4[i] = (hi1 ? s0[4 + i] : s0[i]) + __shfl_xor_sync(gmask, send, T / 2, T);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const double send = hi2 ? t4[i] : t4[2 + i];
+            t2[i] = (hi2 ? t4[2 + i] : t4[i]) + __shfl_xor_sync(gmask, send, T / 4, T);
+        }
+        w = (hi3 ? t2[1] : t2[0]) + __shfl_xor_sync(gmask, hi3 ? t2[0] : t2[1], T / 8, T);
+#pragma unroll
+        for (int o = T / 16; o >= 1; o >>= 1) w += __shfl_xor_sync(gmask, w, o, T);
     }
-    MX *= 0.25;
-    MY *= 0.25;
-    MZ *= 0.25;
-    M2 *= 0.05;
+    const double V = __shfl_sync(gmask, w, 0, T);
+    const double MX = 0.25 * __shfl_sync(gmask, w, T / 8, T);
+    const double MY = 0.25 * __shfl_sync(gmask, w, T / 4, T);
+    const double MZ = 0.25 * __shfl_sync(gmask, w, T / 4 + T / 8, T);
+    const double M2 = 0.05 * __shfl_sync(gmask, w, T / 2, T);
     __syncwarp(gmask);
     // neighbour keys: planes with a face of area above the threshold (the
     // threshold of the FP32 form in float32: the FP64 pipe is scarce)
@@ -959,10 +975,11 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
     }
     for (int f = gl; f < np; f += T) {
         const int src = sm.psrc[f];
-        int key = INT_MAX;
-        if (src >= 0 && sm.u.tail.first[f] >= 0 && sm.u.tail.area[f] > tau)
-            key = A.index_space == VT_INDEX_ORIGINAL ? __float_as_int(A.sorted[src].w) : src;
-        sm.u.tail.key[f] = key;
+        int oid = src;  // wall ids stay
+        if (src >= 0 && sm.u.tail.first[f] >= 0 && A.index_space == VT_INDEX_ORIGINAL)
+            oid = __float_as_int(A.sorted[src].w);
+        sm.u.tail.oid[f] = oid;
+        sm.u.tail.key[f] = (src >= 0 && sm.u.tail.first[f] >= 0 && sm.u.tail.area[f] > tau) ? oid : INT_MAX;
     }
     __syncwarp(gmask);
     if (gl == 0) {
@@ -998,21 +1015,26 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
         uint8_t* rdeg = rec + REC_FDEG_OFF;
         uint8_t* rfv = rec + REC_FVTX_OFF;
         double* rv = reinterpret_cast<double*>(rec + REC_VTX_OFF);
-        int fc = 0, fvc = 0;
-        for (int f = gl; f < np; f += T) {
-            const int deg = sm.u.tail.deg[f];
-            if (deg == 0) continue;
-            ++fc;
-            fvc += deg;
-            int fi = 0, pos = 0;
-            for (int g2 = 0; g2 < f; ++g2) {
-                const int dg = sm.u.tail.deg[g2];
-                fi += dg ? 1 : 0;
-                pos += dg;
+        // face slot and face-vertex offset of every plane with a face: an
+        // exclusive scan of (1, degree) over the planes, T planes at a time
+        int base_fi = 0, base_pos = 0;
+        for (int f0 = 0; f0 < np; f0 += T) {
+            const int f = f0 + gl;
+            const int deg = f < np ? sm.u.tail.deg[f] : 0;
+            const int v = deg | ((deg ? 1 : 0) << 16);
+            int inc = v;
+#pragma unroll
+            for (int d = 1; d < T; d <<= 1) {
+                const int u = __shfl_up_sync(gmask, inc, d, T);
+                if (gl >= d) inc += u;
             }
-            if (fi >= REC_FACES || pos + deg > 3 * REC_VERTS) continue;
-            const int src = sm.psrc[f];
-            rfn[fi] = src < 0 ? src : (A.index_space == VT_INDEX_ORIGINAL ? __float_as_int(A.sorted[src].w) : src);
+            const int tot = __shfl_sync(gmask, inc, T - 1, T);
+            const int ex = inc - v;
+            const int fi = base_fi + (ex >> 16), pos = base_pos + (ex & 0xffff);
+            base_fi += tot >> 16;
+            base_pos += tot & 0xffff;
+            if (deg == 0 || fi >= REC_FACES || pos + deg > 3 * REC_VERTS) continue;
+            rfn[fi] = sm.u.tail.oid[f];
             rdeg[fi] = (uint8_t)deg;
             int cur = sm.u.tail.first[f];
             for (int t2 = 0; t2 < deg; ++t2) {
@@ -1032,13 +1054,8 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
                 rv[3 * li + 2] = (double)pi.z + (double)sm.vpos[s][2];
             }
         }
-        nface = fc;
-        nfv = fvc;
-#pragma unroll
-        for (int o = T / 2; o >= 1; o >>= 1) {
-            nface += __shfl_xor_sync(gmask, nface, o, T);
-            nfv += __shfl_xor_sync(gmask, nfv, o, T);
-        }
+        nface = base_fi;
+        nfv = base_pos;
     }
     if (gl == 0) {
         const bool over = nn_total > REC_FACES || nface > REC_FACES || nvtx > REC_VERTS || nfv > 3 * REC_VERTS;
