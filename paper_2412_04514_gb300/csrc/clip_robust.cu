@@ -9,6 +9,11 @@ cudaError_t launch_clip_f32(const ClipArgs& a, int t, cudaStream_t s);
 cudaError_t launch_clip_f64(const ClipArgs& a, int t, cudaStream_t s);
 cudaError_t launch_clip_big(const ClipArgs& a, cudaStream_t s);
 
+size_t clip_state_pos_offset(int precision)
+{
+    return precision == VT_FP64 ? StateLayout<double, 64, 64>::POS : StateLayout<float, 64, 64>::POS;
+}
+
 size_t clip_state_bytes(int precision)
 {
     // the regular variants all hold 64 vertex slots and 64 planes

@@ -10,8 +10,10 @@
 // the list already covered -- and writes them sorted by the kNN key, so the
 // clipper can process them nearest first and stop by the security radius.
 // R, the bounding box and the last list key come from the cell's saved
-// state. A cell with more than `cap` candidates is handed to the clipper's
-// own exhaustive walk instead (overflow list).
+// state. In the FP64 form a cell with more than `cap` candidates walks again,
+// keeping only the generators whose bisector comes near one of its saved
+// vertices; what still overflows goes to the clipper's own exhaustive walk
+// (overflow list).
 #include <float.h>
 #include <limits.h>
 
@@ -23,6 +25,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int RANGE_BLOCK = 256;
+constexpr int RANGE_VCAP = 64;  // vertex slots of the regular clipper's saved state
 
 template <typename Real>
 struct RangeKey;
@@ -35,6 +38,66 @@ struct RangeKey<double> {
     static __device__ __forceinline__ double d2(float4 a, float4 b) { return knn_d2_f64(a, b); }
 };
 
+// The cell's far vertices into vb (x, y, z, |v|^2 rows of RANGE_VCAP), sorted
+// by |v| descending: a generator at distance d >= sqrt(lkey) cuts only
+// vertices with |v| > d / 2 (less the test's tolerance), so only vertices
+// beyond sqrt(lkey) / 2 are kept. Returns their count; warp-collective.
+template <typename Real>
+__device__ __forceinline__ int load_far_vertices_t(const StateHdr* h, const uint8_t* st_pos, Real lkey, int last_orig,
+                                                   float R2, float* vb, int lane)
+{
+    const uint64_t alive = h->alive[0];
+    const Real* pos = reinterpret_cast<const Real*>(st_pos);
+    const float rmin = 0.5f * sqrtf((float)lkey) * (1.0f - 1e-5f) - 2e-5f * sqrtf(R2);
+    const float rmin2 = last_orig >= 0 && rmin > 0.0f ? rmin * rmin : -1.0f;
+    float vx[2], vy[2], vz[2], vr[2];
+    bool far[2];
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+        const int v = lane + 32 * h2;
+        far[h2] = false;
+        vx[h2] = vy[h2] = vz[h2] = vr[h2] = 0.0f;
+        if ((alive >> v) & 1ull) {
+            vx[h2] = (float)pos[v];
+            vy[h2] = (float)pos[RANGE_VCAP + v];
+            vz[h2] = (float)pos[2 * RANGE_VCAP + v];
+            vr[h2] = vx[h2] * vx[h2] + vy[h2] * vy[h2] + vz[h2] * vz[h2];
+            far[h2] = vr[h2] > rmin2;
+        }
+    }
+    const unsigned f0 = __ballot_sync(FULL, far[0]), f1 = __ballot_sync(FULL, far[1]);
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+        int rank = 0;  // by |v|^2 descending, ties by slot
+        for (int w = 0; w < 2; ++w) {
+            for (unsigned m = w ? f1 : f0; m; m &= m - 1u) {
+                const int src = __ffs(m) - 1;
+                const float r = __shfl_sync(FULL, w ? vr[1] : vr[0], src);
+                rank += (r > vr[h2] || (r == vr[h2] && src + 32 * w < lane + 32 * h2)) ? 1 : 0;
+            }
+        }
+        if (far[h2]) {
+            vb[rank] = vx[h2];
+            vb[RANGE_VCAP + rank] = vy[h2];
+            vb[2 * RANGE_VCAP + rank] = vz[h2];
+            vb[3 * RANGE_VCAP + rank] = vr[h2];
+        }
+    }
+    __syncwarp();
+    return __popc(f0) + __popc(f1);
+}
+
+// true when the bisector of n (|n|^2 = d2) comes within 1e-5 |n| R of a far vertex
+__device__ __forceinline__ bool reaches_far(const float* vb, int nv, float nx, float ny, float nz, float d2, float R2)
+{
+    const float lim = 0.5f * d2 - 1e-5f * sqrtf(d2 * R2) - 1e-30f;
+    const float vmin = 0.5f * sqrtf(d2) * (1.0f - 1e-5f) - 2e-5f * sqrtf(R2);
+    const float vmin2 = vmin > 0.0f ? vmin * vmin : -1.0f;
+    for (int v = 0; v < nv && vb[3 * RANGE_VCAP + v] > vmin2; ++v)
+        if (nx * vb[v] + ny * vb[RANGE_VCAP + v] + nz * vb[2 * RANGE_VCAP + v] > lim) return true;
+    return false;
+}
+
 template <typename Real>
 __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict__ sorted,
                                                        const int32_t* __restrict__ cell_off0,
@@ -44,7 +107,7 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
                                                        const int32_t* __restrict__ queries, int64_t nq_host,
                                                        const int32_t* __restrict__ nq_dev, int64_t nq_off,
                                                        const uint8_t* __restrict__ state, size_t state_stride,
-                                                       int cap, int32_t* __restrict__ rnbr, Real* __restrict__ rd2,
+                                                       size_t pos_off, int cap, int32_t* __restrict__ rnbr, Real* __restrict__ rd2,
                                                        int32_t* __restrict__ rlen, int32_t* __restrict__ over_list,
                                                        int32_t* __restrict__ over_ctr, DevStatus* st)
 {
@@ -55,6 +118,8 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
     int32_t* bo = reinterpret_cast<int32_t*>(smem_raw + sizeof(Real) * RANGE_CAP * (RANGE_BLOCK / 32)) +
                   warp * RANGE_CAP;
     int32_t* bj = bo + RANGE_CAP * (RANGE_BLOCK / 32);
+    float* vb = reinterpret_cast<float*>(smem_raw + (sizeof(Real) + 2 * sizeof(int32_t)) * RANGE_CAP * (RANGE_BLOCK / 32)) +
+                warp * 4 * RANGE_VCAP;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t nq = nq_host;
@@ -82,6 +147,22 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
         const int iz = cell_coord(pq.z, g.lo[2], g.scale[2], G);
         int count = 0;
         bool over = false;
+        int nv = 0;  // far vertices in vb (second attempt)
+        // first attempt: radius and bounding-box tests. In the FP64 form a cell
+        // whose candidates overflow the list (a sparse cell next to a clump)
+        // walks again with the exact test against its saved vertices, which
+        // keeps only the generators whose bisector can reach a vertex: cheaper
+        // there than the FP64 clipper's own walk (measured); the FP32 clipper's
+        // walk is cheaper than a second attempt
+        constexpr int attempts = sizeof(Real) == 8 ? 2 : 1;
+        for (int attempt = 0; attempt < attempts; ++attempt) {
+        if (attempt == 1) {
+            if (!over) break;
+            over = false;
+            count = 0;
+            nv = load_far_vertices_t<Real>(h, state + (size_t)q * state_stride + pos_off, lkey, last_orig, R2, vb,
+                                           lane);
+        }
         for (int s = 0; !over; ++s) {
             const int nseg = 2 * (2 * s + 1) * (2 * s + 1);
             for (int e0 = 0; e0 < nseg && !over; e0 += 32) {
@@ -115,6 +196,7 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
                         const float hb = fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) +
                                          fmaxf(ez * lo3[2], ez * hi3[2]);
                         keep = r4 > d2 && hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * R2) - 1e-30f;
+                        if (keep && attempt == 1) keep = reaches_far(vb, nv, ex, ey, ez, d2, R2);
                         if (keep) {
                             key = RangeKey<Real>::d2(pq, pc);
                             ko = __float_as_int(pc.w);
@@ -139,6 +221,7 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
             if (covers) break;
             const float gap = shell_gap(g, pq, ix, iy, iz, s);
             if (gap > 0.0f && 4.0f * R2 * (1.0f + 2e-5f) <= gap * gap) break;
+        }
         }
         if (over) {
             if (lane == 0) {
@@ -168,7 +251,7 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
 size_t range_smem_bytes(int precision)
 {
     const size_t key = precision == VT_FP64 ? sizeof(double) : sizeof(float);
-    return (key + 2 * sizeof(int32_t)) * RANGE_CAP * (RANGE_BLOCK / 32);
+    return ((key + 2 * sizeof(int32_t)) * RANGE_CAP + 4 * sizeof(float) * RANGE_VCAP) * (RANGE_BLOCK / 32);
 }
 
 cudaError_t launch_range(const RangeArgs& a, cudaStream_t s)
@@ -179,11 +262,11 @@ cudaError_t launch_range(const RangeArgs& a, cudaStream_t s)
     const size_t smem = range_smem_bytes(a.precision);
     if (a.precision == VT_FP64)
         k_range<double><<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(
-            a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.nq_off, a.state, a.state_stride,
+            a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.nq_off, a.state, a.state_stride, a.pos_off,
             RANGE_CAP, a.rnbr, (double*)a.rd2, a.rlen, a.over_list, a.over_ctr, a.st);
     else
         k_range<float><<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(
-            a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.nq_off, a.state, a.state_stride,
+            a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.nq_off, a.state, a.state_stride, a.pos_off,
             RANGE_CAP, a.rnbr, (float*)a.rd2, a.rlen, a.over_list, a.over_ctr, a.st);
     count_launch();
     return cudaGetLastError();

@@ -401,6 +401,7 @@ int range_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m,
         r.nq_off = o;
         r.state = c.at<uint8_t>(L.state);
         r.state_stride = L.state_stride;
+        r.pos_off = clip_state_pos_offset(p->precision);
         r.precision = p->precision;
         r.rnbr = c.at<int32_t>(L.knn_nbr);
         r.rd2 = c.at<void>(L.knn_d2);

@@ -229,7 +229,8 @@ struct RangeArgs {
     int64_t nq_off;
     const uint8_t* state;
     size_t state_stride;
-    int precision;           // key precision: VT_FP64 or VT_FP32_RECHECK
+    size_t pos_off;          // offset of the saved vertex positions (Real[3][64]) in a state
+    int precision;           // key and position precision: VT_FP64 or VT_FP32_RECHECK
     int32_t* rnbr;           // [nq * RANGE_CAP] sorted indices, nearest first
     void* rd2;               // [nq * RANGE_CAP] their keys (float or double)
     int32_t* rlen;           // [nq] list length, -1 when the cell overflowed
@@ -362,7 +363,8 @@ struct ClipArgs {
 // variant: 0 = FP32 regular, 1 = FP64 regular, 2 = FP64 robust (bigger capacity),
 // 3 = FP32 with the robust capacity (the FP32 form's first fallback)
 cudaError_t launch_clip(const ClipArgs& a, int variant, int threads_per_cell, cudaStream_t s);
-size_t clip_state_bytes(int precision);  // per-cell state of the regular variant
+size_t clip_state_bytes(int precision);       // per-cell state of the regular variant (64 slots)
+size_t clip_state_pos_offset(int precision);  // offset of its vertex positions: Real[3][64], x, y, z rows
 
 struct EmitArgs {
     int64_t n;
