@@ -144,6 +144,21 @@ __device__ __forceinline__ MaskW<W> mask_not(MaskW<W> a, int cap)
     }
     return a;
 }
+// position of the n-th (0-based) set bit of x, given popc(x) > n: a binary
+// search on population counts
+__device__ __forceinline__ int nth_bit32(uint32_t x, int n)
+{
+    int pos = 0, c = __popc(x & 0xffffu);
+    if (n >= c) { n -= c; x >>= 16; pos += 16; }
+    c = __popc(x & 0xffu);
+    if (n >= c) { n -= c; x >>= 8; pos += 8; }
+    c = __popc(x & 0xfu);
+    if (n >= c) { n -= c; x >>= 4; pos += 4; }
+    c = __popc(x & 0x3u);
+    if (n >= c) { n -= c; x >>= 2; pos += 2; }
+    if (n >= (int)(x & 1u)) pos += 1;
+    return pos;
+}
 // position of the i-th (0-based) set bit, or -1
 template <int W>
 __device__ __forceinline__ int nth_set(MaskW<W> m, int i)
@@ -152,10 +167,10 @@ __device__ __forceinline__ int nth_set(MaskW<W> m, int i)
     for (int h = 0; h < W; ++h) {
         const uint32_t lo = (uint32_t)m.w[h], hi = (uint32_t)(m.w[h] >> 32);
         const int cl = __popc(lo);
-        if (i < cl) return h * 64 + (int)__fns(lo, 0, i + 1);
+        if (i < cl) return h * 64 + nth_bit32(lo, i);
         i -= cl;
         const int ch = __popc(hi);
-        if (i < ch) return h * 64 + 32 + (int)__fns(hi, 0, i + 1);
+        if (i < ch) return h * 64 + 32 + nth_bit32(hi, i);
         i -= ch;
     }
     return -1;
