@@ -101,6 +101,42 @@ struct WarpList {
     }
 };
 
+// One compare-exchange stage of a warp-wide bitonic network over (key,
+// original index, payload), one element per lane: partner lane ^ j; the lane
+// keeps the smaller of the pair when it is the lower lane of an ascending
+// block (or the upper lane of a descending one).
+__device__ __forceinline__ void bitonic_step(float& d, int& o, int& jv, int j, bool asc, int lane)
+{
+    const float pd = __shfl_xor_sync(FULL, d, j);
+    const int po = __shfl_xor_sync(FULL, o, j);
+    const int pj = __shfl_xor_sync(FULL, jv, j);
+    const bool lower = (lane & j) == 0;
+    const bool partner_less = pd < d || (pd == d && po < o);
+    const bool take = (lower == asc) ? partner_less : (!partner_less && !(pd == d && po == o));
+    if (take) { d = pd; o = po; jv = pj; }
+}
+
+// sorts 32 elements ascending (one per lane)
+__device__ __forceinline__ void bitonic_sort32(float& d, int& o, int& jv, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) bitonic_step(d, o, jv, j, (lane & k) == 0 || k == 32, lane);
+}
+
+// merges a sorted batch into the sorted list (both ascending, one element per
+// lane), keeping the 32 smallest: the element-wise minimum of the list and
+// the reversed batch is bitonic, and one merge network sorts it
+__device__ __forceinline__ void merge32(float& ld, int& lo, int& lj, float bd, int bo, int bj, int lane)
+{
+    const float rd = __shfl_sync(FULL, bd, 31 - lane);
+    const int ro = __shfl_sync(FULL, bo, 31 - lane), rj = __shfl_sync(FULL, bj, 31 - lane);
+    if (rd < ld || (rd == ld && ro < lo)) { ld = rd; lo = ro; lj = rj; }
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) bitonic_step(ld, lo, lj, j, true, lane);
+}
+
 // The FP64 form's list: entries keep the float32 key f (relative error below
 // 3e-7 of the exact distance) and the exact FP64 key d, computed only when
 // two float32 keys are too close to order (within 2e-6) or at the end (d is
@@ -270,6 +306,17 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
                         cand = count < k || (F64 ? cd <= kd * (1.0f + 2e-6f) : key_less(cd, co, kd, ko));
                     }
                     unsigned m = __ballot_sync(FULL, cand);
+                    if (!F64 && KPL == 1 && __popc(m) >= 8) {
+                        // many candidates at once (the list filling up): sort the
+                        // batch and merge it into the list with bitonic networks
+                        float bd = cand ? cd : __int_as_float(0x7f800000);
+                        int bo = cand ? co : INT_MAX, bj = cand ? jj : -1;
+                        bitonic_sort32(bd, bo, bj, lane);
+                        merge32(L.d[0], L.o[0], L.j[0], bd, bo, bj, lane);
+                        count = count + __popc(m) < k ? count + __popc(m) : k;
+                        if (count == k) L.entry(k - 1, kd, ko);
+                        m = 0;
+                    }
                     while (m) {
                         const int src = __ffs(m) - 1;
                         m &= m - 1;
