@@ -22,6 +22,12 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// batches with at least this many qualifying candidates are merged into the
+// list by bitonic networks; smaller ones are inserted one at a time
+#ifndef VT_KNN_MERGE_MIN
+#define VT_KNN_MERGE_MIN 12
+#endif
+
 template <typename Real>
 struct Dist;
 
@@ -306,7 +312,7 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
                         cand = count < k || (F64 ? cd <= kd * (1.0f + 2e-6f) : key_less(cd, co, kd, ko));
                     }
                     unsigned m = __ballot_sync(FULL, cand);
-                    if (!F64 && KPL == 1 && __popc(m) >= 8) {
+                    if (!F64 && KPL == 1 && __popc(m) >= VT_KNN_MERGE_MIN) {
                         // many candidates at once (the list filling up): sort the
                         // batch and merge it into the list with bitonic networks
                         float bd = cand ? cd : __int_as_float(0x7f800000);
