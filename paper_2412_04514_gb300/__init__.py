@@ -4,6 +4,7 @@ The computation runs in the CUDA library ``libvt.so`` (C ABI in
 ``include/vt.h``); :mod:`.api` is a thin PyTorch binding over it and
 :mod:`.workloads` draws the seeded synthetic point clouds.
 """
+from .cli import tessellate_numpy
 from .api import (Batch, Cells, Params, VoronoiMoments, Workspace, batch_plan, clip_cells, emit, grid_build,
                   grid_resolution, knn, launch_count, lloyd, moments_adjoint, tessellate, tessellate_batch,
                   tessellate_host, version, voronoi_moments, workspace_size)
@@ -13,4 +14,5 @@ from .tune import (autotune, autotune_batch, batch_cluster_index, cluster_class,
 __all__ = ["Batch", "Cells", "Params", "VoronoiMoments", "Workspace", "batch_plan", "clip_cells", "emit",
            "grid_build", "grid_resolution", "knn", "launch_count", "lloyd", "moments_adjoint", "tessellate",
            "tessellate_batch", "tessellate_host", "version", "voronoi_moments", "workspace_size", "autotune",
-           "autotune_batch", "batch_cluster_index", "cluster_class", "cluster_index", "default_space", "tuned_batch"]
+           "autotune_batch", "batch_cluster_index", "cluster_class", "cluster_index", "default_space", "tuned_batch",
+           "tessellate_numpy"]
