@@ -16,12 +16,17 @@ Contents
 * :func:`tessellate` -- Voronoi cells by nearest-first bisector clipping of
   the box with the security-radius stop and k doubling (paper, Summary), or
   by clipping with every generator (``mode="brute"``) for the pins.
+* :func:`knn_periodic` / ``tessellate(..., periodic=True)`` -- the same in a
+  periodic box: every generator repeats at p + t (hi - lo), each cell starts
+  as the cube of one period around its generator (the Voronoi definition of
+  the Statement of need applied to all images).
 * :func:`moments_adjoint` -- gradients of cell volume, first moment and
   second moment with respect to the generators, from face integrals.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
-against closed forms, library routines (SciPy's Qhull), brute force and
-invariants; none is "parity unpinned".
+against closed forms, library routines (SciPy's Qhull and periodic kd-tree),
+brute force and invariants; the periodic mode also against the non-periodic
+oracle on replicated clouds. None is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -92,6 +97,8 @@ class _Result(ctypes.Structure):
         ("work_sign", ctypes.POINTER(ctypes.c_int64)),
         ("work_newv", ctypes.POINTER(ctypes.c_int64)),
         ("work_nbrs", ctypes.POINTER(ctypes.c_int64)),
+        ("face_img", ctypes.POINTER(ctypes.c_int32)),
+        ("periodic", ctypes.c_int),
     ]
 
 
@@ -107,6 +114,11 @@ def _load():
                                            ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.POINTER(_Result))]
             lib.vto_tessellate.restype = ctypes.c_int
+            lib.vto_tessellate_periodic.argtypes = lib.vto_tessellate.argtypes
+            lib.vto_tessellate_periodic.restype = ctypes.c_int
+            lib.vto_knn_periodic.argtypes = [P, ctypes.c_int64, P, P, P, ctypes.c_int64, ctypes.c_int, P, P, P,
+                                             ctypes.c_int]
+            lib.vto_knn_periodic.restype = ctypes.c_int
             lib.vto_result_free.argtypes = [ctypes.POINTER(_Result)]
             lib.vto_result_free.restype = None
             if hasattr(lib, "vto_moments_adjoint"):
@@ -225,8 +237,43 @@ def knn(points, k: int, queries=None, threads: int | None = None):
     return nbr, d2
 
 
+def img_shift(code):
+    """Image shift t [..., 3] (integers in [-2, 2]) of shift codes (tx+2)*25 + (ty+2)*5 + (tz+2)."""
+    c = np.asarray(code, dtype=np.int64)
+    return np.stack([c // 25 - 2, (c // 5) % 5 - 2, c % 5 - 2], axis=-1)
+
+
+def img_code(t):
+    """Shift code of image shifts t [..., 3]."""
+    t = np.asarray(t, dtype=np.int64)
+    return (t[..., 0] + 2) * 25 + (t[..., 1] + 2) * 5 + (t[..., 2] + 2)
+
+
+def knn_periodic(points, k: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), queries=None, threads: int | None = None):
+    """Exact k nearest images in the periodic box [lo, hi), own images excluded.
+
+    Returns ``(nbr, img, d2)`` [q, k]: generator, shift code and key, ordered
+    by ``(d2, generator, code)`` with ``d2`` from the offsets
+    ``(x_j - x_i) + t L`` in double (L = hi - lo).
+    """
+    p = _pts(points)
+    n = len(p)
+    q = np.arange(n, dtype=np.int64) if queries is None else np.ascontiguousarray(queries, dtype=np.int64)
+    lo32 = np.ascontiguousarray(lo, dtype=np.float32)
+    hi32 = np.ascontiguousarray(hi, dtype=np.float32)
+    nbr = np.empty((len(q), k), dtype=np.int32)
+    img = np.empty((len(q), k), dtype=np.int32)
+    d2 = np.empty((len(q), k), dtype=np.float64)
+    st = _load().vto_knn_periodic(_ptr(p), n, _ptr(lo32), _ptr(hi32), _ptr(q), len(q), k, _ptr(nbr), _ptr(img),
+                                  _ptr(d2), threads or default_threads())
+    if st != VTO_OK:
+        raise OracleError(f"vto_knn_periodic failed with status {st}")
+    return nbr, img, d2
+
+
 def tessellate(points, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), k0: int = 16, mode: str = "security",
-               order=None, cells=None, geometry: bool = False, threads: int | None = None) -> dict:
+               order=None, cells=None, geometry: bool = False, threads: int | None = None,
+               periodic: bool = False) -> dict:
     """FP64 Voronoi cells of ``cells`` (default every generator) in the box ``[lo, hi)``.
 
     ``mode="security"``: k nearest neighbours nearest first with the
@@ -237,8 +284,17 @@ def tessellate(points, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), k0: int = 16, mod
     Returns a dict of NumPy arrays: ``vol``, ``cen`` [c,3], ``m2``,
     ``nbr_off``/``nbr`` (CSR, neighbour indices ascending), ``k_used``,
     ``n_clips``, ``euler``, ``nvert``, ``face_off``/``face_tag``/``face_area``/
-    ``face_cen``/``face_plane``/``face_size`` and, with ``geometry=True``,
-    ``face_vtx`` (CCW loops seen from outside, global coordinates).
+    ``face_cen``/``face_plane``/``face_size``/``face_img`` and, with
+    ``geometry=True``, ``face_vtx`` (CCW loops seen from outside, global
+    coordinates).
+
+    ``periodic=True``: the box is periodic (every generator repeats at
+    p + t (hi - lo)); each cell starts as the cube of one period around its
+    generator and is cut by the images of the others. ``face_tag`` is then the
+    generator of each face (the cell's own index for the cube's faces),
+    ``face_img`` its image shift code, and ``nbr`` lists the generator of every
+    face above the area threshold, repeats included. Requires
+    ``|L|^2 <= 4 min L_a^2`` and ``n < 2^24``.
     """
     p = _pts(points)
     n = len(p)
@@ -249,9 +305,9 @@ def tessellate(points, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), k0: int = 16, mod
     c = None if cells is None else np.ascontiguousarray(cells, dtype=np.int64)
     res = ctypes.POINTER(_Result)()
     lib = _load()
-    st = lib.vto_tessellate(_ptr(p), n, _ptr(lo32), _ptr(hi32), k0, m, _ptr(o), _ptr(c),
-                            0 if c is None else len(c), int(geometry), threads or default_threads(),
-                            ctypes.byref(res))
+    fn = lib.vto_tessellate_periodic if periodic else lib.vto_tessellate
+    st = fn(_ptr(p), n, _ptr(lo32), _ptr(hi32), k0, m, _ptr(o), _ptr(c), 0 if c is None else len(c),
+            int(geometry), threads or default_threads(), ctypes.byref(res))
     if not res:
         raise OracleError(f"vto_tessellate failed with status {st}")
     try:
@@ -275,6 +331,7 @@ def tessellate(points, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), k0: int = 16, mod
             "face_cen": _arr(r.face_cen, 3 * nf, np.float64, (nf, 3)),
             "face_plane": _arr(r.face_plane, 4 * nf, np.float64, (nf, 4)),
             "face_size": _arr(r.face_size, nf, np.int32),
+            "face_img": _arr(r.face_img, nf, np.int32),
             "work_sign": _arr(r.work_sign, nc, np.int64),
             "work_newv": _arr(r.work_newv, nc, np.int64),
             "work_nbrs": _arr(r.work_nbrs, nc, np.int64),

@@ -38,6 +38,10 @@
  *    all n-1 other generators the cell is final by construction;
  *  - a vertex with s = n.v - b == 0 exactly lies on the plane and is kept;
  *  - j is reported as a neighbour when its face has area > 1e-12 V^(2/3).
+ *
+ * Periodic boxes (vto_tessellate_periodic, vto_knn_periodic): the same
+ * definition with every generator repeated at all its images p_j + t L
+ * (L = hi - lo, t integer); see the periodic section below.
  */
 #include "vt_oracle.h"
 
@@ -450,6 +454,210 @@ static void bisector(const float* pi, const float* pj, vec3* n, double* b)
 }
 
 /* ------------------------------------------------------------------ */
+/* periodic boxes                                                      */
+/* ------------------------------------------------------------------ */
+
+/* In a periodic box of periods L = hi - lo every generator p_j stands for all
+ * its images p_j + t L, t integer. The cell of p_i is the set of points closer
+ * to p_i than to any other image, p_i's own images included. The own images
+ * at +-L_a e_a bound it by the cube [-L/2, L/2] around p_i (local frame); the
+ * other own images only touch that cube at its edges and corners. So the cell
+ * is that cube clipped by the bisectors of the images of the other
+ * generators, its radius R is at most |L|/2, and only images closer than |L|
+ * can cut it. With |L| <= 2 min_a L_a (required), an image with |t_a| >= 3 is
+ * at least 2 L_a >= |L| away, so the shifts t in [-2, 2]^3 hold every image
+ * that can cut. A shift is coded as (tx+2)*25 + (ty+2)*5 + (tz+2) (62 = none)
+ * and a face of a periodic cell is tagged j*128 + code (the cube's faces
+ * with j = i and the shift of the own image across them). */
+#define IMG_NONE 62
+#define IMG_CODES 125
+
+static int img_code(int tx, int ty, int tz) { return (tx + 2) * 25 + (ty + 2) * 5 + (tz + 2); }
+static void img_shift(int code, int t[3]) { t[0] = code / 25 - 2; t[1] = (code / 5) % 5 - 2; t[2] = code % 5 - 2; }
+
+/* offset of image (j, code) from p_i: per coordinate ((x_j - x_i) + t L) in
+ * double; the kNN key is its squared length ((dx*dx + dy*dy) + dz*dz) */
+static vec3 image_offset(const float* pi, const float* pj, int code, vec3 L)
+{
+    int t[3];
+    img_shift(code, t);
+    return v3(((double)pj[0] - (double)pi[0]) + (double)t[0] * L.x,
+              ((double)pj[1] - (double)pi[1]) + (double)t[1] * L.y,
+              ((double)pj[2] - (double)pi[2]) + (double)t[2] * L.z);
+}
+
+/* the cube [-L/2, L/2] around generator i, faces tagged with i's own images */
+static void init_cube(poly_t* P, int64_t i, vec3 L, scratch_t* S)
+{
+    vec3 h = vscale(L, 0.5);
+    init_box(P, vscale(h, -1.0), h, S);
+    for (int f = 0; f < P->nf; ++f) {
+        int w = -P->f[f].tag - 1, axis = w / 2, s = (w % 2) ? 1 : -1;
+        P->f[f].tag = (int32_t)(i * 128 + img_code(axis == 0 ? s : 0, axis == 1 ? s : 0, axis == 2 ? s : 0));
+    }
+}
+
+/* kd-tree over the images that lie within `margin` of the box (shifts in
+ * {-1, 0, 1}^3): it holds every image closer than `margin` to any point of
+ * the box. Image coordinates only partition the tree; keys are always the
+ * image_offset expression above. */
+typedef struct {
+    const float* pts;
+    vec3 L;
+    int64_t m;
+    double* X;      /* [3m] image coordinates */
+    int64_t* id;    /* [m] j * 128 + code */
+    int64_t* perm;
+    kd_node* nodes;
+    int64_t n_nodes, cap_nodes;
+} img_tree;
+
+static int img_less(const img_tree* t, int64_t a, int64_t b, int axis)
+{
+    double ca = t->X[3 * a + axis], cb = t->X[3 * b + axis];
+    return ca < cb || (ca == cb && t->id[a] < t->id[b]);
+}
+
+static void img_select(img_tree* t, int64_t lo, int64_t hi, int64_t m, int axis)
+{
+    int64_t* p = t->perm;
+    while (hi - lo > 1) {
+        int64_t mid = lo + (hi - lo) / 2;
+        int64_t tmp = p[mid]; p[mid] = p[hi - 1]; p[hi - 1] = tmp;
+        int64_t pv = p[hi - 1], store = lo;
+        for (int64_t i = lo; i < hi - 1; ++i)
+            if (img_less(t, p[i], pv, axis)) { tmp = p[i]; p[i] = p[store]; p[store] = tmp; ++store; }
+        tmp = p[store]; p[store] = p[hi - 1]; p[hi - 1] = tmp;
+        if (store == m) return;
+        if (m < store) hi = store; else lo = store + 1;
+    }
+}
+
+static int64_t img_build_rec(img_tree* t, int64_t lo, int64_t hi)
+{
+    if (t->n_nodes == t->cap_nodes) {
+        t->cap_nodes = t->cap_nodes * 2 + 16;
+        t->nodes = (kd_node*)realloc(t->nodes, (size_t)t->cap_nodes * sizeof(kd_node));
+    }
+    int64_t id = t->n_nodes++;
+    t->nodes[id].lo = lo; t->nodes[id].hi = hi;
+    t->nodes[id].axis = -1; t->nodes[id].left = t->nodes[id].right = -1;
+    if (hi - lo <= KD_LEAF) return id;
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = lo; i < hi; ++i)
+        for (int a = 0; a < 3; ++a) {
+            double c = t->X[3 * t->perm[i] + a];
+            if (c < mn[a]) mn[a] = c;
+            if (c > mx[a]) mx[a] = c;
+        }
+    int axis = 0;
+    for (int a = 1; a < 3; ++a) if (mx[a] - mn[a] > mx[axis] - mn[axis]) axis = a;
+    int64_t m = lo + (hi - lo) / 2;
+    img_select(t, lo, hi, m, axis);
+    t->nodes[id].axis = axis;
+    t->nodes[id].split = t->X[3 * t->perm[m] + axis];
+    int64_t l = img_build_rec(t, lo, m);
+    int64_t r = img_build_rec(t, m, hi);
+    t->nodes[id].left = l; t->nodes[id].right = r;
+    return id;
+}
+
+static img_tree* img_tree_build(const float* pts, int64_t n, vec3 lo, vec3 L, double margin)
+{
+    img_tree* t = (img_tree*)calloc(1, sizeof(img_tree));
+    t->pts = pts; t->L = L;
+    t->X = (double*)malloc((size_t)(27 * n + 1) * 3 * sizeof(double));
+    t->id = (int64_t*)malloc((size_t)(27 * n + 1) * sizeof(int64_t));
+    double lov[3] = {lo.x, lo.y, lo.z}, Lv[3] = {L.x, L.y, L.z};
+    int64_t m = 0;
+    for (int64_t j = 0; j < n; ++j)
+        for (int tx = -1; tx <= 1; ++tx)
+            for (int ty = -1; ty <= 1; ++ty)
+                for (int tz = -1; tz <= 1; ++tz) {
+                    int tv[3] = {tx, ty, tz}, keep = 1;
+                    double x[3];
+                    for (int a = 0; a < 3; ++a) {
+                        x[a] = (double)pts[3 * j + a] + (double)tv[a] * Lv[a];
+                        if (!(x[a] >= lov[a] - margin && x[a] < lov[a] + Lv[a] + margin)) keep = 0;
+                    }
+                    if (!keep) continue;
+                    t->X[3 * m] = x[0]; t->X[3 * m + 1] = x[1]; t->X[3 * m + 2] = x[2];
+                    t->id[m] = j * 128 + img_code(tx, ty, tz);
+                    ++m;
+                }
+    t->m = m;
+    t->perm = (int64_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < m; ++i) t->perm[i] = i;
+    if (m > 0) img_build_rec(t, 0, m);
+    return t;
+}
+
+static void img_tree_free(img_tree* t)
+{
+    if (!t) return;
+    free(t->X); free(t->id); free(t->perm); free(t->nodes); free(t);
+}
+
+static void img_query_rec(const img_tree* t, int64_t node, int64_t self, const double* q, kheap* H)
+{
+    const kd_node* nd = &t->nodes[node];
+    if (nd->axis < 0) {
+        for (int64_t r = nd->lo; r < nd->hi; ++r) {
+            int64_t id = t->id[t->perm[r]];
+            int64_t j = id >> 7;
+            if (j == self) continue;
+            vec3 o = image_offset(t->pts + 3 * self, t->pts + 3 * j, (int)(id & 127), t->L);
+            kv e = {vdot(o, o), id};
+            kheap_push(H, e);
+        }
+        return;
+    }
+    double diff = q[nd->axis] - nd->split;
+    int64_t nearc = diff < 0 ? nd->left : nd->right, farc = diff < 0 ? nd->right : nd->left;
+    img_query_rec(t, nearc, self, q, H);
+    /* a far-side image is at least |diff| away; keys carry ~1e-15 relative rounding */
+    if (H->size < H->cap || diff * diff <= H->h[0].d2 * (1.0 + 1e-9)) img_query_rec(t, farc, self, q, H);
+}
+
+/* the k nearest images of generator `self` in the tree, sorted by (key, j, code) */
+static int img_knn(const img_tree* t, int64_t self, int k, kv* out)
+{
+    kheap H = {out, 0, k};
+    double q[3] = {t->pts[3 * self], t->pts[3 * self + 1], t->pts[3 * self + 2]};
+    if (k > 0 && t->m > 0) img_query_rec(t, 0, self, q, &H);
+    qsort(out, (size_t)H.size, sizeof(kv), kv_cmp);
+    return H.size;
+}
+
+/* every image (j != self, t in [-2, 2]^3) sorted by (key, j, code); returns a
+ * malloc'd array of *m entries */
+static kv* img_all(const float* pts, int64_t n, vec3 L, int64_t self, int64_t* m)
+{
+    int64_t cnt = (n - 1) * IMG_CODES, w = 0;
+    kv* a = (kv*)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(kv));
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == self) continue;
+        for (int c = 0; c < IMG_CODES; ++c) {
+            vec3 o = image_offset(pts + 3 * self, pts + 3 * j, c, L);
+            kv e = {vdot(o, o), j * 128 + c};
+            a[w++] = e;
+        }
+    }
+    qsort(a, (size_t)w, sizeof(kv), kv_cmp);
+    *m = w;
+    return a;
+}
+
+static double min3(vec3 a) { return fmin(a.x, fmin(a.y, a.z)); }
+
+/* periodic box accepted: positive periods with |L|^2 <= 4 min L_a^2, n < 2^24 */
+static int periodic_ok(vec3 L, int64_t n)
+{
+    double lm = min3(L);
+    return lm > 0 && vdot(L, L) <= 4.0 * lm * lm && n < ((int64_t)1 << 24);
+}
+
+/* ------------------------------------------------------------------ */
 /* vertex positions from their planes                                  */
 /* ------------------------------------------------------------------ */
 
@@ -686,6 +894,93 @@ static int one_cell(const float* pts, int64_t n, vec3 lo, vec3 hi, const vto_kdt
     }
 }
 
+/* The periodic cell of generator i (see "periodic boxes"): the cube around
+ * p_i clipped by the images of the other generators. Security mode takes the
+ * images nearest first from the margin tree with the security-radius stop and
+ * k doubling, as one_cell does; the tree holds every image closer than lim^(1/2),
+ * so a cell that is not final before its list reaches that distance (or
+ * that runs out of images) is finished from the sorted list of all images.
+ * Brute mode clips by every image of every other generator, j in index (or
+ * `order`) order, shift codes ascending. */
+static int one_cell_periodic(const float* pts, int64_t n, vec3 L, const img_tree* T, double lim,
+                             int64_t i, int k0, int mode, const int64_t* order,
+                             scratch_t* S, poly_t** out_poly, int* k_used, int* n_clips)
+{
+    const float* pi = pts + 3 * i;
+    poly_t *cur = &S->a, *nxt = &S->b;
+    *n_clips = 0;
+    S->work_sign = S->work_newv = S->work_nbrs = 0;
+    if (mode != VTO_MODE_SECURITY) {
+        init_cube(cur, i, L, S);
+        for (int64_t t = 0; t < n; ++t) {
+            int64_t j = order ? order[t] : t;
+            if (j == i) continue;
+            for (int c = 0; c < IMG_CODES; ++c) {
+                vec3 nn = image_offset(pi, pts + 3 * j, c, L);
+                double b = 0.5 * vdot(nn, nn);
+                if (b == 0) return VTO_ERR_DUPLICATE;
+                int r = clip(cur, nxt, nn, b, (int32_t)(j * 128 + c), S);
+                if (r < 0) return VTO_ERR_CAPACITY;
+                if (r == 1) { poly_t* tmp = cur; cur = nxt; nxt = tmp; ++*n_clips; }
+            }
+        }
+        *out_poly = cur;
+        *k_used = (int)(n - 1);
+        return VTO_OK;
+    }
+
+    int64_t k = k0 > 0 ? k0 : 1;
+    int all = 0;
+    for (;;) {
+        if (k > S->knn_cap) {
+            S->knn_cap = (int)k;
+            S->knn = (kv*)realloc(S->knn, (size_t)k * sizeof(kv));
+        }
+        int m = img_knn(T, i, (int)k, S->knn);
+        cur = &S->a; nxt = &S->b;
+        init_cube(cur, i, L, S);
+        int valid = 0;
+        *n_clips = 0;
+        S->work_sign = S->work_newv = S->work_nbrs = 0;
+        for (int a = 0; a < m; ++a) {
+            if (S->knn[a].d2 == 0) return VTO_ERR_DUPLICATE;
+            if (4.0 * max_r2(cur) <= S->knn[a].d2) { valid = 1; break; }
+            if (S->knn[a].d2 >= lim) { all = 1; break; }
+            vec3 nn = image_offset(pi, pts + 3 * (S->knn[a].idx >> 7), (int)(S->knn[a].idx & 127), L);
+            int r = clip(cur, nxt, nn, 0.5 * vdot(nn, nn), (int32_t)S->knn[a].idx, S);
+            if (r < 0) return VTO_ERR_CAPACITY;
+            if (r == 1) { poly_t* tmp = cur; cur = nxt; nxt = tmp; ++*n_clips; }
+        }
+        if (!valid && !all) {
+            if (m < k) all = 1;
+            else if (4.0 * max_r2(cur) <= S->knn[m - 1].d2) valid = 1;
+        }
+        if (valid) { *out_poly = cur; *k_used = (int)k; return VTO_OK; }
+        if (all) break;
+        k *= 2;
+    }
+
+    int64_t m = 0;
+    kv* list = img_all(pts, n, L, i, &m);
+    cur = &S->a; nxt = &S->b;
+    init_cube(cur, i, L, S);
+    *n_clips = 0;
+    S->work_sign = S->work_newv = S->work_nbrs = 0;
+    int st = VTO_OK;
+    for (int64_t a = 0; a < m; ++a) {
+        if (list[a].d2 == 0) { st = VTO_ERR_DUPLICATE; break; }
+        if (4.0 * max_r2(cur) <= list[a].d2) break;
+        vec3 nn = image_offset(pi, pts + 3 * (list[a].idx >> 7), (int)(list[a].idx & 127), L);
+        int r = clip(cur, nxt, nn, 0.5 * vdot(nn, nn), (int32_t)list[a].idx, S);
+        if (r < 0) { st = VTO_ERR_CAPACITY; break; }
+        if (r == 1) { poly_t* tmp = cur; cur = nxt; nxt = tmp; ++*n_clips; }
+    }
+    free(list);
+    *out_poly = cur;
+    *k_used = m < INT32_MAX ? (int)m : INT32_MAX;
+    return st;
+}
+
 /* ------------------------------------------------------------------ */
 /* driver                                                              */
 /* ------------------------------------------------------------------ */
@@ -711,10 +1006,10 @@ static int cmp_i32(const void* a, const void* b)
     return (x > y) - (x < y);
 }
 
-int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float hi_f[3],
-                   int k0, int mode, const int64_t* order,
-                   const int64_t* cells, int64_t n_cells, int want_geometry, int nthreads,
-                   vto_result** result)
+static int tess_impl(const float* pts, int64_t n, const float lo_f[3], const float hi_f[3],
+                     int k0, int mode, const int64_t* order,
+                     const int64_t* cells, int64_t n_cells, int want_geometry, int nthreads, int periodic,
+                     vto_result** result)
 {
     if (!result || !pts || n < 0 || !lo_f || !hi_f) return VTO_ERR_ARG;
     *result = NULL;
@@ -724,6 +1019,9 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
             float c = pts[3 * i + a];
             if (!(c >= lo_f[a] && c < hi_f[a])) return VTO_ERR_ARG;
         }
+    vec3 L = v3((double)hi_f[0] - (double)lo_f[0], (double)hi_f[1] - (double)lo_f[1],
+                (double)hi_f[2] - (double)lo_f[2]);
+    if (periodic && !periodic_ok(L, n)) return VTO_ERR_ARG;
     int64_t nc = cells ? n_cells : n;
     vto_result* R = (vto_result*)calloc(1, sizeof(vto_result));
     R->n_cells = nc;
@@ -736,11 +1034,15 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
     R->euler = (int32_t*)calloc((size_t)nc + 1, sizeof(int32_t));
     R->nvert = (int32_t*)calloc((size_t)nc + 1, sizeof(int32_t));
     R->face_off = (int64_t*)calloc((size_t)nc + 1, sizeof(int64_t));
+    R->periodic = periodic;
     R->work_sign = (int64_t*)calloc((size_t)nc + 1, sizeof(int64_t));
     R->work_newv = (int64_t*)calloc((size_t)nc + 1, sizeof(int64_t));
     R->work_nbrs = (int64_t*)calloc((size_t)nc + 1, sizeof(int64_t));
     cell_rec* recs = (cell_rec*)calloc((size_t)nc + 1, sizeof(cell_rec));
-    vto_kdtree* T = mode == VTO_MODE_SECURITY ? vto_kdtree_build(pts, n) : NULL;
+    vto_kdtree* T = mode == VTO_MODE_SECURITY && !periodic ? vto_kdtree_build(pts, n) : NULL;
+    /* periodic: the tree holds every image within half the shortest period of the box */
+    img_tree* TP = mode == VTO_MODE_SECURITY && periodic ? img_tree_build(pts, n, lo, L, 0.5 * min3(L)) : NULL;
+    const double lim = 0.25 * min3(L) * min3(L) * (1.0 - 1e-9);
     int status = VTO_OK;
 
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
@@ -760,7 +1062,9 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
             cell_rec* rc = &recs[c];
             if (i < 0 || i >= n) { rc->status = VTO_ERR_ARG; continue; }
             poly_t* P = NULL;
-            rc->status = one_cell(pts, n, lo, hi, T, i, k0, mode, order, S, &P, &rc->k_used, &rc->n_clips);
+            rc->status = periodic
+                ? one_cell_periodic(pts, n, L, TP, lim, i, k0, mode, order, S, &P, &rc->k_used, &rc->n_clips)
+                : one_cell(pts, n, lo, hi, T, i, k0, mode, order, S, &P, &rc->k_used, &rc->n_clips);
             rc->work_sign = S->work_sign;
             rc->work_newv = S->work_newv;
             rc->work_nbrs = S->work_nbrs;
@@ -800,7 +1104,7 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
                         rc->fvtx[3 * w + 2] = p.z + u.z;
                     }
                 lp += lsize[f];
-                if (F->tag >= 0 && farea[f] > tau) rc->nbr[rc->nnbr++] = F->tag;
+                if (F->tag >= 0 && farea[f] > tau) rc->nbr[rc->nnbr++] = periodic ? F->tag >> 7 : F->tag;
                 ++g;
             }
             qsort(rc->nbr, (size_t)rc->nnbr, sizeof(int32_t), cmp_i32);
@@ -821,6 +1125,7 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
     R->face_cen = (double*)malloc((size_t)tot_f * 3 * sizeof(double) + 8);
     R->face_plane = (double*)malloc((size_t)tot_f * 4 * sizeof(double) + 8);
     R->face_size = (int32_t*)malloc((size_t)tot_f * sizeof(int32_t) + 4);
+    R->face_img = (int32_t*)malloc((size_t)tot_f * sizeof(int32_t) + 4);
     R->face_vtx = want_geometry ? (double*)malloc((size_t)tot_v * 3 * sizeof(double) + 8) : NULL;
     R->n_nbr = tot_nbr; R->n_faces = tot_f; R->n_face_vtx = tot_v;
     int64_t on = 0, of = 0, ov = 0;
@@ -834,7 +1139,10 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
             R->euler[c] = rc->M.nvert - rc->M.nedge + rc->M.nfaces;
             R->nvert[c] = rc->M.nvert;
             memcpy(R->nbr + on, rc->nbr, (size_t)rc->nnbr * sizeof(int32_t));
-            memcpy(R->face_tag + of, rc->tag, (size_t)rc->nf * sizeof(int32_t));
+            for (int g = 0; g < rc->nf; ++g) {
+                R->face_tag[of + g] = periodic ? rc->tag[g] >> 7 : rc->tag[g];
+                R->face_img[of + g] = periodic ? rc->tag[g] & 127 : IMG_NONE;
+            }
             memcpy(R->face_area + of, rc->area, (size_t)rc->nf * sizeof(double));
             memcpy(R->face_cen + 3 * of, rc->fcen, (size_t)rc->nf * 3 * sizeof(double));
             memcpy(R->face_plane + 4 * of, rc->fnrm, (size_t)rc->nf * 4 * sizeof(double));
@@ -853,6 +1161,7 @@ int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float
     R->nbr_off[nc] = on; R->face_off[nc] = of;
     free(recs);
     vto_kdtree_free(T);
+    img_tree_free(TP);
     R->status = status;
     *result = R;
     return status;
@@ -865,6 +1174,63 @@ void vto_result_free(vto_result* R)
     free(R->k_used); free(R->n_clips); free(R->euler); free(R->nvert);
     free(R->face_off); free(R->face_tag); free(R->face_area); free(R->face_cen);
     free(R->face_plane); free(R->face_size); free(R->face_vtx);
-    free(R->work_sign); free(R->work_newv); free(R->work_nbrs);
+    free(R->work_sign); free(R->work_newv); free(R->work_nbrs); free(R->face_img);
     free(R);
+}
+
+int vto_tessellate(const float* pts, int64_t n, const float lo_f[3], const float hi_f[3],
+                   int k0, int mode, const int64_t* order,
+                   const int64_t* cells, int64_t n_cells, int want_geometry, int nthreads,
+                   vto_result** result)
+{
+    return tess_impl(pts, n, lo_f, hi_f, k0, mode, order, cells, n_cells, want_geometry, nthreads, 0, result);
+}
+
+int vto_tessellate_periodic(const float* pts, int64_t n, const float lo_f[3], const float hi_f[3],
+                            int k0, int mode, const int64_t* order,
+                            const int64_t* cells, int64_t n_cells, int want_geometry, int nthreads,
+                            vto_result** result)
+{
+    return tess_impl(pts, n, lo_f, hi_f, k0, mode, order, cells, n_cells, want_geometry, nthreads, 1, result);
+}
+
+int vto_knn_periodic(const float* pts, int64_t n, const float lo_f[3], const float hi_f[3],
+                     const int64_t* queries, int64_t nq, int k, int32_t* nbr, int32_t* img, double* d2,
+                     int nthreads)
+{
+    if (!pts || n < 0 || nq < 0 || k < 0 || (nq > 0 && !queries) || !lo_f || !hi_f) return VTO_ERR_ARG;
+    vec3 lo = v3(lo_f[0], lo_f[1], lo_f[2]);
+    vec3 L = v3((double)hi_f[0] - (double)lo_f[0], (double)hi_f[1] - (double)lo_f[1],
+                (double)hi_f[2] - (double)lo_f[2]);
+    if (!periodic_ok(L, n)) return VTO_ERR_ARG;
+    img_tree* t = img_tree_build(pts, n, lo, L, 0.5 * min3(L));
+    const double lim = 0.25 * min3(L) * min3(L) * (1.0 - 1e-9);
+    int status = VTO_OK;
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
+    {
+        kv* buf = (kv*)malloc((size_t)(k > 0 ? k : 1) * sizeof(kv));
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t q = 0; q < nq; ++q) {
+            int64_t i = queries[q];
+            if (i < 0 || i >= n) { status = VTO_ERR_ARG; continue; }
+            int m = img_knn(t, i, k, buf);
+            kv* use = buf;
+            kv* all = NULL;
+            if (m < k || (m > 0 && buf[m - 1].d2 >= lim)) {  /* the tree may miss images this far */
+                int64_t ma = 0;
+                all = img_all(pts, n, L, i, &ma);
+                use = all;
+                m = ma < k ? (int)ma : k;
+            }
+            for (int a = 0; a < k; ++a) {
+                nbr[q * k + a] = a < m ? (int32_t)(use[a].idx >> 7) : -1;
+                if (img) img[q * k + a] = a < m ? (int32_t)(use[a].idx & 127) : -1;
+                if (d2) d2[q * k + a] = a < m ? use[a].d2 : INFINITY;
+            }
+            free(all);
+        }
+        free(buf);
+    }
+    img_tree_free(t);
+    return status;
 }

@@ -53,6 +53,9 @@ typedef struct {
     int64_t* work_sign;     /* [n_cells] vertex-plane sign tests of the validating run */
     int64_t* work_newv;     /* [n_cells] vertices created by its cuts */
     int64_t* work_nbrs;     /* [n_cells] bisector planes it tested */
+    int32_t* face_img;      /* image shift of each face's generator: (tx+2)*25 + (ty+2)*5 + (tz+2),
+                               t in [-2, 2]^3; 62 (no shift) for every face of a non-periodic box */
+    int periodic;           /* 1 for vto_tessellate_periodic */
 } vto_result;
 
 /* exact k nearest neighbours (self excluded) by (d2, index); missing slots get -1 / +inf */
@@ -66,6 +69,21 @@ int vto_tessellate(const float* pts, int64_t n, const float lo[3], const float h
                    const int64_t* cells, int64_t n_cells, int want_geometry, int nthreads,
                    vto_result** result);
 
+/* Periodic box [lo, hi) of periods L = hi - lo: every generator repeats at
+ * p + t L. The cell of p_i starts as the cube [-L/2, L/2] around p_i; its
+ * faces are tagged by generator (face_tag, p_i itself for the cube's faces)
+ * and image shift (face_img); nbr lists the generator of every face, with
+ * repeats when several images of one generator are faces. Requires
+ * |L|^2 <= 4 min_a L_a^2 and n < 2^24 (else VTO_ERR_ARG). */
+int vto_tessellate_periodic(const float* pts, int64_t n, const float lo[3], const float hi[3],
+                            int k0, int mode, const int64_t* order,
+                            const int64_t* cells, int64_t n_cells, int want_geometry, int nthreads,
+                            vto_result** result);
+/* exact k nearest images (own images excluded) by (d2, index, shift code) in
+ * the periodic box; missing slots get -1 / -1 / +inf */
+int vto_knn_periodic(const float* pts, int64_t n, const float lo[3], const float hi[3],
+                     const int64_t* queries, int64_t nq, int k, int32_t* nbr, int32_t* img, double* d2,
+                     int nthreads);
 void vto_result_free(vto_result* r);
 
 vto_kdtree* vto_kdtree_build(const float* pts, int64_t n);

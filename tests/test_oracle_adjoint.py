@@ -89,3 +89,55 @@ def test_matches_central_finite_differences():
             fd = (4 * d2 - d1) / 3
             assert abs(fd - g[k, a]) <= 1e-6 * max(1.0, abs(g[k, a])), (k, a, fd, g[k, a])
             assert abs(d1 - g[k, a]) <= 1e-4 * max(1.0, abs(g[k, a]))
+
+
+# --------------------------------------------------------------------------
+# periodic box: the same identities, the neighbour across a face being the
+# image its shift names
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def periodic_cloud():
+    p = W.mixed(500, 6, n_clumps=4)
+    return p, oracle.tessellate(p, geometry=True, periodic=True)
+
+
+def test_periodic_lloyd_gradient_closed_form(periodic_cloud):
+    p, res = periodic_cloud
+    g = adj.moments_adjoint(p, gM=np.ones(len(p)), res=res, periodic=True)
+    want = 2 * res["vol"][:, None] * (p.astype(np.float64) - res["cen"])
+    np.testing.assert_allclose(g, want, rtol=1e-9, atol=1e-15)
+
+
+def test_periodic_total_volume_is_conserved(periodic_cloud):
+    p, res = periodic_cloud
+    g = adj.moments_adjoint(p, gV=np.ones(len(p)), res=res, periodic=True)
+    assert np.abs(g).max() < 1e-13
+
+
+def test_periodic_matches_central_finite_differences():
+    n = 200
+    p = W.uniform(n, 7)
+    rng = np.random.default_rng(56)
+    gV, gC, gM = rng.standard_normal(n), rng.standard_normal((n, 3)), rng.standard_normal(n)
+    res = oracle.tessellate(p, geometry=True, periodic=True)
+    g = adj.moments_adjoint(p, gV, gC, gM, res=res, periodic=True)
+    nbrs = oracle.neighbour_lists(res)
+    h = 1e-4
+    # generators whose cells reach across the box's faces (the wrapped images matter)
+    near_wall = np.flatnonzero(np.any((p < 0.15) | (p > 0.85), axis=1) & np.all((p > 2 * h) & (p < 1 - 2 * h), axis=1))
+
+    def central(k, a, hh, cells):
+        pp, pm = p.copy(), p.copy()
+        pp[k, a] = np.float32(p[k, a] + hh)
+        pm[k, a] = np.float32(p[k, a] - hh)
+        step = np.float64(pp[k, a]) - np.float64(pm[k, a])
+        return (adj.loss(pp, gV, gC, gM, cells=cells, periodic=True)
+                - adj.loss(pm, gV, gC, gM, cells=cells, periodic=True)) / step
+
+    for k in rng.choice(near_wall, 8, replace=False):
+        cells = np.unique(np.concatenate([[k], nbrs[k]]))
+        for a in range(3):
+            d1, d2 = central(k, a, h, cells), central(k, a, h / 2, cells)
+            fd = (4 * d2 - d1) / 3
+            assert abs(fd - g[k, a]) <= 1e-6 * max(1.0, abs(g[k, a])), (k, a, fd, g[k, a])
