@@ -83,7 +83,7 @@ typedef struct vt_params {
     int precision;          /* VT_FP64 or VT_FP32_RECHECK */
     int emit;               /* VT_EMIT_* bitmask */
     int index_space;        /* VT_INDEX_ORIGINAL (default) or VT_INDEX_SORTED */
-    float box_lo[3];        /* domain box, non-periodic */
+    float box_lo[3];        /* domain box [box_lo, box_hi); periodic with VT_FLAG_PERIODIC */
     float box_hi[3];
     int flags;              /* VT_FLAG_* bitmask (default 0) */
 } vt_params;
@@ -92,13 +92,25 @@ typedef struct vt_params {
 enum {
     VT_FLAG_STAGE_TIMES = 1, /* time every kernel group with CUDA events on the call's stream
                                (vt_stats.ms_*); costs one event pair per launch group */
-    VT_FLAG_NO_SYNC = 2      /* fixed schedule: passes k0, 2k0, ... <= k_max, then the exhaustive
+    VT_FLAG_NO_SYNC = 2,     /* fixed schedule: passes k0, 2k0, ... <= k_max, then the exhaustive
                                pass, each launched over the worst-case cell count and reading its
                                true count from device memory. The call never waits on the device,
                                so it can be captured in a CUDA graph; errors and output sizes are
                                read afterwards with vt_read_stats. Outputs that do not fit the
                                caller's capacities are not written (VT_ERR_CAPACITY there). The
                                neighbour-list buffer grows to n * k_max entries. */
+    VT_FLAG_PERIODIC = 4     /* periodic box: every generator also stands at all its images
+                               p + t L (L = box_hi - box_lo, t integer). The cell of p_i starts
+                               as the cube [p_i - L/2, p_i + L/2] (the bisectors of p_i's own
+                               images at +-L_a) and is cut by the images of the other
+                               generators. Vertices and centroids are not wrapped: they lie
+                               around p_i and may leave the box. A face's neighbour id is the
+                               generator whose image it faces, so an id may repeat when two
+                               images of one generator are faces, and the cube's own faces
+                               (only in sets of a handful of points) carry the cell's own id.
+                               Requires |L|^2 <= 4 min_a L_a^2 (images shifted by more than two
+                               periods cannot then cut) and fewer than 2^24 points in the call
+                               (a batch counts all its sets); otherwise VT_ERR_INVALID_ARG. */
 };
 
 /* Fills *p with the defaults above, unit box, FP32_RECHECK, emit NBR|VOL|CEN. */
@@ -142,6 +154,8 @@ typedef struct vt_set_desc {
     int64_t cell_base;      /* first global grid cell of this set */
     int64_t pt_begin;       /* first point of this set in the concatenated input */
     int64_t npts;           /* points in this set */
+    int32_t periodic;       /* 1: the set's box is periodic (VT_FLAG_PERIODIC) */
+    int32_t reserved;
 } vt_set_desc;
 
 #define VT_MAX_PASSES 16
@@ -230,7 +244,13 @@ VT_API int vt_grid_build_static(const float* pts, int64_t n, const vt_params* p,
  * and no fused multiply-add, so lists are exact and reproducible;
  * VT_FP32_RECHECK evaluates the same expression in float32.
  * 1 <= k <= 256. If fewer than k other generators exist, the remaining
- * slots get -1 and +inf. */
+ * slots get -1 and +inf.
+ * VT_FLAG_PERIODIC: the candidates are the images p_j + t L, t in
+ * [-2, 2]^3, of every generator but the query's own; an entry packs the
+ * sorted index j (bits 0..23) with the image code (tx+2)*25 + (ty+2)*5 +
+ * (tz+2) (bits 24..30); dx = (double(x_j) - double(x_i)) + tx * L_x in
+ * double; ties go by (original index, code). A list ends early (-1) when
+ * every image closer than |L| is in it (nothing farther can cut a cell). */
 VT_API int vt_knn(const float* sorted, const int32_t* cell_off, int G, int64_t n,
            const int32_t* queries, int64_t nq, int k, const vt_params* p,
            int32_t* nbr, void* d2, void* ws, size_t ws_bytes, void* stream);
@@ -401,18 +421,26 @@ VT_API int vt_autotune_batch(const float* pts, const int64_t* set_off_host, cons
  * moves along its normal with speed (x - p_i).dp_i / |p_j - p_i| and
  * (p_j - x).dp_j / |p_j - p_i|; walls are fixed), so the product is a sum of
  * exact face integrals of cubic polynomials plus 2 gM_k V_k (p_k - c_k).
+ * In a periodic box p_j is the image of the neighbour the face belongs to,
+ * p_j + t L with t read off the face's own plane (t = round of the
+ * reflection of p_i across the face, minus p_j, over L); moving p_j moves
+ * that image.
  * pts[n*3]: the generators of the tessellation (original order).
  * cells: vol, cen and the geometry (vtx_off, vtx, face_off, face_nbr,
  * face_vtx_off, face_vtx) of a vt_tessellate call on pts with
  * VT_EMIT_VOL|VT_EMIT_CEN|VT_EMIT_GEOM and VT_INDEX_ORIGINAL.
  * gV[n], gC[n*3], gM[n]: upstream gradients, each may be NULL (zero).
- * precision: VT_FP64 integrates the faces in FP64; VT_FP32_RECHECK in
- * float32 in each generator's frame (for cells of the FP32 form, whose
- * vertices carry float32 round-off anyway; the per-generator sums stay FP64).
+ * p: the parameters of the tessellation (NULL: the defaults of
+ * vt_params_default with precision VT_FP64). p->precision VT_FP64 integrates
+ * the faces in FP64; VT_FP32_RECHECK in float32 in each generator's frame
+ * (for cells of the FP32 form, whose vertices carry float32 round-off anyway;
+ * the per-generator sums stay FP64). p->box_lo/box_hi and VT_FLAG_PERIODIC
+ * give the periods.
  * grad[n*3] (FP64) is overwritten. Deterministic: each generator's gradient
  * is summed by one warp in a fixed order. Asynchronous on `stream`. */
 VT_API int vt_moments_adjoint(const float* pts, int64_t n, const vt_cells_out* cells, const double* gV,
-                              const double* gC, const double* gM, int precision, double* grad, void* stream);
+                              const double* gC, const double* gM, const vt_params* p, double* grad,
+                              void* stream);
 
 /* ------------------------------------------------------------------ */
 /* diagnostics                                                         */

@@ -33,6 +33,7 @@ VT_EMIT_GEOM = 16
 VT_MAX_PASSES = 16
 VT_FLAG_STAGE_TIMES = 1
 VT_FLAG_NO_SYNC = 2
+VT_FLAG_PERIODIC = 4
 
 STATUS_NAMES = {
     0: "VT_OK", 1: "VT_ERR_INVALID_ARG", 2: "VT_ERR_CUDA", 3: "VT_ERR_CAPACITY", 4: "VT_ERR_UNVALIDATED",
@@ -103,6 +104,8 @@ class VtSetDesc(ctypes.Structure):
         ("cell_base", ctypes.c_int64),
         ("pt_begin", ctypes.c_int64),
         ("npts", ctypes.c_int64),
+        ("periodic", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -240,7 +243,7 @@ def load() -> ctypes.CDLL:
         L.vt_version.restype = ctypes.c_char_p
         L.vt_grid_build_static.argtypes = [P, I64, pp, I, P, P, P, P]
         L.vt_grid_build_static.restype = I
-        L.vt_moments_adjoint.argtypes = [P, I64, po, P, P, P, I, P, P]
+        L.vt_moments_adjoint.argtypes = [P, I64, po, P, P, P, pp, P, P]
         L.vt_moments_adjoint.restype = I
         ps = ctypes.POINTER(VtStats)
         L.vt_batch_plan.argtypes = [P, I, pp, P, P, ctypes.POINTER(I64)]

@@ -21,7 +21,8 @@ _PREC = {"fp64": L.VT_FP64, "fp32": L.VT_FP32_RECHECK}
 @dataclass
 class Params:
     """Run-time parameters (vt_params). ``precision`` is ``"fp32"`` (float32
-    clipping with FP64 rechecks) or ``"fp64"`` (plain FP64)."""
+    clipping with FP64 rechecks) or ``"fp64"`` (plain FP64). ``periodic``:
+    the box [box_lo, box_hi) is periodic (VT_FLAG_PERIODIC)."""
 
     k0: int = 16
     k_max: int = 32
@@ -35,6 +36,7 @@ class Params:
     box_hi: tuple = (1.0, 1.0, 1.0)
     stage_times: bool = False
     no_sync: bool = False
+    periodic: bool = False
 
     def c(self) -> L.VtParams:
         p = L.VtParams()
@@ -50,7 +52,8 @@ class Params:
         for a in range(3):
             p.box_lo[a] = self.box_lo[a]
             p.box_hi[a] = self.box_hi[a]
-        p.flags = (L.VT_FLAG_STAGE_TIMES if self.stage_times else 0) | (L.VT_FLAG_NO_SYNC if self.no_sync else 0)
+        p.flags = ((L.VT_FLAG_STAGE_TIMES if self.stage_times else 0) | (L.VT_FLAG_NO_SYNC if self.no_sync else 0)
+                   | (L.VT_FLAG_PERIODIC if self.periodic else 0))
         return p
 
 
@@ -515,13 +518,14 @@ def version() -> str:
 
 def moments_adjoint(points: torch.Tensor, cells: Cells, gV: torch.Tensor | None = None,
                     gC: torch.Tensor | None = None, gM: torch.Tensor | None = None,
-                    precision: str = "fp64") -> torch.Tensor:
+                    precision: str = "fp64", params: Params | None = None) -> torch.Tensor:
     """d(sum gV.V + gC.c + gM.M2)/d(points) as float64 [n, 3] (vt_moments_adjoint).
 
     ``cells`` must come from :func:`tessellate` on ``points`` with emit
     including vol, cen and geom in the original index space. ``precision``
     ("fp64" or "fp32") is that of the face integrals: "fp32" for cells of the
-    FP32 form."""
+    FP32 form. ``params`` gives the box and whether it is periodic (the
+    tessellation's parameters; default the unit box)."""
     pts = _check_points(points)
     n = pts.shape[0]
     dev = pts.device
@@ -532,8 +536,9 @@ def moments_adjoint(points: torch.Tensor, cells: Cells, gV: torch.Tensor | None 
         return None if t is None else t.to(device=dev, dtype=torch.float64).contiguous()
 
     gV, gC, gM = f64(gV), f64(gC), f64(gM)
+    pc = Params(**{**(params or Params()).__dict__, "precision": precision}).c()
     L.check(L.load().vt_moments_adjoint(_ptr(pts), n, ctypes.byref(o), _ptr(gV), _ptr(gC), _ptr(gM),
-                                        _PREC[precision], _ptr(grad), _stream(dev)))
+                                        ctypes.byref(pc), _ptr(grad), _stream(dev)))
     return grad[:n]
 
 
@@ -550,18 +555,32 @@ class VoronoiMoments(torch.autograd.Function):
         cells = tessellate(points.detach(), p)
         ctx.cells = cells
         ctx.precision = p.precision
+        ctx.params = p
         ctx.save_for_backward(points)
         return cells.vol, cells.cen, cells.m2
 
     @staticmethod
     def backward(ctx, gV, gC, gM):
         (points,) = ctx.saved_tensors
-        g = moments_adjoint(points.detach(), ctx.cells, gV, gC, gM, precision=ctx.precision)
+        g = moments_adjoint(points.detach(), ctx.cells, gV, gC, gM, precision=ctx.precision, params=ctx.params)
         return g.to(points.dtype), None
 
 
 def voronoi_moments(points: torch.Tensor, params: Params | None = None):
     return VoronoiMoments.apply(points, params)
+
+
+def wrap_into_box(points: torch.Tensor, lo, hi) -> torch.Tensor:
+    """Points of a periodic box moved by whole periods into [lo, hi) (float32)."""
+    lo_t = torch.tensor(lo, dtype=torch.float64, device=points.device)
+    hi_t = torch.tensor(hi, dtype=torch.float64, device=points.device)
+    L = hi_t - lo_t
+    x = points.to(torch.float64)
+    x = x - torch.floor((x - lo_t) / L) * L
+    out = x.to(torch.float32)
+    # rounding to float32 can land on hi itself: that point belongs at lo
+    hi32 = hi_t.to(torch.float32).expand_as(out)
+    return torch.where(out >= hi32, lo_t.to(torch.float32).expand_as(out), out)
 
 
 def lloyd(points: torch.Tensor, iterations: int, params: Params | None = None, checkpoint: str | None = None,
@@ -572,7 +591,8 @@ def lloyd(points: torch.Tensor, iterations: int, params: Params | None = None, c
     With ``checkpoint`` the points and the iteration are saved every
     ``checkpoint_every`` iterations; ``resume=True`` continues from the file.
     The pipeline is deterministic, so a resumed run reproduces the points of
-    an uninterrupted one bit for bit."""
+    an uninterrupted one bit for bit. In a periodic box (``params.periodic``)
+    the new points are wrapped back into [box_lo, box_hi)."""
     p = points.detach().clone()
     start = 0
     if resume and checkpoint:
@@ -588,6 +608,8 @@ def lloyd(points: torch.Tensor, iterations: int, params: Params | None = None, c
             g = q.grad.to(torch.float64)
             step = p.to(torch.float64) - g / (2.0 * vol.detach()[:, None])
             p = step.to(torch.float32)
+            if params is not None and params.periodic:
+                p = wrap_into_box(p, params.box_lo, params.box_hi)
         if callback is not None:
             callback(it, float(loss.detach()))
         if checkpoint and ((it + 1) % checkpoint_every == 0 or it + 1 == iterations):

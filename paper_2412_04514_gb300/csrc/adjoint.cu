@@ -21,6 +21,13 @@
 // integrals run in the precision of the tessellation (float32 for the FP32
 // form: the FP64 rate of the part is 1/64 of float32; the local frame keeps
 // the values small), the per-cell sums across lanes in FP64.
+//
+// Periodic box: the neighbour across a face is an image p_j + t L. The face
+// lies on the bisector of p_k and that image, so the image is the reflection
+// of p_k across the face's plane; t is that reflection minus p_j over L,
+// rounded (the plane comes from the face's own vertices: its area vector
+// and its first vertex). Cell j's density is then read through the same
+// image (its centroid shifted by t L).
 #include "vt_internal.cuh"
 
 namespace vt {
@@ -70,8 +77,11 @@ __global__ void __launch_bounds__(256) k_adjoint(const float* __restrict__ pts, 
                                                  const int64_t* __restrict__ face_vtx_off,
                                                  const int32_t* __restrict__ face_vtx, const double* __restrict__ gV,
                                                  const double* __restrict__ gC, const double* __restrict__ gM,
-                                                 double* __restrict__ grad)
+                                                 double* __restrict__ grad, const __grid_constant__ GridDesc box)
 {
+    const bool per = box.periodic != 0;
+    const double Lx = (double)box.hi[0] - (double)box.lo[0], Ly = (double)box.hi[1] - (double)box.lo[1],
+                 Lz = (double)box.hi[2] - (double)box.lo[2];
     // 7-point degree-3 rule: vertices 1/20, edge midpoints 2/15, centroid 9/20
     const Real wv = (Real)(1.0 / 20.0), we = (Real)(2.0 / 15.0), wc = (Real)(9.0 / 20.0);
     const int lane = threadIdx.x & 31;
@@ -94,6 +104,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const float* __restrict__ pts, 
             const Real A[3] = {(Real)(A0[0] - px), (Real)(A0[1] - py), (Real)(A0[2] - pz)};
             const double* B0 = V + 3 * loop[1];
             Real B[3] = {(Real)(B0[0] - px), (Real)(B0[1] - py), (Real)(B0[2] - pz)};
+            Real sx = 0, sy = 0, sz = 0;  // twice the face's area vector (outward)
             for (int t = 1; t + 1 < deg; ++t) {
                 const double* C0 = V + 3 * loop[t + 1];
                 const Real C[3] = {(Real)(C0[0] - px), (Real)(C0[1] - py), (Real)(C0[2] - pz)};
@@ -101,6 +112,9 @@ __global__ void __launch_bounds__(256) k_adjoint(const float* __restrict__ pts, 
                 const Real vx = C[0] - A[0], vy = C[1] - A[1], vz = C[2] - A[2];
                 const Real cx = uy * vz - uz * vy, cy = uz * vx - ux * vz, cz = ux * vy - uy * vx;
                 const Real area = (Real)0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+                sx += cx;
+                sy += cy;
+                sz += cz;
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
                     // barycentric point q of the rule
@@ -120,10 +134,24 @@ __global__ void __launch_bounds__(256) k_adjoint(const float* __restrict__ pts, 
                 }
                 B[0] = C[0]; B[1] = C[1]; B[2] = C[2];
             }
-            const Real dx = (Real)((double)pts[3 * (int64_t)j] - px), dy = (Real)((double)pts[3 * (int64_t)j + 1] - py),
-                       dz = (Real)((double)pts[3 * (int64_t)j + 2] - pz);
+            double ox = 0.0, oy = 0.0, oz = 0.0;  // t L of the image across the face
+            if (per) {
+                // reflection of p_k across the face plane: 2 (n.A) n, n the unit normal
+                const double sn = sqrt((double)sx * sx + (double)sy * sy + (double)sz * sz);
+                if (sn > 0.0) {
+                    const double nx = sx / sn, ny = sy / sn, nz = sz / sn;
+                    const double h2 = 2.0 * (nx * (double)A[0] + ny * (double)A[1] + nz * (double)A[2]);
+                    ox = rint((px + h2 * nx - (double)pts[3 * (int64_t)j]) / Lx) * Lx;
+                    oy = rint((py + h2 * ny - (double)pts[3 * (int64_t)j + 1]) / Ly) * Ly;
+                    oz = rint((pz + h2 * nz - (double)pts[3 * (int64_t)j + 2]) / Lz) * Lz;
+                }
+            }
+            const Real dx = (Real)(((double)pts[3 * (int64_t)j] - px) + ox),
+                       dy = (Real)(((double)pts[3 * (int64_t)j + 1] - py) + oy),
+                       dz = (Real)(((double)pts[3 * (int64_t)j + 2] - pz) + oz);
             const Real inv_d = (Real)1 / sqrt(dx * dx + dy * dy + dz * dz);
-            const Dens<Real> hj = density<Real>(j, px, py, pz, vol, cen, gV, gC, gM);
+            // cell j seen through its image: its density in the frame of p_k - t L
+            const Dens<Real> hj = density<Real>(j, px - ox, py - oy, pz - oz, vol, cen, gV, gC, gM);
             Real own[3], nbr[3];
             face_term(hk, M1, M2, Q1, own);  // integral of h_k y
             face_term(hj, M1, M2, Q1, nbr);  // integral of h_j y
@@ -150,17 +178,17 @@ __global__ void __launch_bounds__(256) k_adjoint(const float* __restrict__ pts, 
 }  // namespace
 
 cudaError_t launch_adjoint(const float* pts, int64_t n, const vt_cells_out& c, const double* gV, const double* gC,
-                           const double* gM, double* grad, int precision, cudaStream_t s)
+                           const double* gM, double* grad, int precision, const GridDesc& g, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + 7) / 8;
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (precision == VT_FP64)
         k_adjoint<double><<<(unsigned)blocks, 256, 0, s>>>(pts, n, c.vol, c.cen, c.vtx_off, c.vtx, c.face_off,
-                                                           c.face_nbr, c.face_vtx_off, c.face_vtx, gV, gC, gM, grad);
+                                                           c.face_nbr, c.face_vtx_off, c.face_vtx, gV, gC, gM, grad, g);
     else
         k_adjoint<float><<<(unsigned)blocks, 256, 0, s>>>(pts, n, c.vol, c.cen, c.vtx_off, c.vtx, c.face_off,
-                                                          c.face_nbr, c.face_vtx_off, c.face_vtx, gV, gC, gM, grad);
+                                                          c.face_nbr, c.face_vtx_off, c.face_vtx, gV, gC, gM, grad, g);
     count_launch();
     return cudaGetLastError();
 }

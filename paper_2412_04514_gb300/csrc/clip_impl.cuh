@@ -258,10 +258,19 @@ __device__ __forceinline__ P64 plane64(int src, const float4* __restrict__ sorte
 {
     P64 p;
     if (src >= 0) {
-        float4 pj = sorted[src];
-        p.x = (double)pj.x - (double)pi.x;
-        p.y = (double)pj.y - (double)pi.y;
-        p.z = (double)pj.z - (double)pi.z;
+        if (g.periodic) {  // the image named by the entry's code
+            const float4 pj = sorted[src & IMG_INDEX_MASK];
+            int tx, ty, tz;
+            img_t((int)((unsigned)src >> 24), tx, ty, tz);
+            p.x = img_d64(pj.x, pi.x, tx, g.lo[0], g.hi[0]);
+            p.y = img_d64(pj.y, pi.y, ty, g.lo[1], g.hi[1]);
+            p.z = img_d64(pj.z, pi.z, tz, g.lo[2], g.hi[2]);
+        } else {
+            float4 pj = sorted[src];
+            p.x = (double)pj.x - (double)pi.x;
+            p.y = (double)pj.y - (double)pi.y;
+            p.z = (double)pj.z - (double)pi.z;
+        }
         p.b = 0.5 * ((p.x * p.x + p.y * p.y) + p.z * p.z);
     } else {
         const int w = -src - 1, axis = w >> 1, upper = w & 1;
@@ -269,7 +278,10 @@ __device__ __forceinline__ P64 plane64(int src, const float4* __restrict__ sorte
         const double pc = axis == 0 ? (double)pi.x : (axis == 1 ? (double)pi.y : (double)pi.z);
         const double v = upper ? 1.0 : -1.0;
         if (axis == 0) p.x = v; else if (axis == 1) p.y = v; else p.z = v;
-        p.b = upper ? (double)g.hi[axis] - pc : pc - (double)g.lo[axis];
+        if (g.periodic)  // the bisector with the own image one period away
+            p.b = 0.5 * ((double)g.hi[axis] - (double)g.lo[axis]);
+        else
+            p.b = upper ? (double)g.hi[axis] - pc : pc - (double)g.lo[axis];
     }
     return p;
 }
@@ -507,12 +519,27 @@ struct Cell {
         hi3[0] = h0; hi3[1] = h1; hi3[2] = h2;
     }
 
-    // the box [lo, hi) in the frame of pi: walls 0..5, corners in slots 0..7
+    // the box [lo, hi) in the frame of pi: walls 0..5, corners in slots 0..7;
+    // in a periodic box the cube [-L/2, L/2] (the bisectors of pi's own images)
     __device__ __forceinline__ void init_box(const Group<T>& G, S& sm, const GridDesc& grid)
     {
-        const Real px = (Real)pi.x, py = (Real)pi.y, pz = (Real)pi.z;
-        const Real lx = (Real)grid.lo[0] - px, ly = (Real)grid.lo[1] - py, lz = (Real)grid.lo[2] - pz;
-        const Real hx = (Real)grid.hi[0] - px, hy = (Real)grid.hi[1] - py, hz = (Real)grid.hi[2] - pz;
+        Real lx, ly, lz, hx, hy, hz;
+        if (grid.periodic) {
+            hx = (Real)(0.5 * ((double)grid.hi[0] - (double)grid.lo[0]));
+            hy = (Real)(0.5 * ((double)grid.hi[1] - (double)grid.lo[1]));
+            hz = (Real)(0.5 * ((double)grid.hi[2] - (double)grid.lo[2]));
+            lx = -hx;
+            ly = -hy;
+            lz = -hz;
+        } else {
+            const Real px = (Real)pi.x, py = (Real)pi.y, pz = (Real)pi.z;
+            lx = (Real)grid.lo[0] - px;
+            ly = (Real)grid.lo[1] - py;
+            lz = (Real)grid.lo[2] - pz;
+            hx = (Real)grid.hi[0] - px;
+            hy = (Real)grid.hi[1] - py;
+            hz = (Real)grid.hi[2] - pz;
+        }
         if (G.gl < 6) {
             const int w = G.gl, axis = w >> 1, upper = w & 1;
             const Real one = upper ? (Real)1 : (Real)-1;
@@ -837,7 +864,21 @@ struct Cell {
                                               const float4* __restrict__ sorted, const GridDesc& grid, DevStatus* st)
     {
         Real nx, ny, nz;
-        if (Tol<Real>::fp32) {
+        if (grid.periodic) {  // j packs the image code
+            const int code = (int)((unsigned)j >> 24);
+            if (Tol<Real>::fp32) {
+                const float3 o = img_off(pi, pj, code, grid);
+                nx = (Real)o.x;
+                ny = (Real)o.y;
+                nz = (Real)o.z;
+            } else {
+                int tx, ty, tz;
+                img_t(code, tx, ty, tz);
+                nx = (Real)img_d64(pj.x, pi.x, tx, grid.lo[0], grid.hi[0]);
+                ny = (Real)img_d64(pj.y, pi.y, ty, grid.lo[1], grid.hi[1]);
+                nz = (Real)img_d64(pj.z, pi.z, tz, grid.lo[2], grid.hi[2]);
+            }
+        } else if (Tol<Real>::fp32) {
             nx = (Real)(pj.x - pi.x);
             ny = (Real)(pj.y - pi.y);
             nz = (Real)(pj.z - pi.z);
@@ -988,13 +1029,18 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
     } else {
         tau = (Real)(Tol<Real>::area_rel * cbrt(V * V));
     }
+    const bool per = A.g.periodic != 0;
     for (int f = gl; f < np; f += T) {
         const int src = sm.psrc[f];
         int oid = src;  // wall ids stay
-        if (src >= 0 && sm.u.tail.first[f] >= 0 && A.index_space == VT_INDEX_ORIGINAL)
+        if (per)  // the generator whose image the face faces; the cube's faces face the cell's own
+            oid = src < 0 ? (int)out_idx
+                          : (A.index_space == VT_INDEX_ORIGINAL ? __float_as_int(A.sorted[src & IMG_INDEX_MASK].w)
+                                                                : (src & IMG_INDEX_MASK));
+        else if (src >= 0 && sm.u.tail.first[f] >= 0 && A.index_space == VT_INDEX_ORIGINAL)
             oid = __float_as_int(A.sorted[src].w);
         sm.u.tail.oid[f] = oid;
-        sm.u.tail.key[f] = (src >= 0 && sm.u.tail.first[f] >= 0 && sm.u.tail.area[f] > tau) ? oid : INT_MAX;
+        sm.u.tail.key[f] = ((src >= 0 || per) && sm.u.tail.first[f] >= 0 && sm.u.tail.area[f] > tau) ? oid : INT_MAX;
     }
     __syncwarp(gmask);
     if (gl == 0) {
@@ -1016,7 +1062,10 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
         if (key == INT_MAX) continue;
         ++c;
         int rank = 0;
-        for (int g2 = 0; g2 < np; ++g2) rank += sm.u.tail.key[g2] < key ? 1 : 0;
+        for (int g2 = 0; g2 < np; ++g2) {  // equal keys (two images of one generator) by plane
+            const int k2 = sm.u.tail.key[g2];
+            rank += (k2 < key || (k2 == key && g2 < f)) ? 1 : 0;
+        }
         if (rank < REC_FACES) rnbr[rank] = key;
     }
     int nn_total = c;
@@ -1093,15 +1142,16 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
 template <typename Real, int T, int VPL, int PCAP>
 __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, const Group<T>& G,
                                                 typename Cell<Real, T, VPL, PCAP>::S& sm, const ClipArgs& A,
-                                                const GridDesc& grid, bool valid, int jj, double last_d2,
+                                                const GridDesc& grid, bool valid, int jj, int code, double last_d2,
                                                 int last_orig, float* lo3, float* hi3)
 {
     const float4 pq = cell.pi;
     float4 pc = make_float4(0.f, 0.f, 0.f, 0.f);
     bool need = false;
     if (valid) {
-        pc = A.sorted[jj];
-        const float ex = pc.x - pq.x, ey = pc.y - pq.y, ez = pc.z - pq.z;
+        pc = A.sorted[img_index(jj, grid)];
+        const float3 o = img_off(pq, pc, code, grid);
+        const float ex = o.x, ey = o.y, ez = o.z;
         const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
         const float r4 = 4.0f * (float)cell.R2;
         const float hb =
@@ -1109,12 +1159,12 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, 
         need = r4 * (1.0f + 1e-4f) > d2 &&
                hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f && cell.reaches(sm, ex, ey, ez);
         if (need && last_orig >= 0) {  // already processed from the list?
-            const int ko = __float_as_int(pc.w);
+            const int ko = img_tie(pc, code, grid);
             if (Tol<Real>::fp32) {  // float keys compare in float (last_d2 holds a float)
-                const float kd = knn_d2_f32(pq, pc), ld = (float)last_d2;
+                const float kd = d2, ld = (float)last_d2;
                 if (kd < ld || (kd == ld && ko <= last_orig)) need = false;
             } else {
-                const double kd = knn_d2_f64(pq, pc);
+                const double kd = img_key64(pq, A.sorted, jj, grid);
                 if (kd < last_d2 || (kd == last_d2 && ko <= last_orig)) need = false;
             }
         }
@@ -1133,7 +1183,8 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, 
         p.w = 0.f;
         const int j = G.bcast(jj, src);
         // re-test against the current (smaller) cell
-        const float ex = p.x - pq.x, ey = p.y - pq.y, ez = p.z - pq.z;
+        const float3 o = img_off(pq, p, img_code_of(j, grid), grid);
+        const float ex = o.x, ey = o.y, ez = o.z;
         const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
         const float hb =
             fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) + fmaxf(ez * lo3[2], ez * hi3[2]);
@@ -1241,7 +1292,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
             const int m0 = (resume && !A.restore) ? A.k_prev : 0;
             int nj = m0 + G.gl < kc ? nb[m0 + G.gl] : -1;
             Real nd = m0 + G.gl < kc ? dd[m0 + G.gl] : (Real)0;
-            float4 np4 = nj >= 0 ? A.sorted[nj] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 np4 = nj >= 0 ? A.sorted[img_index(nj, grid)] : make_float4(0.f, 0.f, 0.f, 0.f);
             bool stop = false;
             for (int base = m0; base < kc && !stop; base += T) {
                 const int cj = nj;
@@ -1250,15 +1301,20 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
                 const int nm = base + T + G.gl;
                 nj = nm < kc ? nb[nm] : -1;
                 nd = nm < kc ? dd[nm] : (Real)0;
-                np4 = nj >= 0 ? A.sorted[nj] : make_float4(0.f, 0.f, 0.f, 0.f);
+                np4 = nj >= 0 ? A.sorted[img_index(nj, grid)] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const int cnt = kc - base < T ? kc - base : T;
                 // range lists: each lane tests its entry against the live vertices
                 // and only the entries that can cut are clipped, in list order
                 // (in k-nearest lists most entries cut, so every one is clipped)
                 bool want = false;
-                if (G.gl < cnt)
-                    want = !A.complete || cj < 0 ||
-                           cell.reaches(sm, cp.x - cell.pi.x, cp.y - cell.pi.y, cp.z - cell.pi.z);
+                if (G.gl < cnt) {
+                    if (!A.complete || cj < 0) {
+                        want = true;
+                    } else {
+                        const float3 o = img_off(cell.pi, cp, img_code_of(cj, grid), grid);
+                        want = cell.reaches(sm, o.x, o.y, o.z);
+                    }
+                }
                 for (unsigned todo = G.ballot(want); todo; todo &= todo - 1u) {
                     const int t = __ffs(todo) - 1;
                     if (A.k_next > k && base + t == k && G.gl == 0) atomicAdd((int*)&A.st->n_second, 1);
@@ -1295,7 +1351,8 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
             }
             if (end == END_NEED_K && kc > 0) {
                 last_d2 = (double)dd[kc - 1];
-                last_orig = __float_as_int(A.sorted[nb[kc - 1]].w);
+                const int jl = nb[kc - 1];
+                last_orig = img_tie(A.sorted[img_index(jl, grid)], img_code_of(jl, grid), grid);
             }
         }
         if (EXH && end == END_NEED_K) {
@@ -1310,9 +1367,11 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
             cell.bbox(G, lo3, hi3);
             const float r_in2 = last_orig >= 0 ? (float)last_d2 * (1.0f - 1e-4f) : -1.0f;
             int status = 0;
+            const bool per = grid.periodic != 0;
             for (int s = 0; status == 0; ++s) {
                 // the shell's segments, T at a time, candidates spread over the lanes
-                const int nseg = 2 * (2 * s + 1) * (2 * s + 1);
+                const int M = seg_per_row(grid, s);
+                const int nseg = M * (2 * s + 1) * (2 * s + 1);
 #ifdef VT_PROFILE
                 if (G.gl == 0) VT_PROF_ADD(16, 1);
 #endif
@@ -1322,10 +1381,15 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
 #endif
                     // only grid cells that reach into the ball of radius 2R and are
                     // not wholly inside the ball the list already covered
-                    int sa = 0, sb = 0;
+                    int sa = 0, sb = 0, sc = IMG_NONE;
                     const float r_out2 = 4.0f * (float)cell.R2 * (1.0f + 2e-4f);
-                    if (e0 + G.gl < nseg)
-                        shell_segment_ball(e0 + G.gl, s, ix, iy, iz, grid, coff, pq, r_out2, r_in2, sa, sb);
+                    if (e0 + G.gl < nseg) {
+                        if (per)
+                            shell_segment_ball_p(e0 + G.gl, s, M, ix, iy, iz, grid, coff, pq, r_out2, r_in2, sa, sb,
+                                                 sc);
+                        else
+                            shell_segment_ball(e0 + G.gl, s, ix, iy, iz, grid, coff, pq, r_out2, r_in2, sa, sb);
+                    }
                     const int len = sb - sa;
                     int total;
                     const int start = G.scan(len, total);
@@ -1343,12 +1407,18 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
                         for (int step = T / 2; step >= 1; step >>= 1)
                             if (G.bcast(incl, (seg + step - 1) & (T - 1)) <= i) seg += step;
                         const int aj = G.bcast(sa, seg & (T - 1)), sj = G.bcast(start, seg & (T - 1));
-                        const int jj = aj + (i - sj);
-                        status = exhaustive_batch(cell, G, sm, A, grid, i < total && jj != q, jj, last_d2, last_orig,
-                                                  lo3, hi3);
+                        const int code = per ? G.bcast(sc, seg & (T - 1)) : IMG_NONE;
+                        const int j0 = aj + (i - sj);
+                        status = exhaustive_batch(cell, G, sm, A, grid, i < total && j0 != q,
+                                                  per ? img_pack(j0, code) : j0, code, last_d2, last_orig, lo3, hi3);
                     }
                 }
                 if (status) break;
+                if (per) {  // R <= |L| / 2: the walk ends within |L|
+                    const float gap = shell_gap_p(grid, pq, ix, iy, iz, s);
+                    if (gap > 0.0f && 4.0f * (float)cell.R2 * (1.0f + 2e-5f) <= gap * gap) { status = -1; break; }
+                    continue;
+                }
                 const bool covers = ix - s <= 0 && iy - s <= 0 && iz - s <= 0 && ix + s >= Gr - 1 &&
                                     iy + s >= Gr - 1 && iz + s >= Gr - 1;
                 if (covers) { status = -1; break; }

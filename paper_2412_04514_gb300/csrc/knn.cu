@@ -169,7 +169,8 @@ struct WarpList64 {
 
     // inserts the candidate (float key cf, original index co, sorted index cj)
     // if it ranks among the first k; warp-uniform call
-    __device__ void insert(float cf, int co, int cj, float4 pq, const float4* __restrict__ sorted, int k, int lane)
+    __device__ void insert(float cf, int co, int cj, float4 pq, const float4* __restrict__ sorted, const GridDesc& g,
+                           int k, int lane)
     {
         const double nanv = __longlong_as_double(0x7ff8000000000000ll);
         double cd = nanv;  // the candidate's exact key, when needed
@@ -179,9 +180,9 @@ struct WarpList64 {
             bool less = f[r] < cf * (1.0f - 2e-6f);
             const bool amb = !less && f[r] <= cf * (1.0f + 2e-6f) && o[r] != INT_MAX;
             if (__any_sync(FULL, amb)) {
-                if (isnan(cd)) cd = knn_d2_f64(pq, sorted[cj]);  // uniform
+                if (isnan(cd)) cd = img_key64(pq, sorted, cj, g);  // uniform
                 if (amb) {
-                    if (isnan(d[r])) d[r] = knn_d2_f64(pq, sorted[j[r]]);
+                    if (isnan(d[r])) d[r] = img_key64(pq, sorted, j[r], g);
                     less = d[r] < cd || (d[r] == cd && o[r] < co);
                 }
             }
@@ -224,15 +225,15 @@ struct WarpList64 {
     }
 
     // every entry's exact key
-    __device__ void finish(float4 pq, const float4* __restrict__ sorted)
+    __device__ void finish(float4 pq, const float4* __restrict__ sorted, const GridDesc& g)
     {
 #pragma unroll
         for (int r = 0; r < KPL; ++r)
-            if (isnan(d[r]) && j[r] >= 0) d[r] = knn_d2_f64(pq, sorted[j[r]]);
+            if (isnan(d[r]) && j[r] >= 0) d[r] = img_key64(pq, sorted, j[r], g);
     }
 };
 
-template <typename Real, int KPL>
+template <typename Real, int KPL, bool PER>
 __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, const int32_t* __restrict__ cell_off0,
                                              const __grid_constant__ GridDesc g0, const GridDesc* __restrict__ sets,
                                              const int32_t* __restrict__ set_of, const int32_t* __restrict__ queries,
@@ -265,17 +266,25 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
         float kd = __int_as_float(0x7f800000);  // float key of the k-th entry once the list is full
         int ko = INT_MAX;
         bool dup = false;
+        // periodic box: candidates are the images of the other generators; no
+        // image farther than |L| can cut a cell, so the walk ends there
+        constexpr bool per = PER;
+        const float lim2 = per ? period_norm2(g) * (1.0f + 1e-4f) : 0.0f;
 
         for (int s = 0;; ++s) {
             // the shell's segments, 32 at a time: lanes load segment bounds in
             // parallel, then the segments' candidates are spread over all lanes
-            const int nseg = 2 * (2 * s + 1) * (2 * s + 1);
+            const int M = seg_per_row(g, s);
+            const int nseg = M * (2 * s + 1) * (2 * s + 1);
             for (int e0 = 0; e0 < nseg; e0 += 32) {
                 // once the list is full, only grid cells that reach into the
                 // ball of the current k-th distance can hold a better candidate
-                int sa = 0, sb = 0;
+                int sa = 0, sb = 0, sc = IMG_NONE;
                 if (e0 + lane < nseg) {
-                    if (count == k)
+                    if (per)
+                        shell_segment_ball_p(e0 + lane, s, M, ix, iy, iz, g, cell_off, pq,
+                                             count == k ? fminf(kd * (1.0f + 1e-5f), lim2) : lim2, -1.0f, sa, sb, sc);
+                    else if (count == k)
                         shell_segment_ball(e0 + lane, s, ix, iy, iz, g, cell_off, pq, kd * (1.0f + 1e-5f), -1.0f, sa,
                                            sb);
                     else
@@ -297,16 +306,24 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
                     for (int step = 16; step >= 1; step >>= 1)
                         if (__shfl_sync(FULL, incl, (seg + step - 1) & 31) <= i) seg += step;
                     const int aj = __shfl_sync(FULL, sa, seg & 31), sj = __shfl_sync(FULL, start, seg & 31);
-                    const int jj = aj + (i - sj);
-                    const bool valid = i < total && jj != q;
+                    const int code = per ? __shfl_sync(FULL, sc, seg & 31) : IMG_NONE;
+                    const int j0 = aj + (i - sj);
+                    const bool valid = i < total && j0 != q;  // (all of the query's own images)
+                    const int jj = per ? img_pack(j0, code) : j0;
                     float cd = __int_as_float(0x7f800000);
                     int co = INT_MAX;
                     bool cand = false;
                     if (valid) {
-                        const float4 pc = sorted[jj];
-                        co = __float_as_int(pc.w);
-                        if (pc.x == pq.x && pc.y == pq.y && pc.z == pq.z) dup = true;
-                        cd = knn_d2_f32(pq, pc);
+                        const float4 pc = sorted[j0];
+                        if (per) {
+                            co = img_tie(pc, code, g);
+                            if (code == IMG_NONE && pc.x == pq.x && pc.y == pq.y && pc.z == pq.z) dup = true;
+                            cd = key_f32(img_off(pq, pc, code, g));
+                        } else {
+                            co = __float_as_int(pc.w);
+                            if (pc.x == pq.x && pc.y == pq.y && pc.z == pq.z) dup = true;
+                            cd = knn_d2_f32(pq, pc);
+                        }
                         // FP64 form: the float key only rules out candidates clearly
                         // beyond the k-th entry; insert() orders the close ones exactly
                         cand = count < k || (F64 ? cd <= kd * (1.0f + 2e-6f) : key_less(cd, co, kd, ko));
@@ -330,7 +347,7 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
                         const int bo = __shfl_sync(FULL, co, src);
                         const int bj = __shfl_sync(FULL, jj, src);
                         if (F64) {
-                            L64.insert(bd, bo, bj, pq, sorted, k, lane);
+                            L64.insert(bd, bo, bj, pq, sorted, g, k, lane);
                             if (count < k) ++count;
                             if (count == k) kd = L64.key(k - 1);
                         } else {
@@ -342,6 +359,12 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
                 }
             }
             // stop rule
+            if (per) {
+                const float gap = shell_gap_p(g, pq, ix, iy, iz, s);
+                if (count == k && gap > 0.0f && kd * (1.0f + 2e-6f) <= gap * gap * (1.0f - 1e-5f)) break;
+                if (gap > 0.0f && gap * gap >= lim2) break;  // every image that can cut is listed
+                continue;
+            }
             const bool covers = ix - s <= 0 && iy - s <= 0 && iz - s <= 0 && ix + s >= G - 1 && iy + s >= G - 1 &&
                                 iz + s >= G - 1;
             if (covers) break;
@@ -351,7 +374,7 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
             }
         }
         if (__any_sync(FULL, dup) && lane == 0) atomicExch((int*)&st->duplicate, 1);
-        if (F64) L64.finish(pq, sorted);
+        if (F64) L64.finish(pq, sorted, g);
 #pragma unroll
         for (int r = 0; r < KPL; ++r) {
             const int e = r * 32 + lane;
@@ -373,14 +396,12 @@ cudaError_t launch_knn_t(const float4* sorted, const int32_t* cell_off, const Gr
     int64_t blocks = (nq + 7) / 8;
     if (blocks > 152 * 32) blocks = 152 * 32;
     dim3 grid((unsigned)blocks), block(256);
-    if (k <= 32)
-        k_knn<Real, 1><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, d2, st);
-    else if (k <= 64)
-        k_knn<Real, 2><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, d2, st);
-    else if (k <= 128)
-        k_knn<Real, 4><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, d2, st);
-    else
-        k_knn<Real, 8><<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, d2, st);
+    // the periodic walk is its own instantiation (the non-periodic kernels keep their registers)
+    auto kern = k <= 32 ? (g.periodic ? k_knn<Real, 1, true> : k_knn<Real, 1, false>)
+              : k <= 64 ? (g.periodic ? k_knn<Real, 2, true> : k_knn<Real, 2, false>)
+              : k <= 128 ? (g.periodic ? k_knn<Real, 4, true> : k_knn<Real, 4, false>)
+                         : (g.periodic ? k_knn<Real, 8, true> : k_knn<Real, 8, false>);
+    kern<<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, d2, st);
     count_launch();
     return cudaGetLastError();
 }

@@ -27,17 +27,6 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int RANGE_BLOCK = 256;
 constexpr int RANGE_VCAP = 64;  // vertex slots of the regular clipper's saved state
 
-template <typename Real>
-struct RangeKey;
-template <>
-struct RangeKey<float> {
-    static __device__ __forceinline__ float d2(float4 a, float4 b) { return knn_d2_f32(a, b); }
-};
-template <>
-struct RangeKey<double> {
-    static __device__ __forceinline__ double d2(float4 a, float4 b) { return knn_d2_f64(a, b); }
-};
-
 // The cell's far vertices into vb (x, y, z, |v|^2 rows of RANGE_VCAP), sorted
 // by |v| descending: a generator at distance d >= sqrt(lkey) cuts only
 // vertices with |v| > d / 2 (less the test's tolerance), so only vertices
@@ -163,12 +152,18 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
             nv = load_far_vertices_t<Real>(h, state + (size_t)q * state_stride + pos_off, lkey, last_orig, R2, vb,
                                            lane);
         }
+        const bool per = g.periodic != 0;
         for (int s = 0; !over; ++s) {
-            const int nseg = 2 * (2 * s + 1) * (2 * s + 1);
+            const int M = seg_per_row(g, s);
+            const int nseg = M * (2 * s + 1) * (2 * s + 1);
             for (int e0 = 0; e0 < nseg && !over; e0 += 32) {
-                int sa = 0, sb = 0;
-                if (e0 + lane < nseg)
-                    shell_segment_ball(e0 + lane, s, ix, iy, iz, g, cell_off, pq, r_out2, r_in2, sa, sb);
+                int sa = 0, sb = 0, sc = IMG_NONE;
+                if (e0 + lane < nseg) {
+                    if (per)
+                        shell_segment_ball_p(e0 + lane, s, M, ix, iy, iz, g, cell_off, pq, r_out2, r_in2, sa, sb, sc);
+                    else
+                        shell_segment_ball(e0 + lane, s, ix, iy, iz, g, cell_off, pq, r_out2, r_in2, sa, sb);
+                }
                 const int len = sb - sa;
                 int incl = len;
 #pragma unroll
@@ -185,21 +180,24 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
                     for (int step = 16; step >= 1; step >>= 1)
                         if (__shfl_sync(FULL, incl, (seg + step - 1) & 31) <= i) seg += step;
                     const int aj = __shfl_sync(FULL, sa, seg & 31), sj = __shfl_sync(FULL, start, seg & 31);
-                    const int jj = aj + (i - sj);
+                    const int code = per ? __shfl_sync(FULL, sc, seg & 31) : IMG_NONE;
+                    const int j0 = aj + (i - sj);
+                    const int jj = per ? img_pack(j0, code) : j0;
                     bool keep = false;
                     Real key = (Real)0;
                     int ko = 0;
-                    if (i < total && jj != q) {
-                        const float4 pc = sorted[jj];
-                        const float ex = pc.x - pq.x, ey = pc.y - pq.y, ez = pc.z - pq.z;
+                    if (i < total && j0 != q) {
+                        const float4 pc = sorted[j0];
+                        const float3 o = img_off(pq, pc, code, g);
+                        const float ex = o.x, ey = o.y, ez = o.z;
                         const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
                         const float hb = fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) +
                                          fmaxf(ez * lo3[2], ez * hi3[2]);
                         keep = r4 > d2 && hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * R2) - 1e-30f;
                         if (keep && attempt == 1) keep = reaches_far(vb, nv, ex, ey, ez, d2, R2);
                         if (keep) {
-                            key = RangeKey<Real>::d2(pq, pc);
-                            ko = __float_as_int(pc.w);
+                            key = sizeof(Real) == 8 ? (Real)img_key64(pq, sorted, jj, g) : (Real)d2;
+                            ko = img_tie(pc, code, g);
                             if (last_orig >= 0 && (key < lkey || (key == lkey && ko <= last_orig)))
                                 keep = false;  // the list already held it
                         }
@@ -216,6 +214,11 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
                 }
             }
             if (over) break;
+            if (per) {  // R <= |L| / 2: the walk ends within |L|
+                const float gap = shell_gap_p(g, pq, ix, iy, iz, s);
+                if (gap > 0.0f && 4.0f * R2 * (1.0f + 2e-5f) <= gap * gap) break;
+                continue;
+            }
             const bool covers = ix - s <= 0 && iy - s <= 0 && iz - s <= 0 && ix + s >= G - 1 && iy + s >= G - 1 &&
                                 iz + s >= G - 1;
             if (covers) break;

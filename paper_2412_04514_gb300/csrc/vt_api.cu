@@ -48,13 +48,33 @@ int check_params(const vt_params* p)
         return fail(VT_ERR_INVALID_ARG, "precision must be VT_FP64 or VT_FP32_RECHECK");
     if (p->index_space != VT_INDEX_ORIGINAL && p->index_space != VT_INDEX_SORTED)
         return fail(VT_ERR_INVALID_ARG, "index_space must be VT_INDEX_ORIGINAL or VT_INDEX_SORTED");
-    if (p->flags & ~(VT_FLAG_STAGE_TIMES | VT_FLAG_NO_SYNC))
+    if (p->flags & ~(VT_FLAG_STAGE_TIMES | VT_FLAG_NO_SYNC | VT_FLAG_PERIODIC))
         return fail(VT_ERR_INVALID_ARG, "unknown flag bits 0x%x", p->flags);
     if (p->emit & ~(VT_EMIT_NBR | VT_EMIT_VOL | VT_EMIT_CEN | VT_EMIT_M2 | VT_EMIT_GEOM))
         return fail(VT_ERR_INVALID_ARG, "unknown emit bits 0x%x", p->emit);
     for (int a = 0; a < 3; ++a)
         if (!(std::isfinite(p->box_lo[a]) && std::isfinite(p->box_hi[a]) && p->box_hi[a] > p->box_lo[a]))
             return fail(VT_ERR_INVALID_ARG, "box must satisfy lo < hi (finite) on every axis");
+    if (p->flags & VT_FLAG_PERIODIC) {
+        // images shifted by more than two periods must be unable to cut: |L| <= 2 min L_a
+        double l2 = 0, lmin = 0;
+        for (int a = 0; a < 3; ++a) {
+            const double L = (double)p->box_hi[a] - (double)p->box_lo[a];
+            l2 += L * L;
+            lmin = a == 0 || L < lmin ? L : lmin;
+        }
+        if (l2 > 4.0 * lmin * lmin)
+            return fail(VT_ERR_INVALID_ARG, "a periodic box needs |L|^2 <= 4 min L_a^2 (got %g > %g)", l2,
+                        4.0 * lmin * lmin);
+    }
+    return VT_OK;
+}
+
+// periodic lists pack a sorted index in 24 bits
+int check_periodic_n(const vt_params* p, int64_t n)
+{
+    if ((p->flags & VT_FLAG_PERIODIC) && n >= ((int64_t)1 << 24))
+        return fail(VT_ERR_INVALID_ARG, "a periodic box holds fewer than 2^24 points per call, got %lld", (long long)n);
     return VT_OK;
 }
 
@@ -101,6 +121,8 @@ GridDesc make_grid(const vt_params* p, int G)
     g.cell_base = 0;
     g.pt_begin = 0;
     g.npts = 0;
+    g.periodic = (p->flags & VT_FLAG_PERIODIC) ? 1 : 0;
+    g.reserved = 0;
     return g;
 }
 
@@ -252,6 +274,8 @@ int make_ctx(const vt_params* p, int64_t n, void* ws, size_t ws_bytes, void* str
     int e = check_params(p);
     if (e) return e;
     if (n < 0 || n > (int64_t)INT32_MAX / 2) return fail(VT_ERR_INVALID_ARG, "n out of range: %lld", (long long)n);
+    e = check_periodic_n(p, n);
+    if (e) return e;
     c.L = make_layout(p, n, cells, batch);
     if (!ws) return fail(VT_ERR_WORKSPACE, "workspace is NULL");
     if (ws_bytes < c.L.total)
@@ -805,6 +829,8 @@ int vt_workspace_size(const vt_params* p, int64_t n, size_t* bytes)
     int e = check_params(p);
     if (e) return e;
     if (n < 0 || !bytes) return fail(VT_ERR_INVALID_ARG, "n < 0 or bytes is NULL");
+    e = check_periodic_n(p, n);
+    if (e) return e;
     *bytes = make_layout(p, n).total;
     return VT_OK;
 }
@@ -927,6 +953,8 @@ int vt_batch_workspace_size(const vt_params* p, int64_t n_total, int64_t total_c
     int e = check_params(p);
     if (e) return e;
     if (n_total < 0 || total_cells < 1 || !bytes) return fail(VT_ERR_INVALID_ARG, "bad batch sizes");
+    e = check_periodic_n(p, n_total);
+    if (e) return e;
     *bytes = make_layout(p, n_total, total_cells, true).total;
     return VT_OK;
 }
@@ -947,17 +975,24 @@ int vt_tessellate_batch(const float* pts, int64_t n_total, const vt_set_desc* pl
 }
 
 int vt_moments_adjoint(const float* pts, int64_t n, const vt_cells_out* cells, const double* gV, const double* gC,
-                       const double* gM, int precision, double* grad, void* stream)
+                       const double* gM, const vt_params* p, double* grad, void* stream)
 {
     if (n < 0) return fail(VT_ERR_INVALID_ARG, "n must be >= 0");
-    if (precision != VT_FP64 && precision != VT_FP32_RECHECK)
-        return fail(VT_ERR_INVALID_ARG, "precision must be VT_FP64 or VT_FP32_RECHECK");
+    vt_params dflt;
+    if (!p) {
+        vt_params_default(&dflt);
+        dflt.precision = VT_FP64;
+        p = &dflt;
+    }
+    int ce0 = check_params(p);
+    if (ce0) return ce0;
+    const int precision = p->precision;
     if (n == 0) return VT_OK;
     if (!pts || !cells || !grad) return fail(VT_ERR_INVALID_ARG, "NULL argument");
     if (!cells->vol || !cells->cen || !cells->vtx_off || !cells->vtx || !cells->face_off || !cells->face_nbr ||
         !cells->face_vtx_off || !cells->face_vtx)
         return fail(VT_ERR_INVALID_ARG, "the adjoint needs vol, cen and the geometry of the tessellation");
-    cudaError_t e = launch_adjoint(pts, n, *cells, gV, gC, gM, grad, precision, (cudaStream_t)stream);
+    cudaError_t e = launch_adjoint(pts, n, *cells, gV, gC, gM, grad, precision, make_grid(p, 1), (cudaStream_t)stream);
     return e == cudaSuccess ? VT_OK : cuda_fail(e, "adjoint");
 }
 

@@ -22,6 +22,8 @@ struct GridDesc {
     int64_t cell_base;  // first global grid cell of this point set (batches)
     int64_t pt_begin;   // first input point of this point set
     int64_t npts;       // points in this point set
+    int32_t periodic;   // 1: periodic box of periods hi - lo
+    int32_t reserved;
 };
 static_assert(sizeof(GridDesc) == sizeof(vt_set_desc), "vt_set_desc mirrors GridDesc");
 
@@ -160,6 +162,57 @@ __device__ __forceinline__ void shell_segment_ball(int e, int s, int ix, int iy,
     b = cell_off[base + zb + 1];
 }
 
+// ---------------------------------------------------------------------------
+// periodic boxes: candidates are images p_j + t L, t in [-2, 2]^3. A list
+// entry (or plane source) packs the sorted index j in bits 0..23 with the
+// image code (tx+2)*25 + (ty+2)*5 + (tz+2) in bits 24..30; IMG_NONE (62) is
+// t = 0. Ties between equal keys go by (original index, code): the tie key
+// orig * 128 + code. Outside periodic boxes entries are plain indices.
+// ---------------------------------------------------------------------------
+constexpr int IMG_NONE = 62;
+constexpr int32_t IMG_INDEX_MASK = (1 << 24) - 1;
+
+__device__ __forceinline__ int img_code(int tx, int ty, int tz) { return (tx + 2) * 25 + (ty + 2) * 5 + (tz + 2); }
+__device__ __forceinline__ void img_t(int code, int& tx, int& ty, int& tz)
+{
+    tx = code / 25 - 2;
+    ty = (code / 5) % 5 - 2;
+    tz = code % 5 - 2;
+}
+__device__ __forceinline__ int img_pack(int j, int code) { return j | (code << 24); }
+__device__ __forceinline__ int img_index(int jp, const GridDesc& g) { return g.periodic ? (jp & IMG_INDEX_MASK) : jp; }
+__device__ __forceinline__ int img_code_of(int jp, const GridDesc& g)
+{
+    return g.periodic ? (int)((unsigned)jp >> 24) : IMG_NONE;
+}
+// tie key of a candidate: its original index, times 128 plus its code when periodic
+__device__ __forceinline__ int img_tie(float4 pc, int code, const GridDesc& g)
+{
+    return g.periodic ? __float_as_int(pc.w) * 128 + code : __float_as_int(pc.w);
+}
+// one coordinate of the offset p_j + t L - p_i in float32: a shifted
+// coordinate is formed in double and rounded once (forming c + t L in
+// float32 first would lose up to an ulp of the period, far more than the
+// offset of a close neighbour across the boundary can bear)
+__device__ __forceinline__ float img_d(float c, float q, int t, float lo, float hi)
+{
+    return t == 0 ? c - q : (float)(((double)c - (double)q) + (double)t * ((double)hi - (double)lo));
+}
+// the same in double, every operation separately rounded: the exact key's coordinate
+__device__ __forceinline__ double img_d64(float c, float q, int t, float lo, float hi)
+{
+    return __dadd_rn(__dsub_rn((double)c, (double)q), (double)t * __dsub_rn((double)hi, (double)lo));
+}
+// float32 offset of candidate pc (code) from pq
+__device__ __forceinline__ float3 img_off(float4 pq, float4 pc, int code, const GridDesc& g)
+{
+    if (code == IMG_NONE) return make_float3(pc.x - pq.x, pc.y - pq.y, pc.z - pq.z);
+    int tx, ty, tz;
+    img_t(code, tx, ty, tz);
+    return make_float3(img_d(pc.x, pq.x, tx, g.lo[0], g.hi[0]), img_d(pc.y, pq.y, ty, g.lo[1], g.hi[1]),
+                       img_d(pc.z, pq.z, tz, g.lo[2], g.hi[2]));
+}
+
 // kNN ordering keys. FP64 form: ((dx*dx + dy*dy) + dz*dz) in double with
 // dx = double(x_j) - double(x_i), every operation separately rounded (no FMA),
 // so lists are exact and reproducible. FP32 form: the same in float32 with FMA.
@@ -174,6 +227,118 @@ __device__ __forceinline__ float knn_d2_f32(float4 a, float4 b)
 {
     const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
     return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+__device__ __forceinline__ float key_f32(float3 o) { return fmaf(o.z, o.z, fmaf(o.y, o.y, o.x * o.x)); }
+// the FP64 key of packed candidate jp (periodic: its image) from pq
+__device__ __forceinline__ double img_key64(float4 pq, const float4* __restrict__ sorted, int jp, const GridDesc& g)
+{
+    if (!g.periodic) return knn_d2_f64(pq, sorted[jp]);
+    const float4 pc = sorted[jp & IMG_INDEX_MASK];
+    int tx, ty, tz;
+    img_t((int)((unsigned)jp >> 24), tx, ty, tz);
+    const double dx = img_d64(pc.x, pq.x, tx, g.lo[0], g.hi[0]);
+    const double dy = img_d64(pc.y, pq.y, ty, g.lo[1], g.hi[1]);
+    const double dz = img_d64(pc.z, pq.z, tz, g.lo[2], g.hi[2]);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// ---------------------------------------------------------------------------
+// periodic shell walk. Shell s of a periodic grid is walked in unwrapped grid
+// coordinates; a cell (x, y, z) is the grid cell (x mod G, ...) seen through
+// the image t = (floor(x / G), ...). A rim row's z-run crosses image
+// boundaries, so each row owns seg_per_row segments: pieces of one z-image
+// each, every piece split in the part below and above the inner ball.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+__device__ __forceinline__ int seg_per_row(const GridDesc& g, int s)
+{
+    if (!g.periodic) return 2;
+    const int W = 2 * s + 1;
+    return 2 * (W <= g.G ? 2 : (W + g.G - 1) / g.G + 1);
+}
+
+// |L| of a periodic box: no image farther than this can cut a cell
+__device__ __forceinline__ float period_norm2(const GridDesc& g)
+{
+    const float lx = g.hi[0] - g.lo[0], ly = g.hi[1] - g.lo[1], lz = g.hi[2] - g.lo[2];
+    return lx * lx + ly * ly + lz * lz;
+}
+
+// distance from q to the outside of the block of shells 0..s (no walls), less
+// the rounding margin
+__device__ __forceinline__ float shell_gap_p(const GridDesc& g, float4 q, int ix, int iy, int iz, int s)
+{
+    const float c0 = (float)g.cw[0], c1 = (float)g.cw[1], c2 = (float)g.cw[2];
+    float gap = fminf(q.x - (g.lo[0] + (float)(ix - s) * c0), (g.lo[0] + (float)(ix + s + 1) * c0) - q.x);
+    gap = fminf(gap, fminf(q.y - (g.lo[1] + (float)(iy - s) * c1), (g.lo[1] + (float)(iy + s + 1) * c1) - q.y));
+    gap = fminf(gap, fminf(q.z - (g.lo[2] + (float)(iz - s) * c2), (g.lo[2] + (float)(iz + s + 1) * c2) - q.z));
+    return gap - 2.0f * (float)g.margin;
+}
+
+// Segment e (of M = seg_per_row per row) of periodic shell s, restricted to
+// cells that reach into the ball r_out2 around q and are not wholly inside
+// the ball r_in2 (see shell_segment_ball): the sorted range [a, b) and the
+// image code of its cells. Images beyond t = +-2 are never returned (no
+// generator there can cut a cell of a box with |L| <= 2 min L_a).
+__device__ __forceinline__ void shell_segment_ball_p(int e, int s, int M, int ix, int iy, int iz, const GridDesc& g,
+                                                     const int32_t* __restrict__ cell_off, float4 q, float r_out2,
+                                                     float r_in2, int& a, int& b, int& code)
+{
+    const int G = g.G;
+    const int W = 2 * s + 1;
+    const int row = e / M, sub = e - (e / M) * M, piece = sub >> 1, half = sub & 1;
+    const int dx = row / W - s, dy = row - (row / W) * W - s;
+    const int x = ix + dx, y = iy + dy;
+    a = b = 0;
+    code = IMG_NONE;
+    const int tx = floordiv(x, G), ty = floordiv(y, G);
+    if (tx < -2 || tx > 2 || ty < -2 || ty > 2) return;
+    const float m = (float)g.margin;
+    const float cx = (float)g.cw[0], cy = (float)g.cw[1];
+    const float x0 = g.lo[0] + (float)x * cx - m, x1 = g.lo[0] + (float)(x + 1) * cx + m;
+    const float y0 = g.lo[1] + (float)y * cy - m, y1 = g.lo[1] + (float)(y + 1) * cy + m;
+    const float dxn = fmaxf(fmaxf(x0 - q.x, q.x - x1), 0.0f), dyn = fmaxf(fmaxf(y0 - q.y, q.y - y1), 0.0f);
+    const float dxf = fmaxf(q.x - x0, x1 - q.x), dyf = fmaxf(q.y - y0, y1 - q.y);
+    const float dn2 = dxn * dxn + dyn * dyn, df2 = dxf * dxf + dyf * dyf;
+    if (dn2 > r_out2) return;
+    const float zr = sqrtf(r_out2 - dn2);
+    const float zmax = 8.0f * (float)G;  // far beyond any image t in [-2, 2]
+    const int zlo = (int)floorf(fminf(fmaxf((q.z - zr - m - g.lo[2]) * g.scale[2] - 1e-3f, -zmax), zmax));
+    const int zhi = (int)floorf(fminf(fmaxf((q.z + zr + m - g.lo[2]) * g.scale[2] + 1e-3f, -zmax), zmax));
+    int zi0 = 1, zi1 = 0;
+    if (r_in2 > df2) {
+        const float zi = sqrtf(r_in2 - df2);
+        zi0 = (int)ceilf(fminf(fmaxf((q.z - zi + m - g.lo[2]) * g.scale[2] + 1e-3f, -zmax), zmax));
+        zi1 = (int)floorf(fminf(fmaxf((q.z + zi - m - g.lo[2]) * g.scale[2] - 1e-3f, -zmax), zmax)) - 1;
+    }
+    const bool rim = dx == -s || dx == s || dy == -s || dy == s;
+    int za, zb, tz;
+    if (rim) {
+        tz = floordiv(iz - s, G) + piece;
+        za = iz - s > zlo ? iz - s : zlo;
+        zb = iz + s < zhi ? iz + s : zhi;
+        za = za > tz * G ? za : tz * G;
+        zb = zb < tz * G + G - 1 ? zb : tz * G + G - 1;
+        if (za > zb) return;
+        if (zi0 <= zi1 && zi0 <= zb && zi1 >= za) {  // the inner cells split this piece
+            if (half) za = zi1 + 1 > za ? zi1 + 1 : za;
+            else zb = zi0 - 1 < zb ? zi0 - 1 : zb;
+        } else if (half) {
+            return;
+        }
+    } else {
+        if (piece != 0) return;
+        const int z = half ? iz + s : iz - s;
+        if (z < zlo || z > zhi || (z >= zi0 && z <= zi1)) return;
+        za = zb = z;
+        tz = floordiv(z, G);
+    }
+    if (za > zb || tz < -2 || tz > 2) return;
+    const int base = ((x - tx * G) * G + (y - ty * G)) * G - tz * G;
+    a = cell_off[base + za];
+    b = cell_off[base + zb + 1];
+    code = img_code(tx, ty, tz);
 }
 
 // ---------------------------------------------------------------------------
@@ -378,7 +543,8 @@ struct EmitArgs {
 };
 cudaError_t launch_emit_count(const EmitArgs& a, cudaStream_t s);  // counts + scans + totals
 cudaError_t launch_emit_write(const EmitArgs& a, const vt_cells_out& out, cudaStream_t s);  // device-checked caps
+// g: the box (lo, hi) and its periodic flag
 cudaError_t launch_adjoint(const float* pts, int64_t n, const vt_cells_out& c, const double* gV, const double* gC,
-                           const double* gM, double* grad, int precision, cudaStream_t s);
+                           const double* gM, double* grad, int precision, const GridDesc& g, cudaStream_t s);
 
 }  // namespace vt

@@ -75,6 +75,7 @@ def clustered(
     lo: float = 0.0,
     hi: float = 1.0,
     log10_sigma: tuple[float, float] = (-3.0, -2.0),
+    periodic: bool = False,
 ) -> np.ndarray:
     """``n`` points from ``n_clumps`` isotropic Gaussian clumps.
 
@@ -82,7 +83,9 @@ def clustered(
     ``10**log10_sigma`` (times the box edge); each point picks a clump
     uniformly. Draws that land outside the box are redrawn from the same clump
     (resampling, not clamping: clamping would pile points onto the walls and
-    create coplanar or duplicate generators).
+    create coplanar or duplicate generators). With ``periodic`` they are
+    wrapped by whole periods instead, so clumps continue across the faces of a
+    periodic box.
     """
     span = hi - lo
     centres = lo + span * rng.random((n_clumps, 3))
@@ -93,6 +96,8 @@ def clustered(
     while len(todo):
         c = which[todo]
         x64 = centres[c] + sigmas[c, None] * rng.standard_normal((len(todo), 3))
+        if periodic:
+            x64 = x64 - np.floor((x64 - lo) / span) * span
         x32, ok = _in_box_f32(x64, lo, hi)
         out[todo[ok]] = x32[ok]
         todo = todo[~ok]
@@ -106,6 +111,7 @@ def mixed(
     clustered_fraction: float = 0.5,
     lo: float = 0.0,
     hi: float = 1.0,
+    periodic: bool = False,
 ) -> np.ndarray:
     """Half uniform, half clustered cloud (the 1M / 8M benchmark recipe).
 
@@ -113,6 +119,7 @@ def mixed(
     rest drawn by :func:`clustered` with ``n_clumps`` clumps, then shuffled so
     the input order carries no spatial structure. Duplicate rows (possible in
     very tight clumps at float32 resolution) are redrawn uniformly.
+    ``periodic``: clumps wrap across the faces of the box (see :func:`clustered`).
     """
     rng = np.random.default_rng(seed)
     n_cl = int(round(n * clustered_fraction))
@@ -121,7 +128,8 @@ def mixed(
     if n_un:
         parts.append((lo + (hi - lo) * rng.random((n_un, 3))))
     pts = np.concatenate(
-        [p.astype(np.float32) for p in parts] + ([clustered(n_cl, n_clumps, rng, lo, hi)] if n_cl else []),
+        [p.astype(np.float32) for p in parts]
+        + ([clustered(n_cl, n_clumps, rng, lo, hi, periodic=periodic)] if n_cl else []),
         axis=0,
     )
     # uniform draws that rounded up to hi in float32

@@ -83,3 +83,22 @@ def test_grid_resolution_agrees_with_the_oracle_reading():
         for rho in (1.0, 2.0, 3.0):
             p.grid_density = rho
             assert lib.vt_grid_resolution(ctypes.byref(p), n) == oracle.grid_resolution(n, rho)
+
+
+def test_periodic_limits_are_checked_on_the_host():
+    lib = L.load()
+    p = L.VtParams()
+    lib.vt_params_default(ctypes.byref(p))
+    p.flags = L.VT_FLAG_PERIODIC
+    b = ctypes.c_size_t()
+    assert lib.vt_workspace_size(ctypes.byref(p), 4096, ctypes.byref(b)) == L.VT_OK
+    # sorted indices of periodic lists have 24 bits
+    assert lib.vt_workspace_size(ctypes.byref(p), 1 << 24, ctypes.byref(b)) == L.VT_ERR_INVALID_ARG
+    assert lib.vt_workspace_size(ctypes.byref(p), (1 << 24) - 1, ctypes.byref(b)) == L.VT_OK
+    # |L|^2 <= 4 min L_a^2: (1, 1, 0.85) passes, (1, 1, 0.8) does not
+    p.box_hi[2] = 0.85
+    assert lib.vt_workspace_size(ctypes.byref(p), 4096, ctypes.byref(b)) == L.VT_OK
+    p.box_hi[2] = 0.8
+    assert lib.vt_workspace_size(ctypes.byref(p), 4096, ctypes.byref(b)) == L.VT_ERR_INVALID_ARG
+    p.flags = 0
+    assert lib.vt_workspace_size(ctypes.byref(p), 4096, ctypes.byref(b)) == L.VT_OK
