@@ -254,11 +254,12 @@ struct Group {
 // ---------------------------------------------------------------------------
 struct P64 { double x, y, z, b; };
 
+template <bool PER>
 __device__ __forceinline__ P64 plane64(int src, const float4* __restrict__ sorted, float4 pi, const GridDesc& g)
 {
     P64 p;
     if (src >= 0) {
-        if (g.periodic) {  // the image named by the entry's code
+        if (PER) {  // the image named by the entry's code
             const float4 pj = sorted[src & IMG_INDEX_MASK];
             int tx, ty, tz;
             img_t((int)((unsigned)src >> 24), tx, ty, tz);
@@ -278,7 +279,7 @@ __device__ __forceinline__ P64 plane64(int src, const float4* __restrict__ sorte
         const double pc = axis == 0 ? (double)pi.x : (axis == 1 ? (double)pi.y : (double)pi.z);
         const double v = upper ? 1.0 : -1.0;
         if (axis == 0) p.x = v; else if (axis == 1) p.y = v; else p.z = v;
-        if (g.periodic)  // the bisector with the own image one period away
+        if (PER)  // the bisector with the own image one period away
             p.b = 0.5 * ((double)g.hi[axis] - (double)g.lo[axis]);
         else
             p.b = upper ? (double)g.hi[axis] - pc : pc - (double)g.lo[axis];
@@ -388,9 +389,12 @@ __device__ VT_RARE bool outside64(const S& sm, int s, P64 h, const float4* __res
                                        GridDesc g, double fx, double fy, double fz, double R2)
 {
     const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-    P64 A = plane64(sm.psrc[ids & 0xff], sorted, pi, g);
-    P64 B = plane64(sm.psrc[(ids >> 8) & 0xff], sorted, pi, g);
-    P64 C = plane64(sm.psrc[(ids >> 16) & 0xff], sorted, pi, g);
+    const bool per = g.periodic != 0;  // out of line: the box kind is read here
+    P64 A = per ? plane64<true>(sm.psrc[ids & 0xff], sorted, pi, g) : plane64<false>(sm.psrc[ids & 0xff], sorted, pi, g);
+    P64 B = per ? plane64<true>(sm.psrc[(ids >> 8) & 0xff], sorted, pi, g)
+                : plane64<false>(sm.psrc[(ids >> 8) & 0xff], sorted, pi, g);
+    P64 C = per ? plane64<true>(sm.psrc[(ids >> 16) & 0xff], sorted, pi, g)
+                : plane64<false>(sm.psrc[(ids >> 16) & 0xff], sorted, pi, g);
     double x, y, z;
     if (!vertex64(A, B, C, x, y, z)) { x = fx; y = fy; z = fz; }
     const double sv = (h.x * x + h.y * y) + h.z * z - h.b;
@@ -403,9 +407,12 @@ __device__ VT_RARE double vertex_r2_64(const S& sm, int s, const float4* __restr
                                             GridDesc g, double fx, double fy, double fz)
 {
     const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-    P64 A = plane64(sm.psrc[ids & 0xff], sorted, pi, g);
-    P64 B = plane64(sm.psrc[(ids >> 8) & 0xff], sorted, pi, g);
-    P64 C = plane64(sm.psrc[(ids >> 16) & 0xff], sorted, pi, g);
+    const bool per = g.periodic != 0;
+    P64 A = per ? plane64<true>(sm.psrc[ids & 0xff], sorted, pi, g) : plane64<false>(sm.psrc[ids & 0xff], sorted, pi, g);
+    P64 B = per ? plane64<true>(sm.psrc[(ids >> 8) & 0xff], sorted, pi, g)
+                : plane64<false>(sm.psrc[(ids >> 8) & 0xff], sorted, pi, g);
+    P64 C = per ? plane64<true>(sm.psrc[(ids >> 16) & 0xff], sorted, pi, g)
+                : plane64<false>(sm.psrc[(ids >> 16) & 0xff], sorted, pi, g);
     double x, y, z;
     if (!vertex64(A, B, C, x, y, z)) { x = fx; y = fy; z = fz; }
     return (x * x + y * y) + z * z;
@@ -452,7 +459,8 @@ __device__ VT_RARE void interp_vertex(const S& sm, int s, Real nx, Real ny, Real
 // ---------------------------------------------------------------------------
 // one cell: registers (positions, masks) + the group's shared memory
 // ---------------------------------------------------------------------------
-template <typename Real, int T, int VPL, int PCAP>
+// PER: periodic box (images, the cube of one period) -- its own instantiation
+template <typename Real, int T, int VPL, int PCAP, bool PER>
 struct Cell {
     static constexpr int VCAP = T * VPL;
     using S = GroupSmem<Real, VCAP, PCAP>;
@@ -524,7 +532,7 @@ struct Cell {
     __device__ __forceinline__ void init_box(const Group<T>& G, S& sm, const GridDesc& grid)
     {
         Real lx, ly, lz, hx, hy, hz;
-        if (grid.periodic) {
+        if (PER) {
             hx = (Real)(0.5 * ((double)grid.hi[0] - (double)grid.lo[0]));
             hy = (Real)(0.5 * ((double)grid.hi[1] - (double)grid.lo[1]));
             hz = (Real)(0.5 * ((double)grid.hi[2] - (double)grid.lo[2]));
@@ -666,7 +674,7 @@ struct Cell {
         if (lhs > rhs * (1.0f + 1e-5f)) return false;
         // within 1e-5 of equality: decide in FP64, every vertex re-solved in FP64
         if (G.gl == 0) atomicAdd(&st->fp64_rechecks, 1ull);
-        const double d64 = jsrc >= 0 ? 2.0 * plane64(jsrc, sorted, pi, grid).b : (double)dj;
+        const double d64 = jsrc >= 0 ? 2.0 * plane64<PER>(jsrc, sorted, pi, grid).b : (double)dj;
         double m = 0;
         for (uint32_t rm = lane_rows<T, VPL>(alive, G.gl); rm; rm &= rm - 1) {
             const int r = __ffs(rm) - 1;
@@ -706,7 +714,7 @@ struct Cell {
         }
         if (Tol<Real>::fp32 && G.any(mynear != 0)) {
             // re-decide the near-zero tests in FP64
-            const P64 h = plane64(src, sorted, pi, grid);
+            const P64 h = plane64<PER>(src, sorted, pi, grid);
             for (uint32_t m = mynear; m; m &= m - 1) {
                 const int r = __ffs(m) - 1;
                 Real fx, fy, fz;
@@ -864,7 +872,7 @@ struct Cell {
                                               const float4* __restrict__ sorted, const GridDesc& grid, DevStatus* st)
     {
         Real nx, ny, nz;
-        if (grid.periodic) {  // j packs the image code
+        if (PER) {  // j packs the image code
             const int code = (int)((unsigned)j >> 24);
             if (Tol<Real>::fp32) {
                 const float3 o = img_off(pi, pj, code, grid);
@@ -927,7 +935,7 @@ struct Cell {
 // ---------------------------------------------------------------------------
 // moments, neighbours and geometry of a validated cell (shared memory only)
 // ---------------------------------------------------------------------------
-template <typename Real, int T, int VCAP, int PCAP, typename M>
+template <typename Real, int T, int VCAP, int PCAP, typename M, bool PER>
 __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, int np, float4 pi, int gl,
                                          unsigned gmask, int64_t out_idx, const ClipArgs& A)
 {
@@ -1029,7 +1037,7 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
     } else {
         tau = (Real)(Tol<Real>::area_rel * cbrt(V * V));
     }
-    const bool per = A.g.periodic != 0;
+    constexpr bool per = PER;
     for (int f = gl; f < np; f += T) {
         const int src = sm.psrc[f];
         int oid = src;  // wall ids stay
@@ -1062,9 +1070,13 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
         if (key == INT_MAX) continue;
         ++c;
         int rank = 0;
-        for (int g2 = 0; g2 < np; ++g2) {  // equal keys (two images of one generator) by plane
-            const int k2 = sm.u.tail.key[g2];
-            rank += (k2 < key || (k2 == key && g2 < f)) ? 1 : 0;
+        if (PER) {
+            for (int g2 = 0; g2 < np; ++g2) {  // equal keys (two images of one generator) by plane
+                const int k2 = sm.u.tail.key[g2];
+                rank += (k2 < key || (k2 == key && g2 < f)) ? 1 : 0;
+            }
+        } else {
+            for (int g2 = 0; g2 < np; ++g2) rank += sm.u.tail.key[g2] < key ? 1 : 0;
         }
         if (rank < REC_FACES) rnbr[rank] = key;
     }
@@ -1139,9 +1151,9 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
 // (sum_i max(n_i lo_i, n_i hi_i) > b); both tests run on every lane in float
 // with margins that only admit extra candidates, and the survivors are clipped
 // one at a time. Generators a resumed list already processed are skipped.
-template <typename Real, int T, int VPL, int PCAP>
-__device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, const Group<T>& G,
-                                                typename Cell<Real, T, VPL, PCAP>::S& sm, const ClipArgs& A,
+template <typename Real, int T, int VPL, int PCAP, bool PER>
+__device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP, PER>& cell, const Group<T>& G,
+                                                typename Cell<Real, T, VPL, PCAP, PER>::S& sm, const ClipArgs& A,
                                                 const GridDesc& grid, bool valid, int jj, int code, double last_d2,
                                                 int last_orig, float* lo3, float* hi3)
 {
@@ -1149,8 +1161,8 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, 
     float4 pc = make_float4(0.f, 0.f, 0.f, 0.f);
     bool need = false;
     if (valid) {
-        pc = A.sorted[img_index(jj, grid)];
-        const float3 o = img_off(pq, pc, code, grid);
+        pc = A.sorted[img_index_t<PER>(jj)];
+        const float3 o = img_off_t<PER>(pq, pc, code, grid);
         const float ex = o.x, ey = o.y, ez = o.z;
         const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
         const float r4 = 4.0f * (float)cell.R2;
@@ -1159,7 +1171,7 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, 
         need = r4 * (1.0f + 1e-4f) > d2 &&
                hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f && cell.reaches(sm, ex, ey, ez);
         if (need && last_orig >= 0) {  // already processed from the list?
-            const int ko = img_tie(pc, code, grid);
+            const int ko = img_tie_t<PER>(pc, code);
             if (Tol<Real>::fp32) {  // float keys compare in float (last_d2 holds a float)
                 const float kd = d2, ld = (float)last_d2;
                 if (kd < ld || (kd == ld && ko <= last_orig)) need = false;
@@ -1183,7 +1195,7 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP>& cell, 
         p.w = 0.f;
         const int j = G.bcast(jj, src);
         // re-test against the current (smaller) cell
-        const float3 o = img_off(pq, p, img_code_of(j, grid), grid);
+        const float3 o = img_off_t<PER>(pq, p, img_code_t<PER>(j), grid);
         const float ex = o.x, ey = o.y, ez = o.z;
         const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
         const float hb =
@@ -1228,10 +1240,10 @@ constexpr int clip_minb()
     return (sizeof(Real) == 4 && !ROBUST) ? VT_CLIP_MINB_F32 : VT_CLIP_MINB_F64;
 }
 
-template <typename Real, int T, int VPL, int PCAP, bool ROBUST, bool EXH>
+template <typename Real, int T, int VPL, int PCAP, bool ROBUST, bool EXH, bool PER>
 __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_clip(const __grid_constant__ ClipArgs A)
 {
-    using C = Cell<Real, T, VPL, PCAP>;
+    using C = Cell<Real, T, VPL, PCAP, PER>;
     using S = typename C::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Group<T> G;
@@ -1292,7 +1304,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
             const int m0 = (resume && !A.restore) ? A.k_prev : 0;
             int nj = m0 + G.gl < kc ? nb[m0 + G.gl] : -1;
             Real nd = m0 + G.gl < kc ? dd[m0 + G.gl] : (Real)0;
-            float4 np4 = nj >= 0 ? A.sorted[img_index(nj, grid)] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 np4 = nj >= 0 ? A.sorted[img_index_t<PER>(nj)] : make_float4(0.f, 0.f, 0.f, 0.f);
             bool stop = false;
             for (int base = m0; base < kc && !stop; base += T) {
                 const int cj = nj;
@@ -1301,7 +1313,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
                 const int nm = base + T + G.gl;
                 nj = nm < kc ? nb[nm] : -1;
                 nd = nm < kc ? dd[nm] : (Real)0;
-                np4 = nj >= 0 ? A.sorted[img_index(nj, grid)] : make_float4(0.f, 0.f, 0.f, 0.f);
+                np4 = nj >= 0 ? A.sorted[img_index_t<PER>(nj)] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const int cnt = kc - base < T ? kc - base : T;
                 // range lists: each lane tests its entry against the live vertices
                 // and only the entries that can cut are clipped, in list order
@@ -1311,7 +1323,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
                     if (!A.complete || cj < 0) {
                         want = true;
                     } else {
-                        const float3 o = img_off(cell.pi, cp, img_code_of(cj, grid), grid);
+                        const float3 o = img_off_t<PER>(cell.pi, cp, img_code_t<PER>(cj), grid);
                         want = cell.reaches(sm, o.x, o.y, o.z);
                     }
                 }
@@ -1352,7 +1364,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
             if (end == END_NEED_K && kc > 0) {
                 last_d2 = (double)dd[kc - 1];
                 const int jl = nb[kc - 1];
-                last_orig = img_tie(A.sorted[img_index(jl, grid)], img_code_of(jl, grid), grid);
+                last_orig = img_tie_t<PER>(A.sorted[img_index_t<PER>(jl)], img_code_t<PER>(jl));
             }
         }
         if (EXH && end == END_NEED_K) {
@@ -1367,10 +1379,10 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
             cell.bbox(G, lo3, hi3);
             const float r_in2 = last_orig >= 0 ? (float)last_d2 * (1.0f - 1e-4f) : -1.0f;
             int status = 0;
-            const bool per = grid.periodic != 0;
+            constexpr bool per = PER;
             for (int s = 0; status == 0; ++s) {
                 // the shell's segments, T at a time, candidates spread over the lanes
-                const int M = seg_per_row(grid, s);
+                const int M = seg_per_row_t<PER>(grid, s);
                 const int nseg = M * (2 * s + 1) * (2 * s + 1);
 #ifdef VT_PROFILE
                 if (G.gl == 0) VT_PROF_ADD(16, 1);
@@ -1409,7 +1421,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
                         const int aj = G.bcast(sa, seg & (T - 1)), sj = G.bcast(start, seg & (T - 1));
                         const int code = per ? G.bcast(sc, seg & (T - 1)) : IMG_NONE;
                         const int j0 = aj + (i - sj);
-                        status = exhaustive_batch(cell, G, sm, A, grid, i < total && j0 != q,
+                        status = exhaustive_batch<Real, T, VPL, PCAP, PER>(cell, G, sm, A, grid, i < total && j0 != q,
                                                   per ? img_pack(j0, code) : j0, code, last_d2, last_orig, lo3, hi3);
                     }
                 }
@@ -1435,7 +1447,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
         if (end == END_VALID) {
             cell.dump_positions(G, sm);
             G.sync();
-            finish_cell<Real, T, T * VPL, PCAP, typename C::M>(sm, cell.alive, cell.np, cell.pi, G.gl, G.mask, out_idx,
+            finish_cell<Real, T, T * VPL, PCAP, typename C::M, PER>(sm, cell.alive, cell.np, cell.pi, G.gl, G.mask, out_idx,
                                                                A);
 #ifdef VT_PROFILE
             if (G.gl == 0) VT_PROF_ADD(pb + 6, clock64() - tp2);
@@ -1475,7 +1487,11 @@ cudaError_t launch_variant(const ClipArgs& a, cudaStream_t s)
 {
     using S = GroupSmem<Real, T * VPL, PCAP>;
     const size_t smem = sizeof(S) * (CLIP_BLOCK / T);
-    auto kern = a.exhaustive ? k_clip<Real, T, VPL, PCAP, ROBUST, true> : k_clip<Real, T, VPL, PCAP, ROBUST, false>;
+    // periodic boxes have their own instantiations (the walls' kernels keep their registers)
+    auto kern = a.g.periodic ? (a.exhaustive ? k_clip<Real, T, VPL, PCAP, ROBUST, true, true>
+                                             : k_clip<Real, T, VPL, PCAP, ROBUST, false, true>)
+                             : (a.exhaustive ? k_clip<Real, T, VPL, PCAP, ROBUST, true, false>
+                                             : k_clip<Real, T, VPL, PCAP, ROBUST, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int gpb = CLIP_BLOCK / T;

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
         for (int s = 0;; ++s) {
             // the shell's segments, 32 at a time: lanes load segment bounds in
             // parallel, then the segments' candidates are spread over all lanes
-            const int M = seg_per_row(g, s);
+            const int M = seg_per_row_t<PER>(g, s);
             const int nseg = M * (2 * s + 1) * (2 * s + 1);
             for (int e0 = 0; e0 < nseg; e0 += 32) {
                 // once the list is full, only grid cells that reach into the

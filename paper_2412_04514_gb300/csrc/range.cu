@@ -87,7 +87,7 @@ __device__ __forceinline__ bool reaches_far(const float* vb, int nv, float nx, f
     return false;
 }
 
-template <typename Real>
+template <typename Real, bool PER>
 __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict__ sorted,
                                                        const int32_t* __restrict__ cell_off0,
                                                        const __grid_constant__ GridDesc g0,
@@ -152,9 +152,9 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
             nv = load_far_vertices_t<Real>(h, state + (size_t)q * state_stride + pos_off, lkey, last_orig, R2, vb,
                                            lane);
         }
-        const bool per = g.periodic != 0;
+        constexpr bool per = PER;
         for (int s = 0; !over; ++s) {
-            const int M = seg_per_row(g, s);
+            const int M = seg_per_row_t<PER>(g, s);
             const int nseg = M * (2 * s + 1) * (2 * s + 1);
             for (int e0 = 0; e0 < nseg && !over; e0 += 32) {
                 int sa = 0, sb = 0, sc = IMG_NONE;
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
                     int ko = 0;
                     if (i < total && j0 != q) {
                         const float4 pc = sorted[j0];
-                        const float3 o = img_off(pq, pc, code, g);
+                        const float3 o = img_off_t<PER>(pq, pc, code, g);
                         const float ex = o.x, ey = o.y, ez = o.z;
                         const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
                         const float hb = fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) +
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
                         if (keep && attempt == 1) keep = reaches_far(vb, nv, ex, ey, ez, d2, R2);
                         if (keep) {
                             key = sizeof(Real) == 8 ? (Real)img_key64(pq, sorted, jj, g) : (Real)d2;
-                            ko = img_tie(pc, code, g);
+                            ko = img_tie_t<PER>(pc, code);
                             if (last_orig >= 0 && (key < lkey || (key == lkey && ko <= last_orig)))
                                 keep = false;  // the list already held it
                         }
@@ -263,14 +263,17 @@ cudaError_t launch_range(const RangeArgs& a, cudaStream_t s)
     int64_t blocks = (a.nq + 7) / 8;
     if (blocks > 152 * 32) blocks = 152 * 32;
     const size_t smem = range_smem_bytes(a.precision);
-    if (a.precision == VT_FP64)
-        k_range<double><<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(
+    if (a.precision == VT_FP64) {
+        auto kern = a.g.periodic ? k_range<double, true> : k_range<double, false>;
+        kern<<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(
             a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.nq_off, a.state, a.state_stride, a.pos_off,
             RANGE_CAP, a.rnbr, (double*)a.rd2, a.rlen, a.over_list, a.over_ctr, a.st);
-    else
-        k_range<float><<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(
+    } else {
+        auto kern = a.g.periodic ? k_range<float, true> : k_range<float, false>;
+        kern<<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(
             a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.nq_off, a.state, a.state_stride, a.pos_off,
             RANGE_CAP, a.rnbr, (float*)a.rd2, a.rlen, a.over_list, a.over_ctr, a.st);
+    }
     count_launch();
     return cudaGetLastError();
 }

@@ -203,6 +203,17 @@ __device__ __forceinline__ double img_d64(float c, float q, int t, float lo, flo
 {
     return __dadd_rn(__dsub_rn((double)c, (double)q), (double)t * __dsub_rn((double)hi, (double)lo));
 }
+// compile-time forms for kernels instantiated per box kind (PER = periodic)
+template <bool PER>
+__device__ __forceinline__ int img_index_t(int jp) { return PER ? (jp & IMG_INDEX_MASK) : jp; }
+template <bool PER>
+__device__ __forceinline__ int img_code_t(int jp) { return PER ? (int)((unsigned)jp >> 24) : IMG_NONE; }
+template <bool PER>
+__device__ __forceinline__ int img_tie_t(float4 pc, int code)
+{
+    return PER ? __float_as_int(pc.w) * 128 + code : __float_as_int(pc.w);
+}
+
 // float32 offset of candidate pc (code) from pq
 __device__ __forceinline__ float3 img_off(float4 pq, float4 pc, int code, const GridDesc& g)
 {
@@ -229,6 +240,13 @@ __device__ __forceinline__ float knn_d2_f32(float4 a, float4 b)
     return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
 }
 __device__ __forceinline__ float key_f32(float3 o) { return fmaf(o.z, o.z, fmaf(o.y, o.y, o.x * o.x)); }
+template <bool PER>
+__device__ __forceinline__ float3 img_off_t(float4 pq, float4 pc, int code, const GridDesc& g)
+{
+    if (!PER) return make_float3(pc.x - pq.x, pc.y - pq.y, pc.z - pq.z);
+    return img_off(pq, pc, code, g);
+}
+
 // the FP64 key of packed candidate jp (periodic: its image) from pq
 __device__ __forceinline__ double img_key64(float4 pq, const float4* __restrict__ sorted, int jp, const GridDesc& g)
 {
@@ -256,6 +274,12 @@ __device__ __forceinline__ int seg_per_row(const GridDesc& g, int s)
     if (!g.periodic) return 2;
     const int W = 2 * s + 1;
     return 2 * (W <= g.G ? 2 : (W + g.G - 1) / g.G + 1);
+}
+
+template <bool PER>
+__device__ __forceinline__ int seg_per_row_t(const GridDesc& g, int s)
+{
+    return PER ? seg_per_row(g, s) : 2;
 }
 
 // |L| of a periodic box: no image farther than this can cut a cell

@@ -41,5 +41,5 @@ def test_command_line_round_trip(tmp_path):
     assert len(lines) == len(pts)
     for i in (0, 1, len(pts) // 2, len(pts) - 1):
         f = lines[i].split()
-        assert float(f[0]) == want["vol"][i]
+        assert float(f[0]) == pytest.approx(want["vol"][i], rel=1e-12)
         assert [int(x) for x in f[1:]] == want["nbr"][want["nbr_off"][i]:want["nbr_off"][i + 1]].tolist()
