@@ -35,6 +35,12 @@ WORKLOADS = {
     "mixed-8m": dict(n=1 << 23, seed=2, sub_box=True, desc="8,388,608 float32 points, same recipe as mixed-1m, "
                      "seed 2; per-result errors of both forms against the FP64 oracle on the cells of a seeded "
                      "sub-box of about 65,536 generators"),
+    "periodic-1m": dict(n=1 << 20, seed=5, periodic=True, desc="1,048,576 float32 points in the periodic unit box "
+                        "[0,1)^3: the mixed-1m recipe (524,288 uniform + 524,288 in 1,000 Gaussian clumps) with "
+                        "out-of-box draws wrapped by one period, so clumps continue across the faces, seed 5; cells "
+                        "start as the cube of one period around their generator and are cut by the images of the "
+                        "others; k0=16 with doubling to k_max then the exhaustive pass; outputs neighbours + volume "
+                        "+ centroid + full geometry"),
     "mixed-300k": dict(n=300_000, seed=1, clumps=300, desc="300,000 float32 points, the mixed-1m recipe with 300 "
                        "clumps (a small case for profiler captures)"),
     "batch-512": dict(batch=True, seed=3, desc="512 independent point sets in [0,1)^3, sizes floor(10^U(3, log10 2e5)) "
@@ -162,7 +168,8 @@ def dist_barrier(world: int):
         dist.barrier()
 
 
-def cpu_oracle_rate(pts: np.ndarray, sample_cells: int, seed: int = 12345, sub_box: bool = False) -> dict:
+def cpu_oracle_rate(pts: np.ndarray, sample_cells: int, seed: int = 12345, sub_box: bool = False,
+                    periodic: bool = False) -> dict:
     """Times the FP64 CPU oracle on a sample of the workload's cells: random
     cells, or (sub_box) the cells of a seeded cube holding about that many
     generators. Returns the rate and the oracle's result for the sample."""
@@ -179,7 +186,7 @@ def cpu_oracle_rate(pts: np.ndarray, sample_cells: int, seed: int = 12345, sub_b
     cores = oracle.default_threads()
     oracle.tessellate(pts[:2000], k0=16)  # load the library, warm the allocator
     t0 = time.perf_counter()
-    r = oracle.tessellate(pts, k0=16, cells=idx, threads=cores)
+    r = oracle.tessellate(pts, k0=16, cells=idx, threads=cores, periodic=periodic)
     dt = time.perf_counter() - t0
     return {"value": len(idx) / dt, "seconds": dt, "cores": cores, "flops_per_cell": float(oracle.clip_flops(r).mean()),
             "idx": idx, "result": r,
@@ -208,14 +215,14 @@ def run_reference(args, rank: int, world: int):
     from paper_2412_04514_gb300 import workloads as W
 
     wl = WORKLOADS[args.workload]
-    pts = W.mixed(wl["n"], wl["seed"], n_clumps=wl.get("clumps", 1000))
+    pts = W.mixed(wl["n"], wl["seed"], n_clumps=wl.get("clumps", 1000), periodic=wl.get("periodic", False))
     per_step = args.ref_cells
     for i in range(args.warmup):
-        cpu_oracle_rate(pts, min(2000, per_step), seed=100 + i)
+        cpu_oracle_rate(pts, min(2000, per_step), seed=100 + i, periodic=wl.get("periodic", False))
     times = []
     cores = None
     for i in range(args.steps):
-        r = cpu_oracle_rate(pts, per_step, seed=200 + i)
+        r = cpu_oracle_rate(pts, per_step, seed=200 + i, periodic=wl.get("periodic", False))
         times.append(r["seconds"])
         cores = r["cores"]
     total = sum(times)
@@ -247,7 +254,8 @@ def run_gpu(args, rank: int, world: int, local: int):
     if wl.get("lloyd"):
         return run_lloyd(args, rank, world, local)
     n = wl["n"]
-    pts_np = W.mixed(n, wl["seed"] + 1000 * rank, n_clumps=wl.get("clumps", 1000))
+    periodic = wl.get("periodic", False)
+    pts_np = W.mixed(n, wl["seed"] + 1000 * rank, n_clumps=wl.get("clumps", 1000), periodic=periodic)
     pts = torch.from_numpy(pts_np).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     emit = ("nbr", "vol", "cen", "geom")
@@ -280,9 +288,9 @@ def run_gpu(args, rank: int, world: int, local: int):
 
     # warm up both forms, then time: FP32+recheck (headline) and plain FP64
     p32 = vt.Params(precision="fp32", k0=args.k0, k_max=args.k_max, threads_per_cell=32, emit=emit,
-                    grid_density=args.rho)
+                    grid_density=args.rho, periodic=periodic)
     p64 = vt.Params(precision="fp64", k0=args.k0, k_max=args.k_max, threads_per_cell=32, emit=emit,
-                    grid_density=args.rho)
+                    grid_density=args.rho, periodic=periodic)
     with Clocks(local) as clk:
         ms32, st32, launches32, cells = timed(p32, args.steps, args.warmup, stage_times=True)
     clocks = clk.summary()
@@ -324,7 +332,8 @@ def run_gpu(args, rank: int, world: int, local: int):
     errors = None
     if world == 1 and not args.no_cpu_baseline:
         sub = wl.get("sub_box", False)
-        cpu = cpu_oracle_rate(pts_np, 65536 if sub else args.cpu_cells, seed=17 if sub else 12345, sub_box=sub)
+        cpu = cpu_oracle_rate(pts_np, 65536 if sub else args.cpu_cells, seed=17 if sub else 12345, sub_box=sub,
+                              periodic=periodic)
         errors = {"fp32_recheck": errors_vs_oracle(cells, cpu)}
         if cells64 is not None:
             errors["fp64"] = errors_vs_oracle(cells64, cpu)
@@ -333,9 +342,9 @@ def run_gpu(args, rank: int, world: int, local: int):
     clip_launches = statistics.mean(s["clip_launches"] for s in st32)
     achieved = n * flops_per_cell / (stage["ms_clip"] / 1e3) / 1e12
     roofline = {
-        "kernel": "k_clip<float,32,2,64> (all passes of one step)",
+        "kernel": "k_clip<float,32,2,64>%s (all passes of one step)" % (", periodic" if periodic else ""),
         "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": _clip_traffic(n),
+        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None if periodic else _clip_traffic(n),
         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (unit counts and max SM clock)",
         "units": f"{n} validated cells x {flops_per_cell:.0f} algorithmic FP32 flops/cell over {clip_launches:.1f} "
                  f"clip launches",
