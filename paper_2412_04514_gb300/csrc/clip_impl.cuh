@@ -872,8 +872,10 @@ struct Cell {
                                               const float4* __restrict__ sorted, const GridDesc& grid, DevStatus* st)
     {
         Real nx, ny, nz;
-        if (PER) {  // j packs the image code
-            const int code = (int)((unsigned)j >> 24);
+        // j packs the image code; an unshifted image (almost every entry) takes
+        // the walled arithmetic (j is uniform over the group: no divergence)
+        const int code = PER ? (int)((unsigned)j >> 24) : IMG_NONE;
+        if (PER && code != IMG_NONE) {
             if (Tol<Real>::fp32) {
                 const float3 o = img_off(pi, pj, code, grid);
                 nx = (Real)o.x;
@@ -1041,14 +1043,21 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
     for (int f = gl; f < np; f += T) {
         const int src = sm.psrc[f];
         int oid = src;  // wall ids stay
-        if (per)  // the generator whose image the face faces; the cube's faces face the cell's own
-            oid = src < 0 ? (int)out_idx
-                          : (A.index_space == VT_INDEX_ORIGINAL ? __float_as_int(A.sorted[src & IMG_INDEX_MASK].w)
-                                                                : (src & IMG_INDEX_MASK));
-        else if (src >= 0 && sm.u.tail.first[f] >= 0 && A.index_space == VT_INDEX_ORIGINAL)
+        if (per) {  // the generator whose image the face faces; the cube's faces face the cell's own
+            if (src < 0)
+                oid = (int)out_idx;
+            else if (sm.u.tail.first[f] >= 0)
+                oid = A.index_space == VT_INDEX_ORIGINAL ? __float_as_int(A.sorted[src & IMG_INDEX_MASK].w)
+                                                         : (src & IMG_INDEX_MASK);
+        } else if (src >= 0 && sm.u.tail.first[f] >= 0 && A.index_space == VT_INDEX_ORIGINAL) {
             oid = __float_as_int(A.sorted[src].w);
+        }
         sm.u.tail.oid[f] = oid;
-        sm.u.tail.key[f] = ((src >= 0 || per) && sm.u.tail.first[f] >= 0 && sm.u.tail.area[f] > tau) ? oid : INT_MAX;
+        // periodic: ids may repeat (two images of one generator); the key
+        // id * PCAP + plane is unique and sorts the same (ids <= 2^24 - 2 and
+        // planes < PCAP <= 128 keep it below the INT_MAX sentinel)
+        const int key = per ? oid * PCAP + f : oid;
+        sm.u.tail.key[f] = ((src >= 0 || per) && sm.u.tail.first[f] >= 0 && sm.u.tail.area[f] > tau) ? key : INT_MAX;
     }
     __syncwarp(gmask);
     if (gl == 0) {
@@ -1070,15 +1079,8 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
         if (key == INT_MAX) continue;
         ++c;
         int rank = 0;
-        if (PER) {
-            for (int g2 = 0; g2 < np; ++g2) {  // equal keys (two images of one generator) by plane
-                const int k2 = sm.u.tail.key[g2];
-                rank += (k2 < key || (k2 == key && g2 < f)) ? 1 : 0;
-            }
-        } else {
-            for (int g2 = 0; g2 < np; ++g2) rank += sm.u.tail.key[g2] < key ? 1 : 0;
-        }
-        if (rank < REC_FACES) rnbr[rank] = key;
+        for (int g2 = 0; g2 < np; ++g2) rank += sm.u.tail.key[g2] < key ? 1 : 0;
+        if (rank < REC_FACES) rnbr[rank] = PER ? key / PCAP : key;
     }
     int nn_total = c;
 #pragma unroll
@@ -1382,7 +1384,9 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
             constexpr bool per = PER;
             for (int s = 0; status == 0; ++s) {
                 // the shell's segments, T at a time, candidates spread over the lanes
-                const int M = seg_per_row_t<PER>(grid, s);
+                const bool wrap = per && (ix - s < 0 || iy - s < 0 || iz - s < 0 || ix + s >= Gr || iy + s >= Gr ||
+                                          iz + s >= Gr);
+                const int M = wrap ? seg_per_row(grid, s) : 2;
                 const int nseg = M * (2 * s + 1) * (2 * s + 1);
 #ifdef VT_PROFILE
                 if (G.gl == 0) VT_PROF_ADD(16, 1);
@@ -1396,7 +1400,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST>())) k_cli
                     int sa = 0, sb = 0, sc = IMG_NONE;
                     const float r_out2 = 4.0f * (float)cell.R2 * (1.0f + 2e-4f);
                     if (e0 + G.gl < nseg) {
-                        if (per)
+                        if (wrap)
                             shell_segment_ball_p(e0 + G.gl, s, M, ix, iy, iz, grid, coff, pq, r_out2, r_in2, sa, sb,
                                                  sc);
                         else

@@ -274,16 +274,18 @@ __global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, 
         for (int s = 0;; ++s) {
             // the shell's segments, 32 at a time: lanes load segment bounds in
             // parallel, then the segments' candidates are spread over all lanes
-            const int M = seg_per_row_t<PER>(g, s);
+            // a periodic shell that stays inside the grid is walked like a walled one
+            const bool wrap = per && (ix - s < 0 || iy - s < 0 || iz - s < 0 || ix + s >= G || iy + s >= G || iz + s >= G);
+            const int M = wrap ? seg_per_row_outer(g, s) : 2;
             const int nseg = M * (2 * s + 1) * (2 * s + 1);
             for (int e0 = 0; e0 < nseg; e0 += 32) {
                 // once the list is full, only grid cells that reach into the
                 // ball of the current k-th distance can hold a better candidate
                 int sa = 0, sb = 0, sc = IMG_NONE;
                 if (e0 + lane < nseg) {
-                    if (per)
-                        shell_segment_ball_p(e0 + lane, s, M, ix, iy, iz, g, cell_off, pq,
-                                             count == k ? fminf(kd * (1.0f + 1e-5f), lim2) : lim2, -1.0f, sa, sb, sc);
+                    if (wrap)
+                        shell_segment_outer_p(e0 + lane, s, M, ix, iy, iz, g, cell_off, pq,
+                                              count == k ? fminf(kd * (1.0f + 1e-5f), lim2) : lim2, sa, sb, sc);
                     else if (count == k)
                         shell_segment_ball(e0 + lane, s, ix, iy, iz, g, cell_off, pq, kd * (1.0f + 1e-5f), -1.0f, sa,
                                            sb);

@@ -154,12 +154,13 @@ __global__ void __launch_bounds__(RANGE_BLOCK) k_range(const float4* __restrict_
         }
         constexpr bool per = PER;
         for (int s = 0; !over; ++s) {
-            const int M = seg_per_row_t<PER>(g, s);
+            const bool wrap = per && (ix - s < 0 || iy - s < 0 || iz - s < 0 || ix + s >= G || iy + s >= G || iz + s >= G);
+            const int M = wrap ? seg_per_row(g, s) : 2;
             const int nseg = M * (2 * s + 1) * (2 * s + 1);
             for (int e0 = 0; e0 < nseg && !over; e0 += 32) {
                 int sa = 0, sb = 0, sc = IMG_NONE;
                 if (e0 + lane < nseg) {
-                    if (per)
+                    if (wrap)
                         shell_segment_ball_p(e0 + lane, s, M, ix, iy, iz, g, cell_off, pq, r_out2, r_in2, sa, sb, sc);
                     else
                         shell_segment_ball(e0 + lane, s, ix, iy, iz, g, cell_off, pq, r_out2, r_in2, sa, sb);

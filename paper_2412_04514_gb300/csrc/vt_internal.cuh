@@ -198,10 +198,12 @@ __device__ __forceinline__ float img_d(float c, float q, int t, float lo, float 
 {
     return t == 0 ? c - q : (float)(((double)c - (double)q) + (double)t * ((double)hi - (double)lo));
 }
-// the same in double, every operation separately rounded: the exact key's coordinate
+// the same in double, every operation separately rounded: the exact key's
+// coordinate (t = 0 adds nothing: x + 0 = x, and the FP64 pipe is scarce)
 __device__ __forceinline__ double img_d64(float c, float q, int t, float lo, float hi)
 {
-    return __dadd_rn(__dsub_rn((double)c, (double)q), (double)t * __dsub_rn((double)hi, (double)lo));
+    const double d = __dsub_rn((double)c, (double)q);
+    return t == 0 ? d : __dadd_rn(d, (double)t * __dsub_rn((double)hi, (double)lo));
 }
 // compile-time forms for kernels instantiated per box kind (PER = periodic)
 template <bool PER>
@@ -250,7 +252,7 @@ __device__ __forceinline__ float3 img_off_t(float4 pq, float4 pc, int code, cons
 // the FP64 key of packed candidate jp (periodic: its image) from pq
 __device__ __forceinline__ double img_key64(float4 pq, const float4* __restrict__ sorted, int jp, const GridDesc& g)
 {
-    if (!g.periodic) return knn_d2_f64(pq, sorted[jp]);
+    if (!g.periodic || (int)((unsigned)jp >> 24) == IMG_NONE) return knn_d2_f64(pq, sorted[jp & (g.periodic ? IMG_INDEX_MASK : -1)]);
     const float4 pc = sorted[jp & IMG_INDEX_MASK];
     int tx, ty, tz;
     img_t((int)((unsigned)jp >> 24), tx, ty, tz);
@@ -276,10 +278,11 @@ __device__ __forceinline__ int seg_per_row(const GridDesc& g, int s)
     return 2 * (W <= g.G ? 2 : (W + g.G - 1) / g.G + 1);
 }
 
-template <bool PER>
-__device__ __forceinline__ int seg_per_row_t(const GridDesc& g, int s)
+// segments per row when no inner ball is skipped (the kNN): one per z-image piece
+__device__ __forceinline__ int seg_per_row_outer(const GridDesc& g, int s)
 {
-    return PER ? seg_per_row(g, s) : 2;
+    const int W = 2 * s + 1;
+    return W <= g.G ? 2 : (W + g.G - 1) / g.G + 1;
 }
 
 // |L| of a periodic box: no image farther than this can cut a cell
@@ -355,6 +358,55 @@ __device__ __forceinline__ void shell_segment_ball_p(int e, int s, int M, int ix
         if (piece != 0) return;
         const int z = half ? iz + s : iz - s;
         if (z < zlo || z > zhi || (z >= zi0 && z <= zi1)) return;
+        za = zb = z;
+        tz = floordiv(z, G);
+    }
+    if (za > zb || tz < -2 || tz > 2) return;
+    const int base = ((x - tx * G) * G + (y - ty * G)) * G - tz * G;
+    a = cell_off[base + za];
+    b = cell_off[base + zb + 1];
+    code = img_code(tx, ty, tz);
+}
+
+// The same without an inner ball (M = seg_per_row_outer segments per row):
+// a rim row's segments are its z-image pieces, an inner row's are its two
+// cells z = iz - s and z = iz + s.
+__device__ __forceinline__ void shell_segment_outer_p(int e, int s, int M, int ix, int iy, int iz, const GridDesc& g,
+                                                      const int32_t* __restrict__ cell_off, float4 q, float r_out2,
+                                                      int& a, int& b, int& code)
+{
+    const int G = g.G;
+    const int W = 2 * s + 1;
+    const int row = e / M, piece = e - (e / M) * M;
+    const int dx = row / W - s, dy = row - (row / W) * W - s;
+    const int x = ix + dx, y = iy + dy;
+    a = b = 0;
+    code = IMG_NONE;
+    const int tx = floordiv(x, G), ty = floordiv(y, G);
+    if (tx < -2 || tx > 2 || ty < -2 || ty > 2) return;
+    const float m = (float)g.margin;
+    const float cx = (float)g.cw[0], cy = (float)g.cw[1];
+    const float x0 = g.lo[0] + (float)x * cx - m, x1 = g.lo[0] + (float)(x + 1) * cx + m;
+    const float y0 = g.lo[1] + (float)y * cy - m, y1 = g.lo[1] + (float)(y + 1) * cy + m;
+    const float dxn = fmaxf(fmaxf(x0 - q.x, q.x - x1), 0.0f), dyn = fmaxf(fmaxf(y0 - q.y, q.y - y1), 0.0f);
+    const float dn2 = dxn * dxn + dyn * dyn;
+    if (dn2 > r_out2) return;
+    const float zr = sqrtf(r_out2 - dn2);
+    const float zmax = 8.0f * (float)G;
+    const int zlo = (int)floorf(fminf(fmaxf((q.z - zr - m - g.lo[2]) * g.scale[2] - 1e-3f, -zmax), zmax));
+    const int zhi = (int)floorf(fminf(fmaxf((q.z + zr + m - g.lo[2]) * g.scale[2] + 1e-3f, -zmax), zmax));
+    const bool rim = dx == -s || dx == s || dy == -s || dy == s;
+    int za, zb, tz;
+    if (rim) {
+        tz = floordiv(iz - s, G) + piece;
+        za = iz - s > zlo ? iz - s : zlo;
+        zb = iz + s < zhi ? iz + s : zhi;
+        za = za > tz * G ? za : tz * G;
+        zb = zb < tz * G + G - 1 ? zb : tz * G + G - 1;
+    } else {
+        if (piece > 1) return;
+        const int z = piece ? iz + s : iz - s;
+        if (z < zlo || z > zhi) return;
         za = zb = z;
         tz = floordiv(z, G);
     }
