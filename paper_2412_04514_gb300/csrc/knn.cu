@@ -233,8 +233,14 @@ struct WarpList64 {
     }
 };
 
+// resident blocks per SM the one-row lists are compiled for: 4 blocks of 256
+// threads (64 registers, no spills) hide more of the walk's load latency than
+// 3 (measured: kNN 7.07 vs 7.74 ms on the 1M mixed cloud)
+#ifndef VT_KNN_MINB
+#define VT_KNN_MINB 4
+#endif
 template <typename Real, int KPL, bool PER>
-__global__ void __launch_bounds__(256) k_knn(const float4* __restrict__ sorted, const int32_t* __restrict__ cell_off0,
+__global__ void __launch_bounds__(256, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn(const float4* __restrict__ sorted, const int32_t* __restrict__ cell_off0,
                                              const __grid_constant__ GridDesc g0, const GridDesc* __restrict__ sets,
                                              const int32_t* __restrict__ set_of, const int32_t* __restrict__ queries,
                                              int64_t nq_host, const int32_t* __restrict__ nq_dev,
