@@ -14,6 +14,14 @@
  *
  * Conventions (every entry point):
  *  - Every array argument is a DEVICE pointer unless its comment says host.
+ *    "Device" means memory device code can use at that address: device or
+ *    managed allocations, or pinned host memory (cudaHostAlloc /
+ *    cudaHostRegister, mapped at the same address under unified addressing),
+ *    so outputs can be written straight into host memory. vt_tessellate,
+ *    vt_tessellate_batch and vt_emit check their points, workspace and output
+ *    pointers first (cudaPointerGetAttributes, skipped while the stream is
+ *    being captured) and return VT_ERR_INVALID_ARG for any other memory
+ *    (pageable host memory) without launching a kernel.
  *    Buffers are owned by the caller; the library never allocates, frees or
  *    keeps a pointer after a call returns.
  *  - Scratch memory is a caller-allocated device workspace of at least

@@ -83,6 +83,44 @@ int cuda_fail(cudaError_t e, const char* what)
     return fail(VT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// true when device code can use p as it is: device or managed memory, or
+// pinned host memory (mapped at the same address under unified addressing);
+// NULL passes (optional buffers). A kernel is never launched on a pointer
+// that fails, so a pageable host buffer is an argument error, not a fault.
+bool device_accessible(const void* p)
+{
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.devicePointer == p;
+}
+
+// the caller's buffers of a call (skipped while the stream is being captured:
+// the same buffers were checked by the uncaptured calls before)
+int check_buffers(void* stream, const void* pts, const void* ws, const vt_cells_out* out,
+                  const void* extra0 = nullptr, const void* extra1 = nullptr)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) (void)cudaGetLastError();
+    if (cs != cudaStreamCaptureStatusNone) return VT_OK;
+    if (!device_accessible(pts)) return fail(VT_ERR_INVALID_ARG, "pts is not device-accessible memory");
+    if (!device_accessible(ws)) return fail(VT_ERR_INVALID_ARG, "the workspace is not device-accessible memory");
+    if (!device_accessible(extra0) || !device_accessible(extra1))
+        return fail(VT_ERR_INVALID_ARG, "the batch plan and set offsets must be device-accessible memory");
+    if (out) {
+        const void* ps[] = {out->vol, out->cen, out->m2, out->nbr_off, out->nbr, out->vtx_off, out->vtx,
+                            out->face_off, out->face_nbr, out->face_vtx_off, out->face_vtx, out->perm};
+        for (const void* q : ps)
+            if (!device_accessible(q))
+                return fail(VT_ERR_INVALID_ARG,
+                            "an output buffer is not device-accessible memory (device, managed or pinned host)");
+    }
+    return VT_OK;
+}
+
 }  // namespace
 
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
@@ -911,6 +949,8 @@ int vt_emit(int64_t n, const vt_params* p, vt_cells_out* out, void* ws, size_t w
     int e = make_ctx(p, n, ws, ws_bytes, stream, c);
     if (e) return e;
     if (!out) return fail(VT_ERR_INVALID_ARG, "out is NULL");
+    e = check_buffers(stream, nullptr, ws, out);
+    if (e) return e;
     return emit_outputs(c, p, out);
 }
 
@@ -919,6 +959,8 @@ int vt_tessellate(const float* pts, int64_t n, const vt_params* p, vt_cells_out*
 {
     Ctx c;
     int e = make_ctx(p, n, ws, ws_bytes, stream, c);
+    if (e) return e;
+    e = check_buffers(stream, pts, ws, out);
     if (e) return e;
     return tessellate_run(c, pts, n, p, out, stats);
 }
@@ -967,6 +1009,8 @@ int vt_tessellate_batch(const float* pts, int64_t n_total, const vt_set_desc* pl
         return fail(VT_ERR_INVALID_ARG, "a batch needs its device plan, set offsets and cell count");
     Ctx c;
     int e = make_ctx(p, n_total, ws, ws_bytes, stream, c, total_cells, true);
+    if (e) return e;
+    e = check_buffers(stream, pts, ws, out, plan, set_off);
     if (e) return e;
     c.sets = reinterpret_cast<const GridDesc*>(plan);
     c.set_off = set_off;

@@ -116,7 +116,7 @@ def size_bucket(n: int) -> int:
 
 def cache_key(params: Params, n: int, cls: int) -> str:
     emit = "+".join(sorted(params.emit))
-    flags = "nosync" if params.no_sync else "sync"
+    flags = ("nosync" if params.no_sync else "sync") + ("+periodic" if params.periodic else "")
     return f"{params.precision}|{emit}|{flags}|n4^{size_bucket(n)}|c{cls}"
 
 

@@ -64,6 +64,8 @@ def test_params_from_args():
     assert (p.k0, p.k_max, p.grid_density, p.threads_per_cell) == (8, 64, 3.0, 16)
     assert p.index_space == "sorted"
     assert p.box_lo == (-1.0, -2.0, -3.0) and p.box_hi == (1.0, 2.0, 3.0)
+    assert not p.periodic
+    assert cli.params_from_args(cli.parser().parse_args(["i", "-o", "o.npz", "--periodic"])).periodic
     with pytest.raises(ValueError, match="unknown output"):
         cli.params_from_args(cli.parser().parse_args(["i", "-o", "o.npz", "--emit", "nbr,area"]))
     with pytest.raises(SystemExit):

@@ -401,3 +401,20 @@ def test_sparse_cells_next_to_a_dense_clump_fp32(clump_cloud):
     pts, want = clump_cloud
     cells = vt.tessellate(dev(pts), vt.Params(precision="fp32"))
     check_fp32(np_(cells.vol), np_(cells.cen), csr_lists(np_(cells.nbr_off), np_(cells.nbr)), want)
+
+
+def test_host_outputs_written_directly_equal_device_outputs():
+    # the neighbour and geometry arrays written by the emit kernel straight
+    # into pinned host memory are the same bytes as the device-emitted copies
+    pts = W.mixed(30_000, 33, n_clumps=20)
+    p = vt.Params(precision="fp32", emit=("nbr", "vol", "cen", "m2", "geom"))
+    direct = vt.tessellate_host(pts, p, direct=True)
+    copied = vt.tessellate_host(pts, p, direct=False)
+    for name in ("vol", "cen", "m2", "nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx_off",
+                 "face_vtx"):
+        a, b = getattr(direct, name), getattr(copied, name)
+        assert not a.is_cuda and not b.is_cuda
+        assert torch.equal(a, b), name
+    host = vt.tessellate(dev(pts), p, host_csr=True)
+    assert not host.nbr.is_cuda and host.nbr.is_pinned() and host.vol.is_cuda
+    assert torch.equal(host.nbr, copied.nbr) and torch.equal(host.vol.cpu(), copied.vol)

@@ -96,6 +96,9 @@ def test_cache_round_trip(tmp_path):
     assert got.precision == "fp32" and got.emit == prm.emit
     assert T.lookup(path, prm, 1 << 20, 3, "other device") is None
     assert T.lookup(path, prm, 1 << 16, 3, "dev") is None  # other size bucket
+    per = Params(precision="fp32", periodic=True)
+    assert T.cache_key(per, 1 << 20, 3) == "fp32|cen+nbr+vol|sync+periodic|n4^10|c3"
+    assert T.lookup(path, per, 1 << 20, 3, "dev") is None  # a periodic box is tuned on its own
     with open(path, "w") as f:
         json.dump({"version": 99}, f)
     with pytest.raises(ValueError):
