@@ -308,7 +308,12 @@ def run_gpu(args, rank: int, world: int, local: int):
     e2e_ms = []
     h2d = host.numel() * 4
     d2h = 0
+    out = None
     for i in range(args.warmup + args.steps if not args.no_e2e else 0):
+        # a streaming caller hands each step's result on before the next call:
+        # the pinned output buffers then return to torch's cache and are reused
+        # (keeping the previous result alive makes a step pin 1.3 GB afresh)
+        out = None
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -328,6 +333,7 @@ def run_gpu(args, rank: int, world: int, local: int):
     # roofline of the dominant stage (the clipper), from the live event times
     stage = {k: statistics.mean(s[k] for s in st32) for k in ("ms_grid", "ms_knn", "ms_clip", "ms_emit")}
     peaks = _peaks()
+    probe32, probe64 = vt.probe_fma("fp32"), vt.probe_fma("fp64")  # measured FMA rates (after the timed region)
     cpu = None
     errors = None
     if world == 1 and not args.no_cpu_baseline:
@@ -346,6 +352,8 @@ def run_gpu(args, rank: int, world: int, local: int):
         "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None if periodic else _clip_traffic(n),
         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (unit counts and max SM clock)",
+        "peak_probe": {"fp32_tflops": probe32, "fp64_tflops": probe64,
+                       "source": "vt_probe_fma: measured float32 / float64 FMA throughput of this GPU"},
         "units": f"{n} validated cells x {flops_per_cell:.0f} algorithmic FP32 flops/cell over {clip_launches:.1f} "
                  f"clip launches",
         "stage_ms": stage,

@@ -458,6 +458,13 @@ VT_API int vt_moments_adjoint(const float* pts, int64_t n, const vt_cells_out* c
  * returns VT_OK, VT_ERR_INVALID_ARG (bad point) or VT_ERR_DUPLICATE_POINTS. */
 VT_API int vt_read_status(void* ws, size_t ws_bytes, void* stream);
 
+/* Measured fused multiply-add throughput of the current device (blocking on
+ * `stream`): precision VT_FP32_RECHECK times float32 FMAs, VT_FP64 float64
+ * ones (eight independent chains per thread, eight blocks of 256 threads per
+ * SM, CUDA events; about 5 ms each on a GB300). *tflops receives the rate in
+ * TFLOP/s counting an FMA as 2 flops: the measured peak of ALU-bound rooflines. */
+VT_API int vt_probe_fma(int precision, double* tflops, void* stream);
+
 /* After a VT_FLAG_NO_SYNC call (or any call) on workspace ws (blocking on
  * `stream`): fills the device-counted fields of *stats (fp64_rechecks,
  * capacity_retries, precision_retries, unvalidated, clip_events; other fields

@@ -44,7 +44,7 @@ STATUS_NAMES = {
 EXPORTS = [
     "vt_params_default", "vt_grid_resolution", "vt_workspace_size", "vt_grid_build", "vt_knn", "vt_clip_cells",
     "vt_emit", "vt_tessellate", "vt_read_status", "vt_last_error", "vt_launch_count", "vt_version",
-    "vt_grid_build_static", "vt_moments_adjoint", "vt_batch_plan", "vt_batch_workspace_size",
+    "vt_grid_build_static", "vt_moments_adjoint", "vt_probe_fma", "vt_batch_plan", "vt_batch_workspace_size",
     "vt_tessellate_batch", "vt_read_stats", "vt_cluster_index", "vt_cluster_class", "vt_tune_space_default",
     "vt_autotune_workspace_size", "vt_autotune", "vt_autotune_batch_workspace_size", "vt_autotune_batch",
 ]
@@ -245,6 +245,8 @@ def load() -> ctypes.CDLL:
         L.vt_grid_build_static.restype = I
         L.vt_moments_adjoint.argtypes = [P, I64, po, P, P, P, pp, P, P]
         L.vt_moments_adjoint.restype = I
+        L.vt_probe_fma.argtypes = [I, ctypes.POINTER(ctypes.c_double), P]
+        L.vt_probe_fma.restype = I
         ps = ctypes.POINTER(VtStats)
         L.vt_batch_plan.argtypes = [P, I, pp, P, P, ctypes.POINTER(I64)]
         L.vt_batch_plan.restype = I

@@ -525,6 +525,14 @@ def emit(n: int, params: Params, workspace: Workspace, guess: dict | None = None
     return cells
 
 
+def probe_fma(precision: str = "fp32") -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (vt_probe_fma)."""
+    out = ctypes.c_double()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    L.check(L.load().vt_probe_fma(_PREC[precision], ctypes.byref(out), _stream(dev)))
+    return float(out.value)
+
+
 def launch_count() -> int:
     return int(L.load().vt_launch_count())
 

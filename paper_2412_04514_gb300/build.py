@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvt.so")
-SOURCES = ["scan.cu", "grid.cu", "knn.cu", "clip_f32.cu", "clip_f64.cu", "clip_robust.cu", "emit.cu", "vt_api.cu", "grid_static.cu", "adjoint.cu", "tune.cu", "range.cu", "clip_big.cu"]
+SOURCES = ["scan.cu", "grid.cu", "knn.cu", "clip_f32.cu", "clip_f64.cu", "clip_robust.cu", "emit.cu", "vt_api.cu", "grid_static.cu", "adjoint.cu", "tune.cu", "range.cu", "clip_big.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

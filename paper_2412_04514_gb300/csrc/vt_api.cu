@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "vt_internal.cuh"
 
 namespace vt {
@@ -235,9 +237,12 @@ constexpr int ROBUST_EXH_K = 128;
 
 
 // CUDA-event timing of kernel groups on the call's stream (VT_FLAG_STAGE_TIMES)
+// CUDA-event stage timer (VT_FLAG_STAGE_TIMES); every stage is also an NVTX
+// range, visible to any profiler that records NVTX (free when none does)
 struct StageTimer {
     enum { GRID = 0, KNN = 1, CLIP = 2, EMIT = 3 };
     bool on = false;
+    int nvtx_depth = 0;
     cudaStream_t s = nullptr;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
     std::vector<int> clip_pass;  // pass index of each CLIP event pair
@@ -245,6 +250,9 @@ struct StageTimer {
     int open_stage = -1;
     void begin(int stage)
     {
+        static const char* const names[4] = {"vt grid sort", "vt kNN / range lists", "vt clip", "vt emit"};
+        nvtxRangePushA(names[stage]);
+        ++nvtx_depth;
         if (!on) return;
         cudaEvent_t a, b;
         cudaEventCreate(&a);
@@ -264,6 +272,10 @@ struct StageTimer {
     }
     void end()
     {
+        if (nvtx_depth > 0) {
+            nvtxRangePop();
+            --nvtx_depth;
+        }
         if (!on || open_stage < 0) return;
         cudaEventRecord(ev[open_stage].back().second, s);
         open_stage = -1;
