@@ -7,6 +7,8 @@ Tolerances (from the FP64 form's rounding and the stated FP32 target):
     neighbour sets equal except faces the oracle measures below 1e-6 V^(2/3)
     (a face that small is below float32 resolution of the cell).
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -418,3 +420,31 @@ def test_host_outputs_written_directly_equal_device_outputs():
     host = vt.tessellate(dev(pts), p, host_csr=True)
     assert not host.nbr.is_cuda and host.nbr.is_pinned() and host.vol.is_cuda
     assert torch.equal(host.nbr, copied.nbr) and torch.equal(host.vol.cpu(), copied.vol)
+
+
+def test_pageable_host_outputs_are_refused_before_any_launch():
+    # a plain (pageable) host array is not memory device code can use on every
+    # system: the library checks the output pointers first and returns an
+    # argument error without launching; where the system does map such memory
+    # for the device, the call must give the same cells as device outputs
+    pts = W.uniform(2000, 34)
+    d = dev(pts)
+    p = vt.Params(precision="fp64", emit=("nbr", "vol"))
+    want = vt.tessellate(d, p)
+    lib = L.load()
+    ws = vt.Workspace(p, len(pts))
+    vol = torch.zeros(len(pts), dtype=torch.float64)  # pageable host memory
+    nbr_off = torch.zeros(len(pts) + 1, dtype=torch.int64, device="cuda")
+    nbr = torch.zeros(40 * len(pts), dtype=torch.int32, device="cuda")
+    o = L.VtCellsOut()
+    o.vol, o.nbr_off, o.nbr, o.nbr_cap = vol.data_ptr(), nbr_off.data_ptr(), nbr.data_ptr(), nbr.numel()
+    st = L.VtStats()
+    code = lib.vt_tessellate(d.data_ptr(), len(pts), ctypes.byref(p.c()), ctypes.byref(o), ctypes.byref(st),
+                             ws.buf.data_ptr(), ws.buf.numel(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    if code == L.VT_ERR_INVALID_ARG:
+        assert "device-accessible" in lib.vt_last_error().decode()
+        assert torch.count_nonzero(vol) == 0
+    else:
+        assert code == L.VT_OK
+        assert torch.equal(vol, want.vol.cpu())
