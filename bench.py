@@ -4,7 +4,7 @@ One step = one whole tessellation (grid sort, kNN, clipping with every
 re-queue pass, emit of neighbours + full geometry + volume + centroid) of the
 1,048,576-point half-uniform / half-clustered cloud, inputs resident in HBM.
 
-Prints ONE JSON line (rank 0). See the design doc for the roofline figures.
+Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload mixed-1m|mixed-8m]
   python bench.py --impl reference ...   # the FP64 CPU oracle as the reference arm

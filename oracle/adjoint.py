@@ -6,7 +6,7 @@ generator p_k, for upstream gradients (gV_i, gC_i, gM_i):
 
     grad_k = sum_i gV_i dV_i/dp_k + gC_i . dc_i/dp_k + gM_i dM2_i/dp_k.
 
-Derivation (Reynolds transport; the paper gives no formula, see DESIGN.md).
+Derivation (Reynolds transport; the paper gives no formula).
 The face f_ij of cell i lies on the bisector n.x = (|p_j|^2 - |p_i|^2)/2,
 n = p_j - p_i, d = |n|. Moving p_j moves the face along its outward normal
 with speed (p_j - x).dp_j / d; moving p_i, with speed (x - p_i).dp_i / d.

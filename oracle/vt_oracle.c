@@ -27,7 +27,7 @@
  * (build with -ffp-contract=off) so results are identical on x86-64 and
  * aarch64 hosts.
  *
- * Readings where the paper is silent (each one is listed in the design doc):
+ * Readings where the paper is silent:
  *  - the bounding box is the non-periodic domain box (walls are clip planes);
  *  - the cell is computed in the local frame of p_i (coordinates p - p_i);
  *  - kNN order is (d2, index) with d2 = ((dx*dx + dy*dy) + dz*dz) in double
