@@ -58,7 +58,9 @@ namespace vt {
 // section clocks and event counts of the clip kernels (diagnostic builds only):
 // [8 * EXH + i], i = 0 cells, 1 setup cycles, 2 list/walk cycles, 3 clip
 // cycles, 4 clip calls, 5 cuts, 6 finish cycles, 7 walk candidates; walk:
-// 16 shells, 17 segment groups, 18 candidate batches, 19 raw candidates
+// 16 shells, 17 segment groups, 18 candidate batches, 19 raw candidates,
+// 20 segment cycles, 21 candidate-test cycles, 22 survivor cycles (clips
+// included), 23 batches without a survivor
 static __device__ unsigned long long g_vt_prof[32];  // one copy per translation unit
 #define VT_PROF_ADD(i, v) atomicAdd(&g_vt_prof[(i)], (unsigned long long)(v))
 #else
@@ -1159,6 +1161,9 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP, PER>& c
                                                 const GridDesc& grid, bool valid, int jj, int code, double last_d2,
                                                 int last_orig, float* lo3, float* hi3)
 {
+#ifdef VT_PROFILE
+    const long long tb0 = clock64();
+#endif
     const float4 pq = cell.pi;
     float4 pc = make_float4(0.f, 0.f, 0.f, 0.f);
     bool need = false;
@@ -1186,6 +1191,9 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP, PER>& c
     unsigned mm = G.ballot(need);
 #ifdef VT_PROFILE
     if (G.gl == 0) VT_PROF_ADD(8 + 7, __popc(mm));
+    if (G.gl == 0) VT_PROF_ADD(21, clock64() - tb0);
+    if (G.gl == 0 && mm == 0) VT_PROF_ADD(23, 1);
+    const long long tb1 = clock64();
 #endif
     while (mm) {
         const int src = __ffs(mm) - 1;
@@ -1220,6 +1228,9 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP, PER>& c
         if (r == CLIP_INCONSISTENT) return END_INCONSISTENT;
         if (r == CLIP_CUT) cell.bbox(G, lo3, hi3);
     }
+#ifdef VT_PROFILE
+    if (G.gl == 0) VT_PROF_ADD(22, clock64() - tb1);
+#endif
     return 0;
 }
 
@@ -1400,6 +1411,9 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
 #ifdef VT_PROFILE
                     if (G.gl == 0) VT_PROF_ADD(17, 1);
 #endif
+#ifdef VT_PROFILE
+                    const long long ts0 = clock64();
+#endif
                     // only grid cells that reach into the ball of radius 2R and are
                     // not wholly inside the ball the list already covered
                     int sa = 0, sb = 0, sc = IMG_NONE;
@@ -1417,6 +1431,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
                     const int incl = start + len;
 #ifdef VT_PROFILE
                     if (G.gl == 0) VT_PROF_ADD(19, total);
+                    if (G.gl == 0) VT_PROF_ADD(20, clock64() - ts0);
 #endif
                     for (int c0 = 0; c0 < total && status == 0; c0 += T) {
 #ifdef VT_PROFILE
