@@ -257,6 +257,79 @@ def tessellate_host(points, params: Params | None = None, device="cuda", direct:
     return out
 
 
+_OUT_NAMES = ("vol", "cen", "m2", "nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx_off",
+              "face_vtx", "perm")
+
+
+def tessellate_stream(clouds, params: Params | None = None, device="cuda"):
+    """Pipelined end-to-end tessellation of a sequence of host point clouds.
+
+    Yields, in order, one :class:`Cells` in host memory per cloud of
+    ``clouds`` (an iterable of float32 host arrays or tensors of shape (n, 3)).
+    Three CUDA streams overlap the work: while cloud i is tessellated, cloud
+    i+1 is copied to the device and the outputs of cloud i-1 are copied back
+    (the copy engines run beside the SMs), so a long sequence costs about the
+    tessellation time per cloud instead of tessellation plus both copies. Every
+    cloud still makes its own host-to-device and device-to-host round trip.
+    The workspace is reused while the clouds keep their size."""
+    params = params or Params()
+    dev = torch.device(device)
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    s_in, s_cmp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def stage_in(points):
+        t = torch.as_tensor(points, dtype=torch.float32)
+        if not t.is_pinned():
+            t = t.pin_memory()
+        with torch.cuda.stream(s_in):
+            d = t.to(dev, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s_in)
+        return d, ev, t
+
+    it = iter(clouds)
+    first = next(it, None)
+    if first is None:
+        return
+    nxt = stage_in(first)
+    ws = None
+    pending = None  # (host cells, copy-back event) of the previous cloud
+    while nxt is not None:
+        d, ev_in, _keep = nxt
+        follow = next(it, None)
+        # the next cloud's copy in is queued before this cloud's compute starts
+        nxt = stage_in(follow) if follow is not None else None
+        with torch.cuda.stream(s_cmp):
+            s_cmp.wait_event(ev_in)
+            d.record_stream(s_cmp)
+            n = d.shape[0]
+            if ws is None or not ws.fits(params, n):
+                ws = Workspace(params, n, dev)
+            cells = tessellate(d, params, workspace=ws)
+            done = torch.cuda.Event()
+            done.record(s_cmp)
+        out = Cells(stats=cells.stats)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(done)
+            for name in _OUT_NAMES:
+                v = getattr(cells, name)
+                if v is None:
+                    continue
+                v.record_stream(s_out)  # the caching allocator keeps it until the copy is done
+                h = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+                h.copy_(v, non_blocking=True)
+                setattr(out, name, h)
+            copied = torch.cuda.Event()
+            copied.record(s_out)
+        if pending is not None:
+            pending[1].synchronize()
+            yield pending[0]
+        pending = (out, copied)
+    pending[1].synchronize()
+    yield pending[0]
+
+
 # ---------------------------------------------------------------------------
 # batches of independent point sets (vt_batch_plan, vt_tessellate_batch)
 # ---------------------------------------------------------------------------

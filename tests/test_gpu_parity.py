@@ -448,3 +448,19 @@ def test_pageable_host_outputs_are_refused_before_any_launch():
     else:
         assert code == L.VT_OK
         assert torch.equal(vol, want.vol.cpu())
+
+
+def test_tessellate_stream_equals_one_call_at_a_time():
+    # the pipelined stream (copy in / tessellate / copy back on three streams)
+    # yields, in order, the cells of every cloud, bit-identical to single calls;
+    # a change of cloud size re-sizes the workspace on the way
+    clouds = [W.mixed(20_000, 35, n_clumps=10), W.uniform(20_000, 36), W.uniform(5_000, 37),
+              W.mixed(20_000, 38, n_clumps=4)]
+    p = vt.Params(precision="fp32", emit=("nbr", "vol", "cen", "geom"))
+    got = list(vt.tessellate_stream(clouds, p))
+    assert len(got) == len(clouds)
+    for cloud, g in zip(clouds, got):
+        want = vt.tessellate_host(cloud, p)
+        for name in ("vol", "cen", "nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx"):
+            assert torch.equal(getattr(g, name), getattr(want, name)), name
+    assert list(vt.tessellate_stream([], p)) == []
