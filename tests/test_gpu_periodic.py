@@ -242,3 +242,19 @@ def test_periodic_rejects_an_elongated_box():
     pts = (W.uniform(100, 98) * np.float32(0.5)).astype(np.float32)
     with pytest.raises(L.VtError):
         run(pts, "fp32", hi=(1.0, 1.0, 0.5))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_periodic_lattice_on_the_box_faces(prec):
+    # points exactly on the faces and on grid-cell boundaries (a / m, a = 0..m-1):
+    # images land exactly on the other faces, ties everywhere; every cell is a cube
+    m = 8
+    a = np.arange(m) / m
+    pts = np.array(np.meshgrid(a, a, a, indexing="ij")).reshape(3, -1).T.astype(np.float32)
+    want = oracle.tessellate(pts, periodic=True)
+    np.testing.assert_allclose(want["vol"], 1.0 / m ** 3, rtol=1e-13)
+    cells = run(pts, prec, grid_res=m)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(np_(cells.vol), 1.0 / m ** 3, rtol=tol)
+    np.testing.assert_allclose(np_(cells.cen), pts.astype(np.float64), atol=tol / m)
+    assert lists(np_(cells.nbr_off), np_(cells.nbr)) == lists(want["nbr_off"], want["nbr"])
