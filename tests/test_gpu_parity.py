@@ -464,3 +464,30 @@ def test_tessellate_stream_equals_one_call_at_a_time():
         for name in ("vol", "cen", "nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx"):
             assert torch.equal(getattr(g, name), getattr(want, name)), name
     assert list(vt.tessellate_stream([], p)) == []
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", ["plane", "line"])
+def test_coplanar_and_collinear_generators(prec, shape):
+    # every cell reaches the box walls (prisms over the plane's 2D cells, or
+    # slabs along the line), so every security radius is large and the cells
+    # are finished by the exhaustive walk
+    rng = np.random.default_rng(39)
+    n = 1500 if shape == "plane" else 300
+    pts = np.full((n, 3), 0.5, dtype=np.float64)
+    pts[:, 0] = rng.random(n)
+    if shape == "plane":
+        pts[:, 1] = rng.random(n)
+    pts = np.unique(pts.astype(np.float32), axis=0)
+    want = oracle.tessellate(pts)
+    cells = vt.tessellate(dev(pts), vt.Params(precision=prec, emit=("nbr", "vol", "cen")))
+    assert cells.stats["status"] == "VT_OK"
+    assert abs(np_(cells.vol).sum() - 1.0) < (1e-12 if prec == "fp64" else 1e-5)
+    if prec == "fp64":
+        np.testing.assert_allclose(np_(cells.vol), want["vol"], rtol=1e-12)
+        assert np.array_equal(np_(cells.nbr_off), want["nbr_off"]) and np.array_equal(np_(cells.nbr), want["nbr"])
+    else:
+        check_fp32(np_(cells.vol), np_(cells.cen), csr_lists(np_(cells.nbr_off), np_(cells.nbr)), want)
+    if shape == "line":  # slabs: two neighbours each, one at the ends
+        counts = np.diff(np_(cells.nbr_off))
+        assert counts.max() == 2 and (counts == 1).sum() == 2
