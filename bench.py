@@ -375,6 +375,30 @@ def run_gpu(args, rank: int, world: int, local: int):
         "stage_ms": stage,
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
     }
+    # every stage against its own roofline (stage times of the timed FP32 steps)
+    hbm = peaks.get("hbm_gbs") or 6764.0
+    csr_bytes = sum(getattr(cells, f).numel() * getattr(cells, f).element_size()
+                    for f in ("vol", "cen", "nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx_off",
+                              "face_vtx") if getattr(cells, f) is not None)
+    kpre = 2 * args.k0 if 2 * args.k0 <= args.k_max else args.k0
+
+    def hbm_line(nbytes, ms, what):
+        gbs = nbytes / (ms / 1e3) / 1e9
+        return {"bound": "hbm", "bytes": int(nbytes), "ms": ms, "achieved_gbs": gbs, "peak_gbs": hbm,
+                "frac": gbs / hbm, "bytes_are": what}
+
+    stage_rooflines = {
+        "grid_sort": hbm_line(52 * n, stage["ms_grid"], "52 B per point: points read twice, cell id and ticket "
+                                                         "written and read, sorted float4 and permutation written"),
+        "knn_and_range": hbm_line(n * (16 + 8 * kpre), stage["ms_knn"],
+                                  f"the {kpre}-entry lists: 16 B query read + {kpre} x (4 B index + 4 B key) written "
+                                  "(the stage also holds the range-list kernels, whose I/O is not counted; the "
+                                  "stage is ALU- and latency-bound)"),
+        "clip": {"bound": "alu", "achieved_tflops": achieved, "peak_tflops": FP32_PEAK_TFLOPS,
+                 "frac": achieved / FP32_PEAK_TFLOPS, "ms": stage["ms_clip"]},
+        "emit": hbm_line(2 * csr_bytes + 16 * n, stage["ms_emit"],
+                         "the per-cell records read (the outputs' bytes + a 16 B header) and the outputs written"),
+    }
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": len(ms32),
         "warmup": args.warmup, "ms_per_step": tot32 / len(ms32), "higher_is_better": True, "scaling": "weak",
@@ -395,6 +419,7 @@ def run_gpu(args, rank: int, world: int, local: int):
             "serial": {"value": e2e_value, "ms_per_step": e2e_tot / len(e2e_ms),
                        "api": "one tessellate_host call after another"}},
         "roofline": roofline,
+        "stage_rooflines": stage_rooflines,
         "cpu_baseline": None if cpu is None else {"value": cpu["value"], "unit": "cells/s", "cores": cpu["cores"],
                                                   "kind": "oracle", "sample": cpu["sample"]},
         "gpu_launches": int(launches32),

@@ -9,6 +9,8 @@
 //                    ranks are arbitrary): small cells by one thread,
 //   k_grid_fix_big : large cells by a block-wide bitonic sort in place
 //   k_grid_perm    : perm[sorted index] = original index
+#include <limits.h>
+
 #include "vt_internal.cuh"
 
 namespace vt {
@@ -87,13 +89,21 @@ __global__ void k_grid_fix(float4* __restrict__ sorted, const int32_t* __restric
     }
 }
 
-// one block per large grid cell: in-place bitonic sort of sorted[a, a+m) by
-// original index. The network pads virtually to a power of two with +inf
-// keys; every comparator orders ascending (first step of each merge compares
-// mirrored pairs), so a comparator touching the padding is a no-op.
-__global__ void k_grid_fix_big(float4* __restrict__ sorted, const int32_t* __restrict__ cell_off,
-                               const int32_t* __restrict__ big, const DevStatus* st)
+// keys a block sorts in shared memory (48 KB); larger cells sort in place
+constexpr int FIX_SMEM_KEYS = 12288;
+
+// one block per large grid cell: bitonic sort of sorted[a, a+m) by original
+// index. Every comparator orders ascending (first step of each merge compares
+// mirrored pairs). A cell of up to FIX_SMEM_KEYS points sorts its keys (the
+// original indices) in shared memory, padded to a power of two with INT_MAX,
+// and rebuilds its entries from the input points; a larger cell runs the same
+// network in place in global memory, padding virtually (a comparator touching
+// the padding is a no-op).
+__global__ void __launch_bounds__(512) k_grid_fix_big(const float* __restrict__ pts, float4* __restrict__ sorted,
+                                                      const int32_t* __restrict__ cell_off,
+                                                      const int32_t* __restrict__ big, const DevStatus* st)
 {
+    __shared__ int32_t key[FIX_SMEM_KEYS];
     const int nbig = st->n_big_cells;
     for (int b = blockIdx.x; b < nbig; b += gridDim.x) {
         const int c = big[b];
@@ -101,6 +111,35 @@ __global__ void k_grid_fix_big(float4* __restrict__ sorted, const int32_t* __res
         float4* s = sorted + a;
         int P = 1;
         while (P < m) P <<= 1;
+        if (P <= FIX_SMEM_KEYS) {
+            for (int t = threadIdx.x; t < P; t += blockDim.x) key[t] = t < m ? __float_as_int(s[t].w) : INT_MAX;
+            __syncthreads();
+            for (int size = 2; size <= P; size <<= 1) {
+                const int half = size >> 1;
+                for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {  // mirrored step
+                    const int blk = t / half, off = t % half;
+                    const int i = blk * size + off, j = blk * size + size - 1 - off;
+                    const int u = key[i], v = key[j];
+                    if (u > v) { key[i] = v; key[j] = u; }
+                }
+                __syncthreads();
+                for (int h = half >> 1; h >= 1; h >>= 1) {  // half-cleaners
+                    for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                        const int blk = t / h, off = t % h;
+                        const int i = blk * 2 * h + off, j = i + h;
+                        const int u = key[i], v = key[j];
+                        if (u > v) { key[i] = v; key[j] = u; }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int64_t o = key[t];
+                s[t] = make_float4(pts[3 * o], pts[3 * o + 1], pts[3 * o + 2], __int_as_float((int)o));
+            }
+            __syncthreads();  // the next cell reuses key[]
+            continue;
+        }
         for (int size = 2; size <= P; size <<= 1) {
             const int half = size >> 1;
             for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {  // mirrored step
@@ -198,7 +237,7 @@ cudaError_t launch_grid_build(const float* pts, int64_t n, const GridDesc& g, fl
     if (n == 0) return cudaGetLastError();
     k_grid_scatter<<<blocks_for(n, 256), 256, 0, s>>>(pts, n, cid, ticket, cell_off, sorted);
     k_grid_fix<<<blocks_for(g3, 128), 128, 0, s>>>(sorted, cell_off, g3, big, st);
-    k_grid_fix_big<<<152 * 2, 512, 0, s>>>(sorted, cell_off, big, st);
+    k_grid_fix_big<<<152 * 2, 512, 0, s>>>(pts, sorted, cell_off, big, st);
     k_grid_perm<<<blocks_for(n, 256), 256, 0, s>>>(sorted, n, perm, set_off, nsets, set_of);
     count_launch(4);
     return cudaGetLastError();
