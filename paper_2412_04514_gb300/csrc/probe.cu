@@ -35,14 +35,18 @@ int probe(int iters, double* tflops, cudaStream_t s)
         return set_error(VT_ERR_CUDA, "device query failed");
     const unsigned blocks = (unsigned)sms * 8u;
     cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
+    if (cudaEventCreate(&a) != cudaSuccess) return set_error(VT_ERR_CUDA, "event creation failed");
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return set_error(VT_ERR_CUDA, "event creation failed");
+    }
     k_fma<Real><<<blocks, 256, 0, s>>>((Real)1, iters / 8, nullptr);  // warm-up
     cudaEventRecord(a, s);
     k_fma<Real><<<blocks, 256, 0, s>>>((Real)1, iters, nullptr);
     cudaEventRecord(b, s);
     count_launch(2);
-    cudaError_t e = cudaEventSynchronize(b);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.0f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
     cudaEventDestroy(a);
