@@ -7,7 +7,8 @@ non-periodic oracle on a cloud replicated 5 x 5 x 5 times. Dyadic coordinates
 make the replication exact in float32. The other pins are closed forms on
 lattices, the volume of the torus, the symmetry of two generators,
 translation invariance, matching faces seen from both sides, SciPy's periodic
-kd-tree as the owner of random samples, and a brute-force image kNN.
+kd-tree as the owner of random samples, a brute-force image kNN, and the
+Poisson-Voronoi mean face and vertex counts.
 """
 import itertools
 
@@ -245,3 +246,17 @@ def test_rejects_boxes_too_elongated_for_two_periods():
 def test_non_periodic_faces_have_no_shift():
     r = oracle.tessellate(W.uniform(200, 51))
     assert np.all(r["face_img"] == 62)
+
+
+def test_every_periodic_cell_is_a_typical_poisson_voronoi_cell():
+    """On the torus a uniform cloud has no boundary, so every cell counts
+    towards the typical cell's statistics (Meijering: mean faces
+    2 + 48 pi^2 / 35, mean vertices 96 pi^2 / 35), and every cell is simple,
+    V = 2F - 4."""
+    p = W.uniform(300_000, 43)
+    r = oracle.tessellate(p, periodic=True)
+    faces, verts = np.diff(r["face_off"]), r["nvert"]
+    assert np.all(r["face_tag"] >= 0)
+    assert abs(faces.mean() - (2.0 + 48.0 * np.pi ** 2 / 35.0)) < 0.02, faces.mean()
+    assert abs(verts.mean() - 96.0 * np.pi ** 2 / 35.0) < 0.04, verts.mean()
+    np.testing.assert_array_equal(verts, 2 * faces - 4)

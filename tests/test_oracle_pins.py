@@ -284,6 +284,36 @@ def test_vertices_satisfy_the_empty_sphere_property():
 
 
 # --------------------------------------------------------------------------
+# P9: Poisson-Voronoi statistics (Meijering's closed forms)
+# --------------------------------------------------------------------------
+
+MEAN_FACES = 2.0 + 48.0 * np.pi ** 2 / 35.0  # 15.5355: mean faces of the typical Poisson-Voronoi cell
+MEAN_VERTICES = 96.0 * np.pi ** 2 / 35.0  # 27.0709
+
+
+def test_poisson_voronoi_mean_face_and_vertex_counts():
+    """Uniform points are a Poisson-like process: the cells of generators
+    4 mean spacings or more from every wall (chosen by position only, so the
+    choice does not depend on the cells) are typical cells, whose mean face
+    and vertex counts have Meijering's closed forms. Over ~360k such cells
+    the standard error of the mean face count is about 0.005; each cell is
+    also simple (three faces at every vertex), so V = 2F - 4 holds per cell."""
+    n = 500_000
+    p = W.uniform(n, 41)
+    r = oracle.tessellate(p)
+    h = n ** (-1.0 / 3.0)
+    p64 = p.astype(np.float64)
+    deep = np.all((p64 >= 4 * h) & (p64 <= 1 - 4 * h), axis=1)
+    assert deep.sum() > 350_000
+    nf = np.diff(r["face_off"])
+    assert not np.any(r["face_tag"][np.repeat(deep, nf)] < 0)  # no deep cell reaches a wall
+    faces, verts = nf[deep], r["nvert"][deep]
+    assert abs(faces.mean() - MEAN_FACES) < 0.02, faces.mean()
+    assert abs(verts.mean() - MEAN_VERTICES) < 0.04, verts.mean()
+    np.testing.assert_array_equal(verts, 2 * faces - 4)
+
+
+# --------------------------------------------------------------------------
 # membership: random samples lie in the cell of their nearest generator
 # --------------------------------------------------------------------------
 
