@@ -129,7 +129,13 @@ VT_API void vt_params_default(vt_params* p);
  * neighbour / face ids use the same space. Any pointer whose VT_EMIT bit is
  * off may be NULL. Variable-length arrays are CSR: cell i owns entries
  * [off[i], off[i+1]). Every face list is counter-clockwise seen from outside
- * the cell. Wall faces carry ids -1..-6 (x=lo, x=hi, y=lo, y=hi, z=lo, z=hi). */
+ * the cell. Wall faces carry ids -1..-6 (x=lo, x=hi, y=lo, y=hi, z=lo, z=hi).
+ * A generator is a neighbour when its face's area exceeds a small fraction of
+ * V^(2/3) (1e-12 in the FP64 form, 1e-11 in the FP32 form): faces below it
+ * (near-degenerate vertex configurations) stay in the geometry, so a cell's
+ * faces are its neighbours, its walls and those tiny faces. Because the
+ * threshold follows each cell's own volume, such a face can make a pair a
+ * neighbour on one side only. */
 typedef struct vt_cells_out {
     double* vol;            /* [n] */
     double* cen;            /* [n*3] */
