@@ -188,8 +188,14 @@ def cpu_oracle_rate(pts: np.ndarray, sample_cells: int, seed: int = 12345, sub_b
     t0 = time.perf_counter()
     r = oracle.tessellate(pts, k0=16, cells=idx, threads=cores, periodic=periodic)
     dt = time.perf_counter() - t0
+    # the same oracle on one core, on the first tenth of the sample
+    one = idx[: max(1, len(idx) // 10)]
+    t1 = time.perf_counter()
+    oracle.tessellate(pts, k0=16, cells=one, threads=1, periodic=periodic)
+    dt1 = time.perf_counter() - t1
     return {"value": len(idx) / dt, "seconds": dt, "cores": cores, "flops_per_cell": float(oracle.clip_flops(r).mean()),
             "idx": idx, "result": r,
+            "one_core": {"value": len(one) / dt1, "cells": int(len(one)), "seconds": dt1},
             "sample": f"{what} of the same {len(pts)}-point workload (kd-tree build included), FP64 oracle, "
                       f"{cores} threads"}
 
@@ -405,7 +411,8 @@ def run_gpu(args, rank: int, world: int, local: int):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["desc"], "n_points": n, "precision": "fp32+fp64-recheck",
                    "k0": args.k0, "k_max": args.k_max, "grid_density": args.rho, "threads_per_cell": 32,
-                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world} (independent clouds)"},
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world} (independent clouds)"},
         "fp64_form": None if args.steps_fp64 <= 0 else {
             "value": value64, "unit": "cells/s", "ms_per_step": tot64 / len(ms64), "steps": len(ms64),
             "stage_ms": {k: statistics.mean(s[k] for s in st64) for k in ("ms_grid", "ms_knn", "ms_clip", "ms_emit")},
@@ -421,7 +428,8 @@ def run_gpu(args, rank: int, world: int, local: int):
         "roofline": roofline,
         "stage_rooflines": stage_rooflines,
         "cpu_baseline": None if cpu is None else {"value": cpu["value"], "unit": "cells/s", "cores": cpu["cores"],
-                                                  "kind": "oracle", "sample": cpu["sample"]},
+                                                  "kind": "oracle", "sample": cpu["sample"],
+                                                  "one_core": cpu["one_core"]},
         "gpu_launches": int(launches32),
         "clocks": clocks,
         "errors_vs_oracle": errors,
@@ -533,7 +541,8 @@ def run_batch(args, rank: int, world: int, local: int):
             "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (unit counts and max SM clock)",
             "stage_ms": {k: sync[k] for k in ("ms_grid", "ms_knn", "ms_clip", "ms_emit")}},
         "cpu_baseline": None if cpu is None else {"value": cpu["value"], "unit": "cells/s", "cores": cpu["cores"],
-                                                  "kind": "oracle", "sample": cpu["sample"]},
+                                                  "kind": "oracle", "sample": cpu["sample"],
+                                                  "one_core": cpu["one_core"]},
         "gpu_launches": int(per_replay * len(ms)),
         "clocks": clocks,
         "status": cells.stats["status"],
@@ -618,7 +627,8 @@ def run_lloyd(args, rank: int, world: int, local: int):
             "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (unit counts and max SM clock)",
             "stage_ms": {k: st[k] for k in ("ms_grid", "ms_knn", "ms_clip", "ms_emit")}},
         "cpu_baseline": None if cpu is None else {"value": cpu["value"], "unit": "cells/s", "cores": cpu["cores"],
-                                                  "kind": "oracle", "sample": cpu["sample"] + " (tessellation only)"},
+                                                  "kind": "oracle", "sample": cpu["sample"] + " (tessellation only)",
+                                                  "one_core": cpu["one_core"]},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
