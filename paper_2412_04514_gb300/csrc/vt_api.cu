@@ -254,9 +254,20 @@ struct StageTimer {
         nvtxRangePushA(names[stage]);
         ++nvtx_depth;
         if (!on) return;
-        cudaEvent_t a, b;
-        cudaEventCreate(&a);
-        cudaEventCreate(&b);
+        // without events the call runs untimed (stage times stay 0); the
+        // failed creation is cleared so later launch checks do not see it
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (cudaEventCreate(&a) != cudaSuccess) {
+            (void)cudaGetLastError();
+            on = false;
+            return;
+        }
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaEventDestroy(a);
+            on = false;
+            return;
+        }
         cudaEventRecord(a, s);
         ev[stage].push_back({a, b});
         if (stage == CLIP) clip_pass.push_back(pass);
