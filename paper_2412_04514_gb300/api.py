@@ -691,14 +691,19 @@ def lloyd(points: torch.Tensor, iterations: int, params: Params | None = None, c
     adjoint gradient of the loss (the step lands on the cell centroids).
 
     With ``checkpoint`` the points and the iteration are saved every
-    ``checkpoint_every`` iterations; ``resume=True`` continues from the file.
-    The pipeline is deterministic, so a resumed run reproduces the points of
-    an uninterrupted one bit for bit. In a periodic box (``params.periodic``)
-    the new points are wrapped back into [box_lo, box_hi)."""
+    ``checkpoint_every`` iterations (written to a temporary file and renamed,
+    so an interrupted write leaves the previous checkpoint intact);
+    ``resume=True`` continues from the file, or starts from ``points`` when
+    no checkpoint has been written yet. The pipeline is deterministic, so a
+    resumed run reproduces the points of an uninterrupted one bit for bit. In
+    a periodic box (``params.periodic``) the new points are wrapped back into
+    [box_lo, box_hi)."""
+    import os
+
     p = points.detach().clone()
     start = 0
-    if resume and checkpoint:
-        state = torch.load(checkpoint, map_location=p.device)
+    if resume and checkpoint and os.path.exists(checkpoint):
+        state = torch.load(checkpoint, map_location=p.device, weights_only=True)
         p = state["points"].to(p.device)
         start = int(state["iteration"])
     for it in range(start, iterations):
@@ -715,5 +720,7 @@ def lloyd(points: torch.Tensor, iterations: int, params: Params | None = None, c
         if callback is not None:
             callback(it, float(loss.detach()))
         if checkpoint and ((it + 1) % checkpoint_every == 0 or it + 1 == iterations):
-            torch.save({"points": p.cpu(), "iteration": it + 1}, checkpoint)
+            tmp = f"{checkpoint}.{os.getpid()}.tmp"
+            torch.save({"points": p.cpu(), "iteration": it + 1}, tmp)
+            os.replace(tmp, checkpoint)
     return p
