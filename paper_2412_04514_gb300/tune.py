@@ -138,7 +138,7 @@ def load_cache(path: str) -> dict:
 
 
 def store_cache(path: str, d: dict) -> None:
-    tmp = path + ".tmp"
+    tmp = f"{path}.{os.getpid()}.tmp"
     with open(tmp, "w") as f:
         json.dump(d, f, indent=1, sort_keys=True)
     os.replace(tmp, path)
