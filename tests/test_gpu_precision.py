@@ -2,7 +2,9 @@
 (half uniform, half in 1,000 clumps), the FP32 form (float32 kNN and
 clipping, FP64 security radius, near-zero sign rechecks and accumulation)
 and the plain FP64 form, each against the FP64 oracle on the cells of a
-seeded sub-box holding about 65,536 generators.
+seeded sub-box holding about 65,536 generators, in the launch configuration
+the benchmark times (32 lanes per cell, k0 16 doubled to k_max 32, two
+points per grid cell, geometry emitted).
 
 Tolerances: FP64 form -- neighbours exact, volumes and centroids 1e-12
 relative; FP32 form -- volumes and centroids 1e-5 relative, neighbour lists
@@ -17,6 +19,11 @@ import paper_2412_04514_gb300 as vt
 from paper_2412_04514_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+
+def bench_params(precision):
+    return vt.Params(precision=precision, k0=16, k_max=32, threads_per_cell=32, grid_density=2.0,
+                     emit=("nbr", "vol", "cen", "geom"))
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +47,7 @@ def _face_area(w, a, j):
 
 def test_fp64_form_on_the_sub_box(cloud8m):
     pts, idx, w = cloud8m
-    cells = vt.tessellate(torch.from_numpy(pts).cuda(), vt.Params(precision="fp64"))
+    cells = vt.tessellate(torch.from_numpy(pts).cuda(), bench_params("fp64"))
     np.testing.assert_allclose(cells.vol.cpu().numpy()[idx], w["vol"], rtol=1e-12)
     np.testing.assert_allclose(cells.cen.cpu().numpy()[idx], w["cen"], rtol=1e-12)
     for a, g in enumerate(_lists(cells, idx)):
@@ -50,7 +57,7 @@ def test_fp64_form_on_the_sub_box(cloud8m):
 
 def test_fp32_form_on_the_sub_box(cloud8m):
     pts, idx, w = cloud8m
-    cells = vt.tessellate(torch.from_numpy(pts).cuda(), vt.Params(precision="fp32"))
+    cells = vt.tessellate(torch.from_numpy(pts).cuda(), bench_params("fp32"))
     vol = cells.vol.cpu().numpy()[idx]
     cen = cells.cen.cpu().numpy()[idx]
     np.testing.assert_allclose(vol, w["vol"], rtol=1e-5)
