@@ -198,7 +198,11 @@ typedef struct vt_stats {
 /* sizing                                                              */
 /* ------------------------------------------------------------------ */
 
-/* Grid resolution G per axis that vt_tessellate uses for n generators. */
+/* Grid resolution G per axis that vt_tessellate uses for n generators (the
+ * uniform grid of the paper's Summary; its size is a reading): p->grid_res
+ * when positive, else G = ceil(cbrt(n / p->grid_density)), at most
+ * ceil(cbrt(8 n)) + 1 and 1024, at least 1 (n <= 0 gives 1). Returns G, or
+ * -1 when p is invalid (the reason in vt_last_error). Host-only. */
 VT_API int vt_grid_resolution(const vt_params* p, int64_t n);
 
 /* Bytes of device workspace needed by vt_tessellate (and by any stage call
@@ -303,7 +307,8 @@ VT_API int vt_emit(int64_t n, const vt_params* p, vt_cells_out* out, void* ws, s
 /* Tessellates the n generators pts[n*3] (device) in the box of p: grid sort,
  * kNN with k0, clipping, re-queue with k doubled up to k_max, exhaustive pass
  * for what is left, then the requested outputs. Synchronises `stream` once
- * per pass (a 64-byte device-to-host read of the failed count) and once at
+ * per pass (a 128-byte device-to-host read of the status block, which holds
+ * the failed count) and once at
  * the end. Returns VT_ERR_CAPACITY (with out->needed_* set and vol/cen/m2
  * written) when a variable-length buffer is too small: allocate and call
  * vt_emit. stats may be NULL. n = 0 is valid (nothing to do); n = 1 gives
@@ -332,7 +337,8 @@ VT_API int vt_batch_plan(const int64_t* set_off, int n_sets, const vt_params* p,
                          vt_set_desc* plan, int64_t* total_cells);
 
 /* Workspace bytes of a batch of n_total points whose grids have total_cells
- * cells (from vt_batch_plan). */
+ * cells (from vt_batch_plan). Host-only; VT_ERR_INVALID_ARG for a bad p,
+ * n_total < 0, total_cells < 1 or, in a periodic box, n_total >= 2^24. */
 VT_API int vt_batch_workspace_size(const vt_params* p, int64_t n_total, int64_t total_cells, size_t* bytes);
 
 /* Tessellates every set of a batch. pts[n_total*3] (device), plan[n_sets] and
