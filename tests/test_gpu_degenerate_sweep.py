@@ -1,0 +1,108 @@
+"""Degenerate and nearly degenerate inputs, GPU against the oracle.
+
+Each case draws a subset of a coarse dyadic lattice (exact in float32: many
+co-spherical vertices and coplanar generators, the degenerate cases of the
+method) and optionally moves every coordinate by a few float32 ulps (nearly
+degenerate), walled or periodic, from one seed. Both forms run on the same
+points. FP64 form: volumes and centroids to 1e-12 and the oracle's neighbour
+lists exactly. FP32 form: volumes to 1e-5, centroids to 1e-5 of |c|, and
+every neighbour difference a face the oracle measures below 1e-6 V^(2/3);
+the ulp-moved lattices have such sliver faces (about 1e-7 V^(2/3), the size
+of float32 round-off) in most cells, so their number is not bounded.
+
+Either form must return VT_OK with those results or report the cells it could
+not validate (VT_ERR_UNVALIDATED) and be right on all others. One case is
+known to take the second branch: seed 11, a 2 x 2 x 2 periodic lattice moved
+by one ulp, where seven planes (a face, three edge and one corner neighbour's
+bisectors, with the jitter) pass within ~1e-8 of each cube vertex and the
+robust variant's ring closure fails for two cells.
+"""
+from collections import Counter
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2412_04514_gb300 as vt
+
+pytestmark = pytest.mark.gpu
+
+N_CASES = 32
+
+
+def draw(seed):
+    rng = np.random.default_rng(5000 + seed)
+    m = int(rng.choice([2, 3, 4, 8, 16]))
+    n = int(rng.integers(2, 81))
+    periodic = bool(rng.random() < 0.5)
+    ulps = int(rng.choice([0, 0, 1, 4, 64]))
+    cells = rng.choice(m ** 3, size=min(n, m ** 3), replace=False)
+    pts = ((np.stack(np.unravel_index(cells, (m, m, m)), 1) + 0.5) / m).astype(np.float32)
+    if ulps:
+        k = rng.integers(-ulps, ulps + 1, size=pts.shape).astype(np.int32)
+        pts = (pts.view(np.int32) + k).view(np.float32)
+        pts = np.unique(np.clip(pts, 0, np.nextafter(np.float32(1), np.float32(0))), axis=0)
+        pts = pts[rng.permutation(len(pts))]
+    return pts, periodic
+
+
+def multisets(off, val):
+    return [sorted(val[off[i]:off[i + 1]].tolist()) for i in range(len(off) - 1)]
+
+
+def small_face(want, i, j, rel):
+    f0, f1 = want["face_off"][i], want["face_off"][i + 1]
+    area = want["face_area"][f0:f1][want["face_tag"][f0:f1] == j]
+    return len(area) == 0 or area.min() < rel * want["vol"][i] ** (2 / 3)
+
+
+KNOWN_UNVALIDATED = {11}
+
+
+def cell_ok(i, precision, vol, cen, got, want, ref):
+    fp64 = precision == "fp64"
+    if abs(vol[i] - want["vol"][i]) > (1e-12 if fp64 else 1e-5) * want["vol"][i]:
+        return False
+    dc = np.linalg.norm(cen[i] - want["cen"][i])
+    if dc > (1e-12 if fp64 else 1e-5 * np.linalg.norm(want["cen"][i])):
+        return False
+    if got[i] == ref[i]:
+        return True
+    g, w = Counter(got[i]), Counter(ref[i])  # periodic lists may hold two images of one generator
+    return not fp64 and all(small_face(want, i, j, 1e-6) for j in set((g - w) + (w - g)))
+
+
+def run_case(seed):
+    pts, periodic = draw(seed)
+    want = oracle.tessellate(pts, periodic=periodic)
+    ref = multisets(want["nbr_off"], want["nbr"])
+    d = torch.from_numpy(pts).cuda()
+    results = {}
+    for precision in ("fp64", "fp32"):
+        cells = vt.tessellate(d, vt.Params(precision=precision, emit=("nbr", "vol", "cen"), periodic=periodic),
+                              strict=False)
+        vol, cen = cells.vol.cpu().numpy(), cells.cen.cpu().numpy()
+        got = multisets(cells.nbr_off.cpu().numpy(), cells.nbr.cpu().numpy())
+        wrong = [i for i in range(len(pts)) if not cell_ok(i, precision, vol, cen, got, want, ref)]
+        results[precision] = (cells.stats, wrong, vol)
+    return results
+
+
+@pytest.mark.parametrize("seed", range(N_CASES))
+def test_degenerate_case_is_right_or_reported(seed):
+    for precision, (stats, wrong, vol) in run_case(seed).items():
+        if stats["status"] == "VT_OK":
+            assert not wrong, (precision, wrong)
+            assert abs(vol.sum() - 1.0) < (1e-12 if precision == "fp64" else 1e-5)
+        else:
+            assert stats["status"] == "VT_ERR_UNVALIDATED", (precision, stats["status"])
+            assert len(wrong) <= stats["unvalidated"], (precision, wrong, stats["unvalidated"])
+
+
+@pytest.mark.xfail(strict=True, reason="near-coincident planes at the vertices of a one-ulp-moved periodic "
+                   "2x2x2 lattice: two cells stay unvalidated in both forms")
+@pytest.mark.parametrize("seed", sorted(KNOWN_UNVALIDATED))
+def test_known_degenerate_case_validates(seed):
+    for precision, (stats, wrong, _) in run_case(seed).items():
+        assert stats["status"] == "VT_OK" and not wrong, precision
