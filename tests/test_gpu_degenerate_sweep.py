@@ -15,7 +15,9 @@ not validate (VT_ERR_UNVALIDATED) and be right on all others. One case is
 known to take the second branch: seed 11, a 2 x 2 x 2 periodic lattice moved
 by one ulp, where seven planes (a face, three edge and one corner neighbour's
 bisectors, with the jitter) pass within ~1e-8 of each cube vertex and the
-robust variant's ring closure fails for two cells.
+robust variant's ring closure fails for two cells: the FP64 on-plane rule
+keeps a vertex less than 1e-14 |n| R outside a plane while cutting vertices
+beyond it, which splits the outside set.
 """
 from collections import Counter
 
