@@ -30,7 +30,10 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream). Stage calls (vt_grid_build, vt_knn, vt_clip_cells, vt_emit) only
  *    enqueue work and return; vt_tessellate synchronises the stream once per
- *    re-queue pass to read a 64-byte status block (documented below).
+ *    re-queue pass to read a 128-byte status block (documented below).
+ *  - Work runs on the calling thread's current CUDA device; every device
+ *    buffer and the stream must belong to it (the library never switches
+ *    devices: make the buffers' device current first).
  *  - Points are float32 (x, y, z) triples inside the half-open box
  *    [box_lo, box_hi), pairwise distinct.
  *  - Return value: vt_status. On failure vt_last_error() (per host thread)
