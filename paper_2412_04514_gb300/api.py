@@ -3,6 +3,9 @@
 Every computation happens in libvt.so's CUDA kernels; these functions only
 allocate torch tensors (device memory), pass their pointers and the current
 CUDA stream through the C ABI of include/vt.h, and wrap the results.
+The library runs on the current CUDA device, so with several GPUs make the
+tensors' device current first (``torch.cuda.set_device`` or
+``with torch.cuda.device(...)``).
 """
 from __future__ import annotations
 
