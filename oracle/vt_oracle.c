@@ -377,8 +377,10 @@ static int add_unique(vec3* set, int m, vec3 p)
     return m + 1;
 }
 
-/* clip P by the half-space n.x <= b (face tag `tag`) into Q.
- * returns 0 if nothing is cut (Q untouched), 1 if clipped into Q, <0 on capacity error */
+/* clip P by the half-space n.x <= b (face tag `tag`) into Q: one step of the
+ * cell-by-cell construction (Summary: the box is cut by the bisector of each
+ * neighbour in turn). Returns 0 if nothing is cut (Q untouched), 1 if clipped
+ * into Q, <0 on capacity error */
 static int clip(const poly_t* P, poly_t* Q, vec3 n, double b, int32_t tag, scratch_t* S)
 {
     int fv = 0;
@@ -446,7 +448,9 @@ static double max_r2(const poly_t* P)
     return r2;
 }
 
-/* bisector of (p_i, p_j) in the local frame of p_i: n = p_j - p_i, b = |n|^2 / 2 */
+/* bisector of (p_i, p_j) in the local frame of p_i: n = p_j - p_i, b = |n|^2 / 2
+ * (the points x with |x - p_i| = |x - p_j|; Statement of need: the Voronoi cell
+ * is the set closer to p_i than to any other generator) */
 static void bisector(const float* pi, const float* pj, vec3* n, double* b)
 {
     *n = v3((double)pj[0] - (double)pi[0], (double)pj[1] - (double)pi[1], (double)pj[2] - (double)pi[2]);
@@ -756,7 +760,10 @@ typedef struct {
 
 /* Volume, first and second moment by a tetrahedron fan from the generator
  * (the local origin, inside its own cell); face area and centroid by a
- * triangle fan from the face's first vertex.
+ * triangle fan from the face's first vertex. The paper's library returns
+ * several per-cell outputs and names the neighbour lists among them
+ * (Features); these moments are the ones this implementation returns beside
+ * the neighbours (a Lloyd step needs volume and centroid).
  *
  * Topology: exact FP64 clipping at degenerate inputs (lattices) can leave
  * vertices a few ulps apart and zero-area sliver faces. For the reported
@@ -831,7 +838,9 @@ static void measure(const poly_t* P, vec3 pi, cell_meas* M, double* farea, vec3*
 /* ------------------------------------------------------------------ */
 
 /* Computes the cell of generator i into *out_poly (a pointer into S).
- * mode VTO_MODE_SECURITY: kNN + security radius with k doubling.
+ * mode VTO_MODE_SECURITY: kNN + security radius with k doubling (Summary: the
+ * neighbours nearest first, stopping once the security radius shows that no
+ * farther generator can cut the cell, and a larger k when the list runs out).
  * mode VTO_MODE_BRUTE: every other generator, in index order (order == NULL)
  *   or in the order given by `order` (a permutation of 0..n-1), no stop test.
  * Returns status; *k_used gets the final k (n-1 for brute force). */
