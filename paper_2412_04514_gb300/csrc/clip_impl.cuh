@@ -346,10 +346,11 @@ struct GroupSmem {
 enum ClipResult { CLIP_NONE = 0, CLIP_CUT = 1, CLIP_OVERFLOW = 2, CLIP_INCONSISTENT = 3 };
 enum CellEnd { END_VALID = 0, END_NEED_K = 1, END_OVERFLOW = 2, END_INCONSISTENT = 3 };
 
-// A vertex counts as outside a plane n.x <= b when s = n.v - b exceeds
-// on_plane_rel * |n| * R (R = cell radius): round-off of FP64 vertex
-// positions at exactly degenerate inputs (lattices) must not cut slivers.
-// A 3x3 solve whose determinant is below cond_rel * |A||B||C| is replaced by
+// A plane n.x <= b whose outside vertices (s = n.v - b > 0) all have s below
+// on_plane_rel * |n| * R (R = cell radius) only touches the cell and is
+// skipped: round-off of FP64 vertex positions at exactly degenerate inputs
+// (lattices) must not cut slivers. Any other plane removes every vertex with
+// s > 0. A 3x3 solve whose determinant is below cond_rel * |A||B||C| is replaced by
 // interpolation along the cut edge.
 template <typename Real>
 struct Tol;
@@ -385,10 +386,12 @@ struct StateLayout {
 // rarely taken paths, kept out of line so the hot loop stays small
 // ---------------------------------------------------------------------------
 
-// FP64 re-decision of a sign test: the vertex re-solved from its planes
+// FP64 re-decision of a sign test, the vertex re-solved from its planes:
+// 0 inside or on the plane (s <= 0), 1 outside within the on-plane band
+// (s^2 <= 1e-28 |n|^2 R^2), 2 outside beyond it
 template <typename S>
-__device__ VT_RARE bool outside64(const S& sm, int s, P64 h, const float4* __restrict__ sorted, float4 pi,
-                                       GridDesc g, double fx, double fy, double fz, double R2)
+__device__ VT_RARE int outside64(const S& sm, int s, P64 h, const float4* __restrict__ sorted, float4 pi,
+                                      GridDesc g, double fx, double fy, double fz, double R2)
 {
     const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
     const bool per = g.periodic != 0;  // out of line: the box kind is read here
@@ -400,7 +403,8 @@ __device__ VT_RARE bool outside64(const S& sm, int s, P64 h, const float4* __res
     double x, y, z;
     if (!vertex64(A, B, C, x, y, z)) { x = fx; y = fy; z = fz; }
     const double sv = (h.x * x + h.y * y) + h.z * z - h.b;
-    return sv > 0.0 && sv * sv > ON_PLANE_REL2 * 2.0 * h.b * R2;
+    if (!(sv > 0.0)) return 0;
+    return sv * sv > ON_PLANE_REL2 * 2.0 * h.b * R2 ? 2 : 1;
 }
 
 // FP64 squared distance of slot s's vertex, re-solved from its planes
@@ -692,9 +696,16 @@ struct Cell {
     __device__ __forceinline__ int clip(const Group<T>& G, S& sm, Real nx, Real ny, Real nz, Real b, int src,
                                         const float4* __restrict__ sorted, const GridDesc& grid, DevStatus* st)
     {
+        // The on-plane rule applies to the cut as a whole: a plane whose
+        // outside vertices all lie within the on-plane band (|s| below
+        // 1e-14 |n| R, FP64 round-off at exactly degenerate vertices) only
+        // touches the cell and is skipped; any other plane cuts every vertex
+        // strictly outside it (s > 0). Keeping a vertex inside the band while
+        // cutting the ones beyond it would split the outside set and break
+        // the ring of the new face.
         M out;
         out.clear();
-        uint32_t myout = 0, mynear = 0;
+        uint32_t myout = 0, mynear = 0, myfar = 0;
         const double tol2 = Tol<Real>::fp32 ? 0.0 : ON_PLANE_REL2 * 2.0 * (double)b * (double)R2;
         const float near2 = Tol<Real>::fp32 ? 2e-12f * (float)b * (float)R2 : 0.0f;
 #pragma unroll
@@ -703,12 +714,13 @@ struct Cell {
                 const int s = r * T + G.gl;
                 const Real sv = nx * vx[r] + ny * vy[r] + nz * vz[r] - b;
                 const bool al = alive.test(s);
-                bool o;
+                const bool o = al && sv > (Real)0;
                 if (Tol<Real>::fp32) {
-                    o = al && sv > (Real)0;
+                    // beyond the FP32 recheck band an outside vertex is far outside
                     if (al && (float)sv * (float)sv < near2) mynear |= 1u << r;
+                    else myfar |= (uint32_t)o << r;
                 } else {
-                    o = al && sv > (Real)0 && (double)sv * (double)sv > tol2;
+                    myfar |= (uint32_t)(o && (double)sv * (double)sv > tol2) << r;
                 }
                 myout |= (uint32_t)o << r;
                 out.or_bits((uint64_t)G.ballot(o), r * T);
@@ -721,9 +733,10 @@ struct Cell {
                 const int r = __ffs(m) - 1;
                 Real fx, fy, fz;
                 get_row(r, fx, fy, fz);
-                const bool o = outside64(sm, r * T + G.gl, h, sorted, pi, grid, (double)fx, (double)fy, (double)fz,
-                                         (double)R2);
+                const int o = outside64(sm, r * T + G.gl, h, sorted, pi, grid, (double)fx, (double)fy, (double)fz,
+                                        (double)R2);
                 myout = o ? (myout | (1u << r)) : (myout & ~(1u << r));
+                if (o == 2) myfar |= 1u << r;
                 atomicAdd(&st->fp64_rechecks, 1ull);
             }
             out.clear();
@@ -731,7 +744,7 @@ struct Cell {
             for (int r = 0; r < VPL; ++r)
                 if (r < rows) out.or_bits((uint64_t)G.ballot((myout >> r) & 1u), r * T);
         }
-        if (out.none()) return CLIP_NONE;
+        if (out.none() || !G.any(myfar != 0)) return CLIP_NONE;
         const M keep = mask_and(alive, mask_not(out, VCAP));
         if (keep.none()) {  // the generator itself is always inside
             if (G.gl == 0) atomicAdd(&st->detail[0], 1u);

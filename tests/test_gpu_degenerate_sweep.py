@@ -10,14 +10,14 @@ every neighbour difference a face the oracle measures below 1e-6 V^(2/3);
 the ulp-moved lattices have such sliver faces (about 1e-7 V^(2/3), the size
 of float32 round-off) in most cells, so their number is not bounded.
 
-Either form must return VT_OK with those results or report the cells it could
-not validate (VT_ERR_UNVALIDATED) and be right on all others. One case is
-known to take the second branch: seed 11, a 2 x 2 x 2 periodic lattice moved
-by one ulp, where seven planes (a face, three edge and one corner neighbour's
-bisectors, with the jitter) pass within ~1e-8 of each cube vertex and the
-robust variant's ring closure fails for two cells: the FP64 on-plane rule
-keeps a vertex less than 1e-14 |n| R outside a plane while cutting vertices
-beyond it, which splits the outside set.
+Both forms must return VT_OK with those results on every case. Seed 11, a
+2 x 2 x 2 periodic lattice moved by one ulp, is the hardest: seven planes (a
+face, three edge and one corner neighbour's bisectors, with the jitter) pass
+within ~1e-8 of each cube vertex. It validates because the on-plane tolerance
+applies to a cut as a whole (a plane whose outside vertices all lie within
+1e-14 |n| R only touches the cell and is skipped; any other plane removes
+every vertex strictly outside it): keeping a vertex inside the band while
+cutting vertices beyond it would split the outside set.
 """
 from collections import Counter
 
@@ -59,9 +59,6 @@ def small_face(want, i, j, rel):
     return len(area) == 0 or area.min() < rel * want["vol"][i] ** (2 / 3)
 
 
-KNOWN_UNVALIDATED = {11}
-
-
 def cell_ok(i, precision, vol, cen, got, want, ref):
     fp64 = precision == "fp64"
     if abs(vol[i] - want["vol"][i]) > (1e-12 if fp64 else 1e-5) * want["vol"][i]:
@@ -92,19 +89,8 @@ def run_case(seed):
 
 
 @pytest.mark.parametrize("seed", range(N_CASES))
-def test_degenerate_case_is_right_or_reported(seed):
+def test_degenerate_case_is_right(seed):
     for precision, (stats, wrong, vol) in run_case(seed).items():
-        if stats["status"] == "VT_OK":
-            assert not wrong, (precision, wrong)
-            assert abs(vol.sum() - 1.0) < (1e-12 if precision == "fp64" else 1e-5)
-        else:
-            assert stats["status"] == "VT_ERR_UNVALIDATED", (precision, stats["status"])
-            assert len(wrong) <= stats["unvalidated"], (precision, wrong, stats["unvalidated"])
-
-
-@pytest.mark.xfail(strict=True, reason="near-coincident planes at the vertices of a one-ulp-moved periodic "
-                   "2x2x2 lattice: two cells stay unvalidated in both forms")
-@pytest.mark.parametrize("seed", sorted(KNOWN_UNVALIDATED))
-def test_known_degenerate_case_validates(seed):
-    for precision, (stats, wrong, _) in run_case(seed).items():
-        assert stats["status"] == "VT_OK" and not wrong, precision
+        assert stats["status"] == "VT_OK", (precision, stats["status"], stats["unvalidated"])
+        assert not wrong, (precision, wrong)
+        assert abs(vol.sum() - 1.0) < (1e-12 if precision == "fp64" else 1e-5)
