@@ -47,6 +47,7 @@ EXPORTS = [
     "vt_grid_build_static", "vt_moments_adjoint", "vt_probe_fma", "vt_batch_plan", "vt_batch_workspace_size",
     "vt_tessellate_batch", "vt_read_stats", "vt_cluster_index", "vt_cluster_class", "vt_tune_space_default",
     "vt_autotune_workspace_size", "vt_autotune", "vt_autotune_batch_workspace_size", "vt_autotune_batch",
+    "vt_unvalidated_cells", "vt_lloyd_step",
 ]
 VT_TUNE_CLASSES = 4
 VT_TUNE_MAX_TRIED = 64
@@ -256,6 +257,10 @@ def load() -> ctypes.CDLL:
         L.vt_tessellate_batch.restype = I
         L.vt_read_stats.argtypes = [P, ctypes.c_size_t, ps, po, P]
         L.vt_read_stats.restype = I
+        L.vt_unvalidated_cells.argtypes = [pp, I64, P, I64, ctypes.POINTER(I64), P, ctypes.c_size_t, P]
+        L.vt_unvalidated_cells.restype = I
+        L.vt_lloyd_step.argtypes = [P, I64, P, P, pp, P, P]
+        L.vt_lloyd_step.restype = I
         pts_ = ctypes.POINTER(VtTuneSpace)
         ptr_ = ctypes.POINTER(VtTuneResult)
         L.vt_cluster_index.argtypes = [P, I64, P, P, I, I64, pp, P, P, ctypes.c_size_t, P]

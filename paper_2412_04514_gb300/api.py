@@ -118,6 +118,9 @@ class Cells:
     face_vtx: torch.Tensor | None = None
     perm: torch.Tensor | None = None
     stats: dict = field(default_factory=dict)
+    # ids (in the call's index space) of the cells left unvalidated, whose
+    # vol / cen / m2 are NaN; empty when every cell was validated
+    unvalidated: torch.Tensor | None = None
 
 
 def _out_struct(cells: Cells) -> L.VtCellsOut:
@@ -178,6 +181,26 @@ def _trim(c: Cells, o: L.VtCellsOut) -> None:
         c.face_vtx = c.face_vtx[: o.needed_face_vtx]
 
 
+def _unvalidated_ids(params: Params, n: int, ws: torch.Tensor, dev, s, code: int, cells: Cells) -> int:
+    """Fills cells.unvalidated (vt_unvalidated_cells) and returns the call's
+    status, VT_ERR_UNVALIDATED whenever cells were left unvalidated."""
+    if code != L.VT_ERR_UNVALIDATED and not cells.stats.get("unvalidated"):
+        cells.unvalidated = torch.empty(0, dtype=torch.int32, device=dev)  # nothing to read back
+        return code
+    lib = L.load()
+    cnt = ctypes.c_int64()
+    pc = params.c()
+    L.check(lib.vt_unvalidated_cells(ctypes.byref(pc), n, None, 0, ctypes.byref(cnt), _ptr(ws), ws.numel(), s))
+    ids = torch.empty(max(cnt.value, 1), dtype=torch.int32, device=dev)
+    if cnt.value:
+        L.check(lib.vt_unvalidated_cells(ctypes.byref(pc), n, _ptr(ids), ids.numel(), ctypes.byref(cnt), _ptr(ws),
+                                         ws.numel(), s))
+        if code == L.VT_OK:
+            code = L.VT_ERR_UNVALIDATED
+    cells.unvalidated = ids[: cnt.value]
+    return code
+
+
 def tessellate(points: torch.Tensor, params: Params | None = None, workspace: Workspace | None = None,
                want_perm: bool = False, strict: bool = True, host_csr: bool = False) -> Cells:
     """Voronoi cells of the generators ``points`` (float32 CUDA tensor (n, 3)).
@@ -216,6 +239,9 @@ def tessellate(points: torch.Tensor, params: Params | None = None, workspace: Wo
         o = _out_struct(cells)
         code = lib.vt_emit(n, ctypes.byref(pc), ctypes.byref(o), _ptr(ws.buf), ws.buf.numel(), s)
     cells.stats = st.as_dict()
+    if code in (L.VT_OK, L.VT_ERR_UNVALIDATED):
+        code = _unvalidated_ids(params, n, ws.buf, dev, s, code, cells)
+        cells.stats["unvalidated"] = cells.unvalidated.numel()
     cells.stats["status"] = L.STATUS_NAMES.get(code, code)
     if code not in (L.VT_OK, L.VT_ERR_UNVALIDATED) or (strict and code != L.VT_OK):
         L.check(code)
@@ -443,6 +469,7 @@ class Batch:
         stats["clip_events"] = list(st.clip_events)
         stats["status"] = L.STATUS_NAMES.get(code, code)
         out.stats = stats
+        _unvalidated_ids(self.params, self.n, self.ws, self.points.device, _stream(self.points.device), code, out)
         _trim(out, o)
         return out
 
@@ -501,6 +528,9 @@ def tessellate_batch(points: torch.Tensor, set_off, params: Params | None = None
         o = _out_struct(cells)
         code = lib.vt_emit(n, ctypes.byref(pc), ctypes.byref(o), _ptr(ws), ws.numel(), s)
     cells.stats = st.as_dict()
+    if code in (L.VT_OK, L.VT_ERR_UNVALIDATED):
+        code = _unvalidated_ids(params, n, ws, dev, s, code, cells)
+        cells.stats["unvalidated"] = cells.unvalidated.numel()
     cells.stats["status"] = L.STATUS_NAMES.get(code, code)
     if code not in (L.VT_OK, L.VT_ERR_UNVALIDATED) or (strict and code != L.VT_OK):
         L.check(code)
@@ -675,17 +705,21 @@ def voronoi_moments(points: torch.Tensor, params: Params | None = None):
     return VoronoiMoments.apply(points, params)
 
 
-def wrap_into_box(points: torch.Tensor, lo, hi) -> torch.Tensor:
-    """Points of a periodic box moved by whole periods into [lo, hi) (float32)."""
-    lo_t = torch.tensor(lo, dtype=torch.float64, device=points.device)
-    hi_t = torch.tensor(hi, dtype=torch.float64, device=points.device)
-    L = hi_t - lo_t
-    x = points.to(torch.float64)
-    x = x - torch.floor((x - lo_t) / L) * L
-    out = x.to(torch.float32)
-    # rounding to float32 can land on hi itself: that point belongs at lo
-    hi32 = hi_t.to(torch.float32).expand_as(out)
-    return torch.where(out >= hi32, lo_t.to(torch.float32).expand_as(out), out)
+def lloyd_step(points: torch.Tensor, grad: torch.Tensor, vol: torch.Tensor, params: Params | None = None
+               ) -> torch.Tensor:
+    """One Lloyd update p <- p - grad / (2 vol) (vt_lloyd_step): the cell
+    centroids when ``grad`` is the gradient of sum_i M2_i. Float32 points,
+    FP64 gradient and volumes, all on the device; in a periodic box
+    (``params.periodic``) the new points are wrapped into [box_lo, box_hi)."""
+    pts = _check_points(points)
+    n = pts.shape[0]
+    dev = pts.device
+    g = grad.to(device=dev, dtype=torch.float64).contiguous()
+    v = vol.to(device=dev, dtype=torch.float64).contiguous()
+    out = torch.empty_like(pts)
+    pc = (params or Params()).c()
+    L.check(L.load().vt_lloyd_step(_ptr(pts), n, _ptr(g), _ptr(v), ctypes.byref(pc), _ptr(out), _stream(dev)))
+    return out
 
 
 def lloyd(points: torch.Tensor, iterations: int, params: Params | None = None, checkpoint: str | None = None,
@@ -715,11 +749,7 @@ def lloyd(points: torch.Tensor, iterations: int, params: Params | None = None, c
         loss = m2.sum()
         loss.backward()
         with torch.no_grad():
-            g = q.grad.to(torch.float64)
-            step = p.to(torch.float64) - g / (2.0 * vol.detach()[:, None])
-            p = step.to(torch.float32)
-            if params is not None and params.periodic:
-                p = wrap_into_box(p, params.box_lo, params.box_hi)
+            p = lloyd_step(p, q.grad, vol.detach(), params)
         if callback is not None:
             callback(it, float(loss.detach()))
         if checkpoint and ((it + 1) % checkpoint_every == 0 or it + 1 == iterations):

@@ -91,7 +91,60 @@ __global__ void k_emit_write(const uint8_t* __restrict__ rec, size_t stride, int
     }
 }
 
+// Cells left unvalidated: NaN into their moments, so that no stale or
+// partial value is mistaken for a cell. list[] holds sorted indices; the
+// count is *n_dev when set (the no-sync schedule), else n_host, which the
+// first thread also stores in the status block for vt_read_stats.
+__global__ void k_mark_unvalidated(const int32_t* __restrict__ list, const int32_t* n_dev, int64_t n_host,
+                                   const float4* __restrict__ sorted, int index_space, double* vol, double* cen,
+                                   double* m2, DevStatus* st)
+{
+    const int64_t cnt = n_dev ? (int64_t)*n_dev : n_host;
+    if (!n_dev && blockIdx.x == 0 && threadIdx.x == 0) st->n_unval = (int32_t)n_host;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = list[i];
+        const int64_t o = index_space == VT_INDEX_ORIGINAL ? (int64_t)__float_as_int(sorted[q].w) : (int64_t)q;
+        if (vol) vol[o] = nan;
+        if (cen) cen[3 * o] = cen[3 * o + 1] = cen[3 * o + 2] = nan;
+        if (m2) m2[o] = nan;
+    }
+}
+
+// ids of the unvalidated cells in the chosen index space (at most cap)
+__global__ void k_unvalidated_ids(const int32_t* __restrict__ list, int64_t cnt, const float4* __restrict__ sorted,
+                                  int index_space, int32_t* __restrict__ ids)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = list[i];
+        ids[i] = index_space == VT_INDEX_ORIGINAL ? __float_as_int(sorted[q].w) : q;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_mark_unvalidated(const int32_t* list, const int32_t* n_dev, int64_t n_host, int64_t n_bound,
+                                    const float4* sorted, int index_space, double* vol, double* cen, double* m2,
+                                    DevStatus* st, cudaStream_t s)
+{
+    int64_t blocks = (n_bound + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    k_mark_unvalidated<<<(unsigned)blocks, 256, 0, s>>>(list, n_dev, n_host, sorted, index_space, vol, cen, m2, st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unvalidated_ids(const int32_t* list, int64_t cnt, const float4* sorted, int index_space,
+                                   int32_t* ids, cudaStream_t s)
+{
+    if (cnt <= 0) return cudaSuccess;
+    int64_t blocks = (cnt + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_unvalidated_ids<<<(unsigned)blocks, 256, 0, s>>>(list, cnt, sorted, index_space, ids);
+    count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_emit_count(const EmitArgs& a, cudaStream_t s)
 {

@@ -127,6 +127,18 @@ int check_buffers(void* stream, const void* pts, const void* ws, const vt_cells_
 
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
+int check_device_buffers(void* stream, const void* const* ptrs, const char* const* names, int count)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) (void)cudaGetLastError();
+    if (cs != cudaStreamCaptureStatusNone) return VT_OK;
+    for (int i = 0; i < count; ++i)
+        if (!device_accessible(ptrs[i]))
+            return fail(VT_ERR_INVALID_ARG, "%s is not device-accessible memory (device, managed or pinned host)",
+                        names[i]);
+    return VT_OK;
+}
+
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
@@ -738,6 +750,11 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
             if (kk) k_prev = kk;
         }
         S.passes = lp;
+        ce = launch_mark_unvalidated(unval, &c.st->n_unval, 0, n, c.at<float4>(L.sorted), p->index_space,
+                                     (p->emit & VT_EMIT_VOL) ? out->vol : nullptr,
+                                     (p->emit & VT_EMIT_CEN) ? out->cen : nullptr,
+                                     (p->emit & VT_EMIT_M2) ? out->m2 : nullptr, c.st, c.s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "unvalidated marks");
         r = emit_outputs(c, p, out);
         S.launches = (int)(launches() - l0);
         if (stats) *stats = S;
@@ -769,7 +786,8 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
                 count_launch();
                 implicit = false;
             }
-            if (exhaustive && k_prev > 0 && !implicit)
+            const bool by_range = exhaustive && k_prev > 0 && !implicit;
+            if (by_range)
                 r = range_pass(c, p, reg_cur, m_reg, nullptr, k_prev, variant_reg, out, reg_nxt, &c.st->n_range_over,
                                rob_new, &c.st->n_fail_robust, unval + n_unval, &c.st->n_fail_next);
             else
@@ -785,6 +803,17 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
             if ((r = status_errors(h))) return r;
             got_next = h.n_fail_next;
             got_rob = h.n_fail_robust;
+            if (exhaustive && got_next > 0) {
+                // the exhaustive pass concludes every cell; what it hands on
+                // is unvalidated (range lists write it to unval + n_unval)
+                if (!by_range) {
+                    ce = cudaMemcpyAsync(unval + n_unval, reg_nxt, sizeof(int32_t) * got_next,
+                                         cudaMemcpyDeviceToDevice, c.s);
+                    if (ce != cudaSuccess) return cuda_fail(ce, "list copy");
+                }
+                n_unval += got_next;
+                got_next = 0;
+            }
         }
         implicit = false;
         if (got_rob > 0) {
@@ -821,7 +850,11 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
         m_reg = got_next;
         m_rob = rob_next;
         if (exhaustive) {
-            n_unval += m_reg + m_rob;  // cannot happen: the exhaustive pass always concludes
+            if (m_rob > 0) {  // cannot happen: the exhaustive pass always concludes
+                ce = cudaMemcpyAsync(unval + n_unval, rob_cur, sizeof(int32_t) * m_rob, cudaMemcpyDeviceToDevice, c.s);
+                if (ce != cudaSuccess) return cuda_fail(ce, "list copy");
+                n_unval += m_rob;
+            }
             break;
         }
         if (merged) {  // the second list pass ran inside this one
@@ -836,6 +869,13 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
         k *= 2;
     }
     S.unvalidated = n_unval;
+    if (n_unval > 0) {
+        ce = launch_mark_unvalidated(unval, nullptr, n_unval, n_unval, c.at<float4>(L.sorted), p->index_space,
+                                     (p->emit & VT_EMIT_VOL) ? out->vol : nullptr,
+                                     (p->emit & VT_EMIT_CEN) ? out->cen : nullptr,
+                                     (p->emit & VT_EMIT_M2) ? out->m2 : nullptr, c.st, c.s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "unvalidated marks");
+    }
     r = emit_outputs(c, p, out);
     if ((r = r ? r : read_status(c, h))) {
         if (stats) *stats = S;
@@ -904,6 +944,11 @@ int vt_grid_build(const float* pts, int64_t n, const vt_params* p, int G, float*
     if (e) return e;
     if (G != c.L.G) return fail(VT_ERR_INVALID_ARG, "G = %d differs from vt_grid_resolution = %d", G, c.L.G);
     if ((n > 0 && (!pts || !sorted || !perm)) || !cell_off) return fail(VT_ERR_INVALID_ARG, "NULL buffer");
+    {
+        const void* ptrs[] = {pts, sorted, perm, cell_off, ws};
+        const char* names[] = {"pts", "sorted", "perm", "cell_off", "the workspace"};
+        if ((e = check_device_buffers(stream, ptrs, names, 5))) return e;
+    }
     cudaError_t ce = cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s);
     if (ce != cudaSuccess) return cuda_fail(ce, "status reset");
     ce = launch_grid_build(pts, n, c.g, (float4*)sorted, perm, cell_off, c.at<int32_t>(c.L.cid),
@@ -922,6 +967,11 @@ int vt_knn(const float* sorted, const int32_t* cell_off, int G, int64_t n, const
     if (k < 1 || k > 256) return fail(VT_ERR_INVALID_ARG, "k must be in [1, 256], got %d", k);
     if (nq < 0 || (nq > 0 && (!sorted || !cell_off || !nbr))) return fail(VT_ERR_INVALID_ARG, "bad buffers");
     if (!queries && nq > n) return fail(VT_ERR_INVALID_ARG, "nq > n without a query list");
+    {
+        const void* ptrs[] = {sorted, cell_off, queries, nbr, d2, ws};
+        const char* names[] = {"sorted", "cell_off", "queries", "nbr", "d2", "the workspace"};
+        if ((e = check_device_buffers(stream, ptrs, names, 6))) return e;
+    }
     cudaError_t ce = launch_knn((const float4*)sorted, cell_off, c.g, n, queries, nq, k, p->precision, nbr, d2, c.st, c.s);
     return ce == cudaSuccess ? VT_OK : cuda_fail(ce, "knn");
 }
@@ -938,6 +988,12 @@ int vt_clip_cells(const float* sorted, const int32_t* cell_off, int G, int64_t n
     if (!out || !failed || !n_failed || !sorted || !cell_off) return fail(VT_ERR_INVALID_ARG, "NULL buffer");
     if (k > 0 && (!nbr || !d2)) return fail(VT_ERR_INVALID_ARG, "list mode needs nbr and d2");
     if (!queries && nq > n) return fail(VT_ERR_INVALID_ARG, "nq > n without a query list");
+    {
+        const void* ptrs[] = {sorted, cell_off, queries, nbr, d2, failed, n_failed};
+        const char* names[] = {"sorted", "cell_off", "queries", "nbr", "d2", "failed", "n_failed"};
+        if ((e = check_device_buffers(stream, ptrs, names, 7))) return e;
+        if ((e = check_buffers(stream, nullptr, ws, out))) return e;
+    }
     ClipArgs a{};
     a.sorted = (const float4*)sorted;
     a.cell_off = cell_off;
@@ -1059,8 +1115,30 @@ int vt_moments_adjoint(const float* pts, int64_t n, const vt_cells_out* cells, c
     if (!cells->vol || !cells->cen || !cells->vtx_off || !cells->vtx || !cells->face_off || !cells->face_nbr ||
         !cells->face_vtx_off || !cells->face_vtx)
         return fail(VT_ERR_INVALID_ARG, "the adjoint needs vol, cen and the geometry of the tessellation");
+    {
+        const void* ptrs[] = {pts, gV, gC, gM, grad};
+        const char* names[] = {"pts", "gV", "gC", "gM", "grad"};
+        int r = check_device_buffers(stream, ptrs, names, 5);
+        if (!r) r = check_buffers(stream, nullptr, nullptr, cells);
+        if (r) return r;
+    }
     cudaError_t e = launch_adjoint(pts, n, *cells, gV, gC, gM, grad, precision, make_grid(p, 1), (cudaStream_t)stream);
     return e == cudaSuccess ? VT_OK : cuda_fail(e, "adjoint");
+}
+
+int vt_lloyd_step(const float* pts, int64_t n, const double* grad, const double* vol, const vt_params* p,
+                  float* out, void* stream)
+{
+    if (n < 0) return fail(VT_ERR_INVALID_ARG, "n must be >= 0");
+    int e = check_params(p);
+    if (e) return e;
+    if (n == 0) return VT_OK;
+    if (!pts || !grad || !vol || !out) return fail(VT_ERR_INVALID_ARG, "NULL argument");
+    const void* ptrs[] = {pts, grad, vol, out};
+    const char* names[] = {"pts", "grad", "vol", "out"};
+    if ((e = check_device_buffers(stream, ptrs, names, 4))) return e;
+    cudaError_t ce = launch_lloyd_step(pts, n, grad, vol, make_grid(p, 1), out, (cudaStream_t)stream);
+    return ce == cudaSuccess ? VT_OK : cuda_fail(ce, "lloyd step");
 }
 
 int vt_read_status(void* ws, size_t ws_bytes, void* stream)
@@ -1086,6 +1164,7 @@ int vt_cluster_index(const float* pts, int64_t n_total, const vt_set_desc* plan,
                  : make_ctx(p, n_total, ws, ws_bytes, stream, c);
     if (e) return e;
     if (n_total > 0 && !pts) return fail(VT_ERR_INVALID_ARG, "pts is NULL");
+    if ((e = check_buffers(stream, pts, ws, nullptr, plan, set_off))) return e;
     if (plan) {
         if (!set_off) return fail(VT_ERR_INVALID_ARG, "a plan needs set_off");
         c.sets = reinterpret_cast<const GridDesc*>(plan);
@@ -1161,6 +1240,48 @@ int vt_read_stats(void* ws, size_t ws_bytes, vt_stats* stats, vt_cells_out* out,
     if (h.cap_overflow) return fail(VT_ERR_CAPACITY, "an output buffer was too small (needed_* hold the sizes)");
     if (h.n_unval) return fail(VT_ERR_UNVALIDATED, "%d cells could not be validated", h.n_unval);
     return VT_OK;
+}
+
+int vt_unvalidated_cells(const vt_params* p, int64_t n, int32_t* ids, int64_t cap, int64_t* count, void* ws,
+                         size_t ws_bytes, void* stream)
+{
+    int e = check_params(p);
+    if (e) return e;
+    if (!count) return fail(VT_ERR_INVALID_ARG, "count is NULL");
+    if (n < 0 || n > (int64_t)INT32_MAX / 2) return fail(VT_ERR_INVALID_ARG, "n out of range: %lld", (long long)n);
+    if (cap < 0 || (cap > 0 && !ids)) return fail(VT_ERR_INVALID_ARG, "ids is NULL with cap > 0");
+    // the sorted points and the cell lists precede every region whose size
+    // depends on the grid, so their offsets are the same for one set and for
+    // a batch of n points in total
+    const Layout L = make_layout(p, n);
+    const int64_t nn = n > 0 ? n : 1;
+    if (!ws || ws_bytes < L.list_a + sizeof(int32_t) * 7 * (size_t)nn)
+        return fail(VT_ERR_WORKSPACE, "workspace too small for %lld points", (long long)n);
+    if (cap > 0) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) (void)cudaGetLastError();
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(VT_ERR_INVALID_ARG, "vt_unvalidated_cells reads a count and cannot be captured");
+        if (!device_accessible(ids)) return fail(VT_ERR_INVALID_ARG, "ids is not device-accessible memory");
+    }
+    Ctx c;
+    c.base = (uint8_t*)ws;
+    c.s = (cudaStream_t)stream;
+    c.st = reinterpret_cast<DevStatus*>(c.base + L.status);
+    DevStatus h;
+    int r = read_status(c, h);
+    if (r) return r;
+    const int64_t cnt = h.n_unval;
+    *count = cnt;
+    if (!ids) return VT_OK;  // the count only
+    if (cnt > cap)
+        return fail(VT_ERR_CAPACITY, "%lld unvalidated cells, cap %lld", (long long)cnt, (long long)cap);
+    // the unvalidated list is the sixth of the cell lists
+    const int32_t* list = reinterpret_cast<const int32_t*>(c.base + L.list_a) + 5 * nn;
+    cudaError_t ce = launch_unvalidated_ids(list, cnt, reinterpret_cast<const float4*>(c.base + L.sorted),
+                                            p->index_space, ids, c.s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c.s);
+    return ce == cudaSuccess ? VT_OK : cuda_fail(ce, "unvalidated ids");
 }
 
 const char* vt_last_error(void) { return g_err.c_str(); }

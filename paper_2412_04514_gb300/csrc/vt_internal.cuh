@@ -531,6 +531,10 @@ Layout make_layout(const vt_params* p, int64_t n, int64_t cells = -1, bool batch
 // launch helpers shared by the translation units
 // ---------------------------------------------------------------------------
 int set_error(int code, const char* msg);  // records msg for vt_last_error, returns code
+// VT_ERR_INVALID_ARG (naming the buffer) unless every non-NULL ptrs[i] is
+// memory device code can use (device, managed or pinned host); skipped while
+// `stream` is being captured
+int check_device_buffers(void* stream, const void* const* ptrs, const char* const* names, int count);
 void count_launch(int n = 1);
 int64_t launches();
 
@@ -623,6 +627,16 @@ struct EmitArgs {
 };
 cudaError_t launch_emit_count(const EmitArgs& a, cudaStream_t s);  // counts + scans + totals
 cudaError_t launch_emit_write(const EmitArgs& a, const vt_cells_out& out, cudaStream_t s);  // device-checked caps
+// NaN into vol / cen / m2 of the unvalidated cells list[count] (count = *n_dev
+// when set, else n_host; n_bound sizes the grid)
+cudaError_t launch_mark_unvalidated(const int32_t* list, const int32_t* n_dev, int64_t n_host, int64_t n_bound,
+                                    const float4* sorted, int index_space, double* vol, double* cen, double* m2,
+                                    DevStatus* st, cudaStream_t s);
+cudaError_t launch_unvalidated_ids(const int32_t* list, int64_t cnt, const float4* sorted, int index_space,
+                                   int32_t* ids, cudaStream_t s);
+// Lloyd's update p <- p - grad / (2 vol), wrapped into a periodic box
+cudaError_t launch_lloyd_step(const float* pts, int64_t n, const double* grad, const double* vol, const GridDesc& g,
+                              float* out, cudaStream_t s);
 // g: the box (lo, hi) and its periodic flag
 cudaError_t launch_adjoint(const float* pts, int64_t n, const vt_cells_out& c, const double* gV, const double* gC,
                            const double* gM, double* grad, int precision, const GridDesc& g, cudaStream_t s);
