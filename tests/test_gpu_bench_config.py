@@ -20,6 +20,7 @@ import torch
 
 import oracle
 import paper_2412_04514_gb300 as vt
+from geometry_match import emitted_cell, match_cell, oracle_cell
 from paper_2412_04514_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -140,21 +141,20 @@ def test_bench_configuration_sampled_and_whole(workload, precision):
             for j in set(got[a].tolist()) ^ set(ref[a].tolist()):
                 assert tiny_face(want, a, j), (sample[a], j)
         assert len(bad) <= max(2, 1e-3 * len(sample))
-    # geometry of the sampled cells whose neighbours match: vertex count and
-    # vertex positions (FP64 to 1e-12, FP32 to 1e-5 of the cell's size)
-    vo, v = np_(cells.vtx_off), np_(cells.vtx)
-    start = np.concatenate([[0], np.cumsum(want["face_size"])])
+    # geometry of the sampled cells whose neighbours match: a one-to-one
+    # pairing of the vertices (FP64 to 1e-12, FP32 to 1e-5 of the cell's
+    # size) and every face the same cyclic loop with the same neighbour id
+    geo = tuple(np_(t) for t in (cells.vtx_off, cells.vtx, cells.face_off, cells.face_nbr, cells.face_vtx_off,
+                                 cells.face_vtx))
     for a, i in enumerate(sample):
         if not np.array_equal(got[a], ref[a]):
             continue
-        V = v[vo[i]:vo[i + 1]].astype(np.float64)
+        V, fv = emitted_cell(geo, i)
         assert len(V) == want["nvert"][a], (i, len(V), want["nvert"][a])
-        f0, f1 = want["face_off"][a], want["face_off"][a + 1]
-        W_ = np.unique(np.concatenate([want["face_vtx"][start[f]:start[f + 1]] for f in range(f0, f1)]), axis=0)
+        W_, fw = oracle_cell(want, a)
         scale = np.cbrt(want["vol"][a])
         # (FP32 vertices are float32 coordinates: a few ulps of |x| on top)
         amax = np.abs(W_).max()
         atol = 1e-12 * max(1.0, amax) if fp64 else 1e-5 * scale + 4 * np.finfo(np.float32).eps * amax
-        assert len(W_) == len(V)
-        np.testing.assert_allclose(np.sort(V, axis=0), np.sort(W_, axis=0), rtol=0, atol=atol)
+        match_cell(V, fv, W_, fw, atol)
     whole_output_properties(cells, periodic, fp64)

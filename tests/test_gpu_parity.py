@@ -15,6 +15,7 @@ import torch
 
 import oracle
 import paper_2412_04514_gb300 as vt
+from geometry_match import emitted_cell, match_cell, oracle_cell
 from paper_2412_04514_gb300 import _lib as L
 from paper_2412_04514_gb300 import workloads as W
 
@@ -236,22 +237,17 @@ def test_lattices_fp32():
 def test_geometry_fp64_matches_oracle(cfg0):
     pts, want = cfg0
     cells = vt.tessellate(dev(pts), vt.Params(precision="fp64", emit=("nbr", "vol", "geom")))
-    vo, v = np_(cells.vtx_off), np_(cells.vtx)
-    fo, fn, fvo, fv = np_(cells.face_off), np_(cells.face_nbr), np_(cells.face_vtx_off), np_(cells.face_vtx)
-    wfo, wsize, wtag, wv = want["face_off"], want["face_size"], want["face_tag"], want["face_vtx"]
-    wstart = np.concatenate([[0], np.cumsum(wsize)])
+    geo = tuple(np_(t) for t in (cells.vtx_off, cells.vtx, cells.face_off, cells.face_nbr, cells.face_vtx_off,
+                                 cells.face_vtx))
     p64 = pts.astype(np.float64)
     for i in range(0, len(pts), 5):
-        V = v[vo[i]:vo[i + 1]]
+        V, faces = emitted_cell(geo, i)
         assert len(V) == want["nvert"][i]
-        faces = {int(fn[f]): fv[fvo[f]:fvo[f + 1]] for f in range(fo[i], fo[i + 1])}
-        wfaces = {int(wtag[f]): wv[wstart[f]:wstart[f + 1]] for f in range(wfo[i], wfo[i + 1])}
-        assert set(faces) == set(wfaces)
-        for tag, loop in faces.items():
+        # one-to-one vertex pairing and the same cyclic loop per face, by id
+        W_, wfaces = oracle_cell(want, i)
+        match_cell(V, faces, W_, wfaces, 1e-13)
+        for tag, loop in faces:
             P = V[loop]
-            Q = wfaces[tag]
-            assert len(P) == len(Q)
-            np.testing.assert_allclose(np.sort(P, axis=0), np.sort(Q, axis=0), atol=1e-13)
             # counter-clockwise seen from outside: Newell normal points away from the generator
             nrm = np.cross(P - p64[i], np.roll(P, -1, axis=0) - p64[i]).sum(0)
             assert nrm @ (P.mean(0) - p64[i]) > 0
