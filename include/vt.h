@@ -17,11 +17,11 @@
  *    "Device" means memory device code can use at that address: device or
  *    managed allocations, or pinned host memory (cudaHostAlloc /
  *    cudaHostRegister, mapped at the same address under unified addressing),
- *    so outputs can be written straight into host memory. vt_tessellate,
- *    vt_tessellate_batch and vt_emit check their points, workspace and output
- *    pointers first (cudaPointerGetAttributes, skipped while the stream is
- *    being captured) and return VT_ERR_INVALID_ARG for any other memory
- *    (pageable host memory) without launching a kernel.
+ *    so outputs can be written straight into host memory. Every entry point
+ *    that launches work checks its buffers first (cudaPointerGetAttributes,
+ *    skipped while the stream is being captured) and returns
+ *    VT_ERR_INVALID_ARG for any other memory (pageable host memory) without
+ *    launching a kernel.
  *    Buffers are owned by the caller; the library never allocates, frees or
  *    keeps a pointer after a call returns.
  *  - Scratch memory is a caller-allocated device workspace of at least
@@ -66,7 +66,8 @@ typedef enum {
     VT_ERR_INVALID_ARG = 1,      /* bad argument, or a point that is not finite or not inside the box */
     VT_ERR_CUDA = 2,             /* a CUDA call failed (see vt_last_error) */
     VT_ERR_CAPACITY = 3,         /* an output buffer is too small: vt_cells_out.needed_* hold the sizes */
-    VT_ERR_UNVALIDATED = 4,      /* some cells could not be validated (count in vt_stats.unvalidated) */
+    VT_ERR_UNVALIDATED = 4,      /* some cells could not be validated (count in vt_stats.unvalidated, ids
+                                    from vt_unvalidated_cells; their vol / cen / m2 are NaN) */
     VT_ERR_DUPLICATE_POINTS = 5, /* two generators coincide (a neighbour at distance 0) */
     VT_ERR_TIMEOUT = 6,          /* a bounded device wait gave up */
     VT_ERR_WORKSPACE = 7         /* ws_bytes smaller than vt_workspace_size() */
@@ -232,20 +233,23 @@ VT_API int vt_grid_build(const float* pts, int64_t n, const vt_params* p, int G,
 
 /* The grid sort of vt_grid_build for callers that cannot allocate device
  * memory: a host program whose device memory is handed out up front by an
- * arena or pool it does not control, code running where a cudaMalloc would
- * synchronise the device or break a capture in progress, or an embedding
- * that must keep its device footprint fixed after start-up. Its scratch is a
- * device array inside this library, 17 MiB on every GPU that loads the
- * library, held until the process exits; inputs and outputs are still the
- * caller's device buffers (same layout as vt_grid_build; no workspace).
+ * arena or pool it does not control (a cudaMalloc there would fail or
+ * fragment the pool), or an embedding that must keep its device footprint
+ * fixed after start-up. Its scratch is a device array inside this library,
+ * 17 MiB on every GPU that loads the library, held until the process exits;
+ * inputs and outputs are still the caller's buffers (same layout as
+ * vt_grid_build; no workspace). pts, sorted, perm and cell_off must be memory
+ * device code can use; any other memory (pageable host) is VT_ERR_INVALID_ARG
+ * before anything is launched.
  * Limits: n <= 1,048,576 points and G^3 <= 1,048,576 grid cells; larger
  * requests return VT_ERR_INVALID_ARG without launching anything.
- * The first call on each device looks up the array's device address (with
- * that device current) and keeps it; make that first call before any stream
- * capture begins. Every call reuses the same array and clears what must start
- * at zero; calls whose work overlaps on a GPU (other streams, other host
- * threads) race on it, so serialise them. Blocking: returns after the sort has
- * finished on `stream`; a point that is not finite or outside the box gives
+ * Every call looks up the array's device address on the current device (no
+ * address is kept between calls, so a reset device is handled). Every call
+ * reuses the same array and clears what must start at zero; calls whose work
+ * overlaps on a GPU (other streams, other host threads) race on it, so
+ * serialise them. Blocking: synchronises `stream` and returns after the sort
+ * has finished, so it must not be called while `stream` is being captured
+ * (VT_ERR_INVALID_ARG). A point that is not finite or outside the box gives
  * VT_ERR_INVALID_ARG. The paper has no counterpart: this is a deployment
  * variant of the grid-sort stage. */
 VT_API int vt_grid_build_static(const float* pts, int64_t n, const vt_params* p, int G,
@@ -465,6 +469,21 @@ VT_API int vt_moments_adjoint(const float* pts, int64_t n, const vt_cells_out* c
                               const double* gC, const double* gM, const vt_params* p, double* grad,
                               void* stream);
 
+/* Lloyd relaxation (not in the paper; Lloyd's centroid update written as a
+ * gradient step on the energy sum_i M2_i): out[k] = p_k - grad_k / (2 V_k),
+ * which is the centroid c_k when grad is vt_moments_adjoint's gradient of
+ * sum_i M2_i (2 V_k (p_k - c_k)). pts[n*3], out[n*3] float32 (out may equal
+ * pts), grad[n*3] and vol[n] FP64, all device memory. The step runs in FP64
+ * and is rounded once to float32. p->box_lo/box_hi and VT_FLAG_PERIODIC give
+ * the box: in a periodic box the new point is moved by whole periods into
+ * [lo, hi) (from its float32 value, in FP64, rounded again; a coordinate that
+ * rounds onto hi becomes lo); in a walled box a coordinate that rounds onto
+ * hi becomes the largest float below hi. A NaN volume (an unvalidated cell)
+ * gives a NaN point, which the next tessellation refuses. Asynchronous on
+ * `stream`. */
+VT_API int vt_lloyd_step(const float* pts, int64_t n, const double* grad, const double* vol, const vt_params* p,
+                         float* out, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* diagnostics                                                         */
 /* ------------------------------------------------------------------ */
@@ -488,6 +507,19 @@ VT_API int vt_probe_fma(int precision, double* tflops, void* stream);
  * VT_ERR_CAPACITY when an output did not fit (nothing of that output was
  * written), VT_ERR_UNVALIDATED when cells stayed unvalidated, else VT_OK. */
 VT_API int vt_read_stats(void* ws, size_t ws_bytes, vt_stats* stats, vt_cells_out* out, void* stream);
+
+/* The cells the last vt_tessellate / vt_tessellate_batch call on workspace
+ * ws left unvalidated (the paper's security radius never proved them final;
+ * the call returned VT_ERR_UNVALIDATED). p and n are that call's parameters
+ * and point count (n_total for a batch). Blocking on `stream`: *count (host)
+ * receives how many there are, and, when ids is not NULL, ids[0..count)
+ * (device) their indices in p->index_space, in no particular order;
+ * VT_ERR_CAPACITY when count > cap (nothing written). The calls themselves
+ * write NaN into vol, cen and m2 of those cells, leave them without
+ * neighbours, faces or vertices, and keep every other cell exact. Not
+ * capturable (it reads a count). */
+VT_API int vt_unvalidated_cells(const vt_params* p, int64_t n, int32_t* ids, int64_t cap, int64_t* count, void* ws,
+                                size_t ws_bytes, void* stream);
 
 /* Message of the last failure on this host thread ("" if none). */
 VT_API const char* vt_last_error(void);

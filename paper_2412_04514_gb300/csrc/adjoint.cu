@@ -175,7 +175,44 @@ __global__ void __launch_bounds__(256) k_adjoint(const float* __restrict__ pts, 
     }
 }
 
+// Lloyd's update written as a gradient step on the energy sum_i M2_i:
+// p <- p - g / (2 V) with g = d(sum M2)/dp = 2 V (p - c), which lands on the
+// centroid (Lloyd 1982), in FP64 and rounded once to float32. In a periodic
+// box the new point is moved by whole periods into [lo, hi) (in FP64 from the
+// rounded value, rounded again; a value that rounds onto hi belongs at lo);
+// in a walled box a value that rounds onto hi is moved to the largest float
+// below it, so the next tessellation gets a valid point.
+__global__ void k_lloyd_step(const float* __restrict__ pts, int64_t n, const double* __restrict__ grad,
+                             const double* __restrict__ vol, GridDesc g, float* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / 3;
+        const int a = (int)(i - 3 * k);
+        const double lo = (double)g.lo[a], hi = (double)g.hi[a];
+        float x = (float)((double)pts[i] - grad[i] / (2.0 * vol[k]));
+        if (g.periodic) {
+            const double L = hi - lo, xd = (double)x;
+            x = (float)(xd - floor((xd - lo) / L) * L);
+            if (x >= g.hi[a]) x = g.lo[a];
+        } else if (x >= g.hi[a]) {
+            x = nextafterf(g.hi[a], g.lo[a]);
+        }
+        out[i] = x;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_lloyd_step(const float* pts, int64_t n, const double* grad, const double* vol, const GridDesc& g,
+                              float* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (3 * n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_lloyd_step<<<(unsigned)blocks, 256, 0, s>>>(pts, n, grad, vol, g, out);
+    count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_adjoint(const float* pts, int64_t n, const vt_cells_out& c, const double* gV, const double* gC,
                            const double* gM, double* grad, int precision, const GridDesc& g, cudaStream_t s)

@@ -5,10 +5,12 @@
 // The scratch is a file-scope __device__ array of STATIC_SCRATCH_BYTES. Every
 // GPU that loads the library holds it until the process exits. Host code may
 // not use the array's name as a device pointer (it names a host-side shadow),
-// so each device's first call resolves the real address with
-// cudaGetSymbolAddress, with that device current, and caches it.
+// so every call resolves the real address with cudaGetSymbolAddress on the
+// current device. Nothing is cached: after cudaDeviceReset, or when the
+// primary context is torn down and made again, the module is loaded anew and
+// the array may sit at another address. The lookup costs microseconds, next
+// to a blocking sort.
 #include <cstdio>
-#include <mutex>
 
 #include "vt_internal.cuh"
 
@@ -18,8 +20,6 @@ namespace {
 
 constexpr int64_t STATIC_MAX_POINTS = int64_t(1) << 20;  // generators per call
 constexpr int64_t STATIC_MAX_CELLS = int64_t(1) << 20;   // grid cells G^3 per call
-constexpr int STATIC_MAX_DEVICES = 64;
-
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // scratch layout (offsets in bytes), sized for the limits above
@@ -34,24 +34,13 @@ constexpr size_t STATIC_SCRATCH_BYTES = OFF_SCAN + SCAN_BYTES;
 
 static __device__ __align__(256) unsigned char g_grid_scratch[STATIC_SCRATCH_BYTES];
 
-std::mutex g_mu;
-unsigned char* g_scratch_addr[STATIC_MAX_DEVICES] = {};
-
-// device address of g_grid_scratch on the current device (resolved once per device)
+// device address of g_grid_scratch in the current device's context
 cudaError_t scratch_address(unsigned char** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_grid_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= STATIC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_grid_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<unsigned char*>(p);
     return cudaSuccess;
 }
 
@@ -78,6 +67,19 @@ extern "C" VT_API int vt_grid_build_static(const float* pts, int64_t n, const vt
     }
     if (scan_tmp_bytes(n > g3 ? n : g3) > SCAN_BYTES) return set_error(VT_ERR_INVALID_ARG, "scan scratch too small");
     if ((n > 0 && (!pts || !sorted || !perm)) || !cell_off) return set_error(VT_ERR_INVALID_ARG, "NULL buffer");
+    // the call waits for its own result, which a stream capture forbids
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) (void)cudaGetLastError();
+    if (cs != cudaStreamCaptureStatusNone)
+        return set_error(VT_ERR_INVALID_ARG, "vt_grid_build_static synchronises its stream and cannot be captured");
+    {
+        // a kernel is never launched on memory it cannot reach (pageable host
+        // memory): that is an argument error, not a fault
+        const void* ptrs[] = {pts, sorted, perm, cell_off};
+        const char* names[] = {"pts", "sorted", "perm", "cell_off"};
+        const int r = check_device_buffers(stream, ptrs, names, 4);
+        if (r) return r;
+    }
     unsigned char* base = nullptr;
     cudaError_t e = scratch_address(&base);
     if (e != cudaSuccess) return set_error(VT_ERR_CUDA, cudaGetErrorString(e));

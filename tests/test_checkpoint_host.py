@@ -1,7 +1,7 @@
 """Checkpoint / resume of Lloyd's iteration, on the host.
 
-The moments come from a stand-in for the GPU call (a smooth function of the
-points with a known gradient), so what is tested is the loop around it: a
+The moments and the update come from stand-ins for the GPU calls (a smooth
+function of the points with a known gradient, and the update on the host), so what is tested is the loop around it: a
 run interrupted by an exception and resumed from its checkpoint ends with
 the same points as an uninterrupted run, resuming with no checkpoint written
 starts from the given points, and no temporary file is left behind.
@@ -22,9 +22,15 @@ def fake_moments(q, params=None):
     return vol, cen, m2
 
 
+def fake_step(p, grad, vol, params=None):
+    # the update the library's vt_lloyd_step applies, on the host
+    return (p.to(torch.float64) - grad.to(torch.float64) / (2.0 * vol[:, None])).to(torch.float32)
+
+
 @pytest.fixture(autouse=True)
 def stand_in(monkeypatch):
     monkeypatch.setattr(api, "voronoi_moments", fake_moments)
+    monkeypatch.setattr(api, "lloyd_step", fake_step)
 
 
 def start_points():

@@ -124,3 +124,22 @@ def test_lloyd_1m_uniform_50_iterations_decreases_the_energy():
     assert all(b <= a * (1 + 1e-9) for a, b in zip(energies, energies[1:]))
     assert energies[-1] < 0.97 * energies[0]
     assert bool(((out >= 0) & (out < 1)).all())
+
+
+def test_lloyd_step_kernel_moves_wraps_and_clamps():
+    # target points t = p - g / (2 V): inside, beyond hi and below lo (periodic
+    # wrap by whole periods), and one that rounds onto hi
+    p = np.array([[0.5, 0.5, 0.5], [0.9, 0.1, 0.2], [0.3, 0.4, 0.6]], np.float32)
+    t = np.array([[0.25, 0.75, 0.125], [1.25, -0.5, 0.2], [1.0 - 1e-12, 0.4, 0.6]])
+    vol = np.array([0.5, 2.0, 1.0])
+    g = 2.0 * vol[:, None] * (p.astype(np.float64) - t)
+    dp, dg, dv = dev(p), dev(g), dev(vol)
+    walled = vt.lloyd_step(dp, dg, dv, vt.Params()).cpu().numpy()
+    want = t.astype(np.float32)
+    want[2, 0] = np.nextafter(np.float32(1), np.float32(0))  # rounds onto hi: the largest float below it
+    want[1] = [1.25, -0.5, 0.2]  # a walled box does not wrap (the centroid never leaves it)
+    assert np.array_equal(walled[[0, 2]], want[[0, 2]])
+    per = vt.lloyd_step(dp, dg, dv, vt.Params(periodic=True)).cpu().numpy()
+    assert np.array_equal(per[0], want[0])
+    assert np.array_equal(per[1], np.array([0.25, 0.5, 0.2], np.float32))
+    assert per[2, 0] == 0.0  # rounds onto hi: belongs at lo

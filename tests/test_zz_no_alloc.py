@@ -63,3 +63,61 @@ def test_static_grid_sort_rejects_requests_beyond_its_limit_and_recovers():
     assert code == L.VT_OK
     w_sorted, w_perm, w_off, _, _ = vt.grid_build(ok)
     assert torch.equal(s_perm, w_perm) and torch.equal(s_off, w_off)
+
+
+def test_static_grid_sort_refuses_pageable_host_buffers():
+    # plain (pageable) host memory is not memory device code can use on every
+    # system: the call checks its buffers first and returns an argument error
+    # without launching; where the system maps such memory for the device
+    # (coherent host memory), the call must give the same sort instead
+    lib = L.load()
+    params = vt.Params().c()
+    pts_h = W.uniform(1000, 8)
+    n = len(pts_h)
+    G = lib.vt_grid_resolution(ctypes.byref(params), n)
+    d_pts = torch.from_numpy(pts_h).cuda()
+    sorted_ = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    cell_off = torch.empty(G**3 + 1, dtype=torch.int32, device="cuda")
+    host_sorted = np.zeros((n, 4), np.float32)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    code, w_sorted, w_perm, w_off = _static_sort(lib, d_pts, params)
+    assert code == L.VT_OK
+    w_sorted = w_sorted.cpu().numpy()
+    code = lib.vt_grid_build_static(ctypes.c_void_p(pts_h.ctypes.data), n, ctypes.byref(params), G, ptr(sorted_),
+                                    ptr(perm), ptr(cell_off), stream)
+    if code == L.VT_ERR_INVALID_ARG:
+        assert b"pts is not device-accessible" in lib.vt_last_error()
+    else:
+        assert code == L.VT_OK
+        assert np.array_equal(sorted_.cpu().numpy().view(np.int32), w_sorted.view(np.int32))
+    code = lib.vt_grid_build_static(ptr(d_pts), n, ctypes.byref(params), G, ctypes.c_void_p(host_sorted.ctypes.data),
+                                    ptr(perm), ptr(cell_off), stream)
+    if code == L.VT_ERR_INVALID_ARG:
+        assert b"sorted is not device-accessible" in lib.vt_last_error()
+        assert not host_sorted.any()
+    else:
+        assert code == L.VT_OK
+        assert np.array_equal(host_sorted.view(np.int32), w_sorted.view(np.int32))
+
+
+def test_static_grid_sort_allocates_no_device_memory():
+    lib = L.load()
+    params = vt.Params().c()
+    pts = torch.from_numpy(W.mixed(200_000, 4, n_clumps=200)).cuda()
+    n = pts.shape[0]
+    G = lib.vt_grid_resolution(ctypes.byref(params), n)
+    sorted_ = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    cell_off = torch.empty(G**3 + 1, dtype=torch.int32, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    args = (ctypes.c_void_p(pts.data_ptr()), n, ctypes.byref(params), G, ctypes.c_void_p(sorted_.data_ptr()),
+            ctypes.c_void_p(perm.data_ptr()), ctypes.c_void_p(cell_off.data_ptr()), stream)
+    assert lib.vt_grid_build_static(*args) == L.VT_OK  # warm-up: the same kernels as the call measured
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    assert lib.vt_grid_build_static(*args) == L.VT_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
