@@ -169,7 +169,7 @@ def dist_barrier(world: int):
 
 
 def cpu_oracle_rate(pts: np.ndarray, sample_cells: int, seed: int = 12345, sub_box: bool = False,
-                    periodic: bool = False) -> dict:
+                    periodic: bool = False, one_core: bool = True) -> dict:
     """Times the FP64 CPU oracle on a sample of the workload's cells: random
     cells, or (sub_box) the cells of a seeded cube holding about that many
     generators. Returns the rate and the oracle's result for the sample."""
@@ -188,30 +188,52 @@ def cpu_oracle_rate(pts: np.ndarray, sample_cells: int, seed: int = 12345, sub_b
     t0 = time.perf_counter()
     r = oracle.tessellate(pts, k0=16, cells=idx, threads=cores, periodic=periodic)
     dt = time.perf_counter() - t0
-    # the same oracle on one core, on the first tenth of the sample
-    one = idx[: max(1, len(idx) // 10)]
-    t1 = time.perf_counter()
-    oracle.tessellate(pts, k0=16, cells=one, threads=1, periodic=periodic)
-    dt1 = time.perf_counter() - t1
+    one_core_rate = None
+    if one_core:  # the same oracle on one core, on the first tenth of the sample
+        one = idx[: max(1, len(idx) // 10)]
+        t1 = time.perf_counter()
+        oracle.tessellate(pts, k0=16, cells=one, threads=1, periodic=periodic)
+        dt1 = time.perf_counter() - t1
+        one_core_rate = {"value": len(one) / dt1, "cells": int(len(one)), "seconds": dt1}
     return {"value": len(idx) / dt, "seconds": dt, "cores": cores, "flops_per_cell": float(oracle.clip_flops(r).mean()),
-            "idx": idx, "result": r,
-            "one_core": {"value": len(one) / dt1, "cells": int(len(one)), "seconds": dt1},
+            "idx": idx, "result": r, "one_core": one_core_rate,
             "sample": f"{what} of the same {len(pts)}-point workload (kd-tree build included), FP64 oracle, "
                       f"{cores} threads"}
 
 
 def errors_vs_oracle(cells, cpu: dict) -> dict:
-    """Per-result error of a GPU tessellation on the oracle's sampled cells."""
+    """Per-result error of a GPU tessellation on the oracle's sampled cells.
+
+    Centroids: |dc| / |c| (the stated tolerance) and the stricter |dc| / V^(1/3).
+    Neighbour lists that differ are classified: a difference made only of
+    faces the oracle measures below 1e-6 V^(2/3) (or does not have) is a tiny
+    face at a near-degenerate vertex; anything else is counted apart."""
     idx, w = cpu["idx"], cpu["result"]
     vol = cells.vol.cpu().numpy()[idx]
     cen = cells.cen.cpu().numpy()[idx]
     rv = np.abs(vol - w["vol"]) / w["vol"]
-    rc = np.linalg.norm(cen - w["cen"], axis=1) / np.linalg.norm(w["cen"], axis=1)
+    dc = np.linalg.norm(cen - w["cen"], axis=1)
+    rc = dc / np.linalg.norm(w["cen"], axis=1)
+    sc = dc / np.cbrt(w["vol"])
     off, nbr = cells.nbr_off.cpu().numpy(), cells.nbr.cpu().numpy()
-    bad = sum(not np.array_equal(nbr[off[i]:off[i + 1]], w["nbr"][w["nbr_off"][a]:w["nbr_off"][a + 1]])
-              for a, i in enumerate(idx))
+    tiny_only, other = 0, 0
+    for a, i in enumerate(idx):
+        g = nbr[off[i]:off[i + 1]]
+        r = w["nbr"][w["nbr_off"][a]:w["nbr_off"][a + 1]]
+        if np.array_equal(g, r):
+            continue
+        f0, f1 = w["face_off"][a], w["face_off"][a + 1]
+        tags, areas = w["face_tag"][f0:f1], w["face_area"][f0:f1]
+        lim = 1e-6 * w["vol"][a] ** (2 / 3)
+        tiny = all((areas[tags == j].min() if np.any(tags == j) else 0.0) < lim
+                   for j in set(g.tolist()) ^ set(r.tolist()))
+        tiny_only += int(tiny)
+        other += int(not tiny)
     return {"cells": int(len(idx)), "vol_rel_max": float(rv.max()), "vol_rel_median": float(np.median(rv)),
-            "cen_rel_max": float(rc.max()), "cen_rel_median": float(np.median(rc)), "nbr_mismatch_cells": int(bad)}
+            "cen_rel_max": float(rc.max()), "cen_rel_median": float(np.median(rc)),
+            "cen_over_size_max": float(sc.max()), "cen_over_size_median": float(np.median(sc)),
+            "nbr_mismatch_cells": tiny_only + other, "nbr_mismatch_tiny_faces_only": tiny_only,
+            "nbr_mismatch_other": other}
 
 
 def run_reference(args, rank: int, world: int):
@@ -224,11 +246,13 @@ def run_reference(args, rank: int, world: int):
     pts = W.mixed(wl["n"], wl["seed"], n_clumps=wl.get("clumps", 1000), periodic=wl.get("periodic", False))
     per_step = args.ref_cells
     for i in range(args.warmup):
-        cpu_oracle_rate(pts, min(2000, per_step), seed=100 + i, periodic=wl.get("periodic", False))
+        cpu_oracle_rate(pts, min(2000, per_step), seed=100 + i, periodic=wl.get("periodic", False), one_core=False)
     times = []
     cores = None
     for i in range(args.steps):
-        r = cpu_oracle_rate(pts, per_step, seed=200 + i, periodic=wl.get("periodic", False))
+        # each step: the oracle's kd-tree over all points, then per_step random
+        # cells, all host threads (the GPU arm's cpu_baseline times the same)
+        r = cpu_oracle_rate(pts, per_step, seed=200 + i, periodic=wl.get("periodic", False), one_core=False)
         times.append(r["seconds"])
         cores = r["cores"]
     total = sum(times)
@@ -239,10 +263,86 @@ def run_reference(args, rank: int, world: int):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "n_points": wl["n"], "l2": "n/a (host)"},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{per_step} random cells per step of the {wl['n']}-point workload"},
+                         "sample": f"{per_step} random cells per step of the {wl['n']}-point workload (the "
+                                   "oracle's kd-tree over all points built inside each step, as in the GPU arm's "
+                                   "cpu_baseline), FP64 oracle, all host threads"},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def time_tessellation(pts, params, steps: int, warmup: int, stage_times: bool, flush, world: int):
+    """`steps` whole tessellations of the device points `pts` after `warmup`
+    untimed ones, each timed with CUDA events on the launching stream, L2
+    flushed before each. Returns (ms per step, stats per step, launches, the
+    last step's cells)."""
+    import torch
+
+    import paper_2412_04514_gb300 as vt
+
+    n = pts.shape[0]
+    dev = pts.device
+    ws = vt.Workspace(params, n, dev)
+    p = vt.Params(**{**params.__dict__, "stage_times": stage_times})
+    for _ in range(warmup):
+        vt.tessellate(pts, p, workspace=ws)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    ms, stats = [], []
+    launches0 = vt.launch_count()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    cells = None
+    for _ in range(steps):
+        cells = None  # the previous step's outputs go back to the allocator first
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        cells = vt.tessellate(pts, p, workspace=ws)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        stats.append(cells.stats)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    launches = vt.launch_count() - launches0
+    return ms, stats, launches, cells
+
+
+def measure_8m(args, dev, flush, world: int, rank: int) -> dict:
+    """The 8,388,608-point half of the metric: both forms on the mixed recipe
+    (seed 2), FP32 steps, then FP64 steps, then (rank 0, one GPU) their errors
+    against the oracle on a seeded sub-box of about 65,536 cells."""
+    import torch
+
+    import paper_2412_04514_gb300 as vt
+    from paper_2412_04514_gb300 import workloads as W
+
+    wl = WORKLOADS["mixed-8m"]
+    n = wl["n"]
+    pts_np = W.mixed(n, wl["seed"] + 1000 * rank, n_clumps=1000)
+    pts = torch.from_numpy(pts_np).to(dev)
+    emit = ("nbr", "vol", "cen", "geom")
+    out = {"workload": wl["desc"]}
+    keep = {}
+    for prec in ("fp32", "fp64"):
+        prm = vt.Params(precision=prec, k0=args.k0, k_max=args.k_max, threads_per_cell=32, emit=emit,
+                        grid_density=args.rho)
+        steps = args.steps_8m if prec == "fp32" else max(1, args.steps_8m - 1)
+        ms, st, _, cells = time_tessellation(pts, prm, steps, 3, False, flush, world)
+        tot = dist_max(sum(ms), world)
+        out[prec] = {"value": n * world * len(ms) / (tot / 1e3), "unit": "cells/s", "ms_per_step": tot / len(ms),
+                     "steps": len(ms), "warmup": 3, "status": st[-1]["status"]}
+        keep[prec] = vt.Cells(vol=cells.vol, cen=cells.cen, nbr_off=cells.nbr_off, nbr=cells.nbr)
+        cells = None
+        torch.cuda.empty_cache()
+    out["fp32_speedup"] = out["fp32"]["value"] / out["fp64"]["value"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(pts_np, 65536, seed=17, sub_box=True)
+        out["errors_vs_oracle"] = {"fp32_recheck": errors_vs_oracle(keep["fp32"], cpu),
+                                   "fp64": errors_vs_oracle(keep["fp64"], cpu), "sample": cpu["sample"]}
+    return out
 
 
 def run_gpu(args, rank: int, world: int, local: int):
@@ -267,30 +367,7 @@ def run_gpu(args, rank: int, world: int, local: int):
     emit = ("nbr", "vol", "cen", "geom")
 
     def timed(params: vt.Params, steps: int, warmup: int, stage_times: bool):
-        ws = vt.Workspace(params, n, dev)
-        p = vt.Params(**{**params.__dict__, "stage_times": stage_times})
-        for _ in range(warmup):
-            vt.tessellate(pts, p, workspace=ws)
-        torch.cuda.synchronize()
-        stream = torch.cuda.current_stream(dev)
-        ms, stats = [], []
-        launches0 = vt.launch_count()
-        dist_barrier(world)
-        torch.cuda.synchronize()
-        for _ in range(steps):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            cells = vt.tessellate(pts, p, workspace=ws)
-            b.record(stream)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
-            stats.append(cells.stats)
-        torch.cuda.synchronize()
-        dist_barrier(world)
-        launches = vt.launch_count() - launches0
-        return ms, stats, launches, cells
+        return time_tessellation(pts, params, steps, warmup, stage_times, flush, world)
 
     # warm up both forms, then time: FP32+recheck (headline) and plain FP64
     p32 = vt.Params(precision="fp32", k0=args.k0, k_max=args.k_max, threads_per_cell=32, emit=emit,
@@ -348,6 +425,12 @@ def run_gpu(args, rank: int, world: int, local: int):
                             "face_vtx") if getattr(out, f) is not None)
     e2e_tot = dist_max(sum(e2e_ms), world) if e2e_ms else 0.0
     e2e_value = n * world * len(e2e_ms) / (e2e_tot / 1e3) if e2e_ms else None
+    out = None
+    m8 = None
+    if args.workload == "mixed-1m" and args.steps_8m > 0:
+        with Clocks(local) as clk8:
+            m8 = measure_8m(args, dev, flush, world, rank)
+        m8["clocks"] = clk8.summary()
 
     if rank != 0:
         return
@@ -413,6 +496,11 @@ def run_gpu(args, rank: int, world: int, local: int):
                    "k0": args.k0, "k_max": args.k_max, "grid_density": args.rho, "threads_per_cell": 32,
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world} (independent clouds)"},
+        "fp64_value": None if args.steps_fp64 <= 0 else value64,
+        "fp32_speedup": None if args.steps_fp64 <= 0 else value / value64,
+        "value_8m": None if m8 is None else m8["fp32"]["value"],
+        "fp64_value_8m": None if m8 is None else m8["fp64"]["value"],
+        "fp32_speedup_8m": None if m8 is None else m8["fp32_speedup"],
         "fp64_form": None if args.steps_fp64 <= 0 else {
             "value": value64, "unit": "cells/s", "ms_per_step": tot64 / len(ms64), "steps": len(ms64),
             "stage_ms": {k: statistics.mean(s[k] for s in st64) for k in ("ms_grid", "ms_knn", "ms_clip", "ms_emit")},
@@ -438,6 +526,7 @@ def run_gpu(args, rank: int, world: int, local: int):
                                        for i in range(len(st32[-1]["ms_clip_pass"]))],
                    "fp64_rechecks": st32[-1]["fp64_rechecks"], "precision_retries": st32[-1]["precision_retries"],
                    "capacity_retries": st32[-1]["capacity_retries"], "unvalidated": st32[-1]["unvalidated"]},
+        "mixed_8m": m8,
     }
     print(json.dumps(line), flush=True)
 
@@ -641,10 +730,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--steps-fp64", type=int, default=3)
+    ap.add_argument("--steps-8m", type=int, default=3, help="steps of the 8M half of the metric (0: skip)")
     ap.add_argument("--workload", default="mixed-1m", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-cells", type=int, default=100_000)
-    ap.add_argument("--ref-cells", type=int, default=20_000)
+    ap.add_argument("--ref-cells", type=int, default=100_000)
     ap.add_argument("--flops-per-cell", type=float, default=25134.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--k0", type=int, default=16)
