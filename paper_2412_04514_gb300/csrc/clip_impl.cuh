@@ -177,16 +177,11 @@ __device__ __forceinline__ int nth_set(MaskW<W> m, int i)
     }
     return -1;
 }
-// the first n set bits of m
+// the bits of m at positions <= last
 template <int W>
-__device__ __forceinline__ MaskW<W> first_n(MaskW<W> m, int n)
+__device__ __forceinline__ MaskW<W> upto(MaskW<W> m, int last)
 {
     MaskW<W> r = m;
-    if (n <= 0) {
-        r.clear();
-        return r;
-    }
-    const int last = nth_set(m, n - 1);
 #pragma unroll
     for (int i = 0; i < W; ++i) {
         const int lim = last - 64 * i;  // keep bits <= lim in word i
@@ -289,6 +284,11 @@ __device__ __forceinline__ P64 plane64(int src, const float4* __restrict__ sorte
     return p;
 }
 
+// 1 / x correctly rounded (the value of the IEEE division, without its
+// general-purpose slow path)
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+
 template <typename Real>
 __device__ __forceinline__ bool solve3(Real ax, Real ay, Real az, Real ab, Real bx, Real by, Real bz, Real bb, Real cx,
                                        Real cy, Real cz, Real cb, Real& x, Real& y, Real& z, Real cond = (Real)0)
@@ -303,7 +303,7 @@ __device__ __forceinline__ bool solve3(Real ax, Real ay, Real az, Real ab, Real 
         const Real na = ax * ax + ay * ay + az * az, nb = bx * bx + by * by + bz * bz, nc = cx * cx + cy * cy + cz * cz;
         if (det * det < cond * cond * na * nb * nc) return false;
     }
-    Real inv = (Real)1 / det;
+    const Real inv = rcp(det);
     x = (ab * bcx + bb * cax + cb * abx) * inv;
     y = (ab * bcy + bb * cay + cb * aby) * inv;
     z = (ab * bcz + bb * caz + cb * abz) * inv;
@@ -762,21 +762,32 @@ struct Cell {
         // boundary edges of the removed patch: edge e of a removed vertex whose
         // neighbour across it survives (bit 3r+e of myedge)
         uint32_t myedge = 0;
-        for (uint32_t m = myout; m; m &= m - 1) {
-            const int r = __ffs(m) - 1;
-            const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[r * T + G.gl]);
 #pragma unroll
-            for (int e = 0; e < 3; ++e)
-                if (!out.test((adj >> (8 * e)) & 0xff)) myedge |= 1u << (3 * r + e);
+        for (int r = 0; r < VPL; ++r) {
+            if ((myout >> r) & 1u) {
+                const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[r * T + G.gl]);
+#pragma unroll
+                for (int e = 0; e < 3; ++e)
+                    if (!out.test((adj >> (8 * e)) & 0xff)) myedge |= 1u << (3 * r + e);
+            }
         }
         int total;
         int idx = G.scan(__popc(myedge), total);
         // new vertices go to slots that were free before this clip, so the
-        // removed vertices' topology stays readable until the ring is closed
+        // removed vertices' topology stays readable until the ring is closed;
+        // dlist[i] = the i-th free slot (the slot of the i-th new vertex)
         const M freem = mask_not(alive, VCAP);
         if (total > freem.count()) {
             if (G.gl == 0) atomicAdd(&st->detail[2], 1u);
             return CLIP_OVERFLOW;
+        }
+#pragma unroll
+        for (int r = 0; r < VPL; ++r) {
+            const int s = r * T + G.gl;
+            if (freem.test(s)) {
+                const int k = freem.rank(s);
+                if (k < total) sm.dlist[k] = (uint8_t)s;
+            }
         }
         for (uint32_t m = myedge; m; m &= m - 1) {
             const int bit = __ffs(m) - 1, r = bit / 3, e = bit - 3 * r;
@@ -799,8 +810,7 @@ struct Cell {
             const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
             const int w = sm.vadj[s][e];
             const int x = (ids >> (8 * e)) & 0xff, y = (ids >> (8 * (e == 2 ? 0 : e + 1))) & 0xff;
-            const int d = nth_set(freem, i);
-            sm.dlist[i] = (uint8_t)d;
+            const int d = sm.dlist[i];
             *reinterpret_cast<uint32_t*>(sm.vid[d]) = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)h << 16);
             sm.vadj[d][0] = (uint8_t)w;
             sm.vsrc[d] = (uint8_t)s;
@@ -865,7 +875,9 @@ struct Cell {
             }
         }
         if (h == np) ++np;
-        const M newm = first_n(freem, total);
+        M newm;
+        newm.clear();
+        if (total > 0) newm = upto(freem, sm.dlist[total - 1]);
         alive = mask_or(keep, newm);
         update_rows();
         G.sync();
@@ -1327,44 +1339,69 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
         int end = END_NEED_K;
         if (LIST && k > 0) {
             // neighbour list, nearest first, from the first unprocessed entry;
-            // each lane holds one entry of the current chunk of T and prefetches
-            // its entry of the next chunk
+            // each lane holds one entry of the current chunk of T (most lists
+            // are one chunk: no prefetch, which would hold registers the
+            // clipper needs)
             const int64_t li = (A.by_cell ? (int64_t)q : c) * (A.kstride ? A.kstride : k);
             const int32_t* nb = A.nbr + li;
             const Real* dd = reinterpret_cast<const Real*>(A.d2) + li;
             const int m0 = (resume && !A.restore) ? A.k_prev : 0;
-            int nj = m0 + G.gl < kc ? nb[m0 + G.gl] : -1;
-            Real nd = m0 + G.gl < kc ? dd[m0 + G.gl] : (Real)0;
-            float4 np4 = nj >= 0 ? A.sorted[img_index_t<PER>(nj)] : make_float4(0.f, 0.f, 0.f, 0.f);
+            // From list entry kf on, only the entries whose bisector still
+            // reaches the polyhedron are clipped: each lane tests its entry
+            // against the live vertices once (at entry kf, or at the start of a
+            // later chunk). A plane that misses the cell cannot cut the smaller
+            // cells that follow, so skipping it changes no cell. kf: the second
+            // half of a merged list (the first half starts from the box, where
+            // every plane reaches), the whole of a resumed list.
+            const int kf = A.complete ? m0 : (A.k_next > k ? k : (resume ? m0 : INT_MAX));
             bool stop = false;
             for (int base = m0; base < kc && !stop; base += T) {
-                const int cj = nj;
-                const Real cd = nd;
-                const float4 cp = np4;
-                const int nm = base + T + G.gl;
-                nj = nm < kc ? nb[nm] : -1;
-                nd = nm < kc ? dd[nm] : (Real)0;
-                np4 = nj >= 0 ? A.sorted[img_index_t<PER>(nj)] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int cj = base + G.gl < kc ? nb[base + G.gl] : -1;
+                const Real cd = base + G.gl < kc ? dd[base + G.gl] : (Real)0;
+                const float4 cp = cj >= 0 ? A.sorted[img_index_t<PER>(cj)] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const int cnt = kc - base < T ? kc - base : T;
                 // range lists: each lane tests its entry against the live vertices
                 // and only the entries that can cut are clipped, in list order
                 // (in k-nearest lists most entries cut, so every one is clipped)
+                const bool filtered = base >= kf;  // this whole chunk is tested at its start
                 bool want = false;
                 if (G.gl < cnt) {
-                    if (!A.complete || cj < 0) {
+                    if (!filtered || cj < 0) {
                         want = true;
                     } else {
                         const float3 o = img_off_t<PER>(cell.pi, cp, img_code_t<PER>(cj), grid);
                         want = cell.reaches(sm, o.x, o.y, o.z);
                     }
                 }
-                for (unsigned todo = G.ballot(want); todo; todo &= todo - 1u) {
+                unsigned todo = G.ballot(want);
+                bool tested = filtered;
+                // cells still open at entry k of a merged list (a filtered chunk
+                // may skip entry k itself: it is counted at the chunk's start)
+                if (A.k_next > k && filtered && base == k && G.gl == 0) atomicAdd((int*)&A.st->n_second, 1);
+                while (todo) {
                     const int t = __ffs(todo) - 1;
-                    if (A.k_next > k && base + t == k && G.gl == 0) atomicAdd((int*)&A.st->n_second, 1);
+                    todo &= todo - 1u;
+                    if (A.k_next > k && !filtered && base + t == k && G.gl == 0) atomicAdd((int*)&A.st->n_second, 1);
                     const int j = G.bcast(cj, t);
                     if (j < 0) { end = END_VALID; stop = true; break; }  // the list holds every other generator
                     const Real dj = G.bcast(cd, t);
                     if (cell.radius_ok(G, sm, dj, j, A.sorted, grid, A.st)) { end = END_VALID; stop = true; break; }
+                    if (!tested && base + t >= kf) {
+                        // entry kf inside this chunk: test it and the entries after it
+                        bool reach = false;
+                        if (G.gl >= t && G.gl < cnt) {
+                            if (cj < 0) {
+                                reach = true;
+                            } else {
+                                const float3 o = img_off_t<PER>(cell.pi, cp, img_code_t<PER>(cj), grid);
+                                reach = cell.reaches(sm, o.x, o.y, o.z);
+                            }
+                        }
+                        const unsigned rm = G.ballot(reach);
+                        todo &= rm;
+                        tested = true;
+                        if (!((rm >> t) & 1u)) continue;  // entry t misses the cell
+                    }
                     float4 p;
                     p.x = G.bcast(cp.x, t);
                     p.y = G.bcast(cp.y, t);
