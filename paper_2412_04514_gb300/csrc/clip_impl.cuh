@@ -1291,23 +1291,24 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Group<T> G;
     S& sm = reinterpret_cast<S*>(smem_raw)[threadIdx.x / T];
-    const int64_t gid = ((int64_t)blockIdx.x * CLIP_BLOCK + threadIdx.x) / T;
-    const int64_t ngroups = ((int64_t)gridDim.x * CLIP_BLOCK) / T;
+    // cell indices fit 32 bits (n < 2^30); 32-bit loop state keeps registers free
+    const int gid = (int)((blockIdx.x * CLIP_BLOCK + threadIdx.x) / T);
+    const int ngroups = (int)((gridDim.x * CLIP_BLOCK) / T);
     const int k = A.k;
     const bool resume = !ROBUST && A.state && (A.k_prev > 0 || A.restore);
     // the robust exhaustive variant first clips by a nearest-first list, so
     // that its walk meets an almost final cell (the regular one resumes the
     // saved polyhedron of the last list pass instead)
     constexpr bool LIST = !EXH || ROBUST;
-    int64_t nq = A.nq;
+    int nq = (int)A.nq;
     if (A.nq_dev) {  // device-counted: list entries [nq_off, nq_off + nq_cap)
         const int64_t want = (int64_t)*A.nq_dev - A.nq_off;
-        nq = want < 0 ? 0 : (want < A.nq_cap ? want : A.nq_cap);
+        nq = (int)(want < 0 ? 0 : (want < A.nq_cap ? want : A.nq_cap));
     }
     C cell;
     cell.stamp = 0;
 
-    for (int64_t c = gid; c < nq; c += ngroups) {
+    for (int c = gid; c < nq; c += ngroups) {
         // this cell's list length; with k_next the doubled list follows at once:
         // validation is tested before every entry, so a cell that the first k
         // entries validate stops at entry k exactly as a re-queue would
@@ -1316,16 +1317,22 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
         const int q = A.queries ? A.queries[c] : (int)c;
         const GridDesc& grid = grid_of(A.g, A.sets, A.set_of, q);
         cell.pi = A.sorted[q];
-        const int orig = __float_as_int(cell.pi.w);
-        const int64_t out_idx = A.index_space == VT_INDEX_ORIGINAL ? (int64_t)orig : (int64_t)q;
-        uint8_t* stp = A.state ? A.state + (size_t)q * A.state_stride : nullptr;
         double last_d2 = -1.0;
         int last_orig = -1;
 #ifdef VT_PROFILE
         long long tp0 = clock64();
         const int pb = EXH ? 8 : (A.complete ? 24 : 0);
 #endif
-        if (resume) cell.restore(G, sm, stp, last_d2, last_orig);
+        if (resume) {
+            // the walk resumes from the last list key; list passes set it anew
+            double ld;
+            int lo;
+            cell.restore(G, sm, A.state + (size_t)q * A.state_stride, ld, lo);
+            if (EXH) {
+                last_d2 = ld;
+                last_orig = lo;
+            }
+        }
         else cell.init_box(G, sm, grid);
         cell.dump_positions(G, sm);  // the per-lane cut tests read positions from shared memory
         G.sync();
@@ -1521,13 +1528,16 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
         if (end == END_VALID) {
             cell.dump_positions(G, sm);
             G.sync();
+            const int64_t out_idx = A.index_space == VT_INDEX_ORIGINAL ? (int64_t)__float_as_int(cell.pi.w) : (int64_t)q;
             finish_cell<Real, T, T * VPL, PCAP, typename C::M, PER>(sm, cell.alive, cell.np, cell.pi, G.gl, G.mask, out_idx,
                                                                A);
 #ifdef VT_PROFILE
             if (G.gl == 0) VT_PROF_ADD(pb + 6, clock64() - tp2);
 #endif
         } else {
-            if (end == END_NEED_K && !EXH && !ROBUST && A.state) cell.save(G, sm, stp, last_d2, last_orig);
+            if (end == END_NEED_K && !EXH && !ROBUST && A.state)
+                cell.save(G, sm, A.state + (size_t)q * A.state_stride, last_d2, last_orig);
+            const int64_t out_idx = A.index_space == VT_INDEX_ORIGINAL ? (int64_t)__float_as_int(cell.pi.w) : (int64_t)q;
             if (G.gl == 0) {
                 if (A.rec) {
                     RecHeader* hd = reinterpret_cast<RecHeader*>(A.rec + (size_t)out_idx * A.rec_stride);
