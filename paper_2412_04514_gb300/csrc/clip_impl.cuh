@@ -10,9 +10,11 @@
 // the generator is the origin):
 //  * planes n.x <= b in shared memory (SoA), with the source of each plane
 //    (sorted index of the neighbour, or -1..-6 for the walls x-,x+,y-,y+,z-,z+);
-//  * vertices in VCAP slots. Slot s lives in lane s % T, register row s / T
-//    (positions in registers, so the per-plane sign pass touches no memory).
-//    In shared memory each slot holds the three planes meeting at the vertex,
+//  * vertices in VCAP slots, all in shared memory. Lane s % T owns slot s
+//    (row s / T) for the per-vertex steps (the sign pass of a cut reads its
+//    rows' positions; keeping them in registers instead cost more spills
+//    than the loads). Each slot holds its position, the three planes meeting
+//    at the vertex,
 //    (a, b, c), counter-clockwise seen from outside, and three adjacency
 //    links: the vertex across the polyhedron edge between faces a&b, b&c and
 //    c&a. A 128-bit mask marks the live slots (group-uniform).
@@ -473,38 +475,35 @@ struct Cell {
     using SL = StateLayout<Real, VCAP, PCAP>;
     using M = MaskW<(VCAP + 63) / 64>;
 
-    Real vx[VPL], vy[VPL], vz[VPL];
+    // vertex positions live in the group's shared memory (sm.vpos): the
+    // registers go to the clip's temporaries instead
     M alive;          // group-uniform
     int np;           // planes in use (ids < np)
-    int rows;         // register rows holding live slots
+    int rows;         // rows (slot / T) holding live slots
     uint32_t stamp;   // clip counter for the ring tables (keeps counting across cells)
     Real R2;          // max |v|^2 over live vertices
     float4 pi;
 
-    __device__ __forceinline__ void set_row(int r, Real x, Real y, Real z)
+    __device__ __forceinline__ void get_row(const S& sm, int gl, int r, Real& x, Real& y, Real& z) const
     {
-#pragma unroll
-        for (int rr = 0; rr < VPL; ++rr)
-            if (rr == r) { vx[rr] = x; vy[rr] = y; vz[rr] = z; }
-    }
-    __device__ __forceinline__ void get_row(int r, Real& x, Real& y, Real& z) const
-    {
-        x = vx[0]; y = vy[0]; z = vz[0];
-#pragma unroll
-        for (int rr = 1; rr < VPL; ++rr)
-            if (rr == r) { x = vx[rr]; y = vy[rr]; z = vz[rr]; }
+        const int s = r * T + gl;
+        x = sm.vpos[s][0];
+        y = sm.vpos[s][1];
+        z = sm.vpos[s][2];
     }
 
     __device__ __forceinline__ void update_rows() { rows = (alive.top() + T - 1) / T; }
 
-    __device__ __forceinline__ void update_r2(const Group<T>& G)
+    __device__ __forceinline__ void update_r2(const Group<T>& G, const S& sm)
     {
         Real m = 0;
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
-            if (r < rows) {
-                const Real d = vx[r] * vx[r] + vy[r] * vy[r] + vz[r] * vz[r];
-                if (alive.test(r * T + G.gl) && d > m) m = d;
+            const int s = r * T + G.gl;
+            if (r < rows && alive.test(s)) {
+                const Real x = sm.vpos[s][0], y = sm.vpos[s][1], z = sm.vpos[s][2];
+                const Real d = x * x + y * y + z * z;
+                m = d > m ? d : m;
             }
         }
         R2 = G.max(m);
@@ -512,15 +511,17 @@ struct Cell {
 
     // axis-aligned bounding box of the live vertices (local frame), for the
     // exhaustive walk's support test
-    __device__ __forceinline__ void bbox(const Group<T>& G, float* lo3, float* hi3) const
+    __device__ __forceinline__ void bbox(const Group<T>& G, const S& sm, float* lo3, float* hi3) const
     {
         float l0 = FLT_MAX, l1 = FLT_MAX, l2 = FLT_MAX, h0 = -FLT_MAX, h1 = -FLT_MAX, h2 = -FLT_MAX;
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
-            if (r < rows && alive.test(r * T + G.gl)) {
-                l0 = fminf(l0, (float)vx[r]); h0 = fmaxf(h0, (float)vx[r]);
-                l1 = fminf(l1, (float)vy[r]); h1 = fmaxf(h1, (float)vy[r]);
-                l2 = fminf(l2, (float)vz[r]); h2 = fmaxf(h2, (float)vz[r]);
+            const int s = r * T + G.gl;
+            if (r < rows && alive.test(s)) {
+                const float x = (float)sm.vpos[s][0], y = (float)sm.vpos[s][1], z = (float)sm.vpos[s][2];
+                l0 = fminf(l0, x); h0 = fmaxf(h0, x);
+                l1 = fminf(l1, y); h1 = fmaxf(h1, y);
+                l2 = fminf(l2, z); h2 = fmaxf(h2, z);
             }
         }
 #pragma unroll
@@ -579,16 +580,15 @@ struct Cell {
         alive.clear();
         alive.w[0] = 0xffull;
         np = 6;
-#pragma unroll
-        for (int r = 0; r < VPL; ++r) {
-            const int s = r * T + G.gl;
-            vx[r] = ((s >> 2) & 1) ? hx : lx;
-            vy[r] = ((s >> 1) & 1) ? hy : ly;
-            vz[r] = (s & 1) ? hz : lz;
+        if (G.gl < 8) {
+            const int c = G.gl;
+            sm.vpos[c][0] = ((c >> 2) & 1) ? hx : lx;
+            sm.vpos[c][1] = ((c >> 1) & 1) ? hy : ly;
+            sm.vpos[c][2] = (c & 1) ? hz : lz;
         }
         update_rows();
         G.sync();
-        update_r2(G);
+        update_r2(G, sm);
     }
 
     // ---- save / restore between passes ------------------------------------
@@ -613,13 +613,13 @@ struct Cell {
             if (r < rows && alive.test(s)) {
                 vi[s] = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
                 va[s] = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
-                pos[s] = vx[r];
-                pos[VCAP + s] = vy[r];
-                pos[2 * VCAP + s] = vz[r];
+                pos[s] = sm.vpos[s][0];
+                pos[VCAP + s] = sm.vpos[s][1];
+                pos[2 * VCAP + s] = sm.vpos[s][2];
             }
         }
         float lo3[3], hi3[3];
-        bbox(G, lo3, hi3);
+        bbox(G, sm, lo3, hi3);
         if (G.gl == 0) {
             StateHdr* h = reinterpret_cast<StateHdr*>(st);
 #pragma unroll
@@ -662,9 +662,9 @@ struct Cell {
             if (r < rows && alive.test(s)) {
                 *reinterpret_cast<uint32_t*>(sm.vid[s]) = vi[s];
                 *reinterpret_cast<uint32_t*>(sm.vadj[s]) = va[s];
-                vx[r] = pos[s];
-                vy[r] = pos[VCAP + s];
-                vz[r] = pos[2 * VCAP + s];
+                sm.vpos[s][0] = pos[s];
+                sm.vpos[s][1] = pos[VCAP + s];
+                sm.vpos[s][2] = pos[2 * VCAP + s];
             }
         }
         G.sync();
@@ -685,7 +685,7 @@ struct Cell {
         for (uint32_t rm = lane_rows<T, VPL>(alive, G.gl); rm; rm &= rm - 1) {
             const int r = __ffs(rm) - 1;
             Real fx, fy, fz;
-            get_row(r, fx, fy, fz);
+            get_row(sm, G.gl, r, fx, fy, fz);
             const double d = vertex_r2_64(sm, r * T + G.gl, sorted, pi, grid, (double)fx, (double)fy, (double)fz);
             m = d > m ? d : m;
         }
@@ -712,7 +712,7 @@ struct Cell {
         for (int r = 0; r < VPL; ++r) {
             if (r < rows) {
                 const int s = r * T + G.gl;
-                const Real sv = nx * vx[r] + ny * vy[r] + nz * vz[r] - b;
+                const Real sv = nx * sm.vpos[s][0] + ny * sm.vpos[s][1] + nz * sm.vpos[s][2] - b;
                 const bool al = alive.test(s);
                 const bool o = al && sv > (Real)0;
                 if (Tol<Real>::fp32) {
@@ -732,7 +732,7 @@ struct Cell {
             for (uint32_t m = mynear; m; m &= m - 1) {
                 const int r = __ffs(m) - 1;
                 Real fx, fy, fz;
-                get_row(r, fx, fy, fz);
+                get_row(sm, G.gl, r, fx, fy, fz);
                 const int o = outside64(sm, r * T + G.gl, h, sorted, pi, grid, (double)fx, (double)fy, (double)fz,
                                         (double)R2);
                 myout = o ? (myout | (1u << r)) : (myout & ~(1u << r));
@@ -853,15 +853,6 @@ struct Cell {
             // ill-conditioned solves: interpolate along the cut edge from the
             // pre-clip positions (the new slots were free, so no overlap)
             if (G.gl == 0) atomicAdd(&st->detail[4], 1u);
-#pragma unroll
-            for (int r = 0; r < VPL; ++r) {
-                const int s = r * T + G.gl;
-                if (r < rows && alive.test(s)) {
-                    sm.vpos[s][0] = vx[r];
-                    sm.vpos[s][1] = vy[r];
-                    sm.vpos[s][2] = vz[r];
-                }
-            }
             G.sync();
             for (int i = G.gl; i < total; i += T) {
                 const int d = sm.dlist[i];
@@ -881,17 +872,7 @@ struct Cell {
         alive = mask_or(keep, newm);
         update_rows();
         G.sync();
-        // owners take the new positions into their registers
-#pragma unroll
-        for (int r = 0; r < VPL; ++r) {
-            const int s = r * T + G.gl;
-            if (r < rows && newm.test(s)) {
-                vx[r] = sm.vpos[s][0];
-                vy[r] = sm.vpos[s][1];
-                vz[r] = sm.vpos[s][2];
-            }
-        }
-        update_r2(G);
+        update_r2(G, sm);
         return CLIP_CUT;
     }
 
@@ -947,18 +928,6 @@ struct Cell {
         return false;
     }
 
-    __device__ __forceinline__ void dump_positions(const Group<T>& G, S& sm) const
-    {
-#pragma unroll
-        for (int r = 0; r < VPL; ++r) {
-            const int s = r * T + G.gl;
-            if (r < rows && alive.test(s)) {
-                sm.vpos[s][0] = vx[r];
-                sm.vpos[s][1] = vy[r];
-                sm.vpos[s][2] = vz[r];
-            }
-        }
-    }
 };
 
 // ---------------------------------------------------------------------------
@@ -1251,7 +1220,7 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP, PER>& c
 #endif
         if (r == CLIP_OVERFLOW) return END_OVERFLOW;
         if (r == CLIP_INCONSISTENT) return END_INCONSISTENT;
-        if (r == CLIP_CUT) cell.bbox(G, lo3, hi3);
+        if (r == CLIP_CUT) cell.bbox(G, sm, lo3, hi3);
     }
 #ifdef VT_PROFILE
     if (G.gl == 0) VT_PROF_ADD(22, clock64() - tb1);
@@ -1334,7 +1303,6 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
             }
         }
         else cell.init_box(G, sm, grid);
-        cell.dump_positions(G, sm);  // the per-lane cut tests read positions from shared memory
         G.sync();
 #ifdef VT_PROFILE
         long long tp1 = clock64();
@@ -1451,7 +1419,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
             const int iy = cell_coord(pq.y, grid.lo[1], grid.scale[1], Gr);
             const int iz = cell_coord(pq.z, grid.lo[2], grid.scale[2], Gr);
             float lo3[3], hi3[3];
-            cell.bbox(G, lo3, hi3);
+            cell.bbox(G, sm, lo3, hi3);
             const float r_in2 = last_orig >= 0 ? (float)last_d2 * (1.0f - 1e-4f) : -1.0f;
             int status = 0;
             constexpr bool per = PER;
@@ -1526,7 +1494,6 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
         if (G.gl == 0) VT_PROF_ADD(pb + 2, tp2 - tp1);
 #endif
         if (end == END_VALID) {
-            cell.dump_positions(G, sm);
             G.sync();
             const int64_t out_idx = A.index_space == VT_INDEX_ORIGINAL ? (int64_t)__float_as_int(cell.pi.w) : (int64_t)q;
             finish_cell<Real, T, T * VPL, PCAP, typename C::M, PER>(sm, cell.alive, cell.np, cell.pi, G.gl, G.mask, out_idx,
