@@ -8,7 +8,10 @@
 // time. The k best candidates so far live in a sorted list spread over the
 // warp's registers (entry e = r*32 + lane, KPL registers per lane); a
 // qualifying candidate is inserted with one ballot per register row and one
-// shuffle-shift. After each shell the walk stops once the list is full and the
+// shuffle-shift. In the one-row float32 lists (k <= 32) qualifying candidates
+// first collect in a per-warp buffer of 32 in shared memory, which joins the
+// list by one bitonic sort and merge when it is full or the shell ends (a few
+// by single insertion). After each shell the walk stops once the list is full and the
 // k-th distance is no larger than the distance from the query to the outside
 // of the scanned block (minus a rounding margin), or the block covers the grid.
 #include <float.h>
@@ -27,6 +30,15 @@ constexpr unsigned FULL = 0xffffffffu;
 #ifndef VT_KNN_MERGE_MIN
 #define VT_KNN_MERGE_MIN 12
 #endif
+// one-row float32 lists: qualifying candidates wait in a per-warp buffer of 32
+// and join the list by one sort-and-merge when it fills or the shell ends
+// (buffers of at most this many are inserted one at a time instead)
+// (measured on the 1M mixed cloud: 12 against 6; merging at 16 buffered
+// entries instead of 32, or inserting batches of 2 or 4 at once, was slower)
+#ifndef VT_KNN_FLUSH_SINGLE
+#define VT_KNN_FLUSH_SINGLE 12
+#endif
+constexpr int KNN_BLOCK = 256;
 
 template <typename Real>
 struct Dist;
@@ -143,6 +155,31 @@ __device__ __forceinline__ void merge32(float& ld, int& lo, int& lj, float bd, i
     for (int j = 16; j > 0; j >>= 1) bitonic_step(ld, lo, lj, j, true, lane);
 }
 
+// Moves the warp's buffered candidates (nb of them, in bd/bo/bj) into the
+// one-row list: a few by single insertion, more by one bitonic sort and merge.
+// Updates count and, once the list holds k entries, the k-th key (kd, ko).
+template <int KPL>
+__device__ __forceinline__ void flush_buffer(WarpList<float, KPL>& L, const float* bd, const int* bo, const int* bj,
+                                             int nb, int k, int& count, float& kd, int& ko, int lane)
+{
+    if (nb <= VT_KNN_FLUSH_SINGLE) {
+        for (int i = 0; i < nb; ++i) {
+            // a buffered candidate may have been overtaken by earlier ones
+            if (count == k && !key_less(bd[i], bo[i], kd, ko)) continue;
+            L.insert(bd[i], bo[i], bj[i], k, lane);
+            if (count < k) ++count;
+            if (count == k) L.entry(k - 1, kd, ko);
+        }
+        return;
+    }
+    float d = lane < nb ? bd[lane] : __int_as_float(0x7f800000);
+    int o = lane < nb ? bo[lane] : INT_MAX, j = lane < nb ? bj[lane] : -1;
+    bitonic_sort32(d, o, j, lane);
+    merge32(L.d[0], L.o[0], L.j[0], d, o, j, lane);
+    count = count + nb < k ? count + nb : k;
+    if (count == k) L.entry(k - 1, kd, ko);
+}
+
 // The FP64 form's list: entries keep the float32 key f (relative error below
 // 3e-7 of the exact distance) and the exact FP64 key d, computed only when
 // two float32 keys are too close to order (within 2e-6) or at the end (d is
@@ -240,7 +277,7 @@ struct WarpList64 {
 #define VT_KNN_MINB 4
 #endif
 template <typename Real, int KPL, bool PER>
-__global__ void __launch_bounds__(256, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn(const float4* __restrict__ sorted, const int32_t* __restrict__ cell_off0,
+__global__ void __launch_bounds__(KNN_BLOCK, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn(const float4* __restrict__ sorted, const int32_t* __restrict__ cell_off0,
                                              const __grid_constant__ GridDesc g0, const GridDesc* __restrict__ sets,
                                              const int32_t* __restrict__ set_of, const int32_t* __restrict__ queries,
                                              int64_t nq_host, const int32_t* __restrict__ nq_dev,
@@ -250,6 +287,13 @@ __global__ void __launch_bounds__(256, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn(const
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // candidate buffer of the warp (one-row float32 lists)
+    __shared__ float s_bd[KNN_BLOCK / 32][32];
+    __shared__ int s_bo[KNN_BLOCK / 32][32], s_bj[KNN_BLOCK / 32][32];
+    float* bufd = s_bd[threadIdx.x >> 5];
+    int* bufo = s_bo[threadIdx.x >> 5];
+    int* bufj = s_bj[threadIdx.x >> 5];
+    constexpr bool BUF = sizeof(Real) == 4 && KPL == 1;
     int64_t nq = nq_host;
     if (nq_dev) {  // device-counted: this launch takes entries [nq_off, nq_off + nq_host) of the list
         const int64_t want = (int64_t)*nq_dev - nq_off;
@@ -269,6 +313,7 @@ __global__ void __launch_bounds__(256, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn(const
         WarpList64<KPL> L64;       // FP64 form
         if (F64) L64.init(); else L.init();
         int count = 0;
+        int nb = 0;  // buffered candidates
         float kd = __int_as_float(0x7f800000);  // float key of the k-th entry once the list is full
         int ko = INT_MAX;
         bool dup = false;
@@ -337,7 +382,34 @@ __global__ void __launch_bounds__(256, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn(const
                         cand = count < k || (F64 ? cd <= kd * (1.0f + 2e-6f) : key_less(cd, co, kd, ko));
                     }
                     unsigned m = __ballot_sync(FULL, cand);
-                    if (!F64 && KPL == 1 && __popc(m) >= VT_KNN_MERGE_MIN) {
+                    if (BUF) {
+                        // into the buffer; a full buffer is merged and the rest
+                        // of the batch re-tested against the new k-th key
+                        int add = __popc(m);
+                        int rank = __popc(m & ((1u << lane) - 1u));
+                        while (add > 0) {
+                            const int room = 32 - nb;
+                            if (cand && rank < room) {
+                                bufd[nb + rank] = cd;
+                                bufo[nb + rank] = co;
+                                bufj[nb + rank] = jj;
+                            }
+                            if (add < room) {
+                                nb += add;
+                                break;
+                            }
+                            __syncwarp();
+                            flush_buffer<KPL>(L, bufd, bufo, bufj, 32, k, count, kd, ko, lane);
+                            nb = 0;
+                            __syncwarp();
+                            cand = cand && rank >= room && (count < k || key_less(cd, co, kd, ko));
+                            m = __ballot_sync(FULL, cand);
+                            add = __popc(m);
+                            rank = __popc(m & ((1u << lane) - 1u));
+                        }
+                        m = 0;
+                    }
+                    if (!BUF && !F64 && KPL == 1 && __popc(m) >= VT_KNN_MERGE_MIN) {
                         // many candidates at once (the list filling up): sort the
                         // batch and merge it into the list with bitonic networks
                         float bd = cand ? cd : __int_as_float(0x7f800000);
@@ -365,6 +437,12 @@ __global__ void __launch_bounds__(256, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn(const
                         }
                     }
                 }
+            }
+            if (BUF && nb > 0) {  // the shell's candidates join the list before the stop test
+                __syncwarp();
+                flush_buffer<KPL>(L, bufd, bufo, bufj, nb, k, count, kd, ko, lane);
+                nb = 0;
+                __syncwarp();
             }
             // stop rule
             if (per) {
@@ -403,7 +481,7 @@ cudaError_t launch_knn_t(const float4* sorted, const int32_t* cell_off, const Gr
     if (nq <= 0) return cudaSuccess;
     int64_t blocks = (nq + 7) / 8;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    dim3 grid((unsigned)blocks), block(256);
+    dim3 grid((unsigned)blocks), block(KNN_BLOCK);
     // the periodic walk is its own instantiation (the non-periodic kernels keep their registers)
     auto kern = k <= 32 ? (g.periodic ? k_knn<Real, 1, true> : k_knn<Real, 1, false>)
               : k <= 64 ? (g.periodic ? k_knn<Real, 2, true> : k_knn<Real, 2, false>)
