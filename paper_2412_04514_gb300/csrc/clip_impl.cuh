@@ -342,8 +342,34 @@ struct GroupSmem {
             uint8_t deg[PCAP];
         } tail;
     } u;
-    Real vpos[VCAP][3];
+    // (x, y, z, |v|^2) of each slot; the slots of dead vertices hold zeros,
+    // so a plane test over all slots of the live rows needs no mask
+    alignas(16) Real vpos[VCAP][4];
 };
+
+// vertex slot access: one 16-byte shared-memory access per float vertex
+template <typename Real>
+struct V4 { Real x, y, z, w; };
+__device__ __forceinline__ V4<float> ldv(const float (*vp)[4], int s)
+{
+    const float4 t = *reinterpret_cast<const float4*>(vp[s]);
+    return {t.x, t.y, t.z, t.w};
+}
+__device__ __forceinline__ V4<double> ldv(const double (*vp)[4], int s)
+{
+    const double2 a = *reinterpret_cast<const double2*>(vp[s]);
+    const double2 b = *reinterpret_cast<const double2*>(vp[s] + 2);
+    return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void stv(float (*vp)[4], int s, float x, float y, float z)
+{
+    *reinterpret_cast<float4*>(vp[s]) = make_float4(x, y, z, x * x + y * y + z * z);
+}
+__device__ __forceinline__ void stv(double (*vp)[4], int s, double x, double y, double z)
+{
+    *reinterpret_cast<double2*>(vp[s]) = make_double2(x, y);
+    *reinterpret_cast<double2*>(vp[s] + 2) = make_double2(z, x * x + y * y + z * z);
+}
 
 enum ClipResult { CLIP_NONE = 0, CLIP_CUT = 1, CLIP_OVERFLOW = 2, CLIP_INCONSISTENT = 3 };
 enum CellEnd { END_VALID = 0, END_NEED_K = 1, END_OVERFLOW = 2, END_INCONSISTENT = 3 };
@@ -454,8 +480,9 @@ template <typename Real, typename S>
 __device__ VT_RARE void interp_vertex(const S& sm, int s, Real nx, Real ny, Real nz, Real b, Real* xyz)
 {
     const int v = sm.vsrc[s], w = sm.vadj[s][0];
-    const Real px = sm.vpos[v][0], py = sm.vpos[v][1], pz = sm.vpos[v][2];
-    const Real qx = sm.vpos[w][0], qy = sm.vpos[w][1], qz = sm.vpos[w][2];
+    const V4<Real> pv = ldv(sm.vpos, v), qv = ldv(sm.vpos, w);
+    const Real px = pv.x, py = pv.y, pz = pv.z;
+    const Real qx = qv.x, qy = qv.y, qz = qv.z;
     const Real sv = nx * px + ny * py + nz * pz - b, sw = nx * qx + ny * qy + nz * qz - b;
     Real t = sv - sw > (Real)0 ? sv / (sv - sw) : (Real)0.5;
     t = t < (Real)0 ? (Real)0 : (t > (Real)1 ? (Real)1 : t);
@@ -486,10 +513,10 @@ struct Cell {
 
     __device__ __forceinline__ void get_row(const S& sm, int gl, int r, Real& x, Real& y, Real& z) const
     {
-        const int s = r * T + gl;
-        x = sm.vpos[s][0];
-        y = sm.vpos[s][1];
-        z = sm.vpos[s][2];
+        const V4<Real> v = ldv(sm.vpos, r * T + gl);
+        x = v.x;
+        y = v.y;
+        z = v.z;
     }
 
     __device__ __forceinline__ void update_rows() { rows = (alive.top() + T - 1) / T; }
@@ -501,8 +528,7 @@ struct Cell {
         for (int r = 0; r < VPL; ++r) {
             const int s = r * T + G.gl;
             if (r < rows && alive.test(s)) {
-                const Real x = sm.vpos[s][0], y = sm.vpos[s][1], z = sm.vpos[s][2];
-                const Real d = x * x + y * y + z * z;
+                const Real d = sm.vpos[s][3];
                 m = d > m ? d : m;
             }
         }
@@ -518,7 +544,8 @@ struct Cell {
         for (int r = 0; r < VPL; ++r) {
             const int s = r * T + G.gl;
             if (r < rows && alive.test(s)) {
-                const float x = (float)sm.vpos[s][0], y = (float)sm.vpos[s][1], z = (float)sm.vpos[s][2];
+                const V4<Real> v = ldv(sm.vpos, s);
+                const float x = (float)v.x, y = (float)v.y, z = (float)v.z;
                 l0 = fminf(l0, x); h0 = fmaxf(h0, x);
                 l1 = fminf(l1, y); h1 = fmaxf(h1, y);
                 l2 = fminf(l2, z); h2 = fmaxf(h2, z);
@@ -580,11 +607,13 @@ struct Cell {
         alive.clear();
         alive.w[0] = 0xffull;
         np = 6;
-        if (G.gl < 8) {
-            const int c = G.gl;
-            sm.vpos[c][0] = ((c >> 2) & 1) ? hx : lx;
-            sm.vpos[c][1] = ((c >> 1) & 1) ? hy : ly;
-            sm.vpos[c][2] = (c & 1) ? hz : lz;
+#pragma unroll
+        for (int r = 0; r < VPL; ++r) {  // the corners in slots 0..7, zeros elsewhere
+            const int c = r * T + G.gl;
+            if (c < 8)
+                stv(sm.vpos, c, ((c >> 2) & 1) ? hx : lx, ((c >> 1) & 1) ? hy : ly, (c & 1) ? hz : lz);
+            else
+                stv(sm.vpos, c, (Real)0, (Real)0, (Real)0);
         }
         update_rows();
         G.sync();
@@ -613,9 +642,10 @@ struct Cell {
             if (r < rows && alive.test(s)) {
                 vi[s] = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
                 va[s] = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
-                pos[s] = sm.vpos[s][0];
-                pos[VCAP + s] = sm.vpos[s][1];
-                pos[2 * VCAP + s] = sm.vpos[s][2];
+                const V4<Real> v = ldv(sm.vpos, s);
+                pos[s] = v.x;
+                pos[VCAP + s] = v.y;
+                pos[2 * VCAP + s] = v.z;
             }
         }
         float lo3[3], hi3[3];
@@ -662,9 +692,9 @@ struct Cell {
             if (r < rows && alive.test(s)) {
                 *reinterpret_cast<uint32_t*>(sm.vid[s]) = vi[s];
                 *reinterpret_cast<uint32_t*>(sm.vadj[s]) = va[s];
-                sm.vpos[s][0] = pos[s];
-                sm.vpos[s][1] = pos[VCAP + s];
-                sm.vpos[s][2] = pos[2 * VCAP + s];
+                stv(sm.vpos, s, pos[s], pos[VCAP + s], pos[2 * VCAP + s]);
+            } else {
+                stv(sm.vpos, s, (Real)0, (Real)0, (Real)0);
             }
         }
         G.sync();
@@ -712,7 +742,8 @@ struct Cell {
         for (int r = 0; r < VPL; ++r) {
             if (r < rows) {
                 const int s = r * T + G.gl;
-                const Real sv = nx * sm.vpos[s][0] + ny * sm.vpos[s][1] + nz * sm.vpos[s][2] - b;
+                const V4<Real> v = ldv(sm.vpos, s);
+                const Real sv = nx * v.x + ny * v.y + nz * v.z - b;
                 const bool al = alive.test(s);
                 const bool o = al && sv > (Real)0;
                 if (Tol<Real>::fp32) {
@@ -837,9 +868,7 @@ struct Cell {
             Real px, py, pz;
             if (solve3<Real>(sm.pnx[x], sm.pny[x], sm.pnz[x], sm.pb[x], sm.pnx[y], sm.pny[y], sm.pnz[y], sm.pb[y], nx,
                              ny, nz, b, px, py, pz, (Real)Tol<Real>::cond_rel)) {
-                sm.vpos[d][0] = px;
-                sm.vpos[d][1] = py;
-                sm.vpos[d][2] = pz;
+                stv(sm.vpos, d, px, py, pz);
             } else {
                 sm.vpos[d][0] = (Real)NAN;  // marks an interpolated vertex
                 need = true;
@@ -859,12 +888,15 @@ struct Cell {
                 if (isnan(sm.vpos[d][0])) {
                     Real xyz[3];
                     interp_vertex<Real>(sm, d, nx, ny, nz, b, xyz);
-                    sm.vpos[d][0] = xyz[0];
-                    sm.vpos[d][1] = xyz[1];
-                    sm.vpos[d][2] = xyz[2];
+                    stv(sm.vpos, d, xyz[0], xyz[1], xyz[2]);
                 }
             }
         }
+        // the removed vertices' slots become zeros (read by whole-row plane
+        // tests); the interpolation above still needed their positions
+#pragma unroll
+        for (int r = 0; r < VPL; ++r)
+            if ((myout >> r) & 1u) stv(sm.vpos, r * T + G.gl, (Real)0, (Real)0, (Real)0);
         if (h == np) ++np;
         M newm;
         newm.clear();
@@ -913,17 +945,31 @@ struct Cell {
     // live vertex, positions read from sm.vpos: false only when each vertex is
     // inside by more than 1e-5 |n| R, beyond the band the sign test re-decides
     // in FP64, so a plane that fails cannot cut and clip() would do nothing.
+    // (Every slot of the live rows is read, four at a time: dead slots hold
+    // zeros, which pass only when lim < 0, a harmless extra clip.)
     __device__ __forceinline__ bool reaches(const S& sm, float nx, float ny, float nz) const
     {
         const float nn = nx * nx + ny * ny + nz * nz;
         const float lim = 0.5f * nn - 1e-5f * sqrtf(nn * (float)R2) - 1e-30f;
+        if (!Tol<Real>::fp32) {  // FP64 slots are twice as wide: only the live ones
 #pragma unroll
-        for (int w = 0; w < M::W_; ++w) {
-            for (uint64_t m = alive.w[w]; m; m &= m - 1ull) {
-                const int s = w * 64 + __ffsll((long long)m) - 1;
-                const float d = nx * (float)sm.vpos[s][0] + ny * (float)sm.vpos[s][1] + nz * (float)sm.vpos[s][2];
-                if (d > lim) return true;
+            for (int w = 0; w < M::W_; ++w) {
+                for (uint64_t m = alive.w[w]; m; m &= m - 1ull) {
+                    const V4<Real> v = ldv(sm.vpos, w * 64 + __ffsll((long long)m) - 1);
+                    if (nx * (float)v.x + ny * (float)v.y + nz * (float)v.z > lim) return true;
+                }
             }
+            return false;
+        }
+        const int ns = rows * T;
+        for (int s = 0; s < ns; s += 4) {
+            const V4<Real> a = ldv(sm.vpos, s), b = ldv(sm.vpos, s + 1), c = ldv(sm.vpos, s + 2),
+                           d = ldv(sm.vpos, s + 3);
+            const float da = nx * (float)a.x + ny * (float)a.y + nz * (float)a.z;
+            const float db = nx * (float)b.x + ny * (float)b.y + nz * (float)b.z;
+            const float dc = nx * (float)c.x + ny * (float)c.y + nz * (float)c.z;
+            const float dd = nx * (float)d.x + ny * (float)d.y + nz * (float)d.z;
+            if (fmaxf(fmaxf(da, db), fmaxf(dc, dd)) > lim) return true;
         }
         return false;
     }
@@ -946,12 +992,14 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
         if (!alive.test(s)) continue;
         const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
         const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[s]);
-        const Real ax = sm.vpos[s][0], ay = sm.vpos[s][1], az = sm.vpos[s][2];
-        const Real a2 = ax * ax + ay * ay + az * az;
+        const V4<Real> va = ldv(sm.vpos, s);
+        const Real ax = va.x, ay = va.y, az = va.z;
+        const Real a2 = va.w;
         for (int t = 0; t < 3; ++t) {
             const int f = (ids >> (8 * t)) & 0xff;
             const int nv = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
-            const Real bx = sm.vpos[nv][0], by = sm.vpos[nv][1], bz = sm.vpos[nv][2];
+            const V4<Real> vb = ldv(sm.vpos, nv);
+            const Real bx = vb.x, by = vb.y, bz = vb.z;
             const Real fnx = sm.pnx[f], fny = sm.pny[f], fnz = sm.pnz[f], fb = sm.pb[f];
             const Real sc = fb / (fnx * fnx + fny * fny + fnz * fnz);
             const Real qx = fnx * sc, qy = fny * sc, qz = fnz * sc;
@@ -984,8 +1032,9 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
                 const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[cur]);
                 const int t = ((ids & 0xff) == (uint32_t)f) ? 0 : ((((ids >> 8) & 0xff) == (uint32_t)f) ? 1 : 2);
                 const int nxt = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
-                const Real ux = sm.vpos[cur][0] - qx, uy = sm.vpos[cur][1] - qy, uz = sm.vpos[cur][2] - qz;
-                const Real wx = sm.vpos[nxt][0] - qx, wy = sm.vpos[nxt][1] - qy, wz = sm.vpos[nxt][2] - qz;
+                const V4<Real> vc = ldv(sm.vpos, cur), vn = ldv(sm.vpos, nxt);
+                const Real ux = vc.x - qx, uy = vc.y - qy, uz = vc.z - qz;
+                const Real wx = vn.x - qx, wy = vn.y - qy, wz = vn.z - qz;
                 area += (uy * wz - uz * wy) * fnx + (uz * wx - ux * wz) * fny + (ux * wy - uy * wx) * fnz;
                 cur = nxt;
                 ++deg;
@@ -1123,9 +1172,10 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
             if (!alive.test(s)) continue;
             const int li = alive.rank(s);
             if (li < REC_VERTS) {
-                rv[3 * li] = (double)pi.x + (double)sm.vpos[s][0];
-                rv[3 * li + 1] = (double)pi.y + (double)sm.vpos[s][1];
-                rv[3 * li + 2] = (double)pi.z + (double)sm.vpos[s][2];
+                const V4<Real> v = ldv(sm.vpos, s);
+                rv[3 * li] = (double)pi.x + (double)v.x;
+                rv[3 * li + 1] = (double)pi.y + (double)v.y;
+                rv[3 * li + 2] = (double)pi.z + (double)v.z;
             }
         }
         nface = base_fi;
