@@ -1210,11 +1210,14 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP, PER>& c
 #endif
     const float4 pq = cell.pi;
     float4 pc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float ex = 0.f, ey = 0.f, ez = 0.f;
     bool need = false;
     if (valid) {
         pc = A.sorted[img_index_t<PER>(jj)];
         const float3 o = img_off_t<PER>(pq, pc, code, grid);
-        const float ex = o.x, ey = o.y, ez = o.z;
+        ex = o.x;
+        ey = o.y;
+        ez = o.z;
         const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
         const float r4 = 4.0f * (float)cell.R2;
         const float hb =
@@ -1239,9 +1242,13 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP, PER>& c
     if (G.gl == 0 && mm == 0) VT_PROF_ADD(23, 1);
     const long long tb1 = clock64();
 #endif
+    // survivors nearest first: the nearest cut most, so the intermediate
+    // polyhedra stay small and fewer of the others still cut
+    const uint32_t dkey = __float_as_uint(fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
     while (mm) {
-        const int src = __ffs(mm) - 1;
-        mm &= mm - 1;
+        const uint32_t mn = __reduce_min_sync(G.mask, ((mm >> G.gl) & 1u) ? dkey : 0xffffffffu);
+        const int src = __ffs(G.ballot(((mm >> G.gl) & 1u) && dkey == mn)) - 1;
+        mm &= ~(1u << src);
         float4 p;
         p.x = G.bcast(pc.x, src);
         p.y = G.bcast(pc.y, src);
@@ -1270,7 +1277,11 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP, PER>& c
 #endif
         if (r == CLIP_OVERFLOW) return END_OVERFLOW;
         if (r == CLIP_INCONSISTENT) return END_INCONSISTENT;
-        if (r == CLIP_CUT) cell.bbox(G, sm, lo3, hi3);
+        if (r == CLIP_CUT) {
+            cell.bbox(G, sm, lo3, hi3);
+            // the batch's other survivors against the smaller cell
+            if (mm) mm &= G.ballot(((mm >> G.gl) & 1u) && cell.reaches(sm, ex, ey, ez));
+        }
     }
 #ifdef VT_PROFILE
     if (G.gl == 0) VT_PROF_ADD(22, clock64() - tb1);
