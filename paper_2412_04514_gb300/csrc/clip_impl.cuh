@@ -335,11 +335,10 @@ struct GroupSmem {
             uint32_t end_of[PCAP];
         } ring;
         struct {
-            Real area[PCAP];
+            Real sc[PCAP];        // b / |n|^2: the foot of the generator's perpendicular is n * sc
             int32_t key[PCAP];
             int32_t first[PCAP];  // lowest live slot on the face (a face's walk starts there)
-            int32_t oid[PCAP];    // the output id of the face's neighbour (or its wall id)
-            uint8_t deg[PCAP];
+            int32_t deg[PCAP];    // live vertices on the face
         } tail;
     } u;
     // (x, y, z, |v|^2) of each slot; the slots of dead vertices hold zeros,
@@ -370,6 +369,7 @@ __device__ __forceinline__ void stv(double (*vp)[4], int s, double x, double y, 
     *reinterpret_cast<double2*>(vp[s]) = make_double2(x, y);
     *reinterpret_cast<double2*>(vp[s] + 2) = make_double2(z, x * x + y * y + z * z);
 }
+
 
 enum ClipResult { CLIP_NONE = 0, CLIP_CUT = 1, CLIP_OVERFLOW = 2, CLIP_INCONSISTENT = 3 };
 enum CellEnd { END_VALID = 0, END_NEED_K = 1, END_OVERFLOW = 2, END_INCONSISTENT = 3 };
@@ -983,10 +983,19 @@ template <typename Real, int T, int VCAP, int PCAP, typename M, bool PER>
 __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, int np, float4 pi, int gl,
                                          unsigned gmask, int64_t out_idx, const ClipArgs& A)
 {
-    for (int f = gl; f < np; f += T) sm.u.tail.first[f] = INT_MAX;
+    // per plane: q_f = n sc, the foot of the perpendicular from the
+    // generator onto it (the apex of the face's fan); counters (the union's
+    // other half is free: its size sets the shared memory per block, and with
+    // it the L1 left to the clipper's spills)
+    for (int f = gl; f < np; f += T) {
+        const Real fnx = sm.pnx[f], fny = sm.pny[f], fnz = sm.pnz[f];
+        sm.u.tail.sc[f] = sm.pb[f] / (fnx * fnx + fny * fny + fnz * fnz);
+        sm.u.tail.first[f] = INT_MAX;
+        sm.u.tail.deg[f] = 0;
+    }
     __syncwarp(gmask);
-    // per (vertex, face) terms: tetrahedron (0, q_f, v, next(v around f)),
-    // q_f = foot of the perpendicular from the generator onto face f
+    // per (vertex, face) terms: tetrahedron (0, q_f, v, next(v around f));
+    // each face's degree and lowest live slot
     Real vol = 0, mx = 0, my = 0, mz = 0, m2 = 0;
     for (int s = gl; s < VCAP; s += T) {
         if (!alive.test(s)) continue;
@@ -1000,9 +1009,8 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
             const int nv = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
             const V4<Real> vb = ldv(sm.vpos, nv);
             const Real bx = vb.x, by = vb.y, bz = vb.z;
-            const Real fnx = sm.pnx[f], fny = sm.pny[f], fnz = sm.pnz[f], fb = sm.pb[f];
-            const Real sc = fb / (fnx * fnx + fny * fny + fnz * fnz);
-            const Real qx = fnx * sc, qy = fny * sc, qz = fnz * sc;
+            const Real sc = sm.u.tail.sc[f];
+            const Real qx = sm.pnx[f] * sc, qy = sm.pny[f] * sc, qz = sm.pnz[f] * sc;
             const Real cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
             const Real dv = (qx * cx + qy * cy + qz * cz) * (Real)(1.0 / 6.0);
             const Real sx = qx + ax + bx, sy = qy + ay + by, sz = qz + az + bz;
@@ -1012,39 +1020,8 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
             mz += dv * sz;
             m2 += dv * (qx * qx + qy * qy + qz * qz + a2 + bx * bx + by * by + bz * bz + sx * sx + sy * sy + sz * sz);
             atomicMin(&sm.u.tail.first[f], s);
+            atomicAdd(&sm.u.tail.deg[f], 1);
         }
-    }
-    __syncwarp(gmask);
-    // face areas (and degrees) by walking each face from its lowest slot, so
-    // the sums and the emitted loops do not depend on thread timing
-    for (int f = gl; f < np; f += T) {
-        Real area = 0;
-        int deg = 0;
-        const int s0 = sm.u.tail.first[f];
-        if (s0 != INT_MAX) {
-            const Real fnx = sm.pnx[f], fny = sm.pny[f], fnz = sm.pnz[f], fb = sm.pb[f];
-            const Real nn = fnx * fnx + fny * fny + fnz * fnz;
-            const Real sc = fb / nn;
-            const Real qx = fnx * sc, qy = fny * sc, qz = fnz * sc;
-            int cur = s0;
-            do {
-                const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[cur]);
-                const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[cur]);
-                const int t = ((ids & 0xff) == (uint32_t)f) ? 0 : ((((ids >> 8) & 0xff) == (uint32_t)f) ? 1 : 2);
-                const int nxt = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
-                const V4<Real> vc = ldv(sm.vpos, cur), vn = ldv(sm.vpos, nxt);
-                const Real ux = vc.x - qx, uy = vc.y - qy, uz = vc.z - qz;
-                const Real wx = vn.x - qx, wy = vn.y - qy, wz = vn.z - qz;
-                area += (uy * wz - uz * wy) * fnx + (uz * wx - ux * wz) * fny + (ux * wy - uy * wx) * fnz;
-                cur = nxt;
-                ++deg;
-            } while (cur != s0 && deg <= VCAP);
-            area *= (Real)0.5 / sqrt(nn);
-        } else {
-            sm.u.tail.first[f] = -1;
-        }
-        sm.u.tail.area[f] = area;
-        sm.u.tail.deg[f] = (uint8_t)(deg > 255 ? 255 : deg);
     }
     // FP64 sums across the lanes by reduce-scatter: the five sums (padded to
     // eight slots) are halved between partners at the first three levels, so
@@ -1074,37 +1051,7 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
     const double MY = 0.25 * __shfl_sync(gmask, w, T / 4, T);
     const double MZ = 0.25 * __shfl_sync(gmask, w, T / 4 + T / 8, T);
     const double M2 = 0.05 * __shfl_sync(gmask, w, T / 2, T);
-    __syncwarp(gmask);
-    // neighbour keys: planes with a face of area above the threshold (the
-    // threshold of the FP32 form in float32: the FP64 pipe is scarce)
-    Real tau;
-    if (Tol<Real>::fp32) {
-        const float cv = cbrtf((float)V);
-        tau = (Real)((float)Tol<Real>::area_rel * cv * cv);
-    } else {
-        tau = (Real)(Tol<Real>::area_rel * cbrt(V * V));
-    }
-    constexpr bool per = PER;
-    for (int f = gl; f < np; f += T) {
-        const int src = sm.psrc[f];
-        int oid = src;  // wall ids stay
-        if (per) {  // the generator whose image the face faces; the cube's faces face the cell's own
-            if (src < 0)
-                oid = (int)out_idx;
-            else if (sm.u.tail.first[f] >= 0)
-                oid = A.index_space == VT_INDEX_ORIGINAL ? __float_as_int(A.sorted[src & IMG_INDEX_MASK].w)
-                                                         : (src & IMG_INDEX_MASK);
-        } else if (src >= 0 && sm.u.tail.first[f] >= 0 && A.index_space == VT_INDEX_ORIGINAL) {
-            oid = __float_as_int(A.sorted[src].w);
-        }
-        sm.u.tail.oid[f] = oid;
-        // periodic: ids may repeat (two images of one generator); the key
-        // id * PCAP + plane is unique and sorts the same (ids <= 2^24 - 2 and
-        // planes < PCAP <= 128 keep it below the INT_MAX sentinel)
-        const int key = per ? oid * PCAP + f : oid;
-        sm.u.tail.key[f] = ((src >= 0 || per) && sm.u.tail.first[f] >= 0 && sm.u.tail.area[f] > tau) ? key : INT_MAX;
-    }
-    __syncwarp(gmask);
+    __syncwarp(gmask);  // the degrees and lowest slots are complete
     if (gl == 0) {
         if (A.vol) A.vol[out_idx] = V;
         if (A.cen) {
@@ -1116,7 +1063,92 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
         if (A.m2) A.m2[out_idx] = M2;
     }
     if (!A.rec) return;
+    // neighbour threshold (in float32 in the FP32 form: the FP64 pipe is scarce)
+    Real tau;
+    if (Tol<Real>::fp32) {
+        const float cv = cbrtf((float)V);
+        tau = (Real)((float)Tol<Real>::area_rel * cv * cv);
+    } else {
+        tau = (Real)(Tol<Real>::area_rel * cbrt(V * V));
+    }
     uint8_t* rec = A.rec + (size_t)out_idx * A.rec_stride;
+    const bool geom = (A.emit & VT_EMIT_GEOM) != 0;
+    int32_t* rfn = reinterpret_cast<int32_t*>(rec + REC_FNBR_OFF);
+    uint8_t* rdeg = rec + REC_FDEG_OFF;
+    uint8_t* rfv = rec + REC_FVTX_OFF;
+    // One walk per face (a lane per plane) from its lowest live slot, so that
+    // the sums and the emitted loops do not depend on thread timing: its area
+    // (the neighbour test) and, with geometry, its loop of vertex ranks, at
+    // the face's place in the record (an exclusive scan of (1, degree) over
+    // the planes, T planes at a time)
+    constexpr bool per = PER;
+    int base_fi = 0, base_pos = 0;
+    for (int f0 = 0; f0 < np; f0 += T) {
+        const int f = f0 + gl;
+        const int deg = f < np ? sm.u.tail.deg[f] : 0;
+        int fi = 0, pos = 0;
+        if (geom) {
+            const int v = deg | ((deg ? 1 : 0) << 16);
+            int inc = v;
+#pragma unroll
+            for (int d = 1; d < T; d <<= 1) {
+                const int u = __shfl_up_sync(gmask, inc, d, T);
+                if (gl >= d) inc += u;
+            }
+            const int tot = __shfl_sync(gmask, inc, T - 1, T);
+            const int ex = inc - v;
+            fi = base_fi + (ex >> 16);
+            pos = base_pos + (ex & 0xffff);
+            base_fi += tot >> 16;
+            base_pos += tot & 0xffff;
+        }
+        if (f >= np) continue;
+        const int src = sm.psrc[f];
+        int oid = src;  // wall ids stay
+        if (per) {  // the generator whose image the face faces; the cube's faces face the cell's own
+            if (src < 0)
+                oid = (int)out_idx;
+            else if (deg > 0)
+                oid = A.index_space == VT_INDEX_ORIGINAL ? __float_as_int(A.sorted[src & IMG_INDEX_MASK].w)
+                                                         : (src & IMG_INDEX_MASK);
+        } else if (src >= 0 && deg > 0 && A.index_space == VT_INDEX_ORIGINAL) {
+            oid = __float_as_int(A.sorted[src].w);
+        }
+        Real area = 0;
+        if (deg > 0) {
+            const bool put = geom && fi < REC_FACES && pos + deg <= 3 * REC_VERTS;
+            if (put) {
+                rfn[fi] = oid;
+                rdeg[fi] = (uint8_t)deg;
+            }
+            const Real fnx = sm.pnx[f], fny = sm.pny[f], fnz = sm.pnz[f];
+            const Real sc = sm.u.tail.sc[f];
+            const V4<Real> q = {fnx * sc, fny * sc, fnz * sc, (Real)0.5 / sqrt(fnx * fnx + fny * fny + fnz * fnz)};
+            int cur = sm.u.tail.first[f];
+            V4<Real> vc = ldv(sm.vpos, cur);
+            for (int t2 = 0; t2 < deg; ++t2) {
+                const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[cur]);
+                const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[cur]);
+                const int t = ((ids & 0xff) == (uint32_t)f) ? 0 : ((((ids >> 8) & 0xff) == (uint32_t)f) ? 1 : 2);
+                const int nxt = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
+                const V4<Real> vn = ldv(sm.vpos, nxt);
+                const Real ux = vc.x - q.x, uy = vc.y - q.y, uz = vc.z - q.z;
+                const Real wx = vn.x - q.x, wy = vn.y - q.y, wz = vn.z - q.z;
+                area += (uy * wz - uz * wy) * fnx + (uz * wx - ux * wz) * fny + (ux * wy - uy * wx) * fnz;
+                if (put) rfv[pos + t2] = (uint8_t)alive.rank(cur);
+                cur = nxt;
+                vc = vn;
+            }
+            area *= q.w;
+        }
+        // periodic: ids may repeat (two images of one generator); the key
+        // id * PCAP + plane is unique and sorts the same (ids <= 2^24 - 2 and
+        // planes < PCAP <= 128 keep it below the INT_MAX sentinel)
+        const int key = per ? oid * PCAP + f : oid;
+        sm.u.tail.key[f] = ((src >= 0 || per) && deg > 0 && area > tau) ? key : INT_MAX;
+    }
+    __syncwarp(gmask);
+    // neighbours ascending: each key's rank among the keys
     int32_t* rnbr = reinterpret_cast<int32_t*>(rec + REC_NBR_OFF);
     int c = 0;
     for (int f = gl; f < np; f += T) {
@@ -1130,44 +1162,10 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
     int nn_total = c;
 #pragma unroll
     for (int o = T / 2; o >= 1; o >>= 1) nn_total += __shfl_xor_sync(gmask, nn_total, o, T);
-    int nface = 0, nvtx = 0, nfv = 0;
-    if (A.emit & VT_EMIT_GEOM) {
+    int nvtx = 0;
+    if (geom) {
         nvtx = alive.count();
-        __syncwarp(gmask);
-        int32_t* rfn = reinterpret_cast<int32_t*>(rec + REC_FNBR_OFF);
-        uint8_t* rdeg = rec + REC_FDEG_OFF;
-        uint8_t* rfv = rec + REC_FVTX_OFF;
         double* rv = reinterpret_cast<double*>(rec + REC_VTX_OFF);
-        // face slot and face-vertex offset of every plane with a face: an
-        // exclusive scan of (1, degree) over the planes, T planes at a time
-        int base_fi = 0, base_pos = 0;
-        for (int f0 = 0; f0 < np; f0 += T) {
-            const int f = f0 + gl;
-            const int deg = f < np ? sm.u.tail.deg[f] : 0;
-            const int v = deg | ((deg ? 1 : 0) << 16);
-            int inc = v;
-#pragma unroll
-            for (int d = 1; d < T; d <<= 1) {
-                const int u = __shfl_up_sync(gmask, inc, d, T);
-                if (gl >= d) inc += u;
-            }
-            const int tot = __shfl_sync(gmask, inc, T - 1, T);
-            const int ex = inc - v;
-            const int fi = base_fi + (ex >> 16), pos = base_pos + (ex & 0xffff);
-            base_fi += tot >> 16;
-            base_pos += tot & 0xffff;
-            if (deg == 0 || fi >= REC_FACES || pos + deg > 3 * REC_VERTS) continue;
-            rfn[fi] = sm.u.tail.oid[f];
-            rdeg[fi] = (uint8_t)deg;
-            int cur = sm.u.tail.first[f];
-            for (int t2 = 0; t2 < deg; ++t2) {
-                rfv[pos + t2] = (uint8_t)alive.rank(cur);
-                const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[cur]);
-                const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[cur]);
-                const int t = ((ids & 0xff) == (uint32_t)f) ? 0 : ((((ids >> 8) & 0xff) == (uint32_t)f) ? 1 : 2);
-                cur = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
-            }
-        }
         for (int s = gl; s < VCAP; s += T) {
             if (!alive.test(s)) continue;
             const int li = alive.rank(s);
@@ -1178,10 +1176,9 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
                 rv[3 * li + 2] = (double)pi.z + (double)v.z;
             }
         }
-        nface = base_fi;
-        nfv = base_pos;
     }
     if (gl == 0) {
+        const int nface = geom ? base_fi : 0, nfv = geom ? base_pos : 0;
         const bool over = nn_total > REC_FACES || nface > REC_FACES || nvtx > REC_VERTS || nfv > 3 * REC_VERTS;
         if (over) atomicAdd((int*)&A.st->record_overflow, 1);
         RecHeader* hd = reinterpret_cast<RecHeader*>(rec);
