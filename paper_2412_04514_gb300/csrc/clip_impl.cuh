@@ -322,29 +322,50 @@ __device__ __forceinline__ bool vertex64(const P64& A, const P64& B, const P64& 
 // ---------------------------------------------------------------------------
 template <typename Real, int VCAP, int PCAP>
 struct GroupSmem {
-    Real pnx[PCAP], pny[PCAP], pnz[PCAP], pb[PCAP];
+    // Planes n.x <= b. In float32 the offset b of a bisector is |n|^2 / 2,
+    // formed from n where it is needed (the expression of clip_point), and
+    // the walls' offsets are kept apart: the footprint of a group sets the
+    // shared memory of a block, and with it the L1 left to the clipper's
+    // spilled registers. FP64 offsets are stored (the FP64 pipe is scarce).
+    static constexpr bool STORE_B = sizeof(Real) == 8;
+    Real pnx[PCAP], pny[PCAP], pnz[PCAP];
+    Real pbs[STORE_B ? PCAP : 1];
+    Real wall_b[8];         // offsets of the six walls (cube faces in a periodic box)
     int32_t psrc[PCAP];
     uint8_t vid[VCAP][4];   // planes a, b, c (ccw from outside)
     uint8_t vadj[VCAP][4];  // neighbour across a&b, b&c, c&a
-    uint8_t vsrc[VCAP];     // removed vertex whose cut edge created the slot (this clip)
-    uint16_t elist[VCAP];   // boundary edges of the current clip: slot | (edge << 8)
-    uint8_t dlist[VCAP];    // slot of the new vertex of each boundary edge
     union {
-        struct {
+        struct {  // one clip
             uint32_t start_of[PCAP];  // (stamp << 8) | slot
             uint32_t end_of[PCAP];
+            uint16_t elist[VCAP];     // boundary edges of the current clip: slot | (edge << 8)
+            uint8_t dlist[VCAP];      // slot of the new vertex of each boundary edge
+            uint8_t vsrc[VCAP];       // removed vertex whose cut edge created the slot
         } ring;
-        struct {
-            Real sc[PCAP];        // b / |n|^2: the foot of the generator's perpendicular is n * sc
-            int32_t key[PCAP];
+        struct {  // the finish of a validated cell
+            Real sc[PCAP];        // b / |n|^2 (the foot of the generator's perpendicular is n * sc); then
+                                  // the neighbour key of the face, written by the plane's own lane
             int32_t first[PCAP];  // lowest live slot on the face (a face's walk starts there)
             int32_t deg[PCAP];    // live vertices on the face
         } tail;
     } u;
+    __device__ __forceinline__ Real pb(int f) const
+    {
+        if (STORE_B) return pbs[f];
+        const int src = psrc[f];
+        if (src < 0) return wall_b[-src - 1];
+        return (Real)0.5 * (pnx[f] * pnx[f] + pny[f] * pny[f] + pnz[f] * pnz[f]);
+    }
     // (x, y, z, |v|^2) of each slot; the slots of dead vertices hold zeros,
     // so a plane test over all slots of the live rows needs no mask
     alignas(16) Real vpos[VCAP][4];
 };
+
+// a face's neighbour key in the slot of its plane's scale (bit patterns)
+__device__ __forceinline__ void put_key(float* a, int f, int key) { a[f] = __int_as_float(key); }
+__device__ __forceinline__ void put_key(double* a, int f, int key) { a[f] = __longlong_as_double((long long)key); }
+__device__ __forceinline__ int get_key(const float* a, int f) { return __float_as_int(a[f]); }
+__device__ __forceinline__ int get_key(const double* a, int f) { return (int)__double_as_longlong(a[f]); }
 
 // vertex slot access: one 16-byte shared-memory access per float vertex
 template <typename Real>
@@ -479,7 +500,7 @@ __device__ VT_RARE int free_plane(const S& sm, M keep, int gl, unsigned gmask, i
 template <typename Real, typename S>
 __device__ VT_RARE void interp_vertex(const S& sm, int s, Real nx, Real ny, Real nz, Real b, Real* xyz)
 {
-    const int v = sm.vsrc[s], w = sm.vadj[s][0];
+    const int v = sm.u.ring.vsrc[s], w = sm.vadj[s][0];
     const V4<Real> pv = ldv(sm.vpos, v), qv = ldv(sm.vpos, w);
     const Real px = pv.x, py = pv.y, pz = pv.z;
     const Real qx = qv.x, qy = qv.y, qz = qv.z;
@@ -590,7 +611,8 @@ struct Cell {
             sm.pnz[w] = axis == 2 ? one : (Real)0;
             const Real lo_a = axis == 0 ? lx : (axis == 1 ? ly : lz);
             const Real hi_a = axis == 0 ? hx : (axis == 1 ? hy : hz);
-            sm.pb[w] = upper ? hi_a : -lo_a;
+            sm.wall_b[w] = upper ? hi_a : -lo_a;
+            if (S::STORE_B) sm.pbs[w] = upper ? hi_a : -lo_a;
             sm.psrc[w] = -(w + 1);
         }
         if (G.gl < 8) {
@@ -630,7 +652,7 @@ struct Cell {
             pl[f] = sm.pnx[f];
             pl[PCAP + f] = sm.pny[f];
             pl[2 * PCAP + f] = sm.pnz[f];
-            pl[3 * PCAP + f] = sm.pb[f];
+            pl[3 * PCAP + f] = sm.pb(f);
             ps[f] = sm.psrc[f];
         }
         uint32_t* vi = reinterpret_cast<uint32_t*>(st + SL::VID);
@@ -679,7 +701,8 @@ struct Cell {
             sm.pnx[f] = pl[f];
             sm.pny[f] = pl[PCAP + f];
             sm.pnz[f] = pl[2 * PCAP + f];
-            sm.pb[f] = pl[3 * PCAP + f];
+            if (ps[f] < 0) sm.wall_b[-ps[f] - 1] = pl[3 * PCAP + f];
+            if (S::STORE_B) sm.pbs[f] = pl[3 * PCAP + f];
             sm.psrc[f] = ps[f];
         }
         update_rows();
@@ -817,34 +840,34 @@ struct Cell {
             const int s = r * T + G.gl;
             if (freem.test(s)) {
                 const int k = freem.rank(s);
-                if (k < total) sm.dlist[k] = (uint8_t)s;
+                if (k < total) sm.u.ring.dlist[k] = (uint8_t)s;
             }
         }
         for (uint32_t m = myedge; m; m &= m - 1) {
             const int bit = __ffs(m) - 1, r = bit / 3, e = bit - 3 * r;
-            sm.elist[idx++] = (uint16_t)((r * T + G.gl) | (e << 8));
+            sm.u.ring.elist[idx++] = (uint16_t)((r * T + G.gl) | (e << 8));
         }
         if (G.gl == 0) {
             sm.pnx[h] = nx;
             sm.pny[h] = ny;
             sm.pnz[h] = nz;
-            sm.pb[h] = b;
             sm.psrc[h] = src;
+            if (S::STORE_B) sm.pbs[h] = b;
         }
         ++stamp;
         const uint32_t tag = stamp << 8;
         G.sync();
         // one boundary edge per lane: the new vertex (x, y, h) on the cut edge
         for (int i = G.gl; i < total; i += T) {
-            const uint32_t ev = sm.elist[i];
+            const uint32_t ev = sm.u.ring.elist[i];
             const int s = ev & 0xff, e = ev >> 8;
             const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
             const int w = sm.vadj[s][e];
             const int x = (ids >> (8 * e)) & 0xff, y = (ids >> (8 * (e == 2 ? 0 : e + 1))) & 0xff;
-            const int d = sm.dlist[i];
+            const int d = sm.u.ring.dlist[i];
             *reinterpret_cast<uint32_t*>(sm.vid[d]) = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)h << 16);
             sm.vadj[d][0] = (uint8_t)w;
-            sm.vsrc[d] = (uint8_t)s;
+            sm.u.ring.vsrc[d] = (uint8_t)s;
             sm.u.ring.start_of[x] = tag | (uint32_t)d;
             sm.u.ring.end_of[y] = tag | (uint32_t)d;
             // the survivor w: its link across y&x now points to d
@@ -857,7 +880,7 @@ struct Cell {
         // close the ring around h and solve the new positions
         bool bad = false, need = false;
         for (int i = G.gl; i < total; i += T) {
-            const int d = sm.dlist[i];
+            const int d = sm.u.ring.dlist[i];
             const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[d]);
             const int x = ids & 0xff, y = (ids >> 8) & 0xff;
             const uint32_t so = sm.u.ring.start_of[y], eo = sm.u.ring.end_of[x];
@@ -866,7 +889,7 @@ struct Cell {
             sm.vadj[d][1] = (uint8_t)(so & 0xff);
             sm.vadj[d][2] = (uint8_t)(eo & 0xff);
             Real px, py, pz;
-            if (solve3<Real>(sm.pnx[x], sm.pny[x], sm.pnz[x], sm.pb[x], sm.pnx[y], sm.pny[y], sm.pnz[y], sm.pb[y], nx,
+            if (solve3<Real>(sm.pnx[x], sm.pny[x], sm.pnz[x], sm.pb(x), sm.pnx[y], sm.pny[y], sm.pnz[y], sm.pb(y), nx,
                              ny, nz, b, px, py, pz, (Real)Tol<Real>::cond_rel)) {
                 stv(sm.vpos, d, px, py, pz);
             } else {
@@ -884,7 +907,7 @@ struct Cell {
             if (G.gl == 0) atomicAdd(&st->detail[4], 1u);
             G.sync();
             for (int i = G.gl; i < total; i += T) {
-                const int d = sm.dlist[i];
+                const int d = sm.u.ring.dlist[i];
                 if (isnan(sm.vpos[d][0])) {
                     Real xyz[3];
                     interp_vertex<Real>(sm, d, nx, ny, nz, b, xyz);
@@ -900,7 +923,7 @@ struct Cell {
         if (h == np) ++np;
         M newm;
         newm.clear();
-        if (total > 0) newm = upto(freem, sm.dlist[total - 1]);
+        if (total > 0) newm = upto(freem, sm.u.ring.dlist[total - 1]);
         alive = mask_or(keep, newm);
         update_rows();
         G.sync();
@@ -989,7 +1012,7 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
     // it the L1 left to the clipper's spills)
     for (int f = gl; f < np; f += T) {
         const Real fnx = sm.pnx[f], fny = sm.pny[f], fnz = sm.pnz[f];
-        sm.u.tail.sc[f] = sm.pb[f] / (fnx * fnx + fny * fny + fnz * fnz);
+        sm.u.tail.sc[f] = sm.pb(f) / (fnx * fnx + fny * fny + fnz * fnz);
         sm.u.tail.first[f] = INT_MAX;
         sm.u.tail.deg[f] = 0;
     }
@@ -1145,18 +1168,18 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
         // id * PCAP + plane is unique and sorts the same (ids <= 2^24 - 2 and
         // planes < PCAP <= 128 keep it below the INT_MAX sentinel)
         const int key = per ? oid * PCAP + f : oid;
-        sm.u.tail.key[f] = ((src >= 0 || per) && deg > 0 && area > tau) ? key : INT_MAX;
+        put_key(sm.u.tail.sc, f, ((src >= 0 || per) && deg > 0 && area > tau) ? key : INT_MAX);
     }
     __syncwarp(gmask);
     // neighbours ascending: each key's rank among the keys
     int32_t* rnbr = reinterpret_cast<int32_t*>(rec + REC_NBR_OFF);
     int c = 0;
     for (int f = gl; f < np; f += T) {
-        const int key = sm.u.tail.key[f];
+        const int key = get_key(sm.u.tail.sc, f);
         if (key == INT_MAX) continue;
         ++c;
         int rank = 0;
-        for (int g2 = 0; g2 < np; ++g2) rank += sm.u.tail.key[g2] < key ? 1 : 0;
+        for (int g2 = 0; g2 < np; ++g2) rank += get_key(sm.u.tail.sc, g2) < key ? 1 : 0;
         if (rank < REC_FACES) rnbr[rank] = PER ? key / PCAP : key;
     }
     int nn_total = c;
