@@ -476,6 +476,17 @@ def run_gpu(args, rank: int, world: int, local: int):
         return {"bound": "hbm", "bytes": int(nbytes), "ms": ms, "achieved_gbs": gbs, "peak_gbs": hbm,
                 "frac": gbs / hbm, "bytes_are": what}
 
+    # the k-nearest-neighbour kernels against the FP32 peak: one squared
+    # distance per candidate examined (3 subtractions, a product, two fused
+    # multiply-adds: 8 flops), over their own CUDA-event time
+    kl_ms = statistics.mean(s["ms_knn_lists"] for s in st32)
+    cands = statistics.mean(s["knn_candidates"] for s in st32)
+    queries = statistics.mean(s["knn_queries"] for s in st32)
+    knn_tflops = cands * 8 / (kl_ms / 1e3) / 1e12 if kl_ms > 0 else None
+    knn_alu = {"bound": "alu", "ms": kl_ms, "candidates_per_query": cands / max(queries, 1), "queries": int(queries),
+               "flops_per_candidate": 8, "achieved_tflops": knn_tflops, "peak_tflops": FP32_PEAK_TFLOPS,
+               "frac": None if knn_tflops is None else knn_tflops / FP32_PEAK_TFLOPS,
+               "range_lists_ms": stage["ms_knn"] - kl_ms}
     stage_rooflines = {
         "grid_sort": hbm_line(52 * n, stage["ms_grid"], "52 B per point: points read twice, cell id and ticket "
                                                          "written and read, sorted float4 and permutation written"),
@@ -483,6 +494,7 @@ def run_gpu(args, rank: int, world: int, local: int):
                                   f"the {kpre}-entry lists: 16 B query read + {kpre} x (4 B index + 4 B key) written "
                                   "(the stage also holds the range-list kernels, whose I/O is not counted; the "
                                   "stage is ALU- and latency-bound)"),
+        "knn_alu": knn_alu,
         "clip": {"bound": "alu", "achieved_tflops": achieved, "peak_tflops": FP32_PEAK_TFLOPS,
                  "frac": achieved / FP32_PEAK_TFLOPS, "ms": stage["ms_clip"]},
         "emit": hbm_line(2 * csr_bytes + 16 * n, stage["ms_emit"],

@@ -30,7 +30,7 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream). Stage calls (vt_grid_build, vt_knn, vt_clip_cells, vt_emit) only
  *    enqueue work and return; vt_tessellate synchronises the stream once per
- *    re-queue pass to read a 128-byte status block (documented below).
+ *    re-queue pass to read a 192-byte status block (documented below).
  *  - Work runs on the calling thread's current CUDA device; every device
  *    buffer and the stream must belong to it (the library never switches
  *    devices: make the buffers' device current first).
@@ -70,7 +70,8 @@ typedef enum {
                                     from vt_unvalidated_cells; their vol / cen / m2 are NaN) */
     VT_ERR_DUPLICATE_POINTS = 5, /* two generators coincide (a neighbour at distance 0) */
     VT_ERR_TIMEOUT = 6,          /* a bounded device wait gave up */
-    VT_ERR_WORKSPACE = 7         /* ws_bytes smaller than vt_workspace_size() */
+    VT_ERR_WORKSPACE = 7,        /* ws_bytes smaller than vt_workspace_size() */
+    VT_ERR_INTERNAL = 8          /* a bounds check of a debug build (VT_CHECKS) failed */
 } vt_status;
 
 enum { VT_FP64 = 0, VT_FP32_RECHECK = 1 };          /* vt_params.precision */
@@ -196,6 +197,11 @@ typedef struct vt_stats {
     int64_t clip_events[5];              /* diagnostic counts of clip steps that: removed every vertex,
                                             hit the plane cap, hit the vertex cap, found an inconsistent
                                             ring, or placed a vertex by edge interpolation */
+    double ms_knn_lists;                 /* the k-nearest-neighbour kernels' part of ms_knn (the rest is
+                                            the range lists of the last pass) */
+    int64_t knn_candidates;              /* candidates the k-nearest-neighbour kernels examined (one
+                                            squared distance each) */
+    int64_t knn_queries;                 /* queries they answered */
 } vt_stats;
 
 /* ------------------------------------------------------------------ */
@@ -314,7 +320,7 @@ VT_API int vt_emit(int64_t n, const vt_params* p, vt_cells_out* out, void* ws, s
 /* Tessellates the n generators pts[n*3] (device) in the box of p: grid sort,
  * kNN with k0, clipping, re-queue with k doubled up to k_max, exhaustive pass
  * for what is left, then the requested outputs. Synchronises `stream` once
- * per pass (a 128-byte device-to-host read of the status block, which holds
+ * per pass (a 192-byte device-to-host read of the status block, which holds
  * the failed count) and once at
  * the end. Returns VT_ERR_CAPACITY (with out->needed_* set and vol/cen/m2
  * written) when a variable-length buffer is too small: allocate and call
@@ -501,7 +507,8 @@ VT_API int vt_probe_fma(int precision, double* tflops, void* stream);
 
 /* After a VT_FLAG_NO_SYNC call (or any call) on workspace ws (blocking on
  * `stream`): fills the device-counted fields of *stats (fp64_rechecks,
- * capacity_retries, precision_retries, unvalidated, clip_events; other fields
+ * capacity_retries, precision_retries, unvalidated, clip_events, knn_candidates,
+ * knn_queries; other fields
  * are left as they are) and out->needed_* (either may be NULL). Returns the
  * call's error: VT_ERR_INVALID_ARG / VT_ERR_DUPLICATE_POINTS for bad input,
  * VT_ERR_CAPACITY when an output did not fit (nothing of that output was

@@ -20,6 +20,7 @@ VT_ERR_UNVALIDATED = 4
 VT_ERR_DUPLICATE_POINTS = 5
 VT_ERR_TIMEOUT = 6
 VT_ERR_WORKSPACE = 7
+VT_ERR_INTERNAL = 8
 
 VT_FP64 = 0
 VT_FP32_RECHECK = 1
@@ -37,7 +38,7 @@ VT_FLAG_PERIODIC = 4
 
 STATUS_NAMES = {
     0: "VT_OK", 1: "VT_ERR_INVALID_ARG", 2: "VT_ERR_CUDA", 3: "VT_ERR_CAPACITY", 4: "VT_ERR_UNVALIDATED",
-    5: "VT_ERR_DUPLICATE_POINTS", 6: "VT_ERR_TIMEOUT", 7: "VT_ERR_WORKSPACE",
+    5: "VT_ERR_DUPLICATE_POINTS", 6: "VT_ERR_TIMEOUT", 7: "VT_ERR_WORKSPACE", 8: "VT_ERR_INTERNAL",
 }
 
 # every entry point declared in include/vt.h
@@ -166,6 +167,9 @@ class VtStats(ctypes.Structure):
         ("ms_emit", ctypes.c_double),
         ("ms_clip_pass", ctypes.c_double * VT_MAX_PASSES),
         ("clip_events", ctypes.c_int64 * 5),
+        ("ms_knn_lists", ctypes.c_double),
+        ("knn_candidates", ctypes.c_int64),
+        ("knn_queries", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -190,6 +194,9 @@ class VtStats(ctypes.Structure):
             "ms_emit": self.ms_emit,
             "ms_clip_pass": list(self.ms_clip_pass[:m]),
             "clip_events": list(self.clip_events),
+            "ms_knn_lists": self.ms_knn_lists,
+            "knn_candidates": self.knn_candidates,
+            "knn_queries": self.knn_queries,
         }
 
 

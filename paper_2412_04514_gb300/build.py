@@ -1,8 +1,10 @@
 """Builds the CUDA library libvt.so in-tree for sm_103a (GB300).
 
 Each translation unit compiles in its own nvcc process (in parallel); the
-objects link into ``paper_2412_04514_gb300/_build/libvt.so``. Only nvcc and a
-host C++ compiler are needed; no cmake, no torch headers.
+objects link into ``paper_2412_04514_gb300/_build/libvt.so`` (or the directory
+named by ``VT_BUILD_DIR``). Only nvcc and a host C++ compiler are needed; no
+cmake, no torch headers. ``VT_NVCC_FLAGS`` adds compiler flags, e.g.
+``-DVT_CHECKS`` for the bounds-checked debug build.
 """
 from __future__ import annotations
 
@@ -16,7 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(HERE, "_build")
+# VT_BUILD_DIR: another build directory (a debug build beside the regular one)
+BUILD = os.environ.get("VT_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvt.so")
 SOURCES = ["scan.cu", "grid.cu", "knn.cu", "clip_f32.cu", "clip_f64.cu", "clip_robust.cu", "emit.cu", "vt_api.cu", "grid_static.cu", "adjoint.cu", "tune.cu", "range.cu", "clip_big.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

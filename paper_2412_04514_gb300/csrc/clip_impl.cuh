@@ -322,6 +322,7 @@ __device__ __forceinline__ bool vertex64(const P64& A, const P64& B, const P64& 
 // ---------------------------------------------------------------------------
 template <typename Real, int VCAP, int PCAP>
 struct GroupSmem {
+    static constexpr int VCAP_ = VCAP;
     // Planes n.x <= b. In float32 the offset b of a bisector is |n|^2 / 2,
     // formed from n where it is needed (the expression of clip_point), and
     // the walls' offsets are kept apart: the footprint of a group sets the
@@ -498,9 +499,9 @@ __device__ VT_RARE int free_plane(const S& sm, M keep, int gl, unsigned gmask, i
 // position of a new vertex by interpolation along its cut edge (the
 // pre-clip vertex positions are in sm.vpos)
 template <typename Real, typename S>
-__device__ VT_RARE void interp_vertex(const S& sm, int s, Real nx, Real ny, Real nz, Real b, Real* xyz)
+__device__ VT_RARE void interp_vertex(const S& sm, int s, Real nx, Real ny, Real nz, Real b, Real* xyz, DevStatus* st)
 {
-    const int v = sm.u.ring.vsrc[s], w = sm.vadj[s][0];
+    const int v = vt_ck(sm.u.ring.vsrc[s], S::VCAP_, CK_SLOT, st), w = vt_ck(sm.vadj[s][0], S::VCAP_, CK_SLOT, st);
     const V4<Real> pv = ldv(sm.vpos, v), qv = ldv(sm.vpos, w);
     const Real px = pv.x, py = pv.y, pz = pv.z;
     const Real qx = qv.x, qy = qv.y, qz = qv.z;
@@ -822,7 +823,7 @@ struct Cell {
                 const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[r * T + G.gl]);
 #pragma unroll
                 for (int e = 0; e < 3; ++e)
-                    if (!out.test((adj >> (8 * e)) & 0xff)) myedge |= 1u << (3 * r + e);
+                    if (!out.test(vt_ck((adj >> (8 * e)) & 0xff, VCAP, CK_SLOT, st))) myedge |= 1u << (3 * r + e);
             }
         }
         int total;
@@ -845,7 +846,7 @@ struct Cell {
         }
         for (uint32_t m = myedge; m; m &= m - 1) {
             const int bit = __ffs(m) - 1, r = bit / 3, e = bit - 3 * r;
-            sm.u.ring.elist[idx++] = (uint16_t)((r * T + G.gl) | (e << 8));
+            sm.u.ring.elist[vt_ck(idx++, VCAP, CK_EDGE, st)] = (uint16_t)((r * T + G.gl) | (e << 8));
         }
         if (G.gl == 0) {
             sm.pnx[h] = nx;
@@ -860,11 +861,12 @@ struct Cell {
         // one boundary edge per lane: the new vertex (x, y, h) on the cut edge
         for (int i = G.gl; i < total; i += T) {
             const uint32_t ev = sm.u.ring.elist[i];
-            const int s = ev & 0xff, e = ev >> 8;
+            const int s = vt_ck(ev & 0xff, VCAP, CK_SLOT, st), e = vt_ck(ev >> 8, 3, CK_EDGE, st);
             const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[s]);
-            const int w = sm.vadj[s][e];
-            const int x = (ids >> (8 * e)) & 0xff, y = (ids >> (8 * (e == 2 ? 0 : e + 1))) & 0xff;
-            const int d = sm.u.ring.dlist[i];
+            const int w = vt_ck(sm.vadj[s][e], VCAP, CK_SLOT, st);
+            const int x = vt_ck((ids >> (8 * e)) & 0xff, PCAP, CK_PLANE, st);
+            const int y = vt_ck((ids >> (8 * (e == 2 ? 0 : e + 1))) & 0xff, PCAP, CK_PLANE, st);
+            const int d = vt_ck(sm.u.ring.dlist[i], VCAP, CK_SLOT, st);
             *reinterpret_cast<uint32_t*>(sm.vid[d]) = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)h << 16);
             sm.vadj[d][0] = (uint8_t)w;
             sm.u.ring.vsrc[d] = (uint8_t)s;
@@ -880,10 +882,14 @@ struct Cell {
         // close the ring around h and solve the new positions
         bool bad = false, need = false;
         for (int i = G.gl; i < total; i += T) {
-            const int d = sm.u.ring.dlist[i];
+            const int d = vt_ck(sm.u.ring.dlist[i], VCAP, CK_SLOT, st);
             const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[d]);
-            const int x = ids & 0xff, y = (ids >> 8) & 0xff;
+            const int x = vt_ck(ids & 0xff, PCAP, CK_PLANE, st), y = vt_ck((ids >> 8) & 0xff, PCAP, CK_PLANE, st);
             const uint32_t so = sm.u.ring.start_of[y], eo = sm.u.ring.end_of[x];
+            if (VT_CHECKED) {
+                vt_ck(so & 0xff, VCAP, CK_SLOT, st);
+                vt_ck(eo & 0xff, VCAP, CK_SLOT, st);
+            }
             if ((so & ~0xffu) != tag || (eo & ~0xffu) != tag || sm.u.ring.start_of[x] != (tag | (uint32_t)d))
                 bad = true;
             sm.vadj[d][1] = (uint8_t)(so & 0xff);
@@ -907,10 +913,10 @@ struct Cell {
             if (G.gl == 0) atomicAdd(&st->detail[4], 1u);
             G.sync();
             for (int i = G.gl; i < total; i += T) {
-                const int d = sm.u.ring.dlist[i];
+                const int d = vt_ck(sm.u.ring.dlist[i], VCAP, CK_SLOT, st);
                 if (isnan(sm.vpos[d][0])) {
                     Real xyz[3];
-                    interp_vertex<Real>(sm, d, nx, ny, nz, b, xyz);
+                    interp_vertex<Real>(sm, d, nx, ny, nz, b, xyz, st);
                     stv(sm.vpos, d, xyz[0], xyz[1], xyz[2]);
                 }
             }
@@ -1028,8 +1034,8 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
         const Real ax = va.x, ay = va.y, az = va.z;
         const Real a2 = va.w;
         for (int t = 0; t < 3; ++t) {
-            const int f = (ids >> (8 * t)) & 0xff;
-            const int nv = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
+            const int f = vt_ck((ids >> (8 * t)) & 0xff, PCAP, CK_PLANE, A.st);
+            const int nv = vt_ck((adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff, VCAP, CK_SLOT, A.st);
             const V4<Real> vb = ldv(sm.vpos, nv);
             const Real bx = vb.x, by = vb.y, bz = vb.z;
             const Real sc = sm.u.tail.sc[f];
@@ -1153,12 +1159,12 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
                 const uint32_t ids = *reinterpret_cast<const uint32_t*>(sm.vid[cur]);
                 const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[cur]);
                 const int t = ((ids & 0xff) == (uint32_t)f) ? 0 : ((((ids >> 8) & 0xff) == (uint32_t)f) ? 1 : 2);
-                const int nxt = (adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff;
+                const int nxt = vt_ck((adj >> (8 * (t == 0 ? 2 : t - 1))) & 0xff, VCAP, CK_SLOT, A.st);
                 const V4<Real> vn = ldv(sm.vpos, nxt);
                 const Real ux = vc.x - q.x, uy = vc.y - q.y, uz = vc.z - q.z;
                 const Real wx = vn.x - q.x, wy = vn.y - q.y, wz = vn.z - q.z;
                 area += (uy * wz - uz * wy) * fnx + (uz * wx - ux * wz) * fny + (ux * wy - uy * wx) * fnz;
-                if (put) rfv[pos + t2] = (uint8_t)alive.rank(cur);
+                if (put) rfv[vt_ck(pos + t2, 3 * REC_VERTS, CK_RECORD, A.st)] = (uint8_t)alive.rank(cur);
                 cur = nxt;
                 vc = vn;
             }

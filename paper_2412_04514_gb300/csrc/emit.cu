@@ -32,6 +32,16 @@ __global__ void k_emit_totals(const int64_t* __restrict__ off, int64_t n, int ge
     }
 }
 
+// CSR index check of debug builds (see vt_ck)
+__device__ __forceinline__ int64_t vt_ck64(int64_t i, int64_t cap, DevStatus* st)
+{
+    if (VT_CHECKED && (uint64_t)i >= (uint64_t)cap) {
+        atomicCAS(&st->check_fail, 0, CK_CSR);
+        return 0;
+    }
+    return i;
+}
+
 __global__ void k_emit_write(const uint8_t* __restrict__ rec, size_t stride, int64_t n, int emit,
                              const int64_t* __restrict__ off, vt_cells_out out, DevStatus* st)
 {
@@ -57,7 +67,7 @@ __global__ void k_emit_write(const uint8_t* __restrict__ rec, size_t stride, int
         if (emit & VT_EMIT_NBR) {
             const int64_t b = o_nbr[i];
             const int32_t* src = reinterpret_cast<const int32_t*>(r + REC_NBR_OFF);
-            for (int t = lane; t < h.nnbr; t += 32) out.nbr[b + t] = src[t];
+            for (int t = lane; t < h.nnbr; t += 32) out.nbr[vt_ck64(b + t, out.nbr_cap, st)] = src[t];
             if (lane == 0) {
                 out.nbr_off[i] = b;
                 if (i == n - 1) out.nbr_off[n] = o_nbr[n];
@@ -66,12 +76,12 @@ __global__ void k_emit_write(const uint8_t* __restrict__ rec, size_t stride, int
         if (emit & VT_EMIT_GEOM) {
             const int64_t bv = o_vtx[i], bf = o_face[i], bfv = o_fv[i];
             const double* v = reinterpret_cast<const double*>(r + REC_VTX_OFF);
-            for (int t = lane; t < 3 * h.nvtx; t += 32) out.vtx[3 * bv + t] = v[t];
+            for (int t = lane; t < 3 * h.nvtx; t += 32) out.vtx[vt_ck64(3 * bv + t, 3 * out.vtx_cap, st)] = v[t];
             const int32_t* fn = reinterpret_cast<const int32_t*>(r + REC_FNBR_OFF);
             const uint8_t* fd = r + REC_FDEG_OFF;
             const uint8_t* fv = r + REC_FVTX_OFF;
-            for (int t = lane; t < h.nface; t += 32) out.face_nbr[bf + t] = fn[t];
-            for (int t = lane; t < h.nfv; t += 32) out.face_vtx[bfv + t] = fv[t];
+            for (int t = lane; t < h.nface; t += 32) out.face_nbr[vt_ck64(bf + t, out.face_cap, st)] = fn[t];
+            for (int t = lane; t < h.nfv; t += 32) out.face_vtx[vt_ck64(bfv + t, out.face_vtx_cap, st)] = fv[t];
             // per-face offsets: prefix of the degrees (faces per cell are few)
             if (lane == 0) {
                 int64_t p = bfv;

@@ -299,7 +299,11 @@ __global__ void __launch_bounds__(KNN_BLOCK, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn
         const int64_t want = (int64_t)*nq_dev - nq_off;
         nq = want < 0 ? 0 : (want < nq_host ? want : nq_host);
     }
+    // statistics: candidates examined (the query itself included) and
+    // queries answered, added once per warp
+    unsigned long long evals = 0, answered = 0;
     for (int64_t c = wid; c < nq; c += nw) {
+        ++answered;
         const int q = queries ? queries[c] : (int)c;
         const float4 pq = sorted[q];
         const GridDesc& g = grid_of(g0, sets, set_of, q);
@@ -352,6 +356,7 @@ __global__ void __launch_bounds__(KNN_BLOCK, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn
                 }
                 const int total = __shfl_sync(FULL, incl, 31);
                 const int start = incl - len;
+                evals += (unsigned)total;
                 for (int c0 = 0; c0 < total; c0 += 32) {
                     const int i = c0 + lane;
                     int seg = 0;  // number of segments ending at or before i
@@ -469,6 +474,10 @@ __global__ void __launch_bounds__(KNN_BLOCK, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn
                 if (d2out) d2out[c * k + e] = F64 ? (Real)L64.d[r] : (Real)L.d[r];
             }
         }
+    }
+    if (lane == 0 && answered) {
+        atomicAdd(&st->knn_evals, evals);
+        atomicAdd(&st->knn_queries, answered);
     }
 }
 

@@ -252,17 +252,17 @@ constexpr int ROBUST_EXH_K = 128;
 // CUDA-event stage timer (VT_FLAG_STAGE_TIMES); every stage is also an NVTX
 // range, visible to any profiler that records NVTX (free when none does)
 struct StageTimer {
-    enum { GRID = 0, KNN = 1, CLIP = 2, EMIT = 3 };
+    enum { GRID = 0, KNN = 1, CLIP = 2, EMIT = 3, KNNL = 4 };  // KNNL: the k-nearest-neighbour lists (within KNN)
     bool on = false;
     int nvtx_depth = 0;
     cudaStream_t s = nullptr;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[5];
     std::vector<int> clip_pass;  // pass index of each CLIP event pair
     int pass = 0;
     int open_stage = -1;
     void begin(int stage)
     {
-        static const char* const names[4] = {"vt grid sort", "vt kNN / range lists", "vt clip", "vt emit"};
+        static const char* const names[5] = {"vt grid sort", "vt range lists", "vt clip", "vt emit", "vt kNN"};
         nvtxRangePushA(names[stage]);
         ++nvtx_depth;
         if (!on) return;
@@ -448,7 +448,7 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
         const int32_t* q = list ? list + o : nullptr;
         if (!list && o > 0) return fail(VT_ERR_INVALID_ARG, "internal: implicit list needs one chunk");
         if (!reuse) {
-            T.begin(StageTimer::KNN);
+            T.begin(StageTimer::KNNL);
             cudaError_t e = launch_knn(a.sorted, a.cell_off, c.g, L.n, q, cnt, kl, knn_prec, lnbr, ld2, c.st, c.s,
                                        c.sets, c.set_of(), m_dev, o);
             T.end();
@@ -556,6 +556,7 @@ int range_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m,
 
 int status_errors(const DevStatus& h)
 {
+    if (h.check_fail) return fail(VT_ERR_INTERNAL, "a debug bounds check failed (code %d)", h.check_fail);
     if (h.bad_point)
         return fail(VT_ERR_INVALID_ARG, "point %d is not finite or not inside [box_lo, box_hi)", h.bad_point - 1);
     if (h.duplicate) return fail(VT_ERR_DUPLICATE_POINTS, "two generators coincide");
@@ -877,7 +878,7 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
         if (ce != cudaSuccess) return cuda_fail(ce, "unvalidated marks");
     }
     r = emit_outputs(c, p, out);
-    if ((r = r ? r : read_status(c, h))) {
+    if ((r = r ? r : read_status(c, h)) || (r = h.check_fail ? status_errors(h) : VT_OK)) {
         if (stats) *stats = S;
         return r;
     }
@@ -885,10 +886,13 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
     S.capacity_retries = (int64_t)h.capacity_events;
     S.precision_retries = (int64_t)h.precision_events;
     for (int a = 0; a < 5; ++a) S.clip_events[a] = (int64_t)h.detail[a];
+    S.knn_candidates = (int64_t)h.knn_evals;
+    S.knn_queries = (int64_t)h.knn_queries;
     S.launches = (int)(launches() - l0);
     if (timer.on) {
         S.ms_grid = timer.total(StageTimer::GRID);
-        S.ms_knn = timer.total(StageTimer::KNN);
+        S.ms_knn_lists = timer.total(StageTimer::KNNL);
+        S.ms_knn = timer.total(StageTimer::KNN) + S.ms_knn_lists;
         S.ms_clip = timer.total(StageTimer::CLIP);
         S.ms_emit = timer.total(StageTimer::EMIT);
         timer.per_pass(S.ms_clip_pass, VT_MAX_PASSES);
@@ -1228,6 +1232,8 @@ int vt_read_stats(void* ws, size_t ws_bytes, vt_stats* stats, vt_cells_out* out,
         stats->precision_retries = (int64_t)h.precision_events;
         stats->unvalidated = h.n_unval;
         for (int a = 0; a < 5; ++a) stats->clip_events[a] = (int64_t)h.detail[a];
+        stats->knn_candidates = (int64_t)h.knn_evals;
+        stats->knn_queries = (int64_t)h.knn_queries;
     }
     if (out) {
         out->needed_nbr = h.totals[0];

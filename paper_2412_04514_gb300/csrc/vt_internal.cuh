@@ -453,8 +453,33 @@ struct DevStatus {
     unsigned int detail[8];   // clip events: 0 keep-none, 1 plane cap, 2 vertex cap, 3 ring, 4 interpolated
     int32_t n_second;         // cells of a merged first pass still open at entry k (stats)
     int32_t n_range_over;     // cells of the last pass with more candidates than a range list holds
+    unsigned long long knn_evals;    // candidate distances the k-nearest-neighbour kernels evaluated
+    unsigned long long knn_queries;  // queries they answered
+    int32_t check_fail;       // VT_CHECKS builds: code of the first failed bounds check, else 0
+    int32_t pad[11];
 };
 static_assert(sizeof(DevStatus) % 64 == 0, "status block must stay 64-byte sized");
+
+// Debug builds (-DVT_CHECKS): every shared-memory plane or vertex-slot index
+// that comes from data (topology links, list entries) and every output-record
+// and CSR index is checked against its bound; a bad one records its code in
+// the status block (the call then returns VT_ERR_INTERNAL) and is replaced
+// by 0, so the access stays in bounds. Without the flag the checks compile
+// to nothing.
+#ifdef VT_CHECKS
+constexpr bool VT_CHECKED = true;
+#else
+constexpr bool VT_CHECKED = false;
+#endif
+enum { CK_PLANE = 1, CK_SLOT = 2, CK_EDGE = 3, CK_RECORD = 4, CK_CSR = 5 };
+__device__ __forceinline__ int vt_ck(int i, int cap, int code, DevStatus* st)
+{
+    if (VT_CHECKED && (unsigned)i >= (unsigned)cap) {
+        atomicCAS(&st->check_fail, 0, code);
+        return 0;
+    }
+    return i;
+}
 
 // candidate lists of the last pass (range.cu): at most RANGE_CAP per cell
 // (64 measured as fast as 96 and faster than 128 on the 1M mixed cloud)
