@@ -1347,9 +1347,6 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Group<T> G;
     S& sm = reinterpret_cast<S*>(smem_raw)[threadIdx.x / T];
-    // cell indices fit 32 bits (n < 2^30); 32-bit loop state keeps registers free
-    const int gid = (int)((blockIdx.x * CLIP_BLOCK + threadIdx.x) / T);
-    const int ngroups = (int)((gridDim.x * CLIP_BLOCK) / T);
     const int k = A.k;
     const bool resume = !ROBUST && A.state && (A.k_prev > 0 || A.restore);
     // the robust exhaustive variant first clips by a nearest-first list, so
@@ -1364,7 +1361,16 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
     C cell;
     cell.stamp = 0;
 
-    for (int c = gid; c < nq; c += ngroups) {
+    // Cells come from a launch-wide counter, one per group at a time (cells
+    // differ in cost by orders of magnitude: a static share per group leaves
+    // the slowest groups running alone at the end). Cell indices fit 32 bits
+    // (n < 2^30).
+    auto next_cell = [&]() {
+        int v = 0;
+        if (G.gl == 0) v = atomicAdd(A.queue, 1);
+        return G.bcast(v, 0);
+    };
+    for (int c = next_cell(); c < nq; c = next_cell()) {
         // this cell's list length; with k_next the doubled list follows at once:
         // validation is tested before every entry, so a cell that the first k
         // entries validate stops at entry k exactly as a re-queue would
@@ -1632,9 +1638,17 @@ cudaError_t launch_variant(const ClipArgs& a, cudaStream_t s)
                                              : k_clip<Real, T, VPL, PCAP, ROBUST, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // as many blocks as are resident at once (they take cells from the queue)
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CLIP_BLOCK, smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.queue, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
     const int gpb = CLIP_BLOCK / T;
     int64_t blocks = (a.nq + gpb - 1) / gpb;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    if (blocks > resident) blocks = resident;
     if (blocks < 1) blocks = 1;
     kern<<<(unsigned)blocks, CLIP_BLOCK, smem, s>>>(a);
     count_launch();

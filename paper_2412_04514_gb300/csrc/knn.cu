@@ -282,11 +282,10 @@ __global__ void __launch_bounds__(KNN_BLOCK, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn
                                              const int32_t* __restrict__ set_of, const int32_t* __restrict__ queries,
                                              int64_t nq_host, const int32_t* __restrict__ nq_dev,
                                              int64_t nq_off, int k,
-                                             int32_t* __restrict__ nbr, Real* __restrict__ d2out, DevStatus* st)
+                                             int32_t* __restrict__ nbr, Real* __restrict__ d2out, DevStatus* st,
+                                             int32_t* __restrict__ queue)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // candidate buffer of the warp (one-row float32 lists)
     __shared__ float s_bd[KNN_BLOCK / 32][32];
     __shared__ int s_bo[KNN_BLOCK / 32][32], s_bj[KNN_BLOCK / 32][32];
@@ -302,7 +301,14 @@ __global__ void __launch_bounds__(KNN_BLOCK, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn
     // statistics: candidates examined (the query itself included) and
     // queries answered, added once per warp
     unsigned long long evals = 0, answered = 0;
-    for (int64_t c = wid; c < nq; c += nw) {
+    // queries come from a launch-wide counter, one per warp at a time (their
+    // costs differ by orders of magnitude between clumps and voids)
+    auto next_query = [&]() {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(queue, 1);
+        return (int64_t)__shfl_sync(FULL, v, 0);
+    };
+    for (int64_t c = next_query(); c < nq; c = next_query()) {
         ++answered;
         const int q = queries ? queries[c] : (int)c;
         const float4 pq = sorted[q];
@@ -485,18 +491,26 @@ template <typename Real>
 cudaError_t launch_knn_t(const float4* sorted, const int32_t* cell_off, const GridDesc& g, const GridDesc* sets,
                          const int32_t* set_of, const int32_t* queries, int64_t nq, const int32_t* nq_dev,
                          int64_t nq_off, int k,
-                         int32_t* nbr, Real* d2, DevStatus* st, cudaStream_t s)
+                         int32_t* nbr, Real* d2, DevStatus* st, cudaStream_t s, int32_t* queue)
 {
     if (nq <= 0) return cudaSuccess;
-    int64_t blocks = (nq + 7) / 8;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    dim3 grid((unsigned)blocks), block(KNN_BLOCK);
     // the periodic walk is its own instantiation (the non-periodic kernels keep their registers)
     auto kern = k <= 32 ? (g.periodic ? k_knn<Real, 1, true> : k_knn<Real, 1, false>)
               : k <= 64 ? (g.periodic ? k_knn<Real, 2, true> : k_knn<Real, 2, false>)
               : k <= 128 ? (g.periodic ? k_knn<Real, 4, true> : k_knn<Real, 4, false>)
                          : (g.periodic ? k_knn<Real, 8, true> : k_knn<Real, 8, false>);
-    kern<<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, d2, st);
+    // as many blocks as are resident at once (their warps take queries from the counter)
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, KNN_BLOCK, 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (nq + KNN_BLOCK / 32 - 1) / (KNN_BLOCK / 32);
+    const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    if (blocks > resident) blocks = resident;
+    dim3 grid((unsigned)blocks), block(KNN_BLOCK);
+    kern<<<grid, block, 0, s>>>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, d2, st, queue);
     count_launch();
     return cudaGetLastError();
 }
@@ -506,15 +520,15 @@ cudaError_t launch_knn_t(const float4* sorted, const int32_t* cell_off, const Gr
 cudaError_t launch_knn(const float4* sorted, const int32_t* cell_off, const GridDesc& g, int64_t n,
                        const int32_t* queries, int64_t nq, int k, int precision, int32_t* nbr, void* d2,
                        DevStatus* st, cudaStream_t s, const GridDesc* sets, const int32_t* set_of,
-                       const int32_t* nq_dev, int64_t nq_off)
+                       const int32_t* nq_dev, int64_t nq_off, int32_t* queue)
 {
     (void)n;
-    if (k < 1 || k > 256) return cudaErrorInvalidValue;
+    if (k < 1 || k > 256 || !queue) return cudaErrorInvalidValue;
     if (precision == VT_FP64)
         return launch_knn_t<double>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, (double*)d2, st,
-                                    s);
+                                    s, queue);
     return launch_knn_t<float>(sorted, cell_off, g, sets, set_of, queries, nq, nq_dev, nq_off, k, nbr, (float*)d2, st,
-                               s);
+                               s, queue);
 }
 
 }  // namespace vt

@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(RANGE_BLOCK, (sizeof(Real) == 4 ? (PER ? 4 : V
                                                        const uint8_t* __restrict__ state, size_t state_stride,
                                                        size_t pos_off, int cap, int32_t* __restrict__ rnbr, Real* __restrict__ rd2,
                                                        int32_t* __restrict__ rlen, int32_t* __restrict__ over_list,
-                                                       int32_t* __restrict__ over_ctr, DevStatus* st)
+                                                       int32_t* __restrict__ over_ctr, DevStatus* st,
+                                                       int32_t* __restrict__ queue)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -120,14 +121,18 @@ __global__ void __launch_bounds__(RANGE_BLOCK, (sizeof(Real) == 4 ? (PER ? 4 : V
     int32_t* bj = bo + RANGE_CAP * (RANGE_BLOCK / 32);
     float* vb = reinterpret_cast<float*>(smem_raw + (sizeof(Real) + 2 * sizeof(int32_t)) * RANGE_CAP * (RANGE_BLOCK / 32)) +
                 warp * 4 * RANGE_VCAP;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int64_t nq = nq_host;
     if (nq_dev) {  // device-counted: list entries [nq_off, nq_off + nq_host)
         const int64_t want = (int64_t)*nq_dev - nq_off;
         nq = want < 0 ? 0 : (want < nq_host ? want : nq_host);
     }
-    for (int64_t c = wid; c < nq; c += nw) {
+    // cells come from a launch-wide counter, one per warp at a time
+    auto next_cell = [&]() {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(queue, 1);
+        return (int64_t)__shfl_sync(FULL, v, 0);
+    };
+    for (int64_t c = next_cell(); c < nq; c = next_cell()) {
         const int q = queries[c];
         const float4 pq = sorted[q];
         const GridDesc& g = grid_of(g0, sets, set_of, q);
@@ -269,25 +274,33 @@ size_t range_smem_bytes(int precision)
     return ((key + 2 * sizeof(int32_t)) * RANGE_CAP + 4 * sizeof(float) * RANGE_VCAP) * (RANGE_BLOCK / 32);
 }
 
+template <typename Real>
+cudaError_t launch_range_t(const RangeArgs& a, cudaStream_t s)
+{
+    const size_t smem = range_smem_bytes(a.precision);
+    auto kern = a.g.periodic ? k_range<Real, true> : k_range<Real, false>;
+    // as many blocks as are resident at once (their warps take cells from the counter)
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RANGE_BLOCK, smem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.queue, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (a.nq + RANGE_BLOCK / 32 - 1) / (RANGE_BLOCK / 32);
+    const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    if (blocks > resident) blocks = resident;
+    kern<<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq,
+                                                     a.nq_dev, a.nq_off, a.state, a.state_stride, a.pos_off, RANGE_CAP,
+                                                     a.rnbr, (Real*)a.rd2, a.rlen, a.over_list, a.over_ctr, a.st,
+                                                     a.queue);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_range(const RangeArgs& a, cudaStream_t s)
 {
     if (a.nq <= 0) return cudaSuccess;
-    int64_t blocks = (a.nq + 7) / 8;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    const size_t smem = range_smem_bytes(a.precision);
-    if (a.precision == VT_FP64) {
-        auto kern = a.g.periodic ? k_range<double, true> : k_range<double, false>;
-        kern<<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(
-            a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.nq_off, a.state, a.state_stride, a.pos_off,
-            RANGE_CAP, a.rnbr, (double*)a.rd2, a.rlen, a.over_list, a.over_ctr, a.st);
-    } else {
-        auto kern = a.g.periodic ? k_range<float, true> : k_range<float, false>;
-        kern<<<(unsigned)blocks, RANGE_BLOCK, smem, s>>>(
-            a.sorted, a.cell_off, a.g, a.sets, a.set_of, a.queries, a.nq, a.nq_dev, a.nq_off, a.state, a.state_stride, a.pos_off,
-            RANGE_CAP, a.rnbr, (float*)a.rd2, a.rlen, a.over_list, a.over_ctr, a.st);
-    }
-    count_launch();
-    return cudaGetLastError();
+    return a.precision == VT_FP64 ? launch_range_t<double>(a, s) : launch_range_t<float>(a, s);
 }
 
 }  // namespace vt

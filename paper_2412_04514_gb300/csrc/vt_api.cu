@@ -417,6 +417,7 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
     a.state = c.at<uint8_t>(L.state);
     a.state_stride = L.state_stride;
     a.st = c.st;
+    a.queue = c.at<int32_t>(c.L.ctr) + CTR_QUEUE;
     const int tpc = p->threads_per_cell;
     StageTimer dummy;
     StageTimer& T = c.timer ? *c.timer : dummy;
@@ -450,7 +451,7 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
         if (!reuse) {
             T.begin(StageTimer::KNNL);
             cudaError_t e = launch_knn(a.sorted, a.cell_off, c.g, L.n, q, cnt, kl, knn_prec, lnbr, ld2, c.st, c.s,
-                                       c.sets, c.set_of(), m_dev, o);
+                                       c.sets, c.set_of(), m_dev, o, c.at<int32_t>(L.ctr) + CTR_QUEUE);
             T.end();
             if (c.knn_launches) ++*c.knn_launches;
             if (e != cudaSuccess) return cuda_fail(e, "knn launch");
@@ -506,6 +507,7 @@ int range_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m,
         r.over_list = over_list;
         r.over_ctr = over_ctr;
         r.st = c.st;
+        r.queue = c.at<int32_t>(L.ctr) + CTR_QUEUE;
         T.begin(StageTimer::KNN);
         e = launch_range(r, c.s);
         T.end();
@@ -543,6 +545,7 @@ int range_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m,
         a.state = c.at<uint8_t>(L.state);
         a.state_stride = L.state_stride;
         a.st = c.st;
+        a.queue = c.at<int32_t>(c.L.ctr) + CTR_QUEUE;
         T.begin(StageTimer::CLIP);
         e = launch_clip(a, variant, p->threads_per_cell, c.s);
         T.end();
@@ -976,7 +979,8 @@ int vt_knn(const float* sorted, const int32_t* cell_off, int G, int64_t n, const
         const char* names[] = {"sorted", "cell_off", "queries", "nbr", "d2", "the workspace"};
         if ((e = check_device_buffers(stream, ptrs, names, 6))) return e;
     }
-    cudaError_t ce = launch_knn((const float4*)sorted, cell_off, c.g, n, queries, nq, k, p->precision, nbr, d2, c.st, c.s);
+    cudaError_t ce = launch_knn((const float4*)sorted, cell_off, c.g, n, queries, nq, k, p->precision, nbr, d2, c.st, c.s,
+                                nullptr, nullptr, nullptr, 0, c.at<int32_t>(c.L.ctr) + CTR_QUEUE);
     return ce == cudaSuccess ? VT_OK : cuda_fail(ce, "knn");
 }
 
@@ -1022,6 +1026,7 @@ int vt_clip_cells(const float* sorted, const int32_t* cell_off, int G, int64_t n
     a.ctr_next = n_failed;
     a.ctr_robust = n_failed;
     a.st = c.st;
+    a.queue = c.at<int32_t>(c.L.ctr) + CTR_QUEUE;
     cudaError_t ce = launch_clip(a, p->precision == VT_FP64 ? 1 : 0, p->threads_per_cell, c.s);
     return ce == cudaSuccess ? VT_OK : cuda_fail(ce, "clip");
 }

@@ -507,6 +507,7 @@ struct RangeArgs {
     int32_t* over_list;      // overflowed cells (appended)
     int32_t* over_ctr;
     DevStatus* st;
+    int32_t* queue;          // the launch's cell counter (zeroed by the launch)
 };
 cudaError_t launch_range(const RangeArgs& a, cudaStream_t s);
 
@@ -537,6 +538,9 @@ enum : int8_t { CELL_DONE = 0, CELL_NEED_K = 1, CELL_NEED_ROBUST = 2, CELL_UNVAL
 // ---------------------------------------------------------------------------
 // workspace layout
 // ---------------------------------------------------------------------------
+// the cell counter of a clip launch, in the workspace's counter region
+constexpr int CTR_QUEUE = 4 * VT_MAX_PASSES + 4;
+
 struct Layout {
     int G;
     int64_t n, g3;
@@ -592,7 +596,7 @@ cudaError_t launch_pair_counts(const int32_t* cell_off, int64_t g3, const GridDe
 cudaError_t launch_knn(const float4* sorted, const int32_t* cell_off, const GridDesc& g, int64_t n,
                        const int32_t* queries, int64_t nq, int k, int precision, int32_t* nbr, void* d2,
                        DevStatus* st, cudaStream_t s, const GridDesc* sets = nullptr, const int32_t* set_of = nullptr,
-                       const int32_t* nq_dev = nullptr, int64_t nq_off = 0);
+                       const int32_t* nq_dev = nullptr, int64_t nq_off = 0, int32_t* queue = nullptr);
 
 struct ClipArgs {
     const float4* sorted;
@@ -633,6 +637,7 @@ struct ClipArgs {
     uint8_t* state;           // per-cell saved polyhedra (sorted index * state_stride), or NULL
     size_t state_stride;
     DevStatus* st;
+    int32_t* queue;           // the launch's cell counter (zeroed by the launch)
 };
 // variant: 0 = FP32 regular, 1 = FP64 regular, 2 = FP64 robust (bigger capacity),
 // 3 = FP32 with the robust capacity (the FP32 form's first fallback)
