@@ -1320,10 +1320,11 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP, PER>& c
 // ---------------------------------------------------------------------------
 constexpr int CLIP_BLOCK = 128;
 // resident blocks per SM the register budget aims for: the FP32 regular
-// variants trade some spills for occupancy (7 blocks: 72 registers, measured
-// fastest on the mixed cloud); FP64 and robust keep 128 registers
+// variants trade some spills for occupancy (8 blocks: 64 registers, measured
+// fastest on the mixed cloud with the work queue: last pass 7.13 ms against
+// 7.31 at 7 blocks and 7.54 at 6); FP64 and robust keep 128 registers
 #ifndef VT_CLIP_MINB_F32
-#define VT_CLIP_MINB_F32 7
+#define VT_CLIP_MINB_F32 8
 #endif
 #ifndef VT_CLIP_MINB_F64
 #define VT_CLIP_MINB_F64 4

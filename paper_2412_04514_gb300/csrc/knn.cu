@@ -270,11 +270,12 @@ struct WarpList64 {
     }
 };
 
-// resident blocks per SM the one-row lists are compiled for: 4 blocks of 256
-// threads (64 registers, no spills) hide more of the walk's load latency than
-// 3 (measured: kNN 7.07 vs 7.74 ms on the 1M mixed cloud)
+// resident blocks per SM the one-row lists are compiled for: 5 blocks of 256
+// threads (48 registers) hide more of the walk's load latency than 4 or 3
+// (measured on the 1M mixed cloud with the work queue: kNN stage 6.17 ms at 5,
+// 6.19 at 4, 6.91 at 3)
 #ifndef VT_KNN_MINB
-#define VT_KNN_MINB 4
+#define VT_KNN_MINB 5
 #endif
 template <typename Real, int KPL, bool PER>
 __global__ void __launch_bounds__(KNN_BLOCK, (KPL == 1 ? VT_KNN_MINB : 1)) k_knn(const float4* __restrict__ sorted, const int32_t* __restrict__ cell_off0,

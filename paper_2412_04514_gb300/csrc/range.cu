@@ -87,12 +87,12 @@ __device__ __forceinline__ bool reaches_far(const float* vb, int nv, float nx, f
     return false;
 }
 
-// resident blocks per SM: 5 for the FP32 kernel (48 registers, a few spilled
-// bytes; measured 0.6 ms faster per 1M-cell step than its unbounded 72
-// registers; 4 for its periodic form, which spills more at 48), 3 for the
-// FP64 one (at most 80 registers)
+// resident blocks per SM: 6 for the FP32 kernel (40 registers; with the work
+// queue measured 0.06 ms faster per 1M-cell step than 5 and 0.18 ms faster
+// than 4; its periodic form 4, which spills more), 3 for the FP64 one (at
+// most 80 registers)
 #ifndef VT_RANGE_MINB_F32
-#define VT_RANGE_MINB_F32 5
+#define VT_RANGE_MINB_F32 6
 #endif
 #ifndef VT_RANGE_MINB_F64
 #define VT_RANGE_MINB_F64 3
