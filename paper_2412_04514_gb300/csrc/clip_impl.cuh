@@ -420,12 +420,16 @@ constexpr double ON_PLANE_REL2 = 1e-28;  // (1e-14)^2
 
 // ---------------------------------------------------------------------------
 // saved polyhedron of a cell between passes (fixed stride per cell): the
-// StateHdr, then planes, topology and positions
+// StateHdr, each plane's source, the topology and the vertex positions; the
+// FP64 form also keeps its planes (forming them again on restore costs FP64
+// operations), the FP32 form forms them again from the generators, exactly as
+// clip_point formed them
 // ---------------------------------------------------------------------------
 template <typename Real, int VCAP, int PCAP>
 struct StateLayout {
-    static constexpr size_t PLANES = 128;                               // Real[4][PCAP]
-    static constexpr size_t PSRC = PLANES + 4 * sizeof(Real) * PCAP;    // int32[PCAP]
+    static constexpr bool PLANES_KEPT = sizeof(Real) == 8;
+    static constexpr size_t PLANES = (sizeof(StateHdr) + 31) / 32 * 32;                // Real[4][PCAP]
+    static constexpr size_t PSRC = PLANES + (PLANES_KEPT ? 4 * sizeof(Real) * PCAP : 0);  // int32[PCAP]
     static constexpr size_t VID = PSRC + 4 * PCAP;                      // uint32[VCAP]
     static constexpr size_t VADJ = VID + 4 * VCAP;                      // uint32[VCAP]
     static constexpr size_t POS = (VADJ + 4 * VCAP + 15) / 16 * 16;     // Real[3][VCAP]
@@ -583,11 +587,10 @@ struct Cell {
         hi3[0] = h0; hi3[1] = h1; hi3[2] = h2;
     }
 
-    // the box [lo, hi) in the frame of pi: walls 0..5, corners in slots 0..7;
-    // in a periodic box the cube [-L/2, L/2] (the bisectors of pi's own images)
-    __device__ __forceinline__ void init_box(const Group<T>& G, S& sm, const GridDesc& grid)
+    // the box's corners lo, hi in the frame of pi
+    __device__ __forceinline__ void box_of(const GridDesc& grid, Real& lx, Real& ly, Real& lz, Real& hx, Real& hy,
+                                           Real& hz) const
     {
-        Real lx, ly, lz, hx, hy, hz;
         if (PER) {
             hx = (Real)(0.5 * ((double)grid.hi[0] - (double)grid.lo[0]));
             hy = (Real)(0.5 * ((double)grid.hi[1] - (double)grid.lo[1]));
@@ -604,18 +607,31 @@ struct Cell {
             hy = (Real)grid.hi[1] - py;
             hz = (Real)grid.hi[2] - pz;
         }
-        if (G.gl < 6) {
-            const int w = G.gl, axis = w >> 1, upper = w & 1;
-            const Real one = upper ? (Real)1 : (Real)-1;
-            sm.pnx[w] = axis == 0 ? one : (Real)0;
-            sm.pny[w] = axis == 1 ? one : (Real)0;
-            sm.pnz[w] = axis == 2 ? one : (Real)0;
-            const Real lo_a = axis == 0 ? lx : (axis == 1 ? ly : lz);
-            const Real hi_a = axis == 0 ? hx : (axis == 1 ? hy : hz);
-            sm.wall_b[w] = upper ? hi_a : -lo_a;
-            if (S::STORE_B) sm.pbs[w] = upper ? hi_a : -lo_a;
-            sm.psrc[w] = -(w + 1);
-        }
+    }
+
+    // wall w (x-, x+, y-, y+, z-, z+) as plane f of the group
+    __device__ __forceinline__ void set_wall(S& sm, int f, int w, Real lx, Real ly, Real lz, Real hx, Real hy,
+                                             Real hz) const
+    {
+        const int axis = w >> 1, upper = w & 1;
+        const Real one = upper ? (Real)1 : (Real)-1;
+        sm.pnx[f] = axis == 0 ? one : (Real)0;
+        sm.pny[f] = axis == 1 ? one : (Real)0;
+        sm.pnz[f] = axis == 2 ? one : (Real)0;
+        const Real lo_a = axis == 0 ? lx : (axis == 1 ? ly : lz);
+        const Real hi_a = axis == 0 ? hx : (axis == 1 ? hy : hz);
+        sm.wall_b[w] = upper ? hi_a : -lo_a;
+        if (S::STORE_B) sm.pbs[f] = upper ? hi_a : -lo_a;
+        sm.psrc[f] = -(w + 1);
+    }
+
+    // the box [lo, hi) in the frame of pi: walls 0..5, corners in slots 0..7;
+    // in a periodic box the cube [-L/2, L/2] (the bisectors of pi's own images)
+    __device__ __forceinline__ void init_box(const Group<T>& G, S& sm, const GridDesc& grid)
+    {
+        Real lx, ly, lz, hx, hy, hz;
+        box_of(grid, lx, ly, lz, hx, hy, hz);
+        if (G.gl < 6) set_wall(sm, G.gl, G.gl, lx, ly, lz, hx, hy, hz);
         if (G.gl < 8) {
             // corner c = 4 sx + 2 sy + sz; planes (x, y, z) in ccw order, swapped
             // when an odd number of its walls are lower walls (mirror image)
@@ -647,14 +663,16 @@ struct Cell {
     __device__ __forceinline__ void save(const Group<T>& G, const S& sm, uint8_t* st, double last_d2,
                                          int last_orig) const
     {
-        Real* pl = reinterpret_cast<Real*>(st + SL::PLANES);
         int32_t* ps = reinterpret_cast<int32_t*>(st + SL::PSRC);
+        Real* pl = reinterpret_cast<Real*>(st + SL::PLANES);
         for (int f = G.gl; f < np; f += T) {
-            pl[f] = sm.pnx[f];
-            pl[PCAP + f] = sm.pny[f];
-            pl[2 * PCAP + f] = sm.pnz[f];
-            pl[3 * PCAP + f] = sm.pb(f);
             ps[f] = sm.psrc[f];
+            if (SL::PLANES_KEPT) {
+                pl[f] = sm.pnx[f];
+                pl[PCAP + f] = sm.pny[f];
+                pl[2 * PCAP + f] = sm.pnz[f];
+                pl[3 * PCAP + f] = sm.pb(f);
+            }
         }
         uint32_t* vi = reinterpret_cast<uint32_t*>(st + SL::VID);
         uint32_t* va = reinterpret_cast<uint32_t*>(st + SL::VADJ);
@@ -687,7 +705,7 @@ struct Cell {
     }
 
     __device__ __forceinline__ void restore(const Group<T>& G, S& sm, const uint8_t* st, double& last_d2,
-                                            int& last_orig)
+                                            int& last_orig, const float4* __restrict__ sorted, const GridDesc& grid)
     {
         const StateHdr* h = reinterpret_cast<const StateHdr*>(st);
         alive.w[0] = h->alive[0];
@@ -696,15 +714,33 @@ struct Cell {
         R2 = (Real)h->R2;
         last_d2 = h->last_d2;
         last_orig = h->last_orig;
-        const Real* pl = reinterpret_cast<const Real*>(st + SL::PLANES);
         const int32_t* ps = reinterpret_cast<const int32_t*>(st + SL::PSRC);
+        Real lx, ly, lz, hx, hy, hz;
+        box_of(grid, lx, ly, lz, hx, hy, hz);
+        const Real* pl = reinterpret_cast<const Real*>(st + SL::PLANES);
         for (int f = G.gl; f < np; f += T) {
-            sm.pnx[f] = pl[f];
-            sm.pny[f] = pl[PCAP + f];
-            sm.pnz[f] = pl[2 * PCAP + f];
-            if (ps[f] < 0) sm.wall_b[-ps[f] - 1] = pl[3 * PCAP + f];
-            if (S::STORE_B) sm.pbs[f] = pl[3 * PCAP + f];
-            sm.psrc[f] = ps[f];
+            const int src = ps[f];
+            if (SL::PLANES_KEPT) {
+                sm.pnx[f] = pl[f];
+                sm.pny[f] = pl[PCAP + f];
+                sm.pnz[f] = pl[2 * PCAP + f];
+                if (S::STORE_B) sm.pbs[f] = pl[3 * PCAP + f];
+                if (src < 0) sm.wall_b[-src - 1] = pl[3 * PCAP + f];
+                sm.psrc[f] = src;
+                continue;
+            }
+            // each plane formed again from its source, exactly as when it cut
+            if (src < 0) {
+                set_wall(sm, f, -src - 1, lx, ly, lz, hx, hy, hz);
+            } else {
+                Real nx, ny, nz;
+                normal_of(sorted[img_index_t<PER>(src)], src, grid, nx, ny, nz);
+                sm.pnx[f] = nx;
+                sm.pny[f] = ny;
+                sm.pnz[f] = nz;
+                if (S::STORE_B) sm.pbs[f] = (Real)0.5 * (nx * nx + ny * ny + nz * nz);
+                sm.psrc[f] = src;
+            }
         }
         update_rows();
         const uint32_t* vi = reinterpret_cast<const uint32_t*>(st + SL::VID);
@@ -937,10 +973,11 @@ struct Cell {
         return CLIP_CUT;
     }
 
-    __device__ __forceinline__ int clip_point(const Group<T>& G, S& sm, float4 pj, int j,
-                                              const float4* __restrict__ sorted, const GridDesc& grid, DevStatus* st)
+    // the bisector normal n = p_j - p_i (the image named by j's code in a
+    // periodic box), in the arithmetic of the form
+    __device__ __forceinline__ void normal_of(float4 pj, int j, const GridDesc& grid, Real& nx, Real& ny,
+                                              Real& nz) const
     {
-        Real nx, ny, nz;
         // j packs the image code; an unshifted image (almost every entry) takes
         // the walled arithmetic (j is uniform over the group: no divergence)
         const int code = PER ? (int)((unsigned)j >> 24) : IMG_NONE;
@@ -966,6 +1003,13 @@ struct Cell {
             ny = (Real)pj.y - (Real)pi.y;
             nz = (Real)pj.z - (Real)pi.z;
         }
+    }
+
+    __device__ __forceinline__ int clip_point(const Group<T>& G, S& sm, float4 pj, int j,
+                                              const float4* __restrict__ sorted, const GridDesc& grid, DevStatus* st)
+    {
+        Real nx, ny, nz;
+        normal_of(pj, j, grid, nx, ny, nz);
         const Real b = (Real)0.5 * (nx * nx + ny * ny + nz * nz);
         return clip(G, sm, nx, ny, nz, b, j, sorted, grid, st);
     }
@@ -1195,14 +1239,21 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
     if (geom) {
         nvtx = alive.count();
         double* rv = reinterpret_cast<double*>(rec + REC_VTX_OFF);
+        float* rv32 = reinterpret_cast<float*>(rec + REC_VTX_OFF);
         for (int s = gl; s < VCAP; s += T) {
             if (!alive.test(s)) continue;
             const int li = alive.rank(s);
             if (li < REC_VERTS) {
                 const V4<Real> v = ldv(sm.vpos, s);
-                rv[3 * li] = (double)pi.x + (double)v.x;
-                rv[3 * li + 1] = (double)pi.y + (double)v.y;
-                rv[3 * li + 2] = (double)pi.z + (double)v.z;
+                if (A.rec_f32) {  // half the record traffic; emit adds the generator in FP64
+                    rv32[3 * li] = (float)v.x;
+                    rv32[3 * li + 1] = (float)v.y;
+                    rv32[3 * li + 2] = (float)v.z;
+                } else {
+                    rv[3 * li] = (double)pi.x + (double)v.x;
+                    rv[3 * li + 1] = (double)pi.y + (double)v.y;
+                    rv[3 * li + 2] = (double)pi.z + (double)v.z;
+                }
             }
         }
     }
@@ -1215,6 +1266,9 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
         hd->nface = over ? 0 : nface;
         hd->nvtx = over ? 0 : nvtx;
         hd->nfv = over ? 0 : nfv;
+        hd->p[0] = pi.x;
+        hd->p[1] = pi.y;
+        hd->p[2] = pi.z;
     }
     __syncwarp(gmask);
 }
@@ -1390,7 +1444,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
             // the walk resumes from the last list key; list passes set it anew
             double ld;
             int lo;
-            cell.restore(G, sm, A.state + (size_t)q * A.state_stride, ld, lo);
+            cell.restore(G, sm, A.state + (size_t)q * A.state_stride, ld, lo, A.sorted, grid);
             if (EXH) {
                 last_d2 = ld;
                 last_orig = lo;

@@ -42,7 +42,7 @@ __device__ __forceinline__ int64_t vt_ck64(int64_t i, int64_t cap, DevStatus* st
     return i;
 }
 
-__global__ void k_emit_write(const uint8_t* __restrict__ rec, size_t stride, int64_t n, int emit,
+__global__ void k_emit_write(const uint8_t* __restrict__ rec, size_t stride, int64_t n, int emit, int vtx_f32,
                              const int64_t* __restrict__ off, vt_cells_out out, DevStatus* st)
 {
     const int lane = threadIdx.x & 31;
@@ -75,8 +75,17 @@ __global__ void k_emit_write(const uint8_t* __restrict__ rec, size_t stride, int
         }
         if (emit & VT_EMIT_GEOM) {
             const int64_t bv = o_vtx[i], bf = o_face[i], bfv = o_fv[i];
-            const double* v = reinterpret_cast<const double*>(r + REC_VTX_OFF);
-            for (int t = lane; t < 3 * h.nvtx; t += 32) out.vtx[vt_ck64(3 * bv + t, 3 * out.vtx_cap, st)] = v[t];
+            if (vtx_f32) {  // float offsets from the generator
+                const float* v = reinterpret_cast<const float*>(r + REC_VTX_OFF);
+                for (int t = lane; t < 3 * h.nvtx; t += 32) {
+                    const int a = t % 3;  // (selected, not indexed: h stays in registers)
+                    const float pa = a == 0 ? h.p[0] : (a == 1 ? h.p[1] : h.p[2]);
+                    out.vtx[vt_ck64(3 * bv + t, 3 * out.vtx_cap, st)] = (double)pa + (double)v[t];
+                }
+            } else {
+                const double* v = reinterpret_cast<const double*>(r + REC_VTX_OFF);
+                for (int t = lane; t < 3 * h.nvtx; t += 32) out.vtx[vt_ck64(3 * bv + t, 3 * out.vtx_cap, st)] = v[t];
+            }
             const int32_t* fn = reinterpret_cast<const int32_t*>(r + REC_FNBR_OFF);
             const uint8_t* fd = r + REC_FDEG_OFF;
             const uint8_t* fv = r + REC_FVTX_OFF;
@@ -177,7 +186,7 @@ cudaError_t launch_emit_write(const EmitArgs& a, const vt_cells_out& out, cudaSt
     if (a.n <= 0) return cudaSuccess;
     int64_t blocks = (a.n + 7) / 8;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    k_emit_write<<<(unsigned)blocks, 256, 0, s>>>(a.rec, a.rec_stride, a.n, a.emit, a.off64, out, a.st);
+    k_emit_write<<<(unsigned)blocks, 256, 0, s>>>(a.rec, a.rec_stride, a.n, a.emit, a.vtx_f32, a.off64, out, a.st);
     count_launch();
     return cudaGetLastError();
 }

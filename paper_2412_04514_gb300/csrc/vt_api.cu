@@ -201,7 +201,9 @@ Layout make_layout(const vt_params* p, int64_t n, int64_t cells, bool batch)
     int64_t rc = nn / 8 > 65536 ? nn / 8 : 65536;
     L.rob_cap = rc * 128;
     const bool recs = (p->emit & (VT_EMIT_NBR | VT_EMIT_GEOM)) != 0;
-    L.rec_stride = !recs ? 0 : ((p->emit & VT_EMIT_GEOM) ? REC_STRIDE_GEOM : REC_STRIDE_NBR);
+    L.rec_stride = !recs ? 0
+                         : ((p->emit & VT_EMIT_GEOM) ? (p->precision == VT_FP64 ? REC_STRIDE_GEOM : REC_STRIDE_GEOM_F32)
+                                                     : REC_STRIDE_NBR);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -228,7 +230,8 @@ Layout make_layout(const vt_params* p, int64_t n, int64_t cells, bool batch)
     size_t st1 = scan_tmp_bytes(L.g3), st2 = scan_tmp_bytes(nn);
     L.scan_tmp = take(st1 > st2 ? st1 : st2);
     L.knn_nbr = take(sizeof(int32_t) * L.knn_cap);
-    L.knn_d2 = take(sizeof(double) * L.knn_cap);
+    // list keys: float in the FP32 form (its lists, range lists included, carry float keys)
+    L.knn_d2 = take((p->precision == VT_FP64 ? sizeof(double) : sizeof(float)) * L.knn_cap);
     L.rob_nbr = take(sizeof(int32_t) * L.rob_cap);
     L.rob_d2 = take(sizeof(double) * L.rob_cap);
     L.set_of = batch ? take(sizeof(int32_t) * nn) : 0;
@@ -417,6 +420,7 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
     a.state = c.at<uint8_t>(L.state);
     a.state_stride = L.state_stride;
     a.st = c.st;
+    a.rec_f32 = p->precision != VT_FP64 ? 1 : 0;
     a.queue = c.at<int32_t>(c.L.ctr) + CTR_QUEUE;
     const int tpc = p->threads_per_cell;
     StageTimer dummy;
@@ -545,6 +549,7 @@ int range_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m,
         a.state = c.at<uint8_t>(L.state);
         a.state_stride = L.state_stride;
         a.st = c.st;
+        a.rec_f32 = p->precision != VT_FP64 ? 1 : 0;
         a.queue = c.at<int32_t>(c.L.ctr) + CTR_QUEUE;
         T.begin(StageTimer::CLIP);
         e = launch_clip(a, variant, p->threads_per_cell, c.s);
@@ -589,6 +594,7 @@ int emit_outputs(const Ctx& c, const vt_params* p, vt_cells_out* out)
     EmitArgs e{};
     e.n = n;
     e.emit = p->emit;
+    e.vtx_f32 = p->precision != VT_FP64 ? 1 : 0;
     e.rec = c.at<uint8_t>(L.rec);
     e.rec_stride = L.rec_stride;
     e.cnt = c.at<int32_t>(L.cnt);
@@ -1026,6 +1032,7 @@ int vt_clip_cells(const float* sorted, const int32_t* cell_off, int G, int64_t n
     a.ctr_next = n_failed;
     a.ctr_robust = n_failed;
     a.st = c.st;
+    a.rec_f32 = p->precision != VT_FP64 ? 1 : 0;
     a.queue = c.at<int32_t>(c.L.ctr) + CTR_QUEUE;
     cudaError_t ce = launch_clip(a, p->precision == VT_FP64 ? 1 : 0, p->threads_per_cell, c.s);
     return ce == cudaSuccess ? VT_OK : cuda_fail(ce, "clip");
@@ -1181,7 +1188,8 @@ int vt_cluster_index(const float* pts, int64_t n_total, const vt_set_desc* plan,
         c.nsets = n_sets;
     }
     const Layout& L = c.L;
-    if ((int64_t)n_sets > L.knn_cap) return fail(VT_ERR_INVALID_ARG, "more sets than the workspace can count");
+    // the per-set counts use the list-key buffer (4 bytes per list entry at least)
+    if ((int64_t)n_sets > L.knn_cap / 2) return fail(VT_ERR_INVALID_ARG, "more sets than the workspace can count");
     std::vector<GridDesc> h_sets(n_sets);
     cudaError_t ce = cudaMemsetAsync(c.st, 0, sizeof(DevStatus), c.s);
     if (ce != cudaSuccess) return cuda_fail(ce, "status reset");

@@ -521,16 +521,22 @@ struct RecHeader {
     int32_t nface;                 // faces written (geometry)
     int32_t nvtx;                  // vertices written (geometry)
     int32_t nfv;                   // face-vertex entries (geometry)
+    float p[3];                    // the generator (float32 vertex records hold offsets from it)
+    int32_t pad;
 };
 // layout: RecHeader | int32 nbr[REC_FACES] | (geometry:) int32 face_nbr[REC_FACES] |
-//         uint8 face_deg[REC_FACES] | uint8 face_vtx[3*REC_VERTS] | double vtx[REC_VERTS*3]
+//         uint8 face_deg[REC_FACES] | uint8 face_vtx[3*REC_VERTS] | vtx[REC_VERTS*3]:
+// in the FP32 form float offsets from the generator (emit adds them to it in
+// FP64: the same values as adding the float vertex to the float generator in
+// FP64), in the FP64 form FP64 coordinates
 constexpr size_t REC_NBR_OFF = sizeof(RecHeader);
 constexpr size_t REC_FNBR_OFF = REC_NBR_OFF + 4 * REC_FACES;
 constexpr size_t REC_FDEG_OFF = REC_FNBR_OFF + 4 * REC_FACES;
 constexpr size_t REC_FVTX_OFF = REC_FDEG_OFF + REC_FACES;
 constexpr size_t REC_VTX_OFF = (REC_FVTX_OFF + 3 * REC_VERTS + 15) / 16 * 16;
-constexpr size_t REC_STRIDE_NBR = REC_FNBR_OFF;                              // 272 B
-constexpr size_t REC_STRIDE_GEOM = REC_VTX_OFF + 8 * 3 * REC_VERTS;          // ~4 KB
+constexpr size_t REC_STRIDE_NBR = REC_FNBR_OFF;                              // 288 B
+constexpr size_t REC_STRIDE_GEOM_F32 = REC_VTX_OFF + 4 * 3 * REC_VERTS;      // ~2.6 KB
+constexpr size_t REC_STRIDE_GEOM = REC_VTX_OFF + 8 * 3 * REC_VERTS;          // ~4.1 KB
 
 // fail reasons stored per cell
 enum : int8_t { CELL_DONE = 0, CELL_NEED_K = 1, CELL_NEED_ROBUST = 2, CELL_UNVALIDATED = 3 };
@@ -638,6 +644,7 @@ struct ClipArgs {
     size_t state_stride;
     DevStatus* st;
     int32_t* queue;           // the launch's cell counter (zeroed by the launch)
+    int rec_f32;              // geometry records hold float offsets from the generator (the FP32 form)
 };
 // variant: 0 = FP32 regular, 1 = FP64 regular, 2 = FP64 robust (bigger capacity),
 // 3 = FP32 with the robust capacity (the FP32 form's first fallback)
@@ -648,6 +655,7 @@ size_t clip_state_pos_offset(int precision);  // offset of its vertex positions:
 struct EmitArgs {
     int64_t n;
     int emit;
+    int vtx_f32;              // vertex records: float offsets from the generator (see RecHeader)
     const uint8_t* rec;
     size_t rec_stride;
     int32_t* cnt;             // [4*n] scratch counts
