@@ -1394,7 +1394,10 @@ constexpr int clip_minb()
     return (sizeof(Real) == 4 && !ROBUST) ? (EXH ? VT_CLIP_MINB_EXH : VT_CLIP_MINB_F32) : VT_CLIP_MINB_F64;
 }
 
-template <typename Real, int T, int VPL, int PCAP, bool ROBUST, bool EXH, bool PER>
+// RES: the cells resume saved polyhedra (range lists, resumed lists, the
+// walk); the kernels that start every cell from the box leave the resume
+// code out (fewer live registers in their list loop)
+template <typename Real, int T, int VPL, int PCAP, bool ROBUST, bool EXH, bool PER, bool RES>
 __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) k_clip(const __grid_constant__ ClipArgs A)
 {
     using C = Cell<Real, T, VPL, PCAP, PER>;
@@ -1403,7 +1406,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
     const Group<T> G;
     S& sm = reinterpret_cast<S*>(smem_raw)[threadIdx.x / T];
     const int k = A.k;
-    const bool resume = !ROBUST && A.state && (A.k_prev > 0 || A.restore);
+    constexpr bool resume = RES && !ROBUST;
     // the robust exhaustive variant first clips by a nearest-first list, so
     // that its walk meets an almost final cell (the regular one resumes the
     // saved polyhedron of the last list pass instead)
@@ -1687,10 +1690,16 @@ cudaError_t launch_variant(const ClipArgs& a, cudaStream_t s)
     using S = GroupSmem<Real, T * VPL, PCAP>;
     const size_t smem = sizeof(S) * (CLIP_BLOCK / T);
     // periodic boxes have their own instantiations (the walls' kernels keep their registers)
-    auto kern = a.g.periodic ? (a.exhaustive ? k_clip<Real, T, VPL, PCAP, ROBUST, true, true>
-                                             : k_clip<Real, T, VPL, PCAP, ROBUST, false, true>)
-                             : (a.exhaustive ? k_clip<Real, T, VPL, PCAP, ROBUST, true, false>
-                                             : k_clip<Real, T, VPL, PCAP, ROBUST, false, false>);
+    const bool res = !ROBUST && a.state && (a.k_prev > 0 || a.restore);
+    auto kern = a.g.periodic
+                    ? (a.exhaustive ? (res ? k_clip<Real, T, VPL, PCAP, ROBUST, true, true, true>
+                                           : k_clip<Real, T, VPL, PCAP, ROBUST, true, true, false>)
+                                    : (res ? k_clip<Real, T, VPL, PCAP, ROBUST, false, true, true>
+                                           : k_clip<Real, T, VPL, PCAP, ROBUST, false, true, false>))
+                    : (a.exhaustive ? (res ? k_clip<Real, T, VPL, PCAP, ROBUST, true, false, true>
+                                           : k_clip<Real, T, VPL, PCAP, ROBUST, true, false, false>)
+                                    : (res ? k_clip<Real, T, VPL, PCAP, ROBUST, false, false, true>
+                                           : k_clip<Real, T, VPL, PCAP, ROBUST, false, false, false>));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // as many blocks as are resident at once (they take cells from the queue)
