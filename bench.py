@@ -383,6 +383,15 @@ def run_gpu(args, rank: int, world: int, local: int):
         tot64 = dist_max(sum(ms64), world)
         value64 = n * world * len(ms64) / (tot64 / 1e3)
 
+    # the fused schedule (VT_FLAG_FUSED): kNN and clip in one walk, no lists
+    cellsF = None
+    if args.steps_fused > 0:
+        pF = vt.Params(**{**p32.__dict__, "fused": True})
+        msF, stF, _, cellsF = timed(pF, args.steps_fused, 3, stage_times=True)
+        totF = dist_max(sum(msF), world)
+        valueF = n * world * len(msF) / (totF / 1e3)
+        wsF, ws32 = vt.workspace_size(pF, n), vt.workspace_size(p32, n)
+
     tot32 = dist_max(sum(ms32), world)
     value = n * world * len(ms32) / (tot32 / 1e3)
 
@@ -448,6 +457,8 @@ def run_gpu(args, rank: int, world: int, local: int):
         errors = {"fp32_recheck": errors_vs_oracle(cells, cpu)}
         if cells64 is not None:
             errors["fp64"] = errors_vs_oracle(cells64, cpu)
+        if cellsF is not None:
+            errors["fused_fp32_recheck"] = errors_vs_oracle(cellsF, cpu)
         errors["sample"] = cpu["sample"]
     flops_per_cell = cpu["flops_per_cell"] if cpu else args.flops_per_cell
     clip_launches = statistics.mean(s["clip_launches"] for s in st32)
@@ -513,6 +524,12 @@ def run_gpu(args, rank: int, world: int, local: int):
         "value_8m": None if m8 is None else m8["fp32"]["value"],
         "fp64_value_8m": None if m8 is None else m8["fp64"]["value"],
         "fp32_speedup_8m": None if m8 is None else m8["fp32_speedup"],
+        "fused_value": None if cellsF is None else valueF,
+        "fused_form": None if cellsF is None else {
+            "value": valueF, "unit": "cells/s", "ms_per_step": totF / len(msF), "steps": len(msF),
+            "schedule": "VT_FLAG_FUSED: every cell clips straight from its grid-shell walk (no neighbour lists)",
+            "stage_ms": {k: statistics.mean(s[k] for s in stF) for k in ("ms_grid", "ms_knn", "ms_clip", "ms_emit")},
+            "workspace_bytes_per_point": wsF / n, "list_schedule_workspace_bytes_per_point": ws32 / n},
         "fp64_form": None if args.steps_fp64 <= 0 else {
             "value": value64, "unit": "cells/s", "ms_per_step": tot64 / len(ms64), "steps": len(ms64),
             "stage_ms": {k: statistics.mean(s[k] for s in st64) for k in ("ms_grid", "ms_knn", "ms_clip", "ms_emit")},
@@ -742,6 +759,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--steps-fp64", type=int, default=3)
+    ap.add_argument("--steps-fused", type=int, default=5, help="steps of the fused schedule (0: skip)")
     ap.add_argument("--steps-8m", type=int, default=3, help="steps of the 8M half of the metric (0: skip)")
     ap.add_argument("--workload", default="mixed-1m", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])

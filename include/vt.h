@@ -112,7 +112,7 @@ enum {
                                read afterwards with vt_read_stats. Outputs that do not fit the
                                caller's capacities are not written (VT_ERR_CAPACITY there). The
                                neighbour-list buffer grows to n * k_max entries. */
-    VT_FLAG_PERIODIC = 4     /* periodic box: every generator also stands at all its images
+    VT_FLAG_PERIODIC = 4,    /* periodic box: every generator also stands at all its images
                                p + t L (L = box_hi - box_lo, t integer). The cell of p_i starts
                                as the cube [p_i - L/2, p_i + L/2] (the bisectors of p_i's own
                                images at +-L_a) and is cut by the images of the other
@@ -124,6 +124,15 @@ enum {
                                Requires |L|^2 <= 4 min_a L_a^2 (images shifted by more than two
                                periods cannot then cut) and fewer than 2^24 points in the call
                                (a batch counts all its sets); otherwise VT_ERR_INVALID_ARG. */
+    VT_FLAG_FUSED = 8        /* kNN and clipping in one kernel: no neighbour lists. Every cell
+                               starts from the box and walks the grid shells around its generator,
+                               clipping the candidates of each batch of grid cells nearest first,
+                               until the security radius (no unvisited generator within 2R)
+                               concludes it. The n x k list buffer and the saved polyhedra are
+                               not allocated (vt_workspace_size is smaller); k0 and k_max are
+                               still validated and size only the robust variant's lists. Cells
+                               and outputs are those of the list schedules. Combines with
+                               VT_FLAG_NO_SYNC and VT_FLAG_PERIODIC. */
 };
 
 /* Fills *p with the defaults above, unit box, FP32_RECHECK, emit NBR|VOL|CEN. */

@@ -35,6 +35,7 @@ VT_MAX_PASSES = 16
 VT_FLAG_STAGE_TIMES = 1
 VT_FLAG_NO_SYNC = 2
 VT_FLAG_PERIODIC = 4
+VT_FLAG_FUSED = 8
 
 STATUS_NAMES = {
     0: "VT_OK", 1: "VT_ERR_INVALID_ARG", 2: "VT_ERR_CUDA", 3: "VT_ERR_CAPACITY", 4: "VT_ERR_UNVALIDATED",

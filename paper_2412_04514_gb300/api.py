@@ -25,7 +25,9 @@ _PREC = {"fp64": L.VT_FP64, "fp32": L.VT_FP32_RECHECK}
 class Params:
     """Run-time parameters (vt_params). ``precision`` is ``"fp32"`` (float32
     clipping with FP64 rechecks) or ``"fp64"`` (plain FP64). ``periodic``:
-    the box [box_lo, box_hi) is periodic (VT_FLAG_PERIODIC)."""
+    the box [box_lo, box_hi) is periodic (VT_FLAG_PERIODIC). ``fused``: no
+    neighbour lists, every cell clips straight from its grid-shell walk
+    (VT_FLAG_FUSED)."""
 
     k0: int = 16
     k_max: int = 32
@@ -40,6 +42,7 @@ class Params:
     stage_times: bool = False
     no_sync: bool = False
     periodic: bool = False
+    fused: bool = False
 
     def c(self) -> L.VtParams:
         p = L.VtParams()
@@ -56,7 +59,7 @@ class Params:
             p.box_lo[a] = self.box_lo[a]
             p.box_hi[a] = self.box_hi[a]
         p.flags = ((L.VT_FLAG_STAGE_TIMES if self.stage_times else 0) | (L.VT_FLAG_NO_SYNC if self.no_sync else 0)
-                   | (L.VT_FLAG_PERIODIC if self.periodic else 0))
+                   | (L.VT_FLAG_PERIODIC if self.periodic else 0) | (L.VT_FLAG_FUSED if self.fused else 0))
         return p
 
 

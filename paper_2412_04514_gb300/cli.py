@@ -81,12 +81,13 @@ def write_cells(path: str, cells: dict, points: np.ndarray | None = None) -> Non
 
 
 def make_params(precision="fp32", emit=("nbr", "vol", "cen"), k0=16, k_max=32, grid_density=2.0, grid_res=0,
-                threads_per_cell=0, index_space="original", box=None, periodic=False):
+                threads_per_cell=0, index_space="original", box=None, periodic=False, fused=False):
     """:class:`.api.Params` from plain values (``box`` = (lo[3], hi[3]))."""
     from .api import Params
 
     p = Params(precision=precision, emit=tuple(emit), k0=k0, k_max=k_max, grid_density=grid_density,
-               grid_res=grid_res, threads_per_cell=threads_per_cell, index_space=index_space, periodic=periodic)
+               grid_res=grid_res, threads_per_cell=threads_per_cell, index_space=index_space, periodic=periodic,
+               fused=fused)
     if box is not None:
         lo, hi = box
         p.box_lo, p.box_hi = tuple(float(x) for x in lo), tuple(float(x) for x in hi)
@@ -139,6 +140,8 @@ def parser() -> argparse.ArgumentParser:
     ap.add_argument("--box", type=float, nargs=6, metavar=("X0", "Y0", "Z0", "X1", "Y1", "Z1"),
                     help="bounding box (default the unit cube)")
     ap.add_argument("--periodic", action="store_true", help="the box is periodic")
+    ap.add_argument("--fused", action="store_true",
+                    help="no neighbour lists: every cell clips straight from its grid walk (smaller workspace)")
     ap.add_argument("--tune", action="store_true", help="autotune the run-time parameters first")
     ap.add_argument("--tune-cache", default=None, help="JSON cache of tuned parameters")
     ap.add_argument("--device", default="cuda")
@@ -154,7 +157,7 @@ def params_from_args(a: argparse.Namespace):
     box = None if a.box is None else (a.box[:3], a.box[3:])
     return make_params(precision=a.precision, emit=emit, k0=a.k0, k_max=a.k_max, grid_density=a.rho,
                        grid_res=a.grid_res, threads_per_cell=a.threads_per_cell, index_space=a.index_space,
-                       box=box, periodic=a.periodic)
+                       box=box, periodic=a.periodic, fused=a.fused)
 
 
 def main(argv=None) -> int:

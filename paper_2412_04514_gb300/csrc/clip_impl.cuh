@@ -1273,74 +1273,115 @@ __device__ VT_RARE void finish_cell(GroupSmem<Real, VCAP, PCAP>& sm, M alive, in
     __syncwarp(gmask);
 }
 
-// one candidate range [a, b) of sorted points for the exhaustive walk. A
-// generator q can cut the cell only if 4 R^2 > |q - p|^2 and its bisector
-// n.x <= b (n = q - p, b = |n|^2 / 2) reaches beyond the cell's bounding box
+// NB batches of T candidates (sorted points of one shell) for the exhaustive
+// walk; lane l holds candidates l, T + l, ... A generator q can cut the cell
+// only if 4 R^2 > |q - p|^2 and its bisector n.x <= b (n = q - p,
+// b = |n|^2 / 2) reaches beyond the cell's bounding box
 // (sum_i max(n_i lo_i, n_i hi_i) > b); both tests run on every lane in float
 // with margins that only admit extra candidates, and the survivors are clipped
 // one at a time. Generators a resumed list already processed are skipped.
-template <typename Real, int T, int VPL, int PCAP, bool PER>
+template <typename Real, int T, int VPL, int PCAP, bool PER, int NB>
 __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP, PER>& cell, const Group<T>& G,
                                                 typename Cell<Real, T, VPL, PCAP, PER>::S& sm, const ClipArgs& A,
-                                                const GridDesc& grid, bool valid, int jj, int code, double last_d2,
-                                                int last_orig, float* lo3, float* hi3)
+                                                const GridDesc& grid, const bool (&valid)[NB], const int (&jj)[NB],
+                                                const int (&code)[NB], double last_d2, int last_orig, float* lo3,
+                                                float* hi3)
 {
 #ifdef VT_PROFILE
     const long long tb0 = clock64();
 #endif
     const float4 pq = cell.pi;
-    float4 pc = make_float4(0.f, 0.f, 0.f, 0.f);
-    float ex = 0.f, ey = 0.f, ez = 0.f;
-    bool need = false;
-    if (valid) {
-        pc = A.sorted[img_index_t<PER>(jj)];
-        const float3 o = img_off_t<PER>(pq, pc, code, grid);
-        ex = o.x;
-        ey = o.y;
-        ez = o.z;
-        const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-        const float r4 = 4.0f * (float)cell.R2;
-        const float hb =
-            fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) + fmaxf(ez * lo3[2], ez * hi3[2]);
-        need = r4 * (1.0f + 1e-4f) > d2 &&
-               hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f && cell.reaches(sm, ex, ey, ez);
-        if (need && last_orig >= 0) {  // already processed from the list?
-            const int ko = img_tie_t<PER>(pc, code);
-            if (Tol<Real>::fp32) {  // float keys compare in float (last_d2 holds a float)
-                const float kd = d2, ld = (float)last_d2;
-                if (kd < ld || (kd == ld && ko <= last_orig)) need = false;
-            } else {
-                const double kd = img_key64(pq, A.sorted, jj, grid);
-                if (kd < last_d2 || (kd == last_d2 && ko <= last_orig)) need = false;
+    float px[NB], py[NB], pz[NB], ex[NB], ey[NB], ez[NB];
+    uint32_t dkey[NB];
+    unsigned mm[NB];
+    unsigned any = 0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        px[b] = py[b] = pz[b] = ex[b] = ey[b] = ez[b] = 0.f;
+        bool need = false;
+        if (valid[b]) {
+            const float4 pc = A.sorted[img_index_t<PER>(jj[b])];
+            px[b] = pc.x;
+            py[b] = pc.y;
+            pz[b] = pc.z;
+            const float3 o = img_off_t<PER>(pq, pc, code[b], grid);
+            ex[b] = o.x;
+            ey[b] = o.y;
+            ez[b] = o.z;
+            const float d2 = fmaf(o.z, o.z, fmaf(o.y, o.y, o.x * o.x));
+            const float r4 = 4.0f * (float)cell.R2;
+            const float hb = fmaxf(o.x * lo3[0], o.x * hi3[0]) + fmaxf(o.y * lo3[1], o.y * hi3[1]) +
+                             fmaxf(o.z * lo3[2], o.z * hi3[2]);
+            need = r4 * (1.0f + 1e-4f) > d2 &&
+                   hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f &&
+                   cell.reaches(sm, o.x, o.y, o.z);
+            if (need && last_orig >= 0) {  // already processed from the list?
+                const int ko = img_tie_t<PER>(pc, code[b]);
+                if (Tol<Real>::fp32) {  // float keys compare in float (last_d2 holds a float)
+                    const float kd = d2, ld = (float)last_d2;
+                    if (kd < ld || (kd == ld && ko <= last_orig)) need = false;
+                } else {
+                    const double kd = img_key64(pq, A.sorted, jj[b], grid);
+                    if (kd < last_d2 || (kd == last_d2 && ko <= last_orig)) need = false;
+                }
             }
         }
+        dkey[b] = __float_as_uint(fmaf(ez[b], ez[b], fmaf(ey[b], ey[b], ex[b] * ex[b])));
+        mm[b] = G.ballot(need);
+        any |= mm[b];
     }
-    unsigned mm = G.ballot(need);
 #ifdef VT_PROFILE
-    if (G.gl == 0) VT_PROF_ADD(8 + 7, __popc(mm));
+    if (G.gl == 0) {
+        int cnt = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) cnt += __popc(mm[b]);
+        VT_PROF_ADD(8 + 7, cnt);
+    }
     if (G.gl == 0) VT_PROF_ADD(21, clock64() - tb0);
-    if (G.gl == 0 && mm == 0) VT_PROF_ADD(23, 1);
+    if (G.gl == 0 && any == 0) VT_PROF_ADD(23, 1);
     const long long tb1 = clock64();
 #endif
-    // survivors nearest first: the nearest cut most, so the intermediate
-    // polyhedra stay small and fewer of the others still cut
-    const uint32_t dkey = __float_as_uint(fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
-    while (mm) {
-        const uint32_t mn = __reduce_min_sync(G.mask, ((mm >> G.gl) & 1u) ? dkey : 0xffffffffu);
-        const int src = __ffs(G.ballot(((mm >> G.gl) & 1u) && dkey == mn)) - 1;
-        mm &= ~(1u << src);
+    // survivors nearest first over all NB batches: the nearest cut most, so
+    // the intermediate polyhedra stay small and fewer of the others still cut
+    while (any) {
+        uint32_t mine = 0xffffffffu;  // this lane's nearest survivor (keys of finite d2 are smaller)
+        int bs = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (((mm[b] >> G.gl) & 1u) && dkey[b] < mine) {
+                mine = dkey[b];
+                bs = b;
+            }
+        const uint32_t mn = __reduce_min_sync(G.mask, mine);
+        const int src = __ffs(G.ballot(mine == mn)) - 1;
+        const int bsrc = G.bcast(bs, src);
+        float sx = px[0], sy = py[0], sz = pz[0];
+        int sj = jj[0];
+#pragma unroll
+        for (int b = 1; b < NB; ++b)
+            if (bs == b) {
+                sx = px[b];
+                sy = py[b];
+                sz = pz[b];
+                sj = jj[b];
+            }
+        any = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (b == bsrc) mm[b] &= ~(1u << src);
+            any |= mm[b];
+        }
         float4 p;
-        p.x = G.bcast(pc.x, src);
-        p.y = G.bcast(pc.y, src);
-        p.z = G.bcast(pc.z, src);
+        p.x = G.bcast(sx, src);
+        p.y = G.bcast(sy, src);
+        p.z = G.bcast(sz, src);
         p.w = 0.f;
-        const int j = G.bcast(jj, src);
+        const int j = G.bcast(sj, src);
         // re-test against the current (smaller) cell
         const float3 o = img_off_t<PER>(pq, p, img_code_t<PER>(j), grid);
-        const float ex = o.x, ey = o.y, ez = o.z;
-        const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+        const float d2 = fmaf(o.z, o.z, fmaf(o.y, o.y, o.x * o.x));
         const float hb =
-            fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) + fmaxf(ez * lo3[2], ez * hi3[2]);
+            fmaxf(o.x * lo3[0], o.x * hi3[0]) + fmaxf(o.y * lo3[1], o.y * hi3[1]) + fmaxf(o.z * lo3[2], o.z * hi3[2]);
         if (!(4.0f * (float)cell.R2 * (1.0f + 1e-4f) > d2 &&
               hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * (float)cell.R2) - 1e-30f))
             continue;
@@ -1359,8 +1400,13 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP, PER>& c
         if (r == CLIP_INCONSISTENT) return END_INCONSISTENT;
         if (r == CLIP_CUT) {
             cell.bbox(G, sm, lo3, hi3);
-            // the batch's other survivors against the smaller cell
-            if (mm) mm &= G.ballot(((mm >> G.gl) & 1u) && cell.reaches(sm, ex, ey, ez));
+            // the other survivors against the smaller cell
+            any = 0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                if (mm[b]) mm[b] &= G.ballot(((mm[b] >> G.gl) & 1u) && cell.reaches(sm, ex[b], ey[b], ez[b]));
+                any |= mm[b];
+            }
         }
     }
 #ifdef VT_PROFILE
@@ -1388,6 +1434,13 @@ constexpr int CLIP_BLOCK = 128;
 #ifndef VT_CLIP_MINB_EXH
 #define VT_CLIP_MINB_EXH 6
 #endif
+// candidates per lane in one step of a walk from the box (fused schedule).
+// Measured on 1M points: 1 is fastest (uniform 25.3 ms, clumps 35.2 ms of
+// clipping), 2, 3 and 4 cost 20-70% more: every cut re-tests the remaining
+// candidates of all NB batches against the whole polyhedron
+#ifndef VT_WALK_NB
+#define VT_WALK_NB 1
+#endif
 template <typename Real, bool ROBUST, bool EXH>
 constexpr int clip_minb()
 {
@@ -1411,6 +1464,9 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
     // that its walk meets an almost final cell (the regular one resumes the
     // saved polyhedron of the last list pass instead)
     constexpr bool LIST = !EXH || ROBUST;
+    // candidates per lane in one step of the walk (VT_WALK_NB batches of T
+    // for a walk from the box, one batch for a resumed walk)
+    constexpr int WNB = (!RES && !ROBUST) ? VT_WALK_NB : 1;
     int nq = (int)A.nq;
     if (A.nq_dev) {  // device-counted: list entries [nq_off, nq_off + nq_cap)
         const int64_t want = (int64_t)*A.nq_dev - A.nq_off;
@@ -1609,20 +1665,28 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
                     if (G.gl == 0) VT_PROF_ADD(19, total);
                     if (G.gl == 0) VT_PROF_ADD(20, clock64() - ts0);
 #endif
-                    for (int c0 = 0; c0 < total && status == 0; c0 += T) {
+                    for (int c0 = 0; c0 < total && status == 0; c0 += WNB * T) {
 #ifdef VT_PROFILE
                         if (G.gl == 0) VT_PROF_ADD(18, 1);
 #endif
-                        const int i = c0 + G.gl;
-                        int seg = 0;  // segments ending at or before i
+                        bool vb[WNB];
+                        int jb[WNB], cb[WNB];
 #pragma unroll
-                        for (int step = T / 2; step >= 1; step >>= 1)
-                            if (G.bcast(incl, (seg + step - 1) & (T - 1)) <= i) seg += step;
-                        const int aj = G.bcast(sa, seg & (T - 1)), sj = G.bcast(start, seg & (T - 1));
-                        const int code = per ? G.bcast(sc, seg & (T - 1)) : IMG_NONE;
-                        const int j0 = aj + (i - sj);
-                        status = exhaustive_batch<Real, T, VPL, PCAP, PER>(cell, G, sm, A, grid, i < total && j0 != q,
-                                                  per ? img_pack(j0, code) : j0, code, last_d2, last_orig, lo3, hi3);
+                        for (int b = 0; b < WNB; ++b) {
+                            const int i = c0 + b * T + G.gl;
+                            int seg = 0;  // segments ending at or before i
+#pragma unroll
+                            for (int step = T / 2; step >= 1; step >>= 1)
+                                if (G.bcast(incl, (seg + step - 1) & (T - 1)) <= i) seg += step;
+                            const int aj = G.bcast(sa, seg & (T - 1)), sj = G.bcast(start, seg & (T - 1));
+                            const int code = per ? G.bcast(sc, seg & (T - 1)) : IMG_NONE;
+                            const int j0 = aj + (i - sj);
+                            vb[b] = i < total && j0 != q;
+                            jb[b] = per ? img_pack(j0, code) : j0;
+                            cb[b] = code;
+                        }
+                        status = exhaustive_batch<Real, T, VPL, PCAP, PER, WNB>(cell, G, sm, A, grid, vb, jb, cb,
+                                                                               last_d2, last_orig, lo3, hi3);
                     }
                 }
                 if (status) break;

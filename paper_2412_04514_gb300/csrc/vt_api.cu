@@ -50,7 +50,7 @@ int check_params(const vt_params* p)
         return fail(VT_ERR_INVALID_ARG, "precision must be VT_FP64 or VT_FP32_RECHECK");
     if (p->index_space != VT_INDEX_ORIGINAL && p->index_space != VT_INDEX_SORTED)
         return fail(VT_ERR_INVALID_ARG, "index_space must be VT_INDEX_ORIGINAL or VT_INDEX_SORTED");
-    if (p->flags & ~(VT_FLAG_STAGE_TIMES | VT_FLAG_NO_SYNC | VT_FLAG_PERIODIC))
+    if (p->flags & ~(VT_FLAG_STAGE_TIMES | VT_FLAG_NO_SYNC | VT_FLAG_PERIODIC | VT_FLAG_FUSED))
         return fail(VT_ERR_INVALID_ARG, "unknown flag bits 0x%x", p->flags);
     if (p->emit & ~(VT_EMIT_NBR | VT_EMIT_VOL | VT_EMIT_CEN | VT_EMIT_M2 | VT_EMIT_GEOM))
         return fail(VT_ERR_INVALID_ARG, "unknown emit bits 0x%x", p->emit);
@@ -193,8 +193,11 @@ Layout make_layout(const vt_params* p, int64_t n, int64_t cells, bool batch)
     // within k_max (2 k0 entries per cell, all cells at once)
     const int kmx = p->k_max > RANGE_CAP ? p->k_max : RANGE_CAP;
     const int kpre = 2 * p->k0 <= p->k_max ? 2 * p->k0 : p->k0;
-    int64_t cap = nn * (int64_t)(nosync ? (kmx > kpre ? kmx : kpre) : kpre);
-    if (cap < (int64_t)p->k_max * 64) cap = (int64_t)p->k_max * 64;
+    // the fused schedule clips from the grid walk: no list buffer (one small
+    // block keeps the layout uniform) and no saved polyhedra
+    const bool fused = (p->flags & VT_FLAG_FUSED) != 0;
+    int64_t cap = fused ? 64 : nn * (int64_t)(nosync ? (kmx > kpre ? kmx : kpre) : kpre);
+    if (!fused && cap < (int64_t)p->k_max * 64) cap = (int64_t)p->k_max * 64;
     L.knn_cap = cap;
     // the robust variant's lists have their own buffer (the regular lists of
     // the first pass stay in place for the second): n / 8 cells of 128
@@ -222,7 +225,7 @@ Layout make_layout(const vt_params* p, int64_t n, int64_t cells, bool batch)
     L.sorted = take(sizeof(float4) * nn);
     L.perm = take(sizeof(int32_t) * nn);
     L.list_a = take(sizeof(int32_t) * nn * 7);  // seven cell lists of n entries
-    L.state_stride = clip_state_bytes(p->precision);
+    L.state_stride = fused ? 0 : clip_state_bytes(p->precision);
     L.state = take(L.state_stride * (size_t)nn);
     L.counts = take(sizeof(int32_t) * (L.g3 + 1));
     L.cell_off = take(sizeof(int32_t) * (L.g3 + 1));
@@ -417,7 +420,7 @@ int clip_pass(const Ctx& c, const vt_params* p, const int32_t* list, int64_t m, 
     a.ctr_next = ctr_next;
     a.ctr_robust = ctr_robust;
     a.k_prev = k_prev;
-    a.state = c.at<uint8_t>(L.state);
+    a.state = L.state_stride ? c.at<uint8_t>(L.state) : nullptr;  // none in the fused schedule
     a.state_stride = L.state_stride;
     a.st = c.st;
     a.rec_f32 = p->precision != VT_FP64 ? 1 : 0;
@@ -652,6 +655,7 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
     if ((p->emit & VT_EMIT_CEN) && n > 0 && !out->cen) return fail(VT_ERR_INVALID_ARG, "VT_EMIT_CEN needs cen");
     if ((p->emit & VT_EMIT_M2) && n > 0 && !out->m2) return fail(VT_ERR_INVALID_ARG, "VT_EMIT_M2 needs m2");
     const bool nosync = (p->flags & VT_FLAG_NO_SYNC) != 0;
+    const bool fused = (p->flags & VT_FLAG_FUSED) != 0;  // one walk pass from the box, no lists
     if (nosync && (p->flags & VT_FLAG_STAGE_TIMES))
         return fail(VT_ERR_INVALID_ARG, "VT_FLAG_STAGE_TIMES needs the synchronising schedule");
     const int64_t l0 = launches();
@@ -714,8 +718,9 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
         // is tested before every entry)
         int ks[VT_MAX_PASSES];
         int np_ = 0;
-        const bool merge = 2 * p->k0 <= p->k_max;
-        for (int k = merge ? 2 * p->k0 : p->k0; k <= p->k_max && np_ < VT_MAX_PASSES - 1; k *= 2) ks[np_++] = k;
+        const bool merge = !fused && 2 * p->k0 <= p->k_max;
+        if (!fused)
+            for (int k = merge ? 2 * p->k0 : p->k0; k <= p->k_max && np_ < VT_MAX_PASSES - 1; k *= 2) ks[np_++] = k;
         ks[np_++] = 0;
         int k_prev = 0;
         int lp = 0;  // logical pass (stats)
@@ -773,7 +778,7 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
 
     int64_t m_reg = n, m_rob = 0, n_unval = 0;
     bool implicit = true;  // the first pass runs over all cells without a list
-    int k = p->k0;
+    int k = fused ? p->k_max + 1 : p->k0;  // fused: the exhaustive walk is the first pass
     int k_prev = 0;  // regular cells resume from their saved state after list entry k_prev
 
     while (m_reg + m_rob > 0) {

@@ -102,3 +102,22 @@ def test_periodic_limits_are_checked_on_the_host():
     assert lib.vt_workspace_size(ctypes.byref(p), 4096, ctypes.byref(b)) == L.VT_ERR_INVALID_ARG
     p.flags = 0
     assert lib.vt_workspace_size(ctypes.byref(p), 4096, ctypes.byref(b)) == L.VT_OK
+
+
+def test_fused_schedule_workspace_holds_no_lists():
+    # VT_FLAG_FUSED clips from the grid walk: neither the n x 2 k0 list (ids
+    # and float keys) nor the saved polyhedra are in the workspace
+    lib = L.load()
+    n = 1 << 20
+    sizes = {}
+    for flags in (0, L.VT_FLAG_FUSED, L.VT_FLAG_FUSED | L.VT_FLAG_NO_SYNC):
+        p = L.VtParams()
+        lib.vt_params_default(ctypes.byref(p))
+        p.flags = flags
+        b = ctypes.c_size_t()
+        assert lib.vt_workspace_size(ctypes.byref(p), n, ctypes.byref(b)) == L.VT_OK
+        sizes[flags] = b.value
+    assert sizes[0] - sizes[L.VT_FLAG_FUSED] >= n * (32 * 8 + 1024)
+    assert sizes[L.VT_FLAG_FUSED | L.VT_FLAG_NO_SYNC] == sizes[L.VT_FLAG_FUSED]
+    p.flags = 16
+    assert lib.vt_workspace_size(ctypes.byref(p), n, ctypes.byref(b)) == L.VT_ERR_INVALID_ARG

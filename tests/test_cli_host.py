@@ -66,6 +66,9 @@ def test_params_from_args():
     assert p.box_lo == (-1.0, -2.0, -3.0) and p.box_hi == (1.0, 2.0, 3.0)
     assert not p.periodic
     assert cli.params_from_args(cli.parser().parse_args(["i", "-o", "o.npz", "--periodic"])).periodic
+    assert not p.fused and p.c().flags == 0
+    pf = cli.params_from_args(cli.parser().parse_args(["i", "-o", "o.npz", "--fused"]))
+    assert pf.fused and pf.c().flags == 8  # VT_FLAG_FUSED
     with pytest.raises(ValueError, match="unknown output"):
         cli.params_from_args(cli.parser().parse_args(["i", "-o", "o.npz", "--emit", "nbr,area"]))
     with pytest.raises(SystemExit):
