@@ -91,17 +91,6 @@ __device__ __forceinline__ bool reaches_far(const float* vb, int nv, float nx, f
 // queue measured 0.06 ms faster per 1M-cell step than 5 and 0.18 ms faster
 // than 4; its periodic form 4, which spills more), 3 for the FP64 one (at
 // most 80 registers)
-// FP32 lists: the vertex test (reaches_far) from the start (STRICT), or in a
-// second walk after an overflow (ATTEMPTS 2), as the FP64 lists do. Both move
-// work from the clipper's walk into this kernel at a loss (1M clumped cloud:
-// clipping 1.2 / 0.8 ms faster, these lists 1.55 / 1.1 ms slower), so the
-// FP32 lists keep the radius and bounding-box tests alone
-#ifndef VT_RANGE_STRICT_F32
-#define VT_RANGE_STRICT_F32 0
-#endif
-#ifndef VT_RANGE_ATTEMPTS_F32
-#define VT_RANGE_ATTEMPTS_F32 1
-#endif
 #ifndef VT_RANGE_MINB_F32
 #define VT_RANGE_MINB_F32 6
 #endif
@@ -169,12 +158,10 @@ __global__ void __launch_bounds__(RANGE_BLOCK, (sizeof(Real) == 4 ? (PER ? 4 : V
         // walks again with the exact test against its saved vertices, which
         // keeps only the generators whose bisector can reach a vertex: cheaper
         // there than the FP64 clipper's own walk (measured); the FP32 clipper's
-        // walk is cheaper than a second attempt
-        constexpr int attempts = sizeof(Real) == 8 ? 2 : VT_RANGE_ATTEMPTS_F32;
-        constexpr bool strict0 = sizeof(Real) == 4 && VT_RANGE_STRICT_F32;  // the vertex test from the start
-        if (strict0)
-            nv = load_far_vertices_t<Real>(h, state + (size_t)q * state_stride + pos_off, lkey, last_orig, R2, vb,
-                                           lane);
+        // walk is cheaper than a second attempt (measured: the range lists 1.1 ms
+        // slower per 1M-cell step, the clipping 0.8 ms faster; the vertex test
+        // from the first attempt on, 1.55 ms slower and 1.2 ms faster)
+        constexpr int attempts = sizeof(Real) == 8 ? 2 : 1;
         for (int attempt = 0; attempt < attempts; ++attempt) {
         if (attempt == 1) {
             if (!over) break;
@@ -226,7 +213,7 @@ __global__ void __launch_bounds__(RANGE_BLOCK, (sizeof(Real) == 4 ? (PER ? 4 : V
                         const float hb = fmaxf(ex * lo3[0], ex * hi3[0]) + fmaxf(ey * lo3[1], ey * hi3[1]) +
                                          fmaxf(ez * lo3[2], ez * hi3[2]);
                         keep = r4 > d2 && hb > 0.5f * d2 * (1.0f - 1e-4f) - 1e-6f * sqrtf(d2 * R2) - 1e-30f;
-                        if (keep && (strict0 || attempt == 1)) keep = reaches_far(vb, nv, ex, ey, ez, d2, R2);
+                        if (keep && attempt == 1) keep = reaches_far(vb, nv, ex, ey, ez, d2, R2);
                         if (keep) {
                             key = sizeof(Real) == 8 ? (Real)img_key64(pq, sorted, jj, g) : (Real)d2;
                             ko = img_tie_t<PER>(pc, code);
@@ -286,7 +273,9 @@ __global__ void __launch_bounds__(RANGE_BLOCK, (sizeof(Real) == 4 ? (PER ? 4 : V
 size_t range_smem_bytes(int precision)
 {
     const size_t key = precision == VT_FP64 ? sizeof(double) : sizeof(float);
-    return ((key + 2 * sizeof(int32_t)) * RANGE_CAP + 4 * sizeof(float) * RANGE_VCAP) * (RANGE_BLOCK / 32);
+    // the far vertices of the second attempt: FP64 form only
+    const size_t far = precision == VT_FP64 ? 4 * sizeof(float) * RANGE_VCAP : 0;
+    return ((key + 2 * sizeof(int32_t)) * RANGE_CAP + far) * (RANGE_BLOCK / 32);
 }
 
 template <typename Real>
