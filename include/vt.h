@@ -211,6 +211,13 @@ typedef struct vt_stats {
     int64_t knn_candidates;              /* candidates the k-nearest-neighbour kernels examined (one
                                             squared distance each) */
     int64_t knn_queries;                 /* queries they answered */
+    int64_t walk_cells;                  /* walks over the grid shells within 2R of a cell in the last
+                                            pass (range lists and the exhaustive walk; a cell whose
+                                            range list overflows walks twice) */
+    int64_t walk_candidates;             /* generators those walks examined. Most cells walking with
+                                            about n each means near-degenerate input (coplanar or
+                                            collinear generators: every cell reaches the walls), whose
+                                            cost grows as n^2 */
 } vt_stats;
 
 /* ------------------------------------------------------------------ */
@@ -517,7 +524,7 @@ VT_API int vt_probe_fma(int precision, double* tflops, void* stream);
 /* After a VT_FLAG_NO_SYNC call (or any call) on workspace ws (blocking on
  * `stream`): fills the device-counted fields of *stats (fp64_rechecks,
  * capacity_retries, precision_retries, unvalidated, clip_events, knn_candidates,
- * knn_queries; other fields
+ * knn_queries, walk_cells, walk_candidates; other fields
  * are left as they are) and out->needed_* (either may be NULL). Returns the
  * call's error: VT_ERR_INVALID_ARG / VT_ERR_DUPLICATE_POINTS for bad input,
  * VT_ERR_CAPACITY when an output did not fit (nothing of that output was

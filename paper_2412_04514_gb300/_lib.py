@@ -171,6 +171,8 @@ class VtStats(ctypes.Structure):
         ("ms_knn_lists", ctypes.c_double),
         ("knn_candidates", ctypes.c_int64),
         ("knn_queries", ctypes.c_int64),
+        ("walk_cells", ctypes.c_int64),
+        ("walk_candidates", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -198,6 +200,8 @@ class VtStats(ctypes.Structure):
             "ms_knn_lists": self.ms_knn_lists,
             "knn_candidates": self.knn_candidates,
             "knn_queries": self.knn_queries,
+            "walk_cells": self.walk_cells,
+            "walk_candidates": self.walk_candidates,
         }
 
 

@@ -10,6 +10,7 @@ tensors' device current first (``torch.cuda.set_device`` or
 from __future__ import annotations
 
 import ctypes
+import warnings
 from dataclasses import dataclass, field
 
 import torch
@@ -248,8 +249,23 @@ def tessellate(points: torch.Tensor, params: Params | None = None, workspace: Wo
     cells.stats["status"] = L.STATUS_NAMES.get(code, code)
     if code not in (L.VT_OK, L.VT_ERR_UNVALIDATED) or (strict and code != L.VT_OK):
         L.check(code)
+    _warn_degenerate(cells.stats, n)
     _trim(cells, o)
     return cells
+
+
+def _warn_degenerate(stats: dict, n: int) -> None:
+    """RuntimeWarning when at least half the cells walked the grid shells
+    within twice their radius in the last pass and those walks examined at
+    least max(1000, n / 4) generators each on average: coplanar or collinear
+    input, whose cells all reach the walls, so that the run costs O(n^2). The
+    cells are exact; only the time grows. (A dense clump makes the few sparse
+    cells next to it walk long, which this does not report.)"""
+    wc = stats.get("walk_cells", 0)
+    if wc > 0 and 2 * wc >= n and stats.get("walk_candidates", 0) >= wc * max(1000, n // 4):
+        warnings.warn(f"near-degenerate input (coplanar or collinear generators?): the exhaustive walk examined "
+                      f"{stats['walk_candidates'] / wc:.0f} generators per walked cell over {wc} cells of {n}; "
+                      f"the run costs O(n^2)", RuntimeWarning, stacklevel=3)
 
 
 def tessellate_host(points, params: Params | None = None, device="cuda", direct: bool = False) -> Cells:

@@ -1474,6 +1474,8 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
     }
     C cell;
     cell.stamp = 0;
+    // walks finished and generators they examined, added once per group
+    unsigned walk_cells = 0, walk_cands = 0;
 
     // Cells come from a launch-wide counter, one per group at a time (cells
     // differ in cost by orders of magnitude: a static share per group leaves
@@ -1660,6 +1662,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
                     const int len = sb - sa;
                     int total;
                     const int start = G.scan(len, total);
+                    walk_cands += (unsigned)total;
                     const int incl = start + len;
 #ifdef VT_PROFILE
                     if (G.gl == 0) VT_PROF_ADD(19, total);
@@ -1702,6 +1705,7 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
                 if (gap > 0.0f && 4.0f * (float)cell.R2 * (1.0f + 2e-5f) <= gap * gap) { status = -1; break; }
             }
             end = status == -1 ? END_VALID : status;
+            ++walk_cells;
         }
 
 #ifdef VT_PROFILE
@@ -1739,6 +1743,10 @@ __global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) 
             }
             G.sync();
         }
+    }
+    if (EXH && G.gl == 0 && walk_cells) {
+        atomicAdd(&A.st->walk_cells, (unsigned long long)walk_cells);
+        atomicAdd(&A.st->walk_cands, (unsigned long long)walk_cands);
     }
 }
 

@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(RANGE_BLOCK, (sizeof(Real) == 4 ? (PER ? 4 : V
         const int64_t want = (int64_t)*nq_dev - nq_off;
         nq = want < 0 ? 0 : (want < nq_host ? want : nq_host);
     }
+    // walks and the generators they examined, added once per warp
+    unsigned walk_cells = 0, walk_cands = 0;
     // cells come from a launch-wide counter, one per warp at a time
     auto next_cell = [&]() {
         int v = 0;
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(RANGE_BLOCK, (sizeof(Real) == 4 ? (PER ? 4 : V
         int count = 0;
         bool over = false;
         int nv = 0;  // far vertices in vb (second attempt)
+        ++walk_cells;
         // first attempt: radius and bounding-box tests. In the FP64 form a cell
         // whose candidates overflow the list (a sparse cell next to a clump)
         // walks again with the exact test against its saved vertices, which
@@ -192,6 +195,7 @@ __global__ void __launch_bounds__(RANGE_BLOCK, (sizeof(Real) == 4 ? (PER ? 4 : V
                 }
                 const int total = __shfl_sync(FULL, incl, 31);
                 const int start = incl - len;
+                walk_cands += (unsigned)total;
                 for (int c0 = 0; c0 < total && !over; c0 += 32) {
                     const int i = c0 + lane;
                     int seg = 0;
@@ -265,6 +269,10 @@ __global__ void __launch_bounds__(RANGE_BLOCK, (sizeof(Real) == 4 ? (PER ? 4 : V
         }
         if (lane == 0) rlen[c] = count;
         __syncwarp();
+    }
+    if (lane == 0 && walk_cells) {
+        atomicAdd(&st->walk_cells, (unsigned long long)walk_cells);
+        atomicAdd(&st->walk_cands, (unsigned long long)walk_cands);
     }
 }
 

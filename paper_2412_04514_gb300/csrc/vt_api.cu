@@ -902,6 +902,8 @@ int tessellate_run(Ctx& c, const float* pts, int64_t n, const vt_params* p, vt_c
     for (int a = 0; a < 5; ++a) S.clip_events[a] = (int64_t)h.detail[a];
     S.knn_candidates = (int64_t)h.knn_evals;
     S.knn_queries = (int64_t)h.knn_queries;
+    S.walk_cells = (int64_t)h.walk_cells;
+    S.walk_candidates = (int64_t)h.walk_cands;
     S.launches = (int)(launches() - l0);
     if (timer.on) {
         S.ms_grid = timer.total(StageTimer::GRID);
@@ -1252,6 +1254,8 @@ int vt_read_stats(void* ws, size_t ws_bytes, vt_stats* stats, vt_cells_out* out,
         for (int a = 0; a < 5; ++a) stats->clip_events[a] = (int64_t)h.detail[a];
         stats->knn_candidates = (int64_t)h.knn_evals;
         stats->knn_queries = (int64_t)h.knn_queries;
+        stats->walk_cells = (int64_t)h.walk_cells;
+        stats->walk_candidates = (int64_t)h.walk_cands;
     }
     if (out) {
         out->needed_nbr = h.totals[0];

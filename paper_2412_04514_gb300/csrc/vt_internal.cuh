@@ -456,7 +456,10 @@ struct DevStatus {
     unsigned long long knn_evals;    // candidate distances the k-nearest-neighbour kernels evaluated
     unsigned long long knn_queries;  // queries they answered
     int32_t check_fail;       // VT_CHECKS builds: code of the first failed bounds check, else 0
-    int32_t pad[11];
+    int32_t pad0;
+    unsigned long long walk_cells;  // last-pass walks over the shells within 2R (range lists, clipper)
+    unsigned long long walk_cands;  // generators of the grid runs those walks examined
+    int32_t pad[6];
 };
 static_assert(sizeof(DevStatus) % 64 == 0, "status block must stay 64-byte sized");
 

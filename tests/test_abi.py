@@ -121,3 +121,25 @@ def test_fused_schedule_workspace_holds_no_lists():
     assert sizes[L.VT_FLAG_FUSED | L.VT_FLAG_NO_SYNC] == sizes[L.VT_FLAG_FUSED]
     p.flags = 16
     assert lib.vt_workspace_size(ctypes.byref(p), n, ctypes.byref(b)) == L.VT_ERR_INVALID_ARG
+
+
+def test_degenerate_input_warning_threshold():
+    # the walks' counts of a coplanar cloud (every cell, about n generators
+    # each) warn; a clumped 1M cloud (about 150 per walk), a dense clump whose
+    # few sparse neighbours walk long, a small line and a run without walks
+    # do not
+    import warnings
+
+    from paper_2412_04514_gb300.api import _warn_degenerate
+
+    with pytest.warns(RuntimeWarning, match="degenerate"):
+        _warn_degenerate({"walk_cells": 1500, "walk_candidates": 1500 * 1500}, 1500)
+    with pytest.warns(RuntimeWarning, match="O\\(n\\^2\\)"):
+        _warn_degenerate({"walk_cells": 10**6, "walk_candidates": 10**6 * 300_000}, 10**6)
+    with warnings.catch_warnings():
+        warnings.simplefilter("error")
+        _warn_degenerate({"walk_cells": 1_003_534, "walk_candidates": 1_003_534 * 150}, 1 << 20)
+        _warn_degenerate({"walk_cells": 164, "walk_candidates": 164 * 7356}, 14_000)
+        _warn_degenerate({"walk_cells": 300, "walk_candidates": 300 * 300}, 300)
+        _warn_degenerate({"walk_cells": 0, "walk_candidates": 0}, 10)
+        _warn_degenerate({}, 10)

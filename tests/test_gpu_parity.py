@@ -8,6 +8,7 @@ Tolerances (from the FP64 form's rounding and the stated FP32 target):
     (a face that small is below float32 resolution of the cell).
 """
 import ctypes
+import warnings
 
 import numpy as np
 import pytest
@@ -476,8 +477,17 @@ def test_coplanar_and_collinear_generators(prec, shape):
         pts[:, 1] = rng.random(n)
     pts = np.unique(pts.astype(np.float32), axis=0)
     want = oracle.tessellate(pts)
-    cells = vt.tessellate(dev(pts), vt.Params(precision=prec, emit=("nbr", "vol", "cen")))
+    with warnings.catch_warnings(record=True) as caught:
+        warnings.simplefilter("always")
+        cells = vt.tessellate(dev(pts), vt.Params(precision=prec, emit=("nbr", "vol", "cen")))
     assert cells.stats["status"] == "VT_OK"
+    # every cell walks the shells within 2R in the last pass (range lists, and
+    # the clipper's walk when they overflow), examining about every generator:
+    # reported (above a floor of 1,000 per walk, so the 300-point line is not)
+    assert cells.stats["walk_cells"] > 0.9 * len(pts)
+    assert cells.stats["walk_candidates"] > 0.25 * len(pts) * cells.stats["walk_cells"]
+    warned = [w for w in caught if issubclass(w.category, RuntimeWarning) and "degenerate" in str(w.message)]
+    assert len(warned) == (1 if shape == "plane" else 0)
     assert abs(np_(cells.vol).sum() - 1.0) < (1e-12 if prec == "fp64" else 1e-5)
     if prec == "fp64":
         np.testing.assert_allclose(np_(cells.vol), want["vol"], rtol=1e-12)
