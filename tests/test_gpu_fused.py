@@ -160,3 +160,37 @@ def test_fused_batch_matches_the_oracle_per_set(prec):
         bad = sum(not np.array_equal(g, x) for g, x in zip(got, oracle.neighbour_lists(w)))
         assert bad == 0 if prec == "fp64" else bad <= max(2, 1e-3 * len(p))
 
+
+
+def test_fused_no_sync_equals_sync_with_geometry():
+    # both schedules run the same single walk pass
+    pts = W.mixed(60000, 8, n_clumps=60)
+    emit = EMIT + ("geom",)
+    a = vt.tessellate(dev(pts), vt.Params(precision="fp32", emit=emit, fused=True))
+    b = vt.tessellate(dev(pts), vt.Params(precision="fp32", emit=emit, fused=True, no_sync=True))
+    for name in ("vol", "cen", "m2", "nbr_off", "nbr", "vtx_off", "vtx", "face_off", "face_nbr", "face_vtx_off",
+                 "face_vtx"):
+        assert torch.equal(getattr(a, name), getattr(b, name)), name
+
+
+def test_fused_batch_graph_replay_matches_eager_and_the_oracle():
+    # a CUDA graph of the fused schedule over a batch, replayed on new points
+    parts = [W.uniform(2000, 11), W.mixed(6000, 12, n_clumps=6), W.uniform(1, 13), W.uniform(40, 14)]
+    off = np.zeros(len(parts) + 1, np.int64)
+    off[1:] = np.cumsum([len(p) for p in parts])
+    pts = np.concatenate(parts).astype(np.float32)
+    prm = vt.Params(precision="fp32", emit=EMIT, fused=True)
+    b = vt.Batch(dev(pts), off, prm)
+    b.capture()
+    other_parts = [W.uniform(len(p), 90 + i) for i, p in enumerate(parts)]
+    other = np.concatenate(other_parts).astype(np.float32)
+    b.points.copy_(dev(other))
+    b.replay()
+    got = b.result()
+    want = vt.tessellate_batch(dev(other), off, prm)
+    for name in ("vol", "cen", "m2", "nbr_off", "nbr"):
+        assert torch.equal(getattr(got, name), getattr(want, name)), name
+    vol = np_(got.vol)
+    for s, p in enumerate(other_parts):
+        w = oracle.tessellate(p)
+        np.testing.assert_allclose(vol[off[s]:off[s + 1]], w["vol"], rtol=1e-5)
