@@ -2,7 +2,8 @@
 
 ``bench.py`` times 32 lanes per cell, k0 = 16 doubled to k_max = 32, two
 points per grid cell and full geometry on 1,048,576 points, walled (mixed
-recipe, seed 1) and periodic (mixed recipe with wrapped clumps, seed 5). At
+recipe, seed 1) and periodic (mixed recipe with wrapped clumps, seed 5), in
+the list schedule and in the fused one (VT_FLAG_FUSED, the bench's fused_form). At
 that size the oracle computes sampled cells one by one (its cells are
 independent, Summary of the paper); on the whole output the tests check
 what holds at any size: the cells fill the box (volumes and first moments),
@@ -29,9 +30,9 @@ N = 1 << 20
 EMIT = ("nbr", "vol", "cen", "geom")
 
 
-def bench_params(precision, periodic):
+def bench_params(precision, periodic, fused=False):
     return vt.Params(precision=precision, k0=16, k_max=32, threads_per_cell=32, grid_density=2.0, emit=EMIT,
-                     periodic=periodic)
+                     periodic=periodic, fused=fused)
 
 
 def np_(t):
@@ -119,10 +120,12 @@ def whole_output_properties(cells, periodic, fp64):
         assert areas[ids == j].min() < tiny(i, j), (i, j, areas[ids == j], vol[i], vol[j])
 
 
+@pytest.mark.parametrize("fused", [False, True], ids=["lists", "fused"])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_bench_configuration_sampled_and_whole(workload, precision):
+def test_bench_configuration_sampled_and_whole(workload, precision, fused):
+    # the list schedule (the bench line) and the fused schedule (its fused_form)
     pts, periodic, sample, want = workload
-    cells = vt.tessellate(torch.from_numpy(pts).cuda(), bench_params(precision, periodic))
+    cells = vt.tessellate(torch.from_numpy(pts).cuda(), bench_params(precision, periodic, fused))
     assert cells.stats["status"] == "VT_OK"
     fp64 = precision == "fp64"
     vol, cen = np_(cells.vol)[sample], np_(cells.cen)[sample]
