@@ -395,24 +395,35 @@ def run_gpu(args, rank: int, world: int, local: int):
     tot32 = dist_max(sum(ms32), world)
     value = n * world * len(ms32) / (tot32 / 1e3)
 
-    # end to end through the public API with host buffers. Headline: the
-    # pipelined stream (tessellate_stream) over `steps` clouds, every one copied
-    # in from pinned host memory and its outputs copied back, the copies of one
-    # step overlapping the tessellation of the next; beside it the serial figure
-    # of one tessellate_host call after another
+    # end to end through the public API with host buffers. Headline: a
+    # pipelined stream (tessellate_stream) of clouds, every one copied in from
+    # pinned host memory and its outputs copied back, the copies of one step
+    # overlapping the tessellation of its neighbours. The stream runs over
+    # warmup + steps + 1 clouds; the timed region is `steps` consecutive
+    # results of its steady state (the pipeline filled by the warm-up results,
+    # one more cloud behind the last timed one), each result's cloud copied in
+    # and its outputs copied back. Beside it the serial figure of one
+    # tessellate_host call after another
     host = torch.from_numpy(pts_np).pin_memory()
     e2e_stream_ms = None
+    e2e_steps_ms = []
     if not args.no_e2e:
-        for out in vt.tessellate_stream([host] * args.warmup, p32, device=dev):
+        stream = vt.tessellate_stream([host] * (args.warmup + args.steps + 1), p32, device=dev)
+        for _ in range(args.warmup):
+            out = next(stream)
             out = None
-        flush.zero_()
-        torch.cuda.synchronize()
         dist_barrier(world)
         t0 = time.perf_counter()
-        for out in vt.tessellate_stream([host] * args.steps, p32, device=dev):
+        t_prev = t0
+        for _ in range(args.steps):
+            out = next(stream)
             out = None
+            now = time.perf_counter()
+            e2e_steps_ms.append(1e3 * (now - t_prev))
+            t_prev = now
+        e2e_stream_ms = dist_max(1e3 * (t_prev - t0), world)
+        stream.close()
         torch.cuda.synchronize()
-        e2e_stream_ms = dist_max(1e3 * (time.perf_counter() - t0), world)
     e2e_ms = []
     h2d = host.numel() * 4
     d2h = 0
@@ -537,9 +548,9 @@ def run_gpu(args, rank: int, world: int, local: int):
         "e2e": None if not e2e_ms else {
             "value": n * world * args.steps / (e2e_stream_ms / 1e3), "unit": "cells/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "ms_per_step": e2e_stream_ms / args.steps,
-            "api": "tessellate_stream over the steps' clouds (pipelined: a step's copies overlap its neighbours' "
-                   "tessellation)",
+            "ms_per_step": e2e_stream_ms / args.steps, "per_step_ms": e2e_steps_ms,
+            "api": "steady state of a tessellate_stream over warmup + steps + 1 clouds: each timed result's cloud "
+                   "copied in and its outputs copied out, overlapped with the neighbouring clouds' tessellation",
             "serial": {"value": e2e_value, "ms_per_step": e2e_tot / len(e2e_ms),
                        "api": "one tessellate_host call after another"}},
         "roofline": roofline,
