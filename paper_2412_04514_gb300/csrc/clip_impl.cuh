@@ -852,14 +852,19 @@ struct Cell {
         }
         // boundary edges of the removed patch: edge e of a removed vertex whose
         // neighbour across it survives (bit 3r+e of myedge)
+        // (predicated, no branch: every lane reads its rows' links, and the
+        // bits of the rows it does not remove stay clear)
         uint32_t myedge = 0;
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
-            if ((myout >> r) & 1u) {
+            if (r < rows) {
+                const bool o = (myout >> r) & 1u;
                 const uint32_t adj = *reinterpret_cast<const uint32_t*>(sm.vadj[r * T + G.gl]);
 #pragma unroll
-                for (int e = 0; e < 3; ++e)
-                    if (!out.test(vt_ck((adj >> (8 * e)) & 0xff, VCAP, CK_SLOT, st))) myedge |= 1u << (3 * r + e);
+                for (int e = 0; e < 3; ++e) {
+                    const int w = o ? vt_ck((adj >> (8 * e)) & 0xff, VCAP, CK_SLOT, st) : 0;
+                    myedge |= (uint32_t)(o && !out.test(w)) << (3 * r + e);
+                }
             }
         }
         int total;
@@ -880,17 +885,21 @@ struct Cell {
                 if (k < total) sm.u.ring.dlist[k] = (uint8_t)s;
             }
         }
-        for (uint32_t m = myedge; m; m &= m - 1) {
-            const int bit = __ffs(m) - 1, r = bit / 3, e = bit - 3 * r;
-            sm.u.ring.elist[vt_ck(idx++, VCAP, CK_EDGE, st)] = (uint16_t)((r * T + G.gl) | (e << 8));
+        // this lane's boundary edges in bit order (a fixed, unrolled loop of
+        // predicated stores: no per-lane trip count)
+#pragma unroll
+        for (int bit = 0; bit < 3 * VPL; ++bit) {
+            if ((myedge >> bit) & 1u) {
+                sm.u.ring.elist[vt_ck(idx, VCAP, CK_EDGE, st)] = (uint16_t)(((bit / 3) * T + G.gl) | ((bit % 3) << 8));
+                ++idx;
+            }
         }
-        if (G.gl == 0) {
-            sm.pnx[h] = nx;
-            sm.pny[h] = ny;
-            sm.pnz[h] = nz;
-            sm.psrc[h] = src;
-            if (S::STORE_B) sm.pbs[h] = b;
-        }
+        // the plane h: every lane stores the same values (no lane-0 branch)
+        sm.pnx[h] = nx;
+        sm.pny[h] = ny;
+        sm.pnz[h] = nz;
+        sm.psrc[h] = src;
+        if (S::STORE_B) sm.pbs[h] = b;
         ++stamp;
         const uint32_t tag = stamp << 8;
         G.sync();
