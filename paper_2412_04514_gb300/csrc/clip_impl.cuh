@@ -549,12 +549,12 @@ struct Cell {
 
     __device__ __forceinline__ void update_r2(const Group<T>& G, const S& sm)
     {
+        // (dead slots hold zeros: every slot of the live rows is read)
         Real m = 0;
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
-            const int s = r * T + G.gl;
-            if (r < rows && alive.test(s)) {
-                const Real d = sm.vpos[s][3];
+            if (r < rows) {
+                const Real d = sm.vpos[r * T + G.gl][3];
                 m = d > m ? d : m;
             }
         }
@@ -565,11 +565,13 @@ struct Cell {
     // exhaustive walk's support test
     __device__ __forceinline__ void bbox(const Group<T>& G, const S& sm, float* lo3, float* hi3) const
     {
+        // every slot of the live rows is read: dead slots hold the origin (the
+        // generator), which the cell contains, so the box is the same
         float l0 = FLT_MAX, l1 = FLT_MAX, l2 = FLT_MAX, h0 = -FLT_MAX, h1 = -FLT_MAX, h2 = -FLT_MAX;
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
             const int s = r * T + G.gl;
-            if (r < rows && alive.test(s)) {
+            if (r < rows) {
                 const V4<Real> v = ldv(sm.vpos, s);
                 const float x = (float)v.x, y = (float)v.y, z = (float)v.z;
                 l0 = fminf(l0, x); h0 = fmaxf(h0, x);
@@ -880,10 +882,8 @@ struct Cell {
 #pragma unroll
         for (int r = 0; r < VPL; ++r) {
             const int s = r * T + G.gl;
-            if (freem.test(s)) {
-                const int k = freem.rank(s);
-                if (k < total) sm.u.ring.dlist[k] = (uint8_t)s;
-            }
+            const int k = freem.rank(s);
+            if (freem.test(s) && k < total) sm.u.ring.dlist[k] = (uint8_t)s;
         }
         // this lane's boundary edges in bit order (a fixed, unrolled loop of
         // predicated stores: no per-lane trip count)
