@@ -1429,11 +1429,17 @@ __device__ __forceinline__ int exhaustive_batch(Cell<Real, T, VPL, PCAP, PER>& c
 // ---------------------------------------------------------------------------
 constexpr int CLIP_BLOCK = 128;
 // resident blocks per SM the register budget aims for: the FP32 regular
-// variants trade some spills for occupancy (8 blocks: 64 registers, measured
-// fastest on the mixed cloud with the work queue: last pass 7.13 ms against
-// 7.31 at 7 blocks and 7.54 at 6); FP64 and robust keep 128 registers
+// variants trade some spills for occupancy. The kernels that start every
+// cell from the box (the list pass) run best at 7 blocks (72 registers), the
+// ones that resume saved polyhedra (range lists) at 9 (56 registers):
+// measured on the mixed cloud, list pass 11.67 / 11.84 / 11.91 ms and last
+// pass 6.93 / 6.74 / 6.66 ms at 7 / 8 / 9 blocks. FP64 and robust keep 128
+// registers
 #ifndef VT_CLIP_MINB_F32
-#define VT_CLIP_MINB_F32 8
+#define VT_CLIP_MINB_F32 7
+#endif
+#ifndef VT_CLIP_MINB_F32_RES
+#define VT_CLIP_MINB_F32_RES 9
 #endif
 #ifndef VT_CLIP_MINB_F64
 #define VT_CLIP_MINB_F64 4
@@ -1450,17 +1456,19 @@ constexpr int CLIP_BLOCK = 128;
 #ifndef VT_WALK_NB
 #define VT_WALK_NB 1
 #endif
-template <typename Real, bool ROBUST, bool EXH>
+template <typename Real, bool ROBUST, bool EXH, bool RES>
 constexpr int clip_minb()
 {
-    return (sizeof(Real) == 4 && !ROBUST) ? (EXH ? VT_CLIP_MINB_EXH : VT_CLIP_MINB_F32) : VT_CLIP_MINB_F64;
+    return (sizeof(Real) == 4 && !ROBUST)
+               ? (EXH ? VT_CLIP_MINB_EXH : (RES ? VT_CLIP_MINB_F32_RES : VT_CLIP_MINB_F32))
+               : VT_CLIP_MINB_F64;
 }
 
 // RES: the cells resume saved polyhedra (range lists, resumed lists, the
 // walk); the kernels that start every cell from the box leave the resume
 // code out (fewer live registers in their list loop)
 template <typename Real, int T, int VPL, int PCAP, bool ROBUST, bool EXH, bool PER, bool RES>
-__global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH>())) k_clip(const __grid_constant__ ClipArgs A)
+__global__ void __launch_bounds__(CLIP_BLOCK, (clip_minb<Real, ROBUST, EXH, RES>())) k_clip(const __grid_constant__ ClipArgs A)
 {
     using C = Cell<Real, T, VPL, PCAP, PER>;
     using S = typename C::S;
