@@ -143,3 +143,37 @@ def test_degenerate_input_warning_threshold():
         _warn_degenerate({"walk_cells": 300, "walk_candidates": 300 * 300}, 300)
         _warn_degenerate({"walk_cells": 0, "walk_candidates": 0}, 10)
         _warn_degenerate({}, 10)
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # every ctypes mirror of a vt.h struct has the C compiler's size and field
+    # offsets (a field added to one side only would shift the other's)
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"vt_params": L.VtParams, "vt_cells_out": L.VtCellsOut, "vt_set_desc": L.VtSetDesc,
+               "vt_tune_space": L.VtTuneSpace, "vt_tune_trial": L.VtTuneTrial, "vt_tune_result": L.VtTuneResult,
+               "vt_stats": L.VtStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "vt.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            cname, what, value = line.split()
+            got[(cname, what)] = int(value)
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
