@@ -119,6 +119,13 @@ def test_fused_schedule_workspace_holds_no_lists():
         sizes[flags] = b.value
     assert sizes[0] - sizes[L.VT_FLAG_FUSED] >= n * (32 * 8 + 1024)
     assert sizes[L.VT_FLAG_FUSED | L.VT_FLAG_NO_SYNC] == sizes[L.VT_FLAG_FUSED]
+    # a batch (the no-sync schedule of a CUDA graph) saves the same per point
+    batch = {}
+    for flags in (L.VT_FLAG_NO_SYNC, L.VT_FLAG_FUSED | L.VT_FLAG_NO_SYNC):
+        p.flags = flags
+        assert lib.vt_batch_workspace_size(ctypes.byref(p), n, 512 * 4096, ctypes.byref(b)) == L.VT_OK
+        batch[flags] = b.value
+    assert batch[L.VT_FLAG_NO_SYNC] - batch[L.VT_FLAG_FUSED | L.VT_FLAG_NO_SYNC] >= n * (64 * 8 + 1024) - 4096
     p.flags = 16
     assert lib.vt_workspace_size(ctypes.byref(p), n, ctypes.byref(b)) == L.VT_ERR_INVALID_ARG
 
